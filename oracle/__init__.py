@@ -1,0 +1,43 @@
+"""FP64 CPU oracle for the pseudospectral Navier-Stokes right-hand side.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or
+executes this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use it.  It
+shares no code, table or helper with the CUDA path.
+
+It is a plain, slow, obviously-correct restatement of what the method
+computes (Rosenberg et al., arXiv:1808.01309, Sec. 2), in float64 numpy:
+
+* the discrete Fourier expansion of Eq. (fftsum) with the forward sum
+  normalised by 1/(Nx Ny Nz) and the backward sum unnormalised,
+* the Galerkin ODEs for the Fourier coefficients (Sec. 2, after Eq. fftsum),
+  with the nonlinear term formed pointwise in physical space (rotational
+  form u x omega) and transformed back,
+* the pressure acting as a projection onto divergence-free fields,
+* 2/3-rule dealiasing, and
+* an explicit Runge-Kutta step (2nd or 4th order, Sec. 2) written with the
+  viscous integrating factor (Lawson form).
+
+The readings taken where the paper is silent or garbled are listed in the
+module docstring of :mod:`oracle.spectral`.
+
+Pinning status: every function is pinned by ``tests/test_oracle_pins.py``
+(brute-force DFT, Parseval, closed-form flows, exact rational Taylor
+coefficients, conservation laws, alias-free brute-force convolution, RK order).
+"""
+
+from .spectral import (  # noqa: F401
+    Config,
+    retained_halfwidth,
+    wavenumbers,
+    dealias_mask,
+    hermitian_weight,
+    forward,
+    inverse,
+    curl_hat,
+    project,
+    nonlinear,
+    rhs,
+    rk_step,
+    diagnostics,
+)
