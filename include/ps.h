@@ -1,0 +1,179 @@
+/*
+ * ps.h - C ABI of the GB300 (sm_103a) pseudospectral Navier-Stokes
+ * right-hand side and its integrating-factor Runge-Kutta step.
+ *
+ * The method is the one of Rosenberg, Mininni, Reddy and Pouquet,
+ * "GPU parallelization of a hybrid pseudospectral fluid turbulence framework
+ * using CUDA" (arXiv:1808.01309), Sec. 2: incompressible Navier-Stokes
+ * (Eq. mom with theta = 0, Eq. divv) on a periodic box, each velocity
+ * component expanded in the discrete Fourier series of Eq. (fftsum), the
+ * Galerkin ODEs for the coefficients advanced by an explicit Runge-Kutta
+ * scheme of 2nd or 4th order, the nonlinear term formed in physical space
+ * between a backward and a forward 3D transform, and the pressure acting as a
+ * projection of that term onto divergence-free fields.
+ *
+ * Conventions fixed by this library (readings of the paper):
+ *   - Forward transform: u_hat(k) = (1/(Nx Ny Nz)) sum_x u(x) exp(-i k.x);
+ *     backward transform unnormalised.  x_i = Lx i/Nx; k = 2 pi (p/Lx, q/Ly, r/Lz).
+ *   - Nonlinear term in rotational form u x omega, omega = curl u.
+ *   - 2/3-rule dealiasing (cubic: |p| < Nx/3, |q| < Ny/3, |r| < Nz/3; spherical
+ *     also requires (3p/Nx)^2 + (3q/Ny)^2 + (3r/Nz)^2 < 1; none keeps all but the
+ *     Nyquist modes).  The state is the truncated Galerkin system: modes
+ *     outside the mask are treated as zero on input and written as zero.
+ *   - Leray projection P(k) = I - k k^T/|k|^2 of the nonlinear term plus the
+ *     forcing; the k = 0 mode of the right-hand side is zero.
+ *   - Runge-Kutta in Lawson (integrating factor) form with
+ *     E = exp(-nu |k|^2 dt/2):
+ *       RK4: k1 = R(u), k2 = R(E(u + dt/2 k1)), k3 = R(E u + dt/2 k2),
+ *            k4 = R(E^2 u + dt E k3), u+ = E^2 u + dt/6 (E^2 k1 + 2E(k2+k3) + k4)
+ *       RK2: k1 = R(u), k2 = R(E^2 (u + dt k1)), u+ = E^2 (u + dt/2 k1) + dt/2 k2
+ *     where R = D P(F[u x omega] + f) is the right-hand side without viscosity.
+ *
+ * Data layout of every spectral vector field (state, right-hand side,
+ * forcing): interleaved complex (float2 for PS_FP32, double2 for PS_FP64),
+ * C order [component 0..2][kz 0..nz-1][ky 0..ny-1][kx 0..nx/2], kx fastest,
+ * ky and kz in FFT order (0..n/2-1, -n/2..-1).  This is the layout of
+ * torch.fft.rfftn / numpy.fft.rfftn of a real (nz, ny, nx) array per
+ * component.  Field bytes: 3 * nz * ny * (nx/2+1) * (8 or 16).
+ *
+ * Ownership: the caller owns the state, right-hand-side and forcing buffers.
+ * The plan owns its scratch (intermediate fields, twiddles, stage registers).
+ * All calls are asynchronous on the plan's CUDA stream except those that
+ * return host values (ps_diagnostics, ps_step_stats, ps_rk_step_host,
+ * ps_plan_get_timing), which synchronise it.  A plan is used by one host
+ * thread at a time.
+ *
+ * Errors: arguments are checked on the host before any launch.  On
+ * PS_ERR_INVALID_ARG / PS_ERR_UNSUPPORTED nothing was launched and the plan
+ * stays usable.  After PS_ERR_CUDA the plan must be destroyed.  No C++
+ * exception crosses this interface.  ps_last_error() gives a message for the
+ * last failure of the calling thread.
+ */
+#ifndef PS_H_
+#define PS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,  /* bad pointer, size, aliasing or config value */
+  PS_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  PS_ERR_OOM = 3,          /* device allocation failed */
+  PS_ERR_CUDA = 4,         /* CUDA runtime or launch error */
+  PS_ERR_NONFINITE = 5,    /* a diagnostic came out NaN or infinite */
+  PS_ERR_TIMEOUT = 6       /* reserved for bounded device-side waits */
+} ps_status;
+
+typedef enum { PS_FP32 = 0, PS_FP64 = 1 } ps_precision;
+typedef enum { PS_HD = 0, PS_MHD = 1 } ps_equations;
+typedef enum { PS_DEALIAS_CUBIC = 0, PS_DEALIAS_SPHERICAL = 1, PS_DEALIAS_NONE = 2 } ps_dealias;
+
+typedef struct ps_plan ps_plan;
+
+/* One solve (Sec. 2: grid and box may differ per axis).
+ *   nx, ny, nz : powers of two in [8, 1024]
+ *   lx, ly, lz : box lengths, finite and > 0
+ *   prec       : arithmetic and storage precision of all fields
+ *   eq         : PS_HD (PS_MHD returns PS_ERR_UNSUPPORTED)
+ *   dealias    : truncation rule
+ *   rk_order   : 2 or 4
+ *   nu         : kinematic viscosity >= 0;  eta: magnetic diffusivity (MHD, unused)
+ *   forcing    : device pointer to a constant-in-time forcing field in the
+ *                state layout and precision, or NULL.  Its retained modes are
+ *                copied at plan creation; later changes are not seen. */
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz;
+  ps_precision prec;
+  ps_equations eq;
+  ps_dealias dealias;
+  int rk_order;
+  double nu, eta;
+  const void* forcing;
+} ps_config;
+
+/* Global diagnostics of the retained state, accumulated in FP64.
+ *   energy    = 1/2 sum w |u_hat|^2   (w = 1 on kx = 0 and kx = nx/2, else 2)
+ *   enstrophy = 1/2 sum w |omega_hat|^2,  helicity = sum w Re(u_hat* . omega_hat)
+ *   max_div   = max |k . u_hat|,  max_u = max over grid points of |u(x)|
+ *   cfl_dt    = cfl * min(lx/nx, ly/ny, lz/nz) / max_u
+ *   spectrum  : caller-owned host array of capacity nshells (or NULL); shell
+ *               K holds 1/2 sum w |u_hat|^2 over modes with floor(|k|+1/2) = K
+ *   nshells   : in: capacity of spectrum; out: number of shells of this grid
+ *   time      : t + dt of the last ps_rk_step on this plan (0 if none) */
+typedef struct {
+  double energy, enstrophy, helicity, max_div, max_u, cfl_dt, time;
+  double* spectrum;
+  int nshells;
+} ps_diag;
+
+#define PS_NKINDS 6
+/* Per-kernel-kind device time measured with CUDA events on the plan stream
+ * while timing is enabled: 0 z-inverse, 1 y-inverse, 2 fused x pass,
+ * 3 y-forward, 4 z-forward (+ spectral ops and RK update), 5 auxiliary. */
+typedef struct {
+  double ms[PS_NKINDS];
+  long long launches[PS_NKINDS];
+} ps_timing;
+
+/* Create a plan: validates cfg, allocates scratch on the current device,
+ * builds FP64-accurate twiddle tables and copies the forcing.  cuda_stream is
+ * a cudaStream_t (NULL = legacy default stream).  Synchronises the stream. */
+ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out);
+
+/* Free every plan-owned allocation.  NULL is accepted. */
+ps_status ps_plan_destroy(ps_plan* plan);
+
+/* Device bytes a plan with this config allocates (without forcing box). */
+ps_status ps_plan_workspace_bytes(const ps_config* cfg, size_t* bytes);
+
+/* Right-hand side of the Galerkin ODEs (Sec. 2):
+ *   rhs_out = D P(F[u x omega] + f) - nu |k|^2 D u_hat
+ * uhat and rhs_out are device buffers in the state layout; they must not
+ * overlap.  t is the time of uhat (the forcing is constant; t is recorded
+ * only).  Asynchronous. */
+ps_status ps_rhs(ps_plan* plan, const void* uhat, void* rhs_out, double t);
+
+/* One integrating-factor Runge-Kutta step of order cfg.rk_order, in place on
+ * the device state uhat (Sec. 2, explicit RK of 2nd-4th order).  Also records,
+ * for the state at the start of the step, its energy and max |u(x)|
+ * (ps_step_stats).  dt must be finite.  Asynchronous. */
+ps_status ps_rk_step(ps_plan* plan, void* uhat, double dt, double t);
+
+/* Same as nsteps calls of ps_rk_step on a HOST buffer: copies the state to a
+ * plan-owned device buffer (allocated on the first call), steps, copies it
+ * back and synchronises.  uhat_host should be page-locked for full speed. */
+ps_status ps_rk_step_host(ps_plan* plan, void* uhat_host, double dt, double t, int nsteps);
+
+/* Energy and max |u(x)| (FP64) of the state at the start of the last
+ * ps_rk_step.  Synchronises the plan stream. */
+ps_status ps_step_stats(ps_plan* plan, double* energy, double* max_u);
+
+/* Diagnostics of the device state uhat (see ps_diag).  Runs the backward
+ * transforms once for max |u(x)|.  Synchronises the plan stream.  Returns
+ * PS_ERR_NONFINITE (with out filled) if a result is not finite. */
+ps_status ps_diagnostics(ps_plan* plan, const void* uhat, double cfl, ps_diag* out);
+
+/* Per-kernel CUDA-event timing (see ps_timing).  Enabling clears the totals;
+ * ps_plan_get_timing synchronises, reports the totals since then and keeps
+ * accumulating. */
+ps_status ps_plan_set_timing(ps_plan* plan, int enable);
+ps_status ps_plan_get_timing(ps_plan* plan, ps_timing* out);
+
+/* Number of kernels this plan has launched since creation. */
+ps_status ps_plan_launch_count(ps_plan* plan, long long* launches);
+
+/* Name of a kernel kind of ps_timing (0..PS_NKINDS-1), or "?". */
+const char* ps_kind_name(int kind);
+
+const char* ps_status_string(ps_status s);
+const char* ps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PS_H_ */

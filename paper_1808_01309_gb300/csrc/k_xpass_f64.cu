@@ -1,0 +1,13 @@
+// xpass pass, double instantiations for every supported line length.
+#include "ps_passes.cuh"
+
+namespace ps {
+
+template <>
+cudaError_t launch_xpass<double>(const PassArgs& a, cudaStream_t s) {
+#define CALL(N) xpass_n<double, N>(a, s)
+  PS_DISPATCH_N(a.g.nx, CALL)
+#undef CALL
+}
+
+}  // namespace ps

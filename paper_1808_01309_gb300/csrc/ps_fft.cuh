@@ -1,0 +1,237 @@
+// Line-FFT building blocks for the pseudospectral passes (sm_103a).
+//
+// One length-N line is spread over G = N/E threads; the thread with index j0
+// holds the E elements n = j0 + m*(N/E), m = 0..E-1, in registers.  A
+// mixed-radix Stockham autosort FFT (Stockham 1966; Cooley-Tukey stages with a
+// self-sorting output order) runs one stage per radix R: the thread does E/R
+// radix-R butterflies on its registers, multiplies by the stage twiddles and,
+// between stages, exchanges elements through shared memory.  The first stage
+// reads, and the last stage leaves, exactly the elements n = j0 + m*(N/E), so
+// the passes load straight from HBM into registers and store straight back:
+// the strided z/y passes are coalesced across neighbouring lines (kx columns),
+// the x pass along the row.
+//
+// Transform convention (Sec. 2, Eq. fftsum): forward X[k] = sum_n x[n]
+// exp(-2 pi i k n/N) (DIR = -1), backward with exp(+2 pi i k n/N) (DIR = +1),
+// both unnormalised; the 1/(Nx Ny Nz) of the forward transform is applied once
+// in the last forward pass.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ps {
+
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) x, decltype(V::x) y) { V v; v.x = x; v.y = y; return v; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+template <typename V> __device__ __forceinline__ V czero() { return mk<V>(0, 0); }
+// i * a and -i * a
+template <typename V> __device__ __forceinline__ V cmul_i(V a) { return mk<V>(-a.y, a.x); }
+template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mk<V>(a.y, -a.x); }
+
+// Multiply by exp(DIR * 2 pi i * s/16) for a compile-time s in [0, 8).
+// cos(pi/8), sin(pi/8) and sqrt(1/2) are the exact mathematical constants,
+// rounded by the compiler to the working precision.
+template <int S16, int DIR, typename V>
+__device__ __forceinline__ V rot16(V v) {
+  using T = decltype(V::x);
+  constexpr double C1 = 0.92387953251128675612818318939678828682;  // cos(pi/8)
+  constexpr double S1 = 0.38268343236508977172845998403039886676;  // sin(pi/8)
+  constexpr double H = 0.70710678118654752440084436210484903928;   // sqrt(1/2)
+  if constexpr (S16 == 0) {
+    return v;
+  } else if constexpr (S16 == 4) {
+    return DIR > 0 ? cmul_i(v) : cmul_mi(v);
+  } else if constexpr (S16 == 2) {  // (1 + DIR i)/sqrt2
+    return DIR > 0 ? mk<V>(T(H) * (v.x - v.y), T(H) * (v.x + v.y))
+                   : mk<V>(T(H) * (v.x + v.y), T(H) * (v.y - v.x));
+  } else if constexpr (S16 == 6) {  // (-1 + DIR i)/sqrt2
+    return DIR > 0 ? mk<V>(-T(H) * (v.x + v.y), T(H) * (v.x - v.y))
+                   : mk<V>(T(H) * (v.y - v.x), -T(H) * (v.x + v.y));
+  } else {
+    constexpr double c = (S16 == 1) ? C1 : (S16 == 3) ? S1 : (S16 == 5) ? -S1 : -C1;
+    constexpr double s = (S16 == 1) ? S1 : (S16 == 3) ? C1 : (S16 == 5) ? C1 : S1;
+    return cmul(v, mk<V>(T(c), T(DIR * s)));
+  }
+}
+
+template <int B> struct ilog2 { static constexpr int v = 1 + ilog2<B / 2>::v; };
+template <> struct ilog2<1> { static constexpr int v = 0; };
+
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+// In-register DFT of size R in {2,4,8,16}: radix-2 decimation in time over a
+// bit-reversed copy; all indices are compile-time after unrolling.
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void dft(V (&x)[R]) {
+  constexpr int L = ilog2<R>::v;
+  V y[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) y[i] = x[bitrev(i, L)];
+#pragma unroll
+  for (int len = 2; len <= R; len *= 2) {
+#pragma unroll
+    for (int i = 0; i < R; i += len) {
+#pragma unroll
+      for (int j = 0; j < len / 2; ++j) {
+        V u = y[i + j];
+        V v = y[i + j + len / 2];
+        // twiddle exp(DIR 2 pi i j/len) = exp(DIR 2 pi i (16 j/len)/16)
+        switch ((16 / len) * j) {
+          case 0: break;
+          case 1: v = rot16<1, DIR>(v); break;
+          case 2: v = rot16<2, DIR>(v); break;
+          case 3: v = rot16<3, DIR>(v); break;
+          case 4: v = rot16<4, DIR>(v); break;
+          case 5: v = rot16<5, DIR>(v); break;
+          case 6: v = rot16<6, DIR>(v); break;
+          case 7: v = rot16<7, DIR>(v); break;
+        }
+        y[i + j] = cadd(u, v);
+        y[i + j + len / 2] = csub(u, v);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) x[i] = y[i];
+}
+
+// Radix schedule per length N and registers per thread E: stage radices
+// R0..R3 (1 = no stage).  E = 16 shortens the wider FP32 transforms by one
+// shared-memory exchange; E = 8 keeps FP64 within the register file.
+template <int N, int E> struct Sched;
+template <> struct Sched<8, 8> { static constexpr int S = 1, R0 = 8, R1 = 1, R2 = 1, R3 = 1; };
+template <> struct Sched<16, 16> { static constexpr int S = 1, R0 = 16, R1 = 1, R2 = 1, R3 = 1; };
+template <> struct Sched<16, 8> { static constexpr int S = 2, R0 = 8, R1 = 2, R2 = 1, R3 = 1; };
+template <> struct Sched<32, 8> { static constexpr int S = 2, R0 = 8, R1 = 4, R2 = 1, R3 = 1; };
+template <> struct Sched<64, 8> { static constexpr int S = 2, R0 = 8, R1 = 8, R2 = 1, R3 = 1; };
+template <> struct Sched<128, 16> { static constexpr int S = 2, R0 = 16, R1 = 8, R2 = 1, R3 = 1; };
+template <> struct Sched<128, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 2, R3 = 1; };
+template <> struct Sched<256, 16> { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, R3 = 1; };
+template <> struct Sched<256, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 4, R3 = 1; };
+template <> struct Sched<512, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 8, R3 = 1; };
+template <> struct Sched<1024, 16> { static constexpr int S = 3, R0 = 16, R1 = 8, R2 = 8, R3 = 1; };
+template <> struct Sched<1024, 8> { static constexpr int S = 4, R0 = 8, R1 = 8, R2 = 8, R3 = 2; };
+
+// Registers per thread for a length-N line in precision T.
+template <typename T, int N> struct EOf {
+  static constexpr int v = (sizeof(T) == 4 && (N == 16 || N == 128 || N == 256 || N == 1024)) ? 16 : 8;
+};
+
+// Twiddle exp(DIR 2 pi i m/N) from the table tw[m] = exp(-2 pi i m/N).
+template <int DIR, typename V>
+__device__ __forceinline__ V twiddle(const V* __restrict__ tw, int idx) {
+  V w = __ldg(tw + idx);
+  return DIR > 0 ? cconj(w) : w;
+}
+
+// One Stockham stage of radix R on a line of length N whose previous stages
+// had total radix NS.  Butterfly j takes x[j + r N/R], multiplies by
+// W_{NS R}^{r k} (k = j mod NS), transforms, and writes y[(j-k) R + k + r NS].
+// Thread j0 owns butterflies j = j0 + b N/E, b < E/R, whose inputs are its
+// registers b + r E/R.  The last stage leaves y[j + r N/R] in the same slots.
+template <int N, int E, int R, int NS, int DIR, bool LAST, typename V, class X>
+__device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ tw, X& ex) {
+  constexpr int NB = E / R;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = j0 + b * (N / E);
+    const int k = j & (NS - 1);
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = a[b + r * NB];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<DIR>(tw, r * k * (N / (NS * R))));
+    }
+    dft<R, DIR>(x);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[b + r * NB] = x[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) ex.put((j - k) * R + k + r * NS, x[r]);
+    }
+  }
+  if constexpr (!LAST) {
+    ex.sync();
+#pragma unroll
+    for (int m = 0; m < E; ++m) a[m] = ex.get(j0 + m * (N / E));
+    ex.flip();
+  }
+}
+
+// Full length-N line transform on the E registers of thread j0 (see header).
+template <int N, int E, int DIR, typename V, class X>
+__device__ __forceinline__ void line_fft(V (&a)[E], int j0, const V* __restrict__ tw, X& ex) {
+  using S = Sched<N, E>;
+  if constexpr (S::S == 1) {
+    stage<N, E, S::R0, 1, DIR, true>(a, j0, tw, ex);
+  } else if constexpr (S::S == 2) {
+    stage<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R1, S::R0, DIR, true>(a, j0, tw, ex);
+  } else if constexpr (S::S == 3) {
+    stage<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R1, S::R0, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R2, S::R0 * S::R1, DIR, true>(a, j0, tw, ex);
+  } else {
+    stage<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R1, S::R0, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R2, S::R0 * S::R1, DIR, false>(a, j0, tw, ex);
+    stage<N, E, S::R3, S::R0 * S::R1 * S::R2, DIR, true>(a, j0, tw, ex);
+  }
+}
+
+// Shared-memory exchange for lines laid out as columns: element n of line l
+// at buf[row(n) * LP + l], two buffers used alternately so that one barrier per
+// exchange suffices (a buffer is rewritten only after the barrier of the
+// following exchange, which every thread passes after finishing its reads).
+// row(n) flips the lowest bit when bit SW of n is set: the first exchange
+// writes rows R1 apart, and this keeps them on alternate bank halves.
+template <typename V, int SW>
+struct ColumnExchange {
+  V* buf;
+  int bufsz;
+  int lp;
+  int l;
+  int par;
+  __device__ __forceinline__ int row(int n) const { return n ^ ((n >> SW) & 1); }
+  __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + row(n) * lp + l] = v; }
+  __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + row(n) * lp + l]; }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ void flip() { par ^= 1; }
+};
+
+// Shared-memory exchange for a line stored as a row: element n at
+// buf[n + (n >> PS)] (one pad slot every 2^PS elements breaks the stride-R
+// bank pattern of the first exchange).
+template <typename V, int PS>
+struct RowExchange {
+  V* buf;
+  int bufsz;
+  int par;
+  __device__ __forceinline__ int pos(int n) const { return n + (n >> PS); }
+  __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + pos(n)] = v; }
+  __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + pos(n)]; }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ void flip() { par ^= 1; }
+};
+
+}  // namespace ps

@@ -1,0 +1,83 @@
+// Internal interface between the plan (ps_plan.cu) and the pass kernels.
+// Not part of the public C ABI (include/ps.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ps {
+
+// Grid geometry and the retained (2/3-rule) cube.
+struct Geo {
+  int nx, ny, nz, nh;
+  int Kx, Ky, Kz;   // largest retained |index| per axis
+  int cx, cy, cz;   // retained counts: Kx+1, 2Ky+1, 2Kz+1
+  int kxp;          // padded kx extent of the compact buffers (multiple of 16)
+  int sphere;       // spherical truncation on top of the cube
+  double sx, sy, sz;  // 2 pi / L per axis
+};
+
+// A spectral vector field in HBM: element (c, r, q, p) at
+// p + ys*row_y(q) + zs*row_z(r) + cs*c, with row(s) = s >= 0 ? s : s + wrap.
+// The caller's layout has wrap = n (FFT order), the compact layout wrap = 2K+1.
+struct Spec {
+  const void* p;
+  long long cs, zs, ys;
+  int zwrap, ywrap;
+};
+
+enum ZfwdMode : int {
+  ZF_RHS = 0,   // out_full = D P(N + f) - nu k^2 u_in
+  ZF_RK4_1 = 1, ZF_RK4_2 = 2, ZF_RK4_3 = 3, ZF_RK4_4 = 4,
+  ZF_RK2_1 = 5, ZF_RK2_2 = 6,
+};
+
+struct PassArgs {
+  Geo g;
+  // inverse z pass input (state or stage buffer)
+  Spec in;
+  // intermediate buffers
+  void* a6;   // [6][nz][cy][kxp]  (z-inverse out) / [3][nz][ny][kxp] (x out)
+  void* b6;   // [6][nz][ny][kxp]  (y-inverse out) / [3][nz][cy][kxp] (y-forward out)
+  const void* tw_x;  // exp(-2 pi i m/nx), m < nx
+  const void* tw_y;
+  const void* tw_z;
+  // fused reductions
+  double* e_part;              // per-CTA energy partials of the z-inverse pass, or null
+  unsigned long long* umax2;   // max |u|^2 (as ordered bits) from the x pass, or null
+  // forward z pass
+  int mode;
+  Spec u_n;          // state at the start of the step (RK) / RHS input (ZF_RHS)
+  void* out_full;    // caller-layout output: RHS or the new state
+  void* nxt;         // compact next-stage input [3][cz][cy][kxp]
+  void* acc;         // compact accumulator        [3][cz][cy][kxp]
+  const void* ifx;   // exp(-nu kx^2 dt/2) for p <= Kx
+  const void* ify;   // ... per retained ky index
+  const void* ifz;   // ... per retained kz index
+  double dt, nu;
+  const void* fbox;  // forcing box [3][2Fz+1][2Fy+1][Fx+1] or null
+  int Fx, Fy, Fz;
+  int xdiag;         // x pass: only the max |u| reduction (no product, no output)
+};
+
+// Launchers (one per pass and precision); return the launch error.
+template <typename T> cudaError_t launch_zinv(const PassArgs& a, cudaStream_t s, int* nblocks_out);
+template <typename T> cudaError_t launch_yinv(const PassArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_xpass(const PassArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_yfwd(const PassArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_zfwd(const PassArgs& a, cudaStream_t s);
+// number of CTAs (energy partials) the z-inverse pass uses for this geometry
+template <typename T> int zinv_blocks(const Geo& g);
+
+// Auxiliary kernels (ps_aux.cu)
+template <typename T>
+cudaError_t launch_if_tables(const Geo& g, double nu, double dt, void* tab, cudaStream_t s);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_forcing_extent(const Geo& g, Spec f, int* ext, cudaStream_t s);
+template <typename T>
+cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, void* box, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, cudaStream_t s);
+cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double* out, cudaStream_t s);
+
+}  // namespace ps

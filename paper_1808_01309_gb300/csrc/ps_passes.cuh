@@ -1,0 +1,557 @@
+// The five passes of one right-hand-side evaluation (Sec. 2 of the paper: the
+// nonlinear term is formed in physical space between a backward and a forward
+// 3D transform, and the pressure projects it onto divergence-free fields;
+// Sec. 2 also describes each 3D transform as per-axis 1D transforms with a
+// transpose between them).
+//
+//   zinv : u_hat (3 fields, retained modes) -> curl in registers -> backward
+//          transform along z of u and omega (6 fields)            [a6]
+//   yinv : backward transform along y                              [a6 -> b6]
+//   xpass: per (z,y) row, backward transform along x of u + i omega (3 complex
+//          lines), n = u x omega pointwise, forward transform of n_x + i n_y and
+//          n_z, split, keep kx <= Kx                               [b6 -> a6]
+//   yfwd : forward transform along y, keep |ky| <= Ky               [a6 -> b6]
+//   zfwd : forward transform along z, keep |kz| <= Kz, 1/(Nx Ny Nz), forcing,
+//          Leray projection, and the right-hand side or the integrating-factor
+//          Runge-Kutta stage update                                 [b6 -> out]
+//
+// Only the retained 2/3-rule cube |p|<=Kx, |q|<=Ky, |r|<=Kz is ever read or
+// transformed where the input is known to vanish elsewhere (pruned transforms);
+// the result is identical to full transforms of the masked field.
+#pragma once
+#include "ps_fft.cuh"
+#include "ps_kernels.h"
+
+namespace ps {
+
+// kx columns per CTA in the strided passes: 64-byte row segments
+template <typename T> struct TXOf { static constexpr int v = sizeof(T) == 4 ? 8 : 4; };
+// lines batched per CTA in the strided passes (about 256 threads per CTA)
+template <typename T, int N> struct NBOf {
+  static constexpr int G = N / EOf<T, N>::v;
+  static constexpr int q = 256 / (TXOf<T>::v * G);
+  static constexpr int v = q < 1 ? 1 : q;
+};
+template <typename T, int N> struct ColThreads {
+  static constexpr int v = TXOf<T>::v * (N / EOf<T, N>::v) * NBOf<T, N>::v;
+};
+// rows per CTA in the x pass
+template <typename T, int N> struct RPCOf {
+  static constexpr int G = N / EOf<T, N>::v;
+  static constexpr int v = G >= 256 ? 1 : 256 / G;
+};
+
+__device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
+__device__ __forceinline__ int rowof(int s, int wrap) { return s >= 0 ? s : s + wrap; }
+__device__ __forceinline__ bool in_cube(const Geo& g, int p, int q, int r) {
+  return p <= g.Kx && q <= g.Ky && q >= -g.Ky && r <= g.Kz && r >= -g.Kz;
+}
+// (p/(Nx/3))^2 + (q/(Ny/3))^2 + (r/(Nz/3))^2 < 1 in exact integer arithmetic
+__device__ __forceinline__ bool in_sphere(const Geo& g, int p, int q, int r) {
+  const long long nx2 = (long long)g.nx * g.nx, ny2 = (long long)g.ny * g.ny, nz2 = (long long)g.nz * g.nz;
+  const long long lhs = 9LL * ((long long)p * p * ny2 * nz2 + (long long)q * q * nx2 * nz2 + (long long)r * r * nx2 * ny2);
+  return lhs < nx2 * ny2 * nz2;
+}
+__device__ __forceinline__ bool kept(const Geo& g, int p, int q, int r) {
+  return in_cube(g, p, q, r) && (!g.sphere || in_sphere(g, p, q, r));
+}
+
+template <typename V> __device__ __forceinline__ V ldv(const V* p) { return __ldg(p); }
+
+// Sum of a per-thread double over the CTA; returns the total in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// zinv: curl + backward transform along z.  CTA = TX kx columns x NB retained
+// ky rows; thread (line, j0, bb) holds kz indices n = j0 + m N/E.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N>::v) k_zinv(const PassArgs a) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const Geo& g = a.g;
+  const int tid = threadIdx.x;
+  const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
+  const int iy = blockIdx.y * NB + bb;
+  const bool bvalid = iy < g.cy;
+  const int kx = blockIdx.x * TX + line;
+  const int q = iy <= g.Ky ? iy : iy - g.cy;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  const V* in = static_cast<const V*>(a.in.p);
+  const V* tw = static_cast<const V*>(a.tw_z);
+  V* out = static_cast<V*>(a.a6);
+  const long long ybase = (long long)rowof(q, a.in.ywrap) * a.in.ys + kx;
+  const T skx = T(kx) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
+  const long long fstride = (long long)g.nz * g.cy * g.kxp;
+  const long long zstride = (long long)g.cy * g.kxp;
+  double esum = 0.0;
+#pragma unroll 1
+  for (int f = 0; f < 6; ++f) {
+    V x[E];
+    T ssq = 0;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = j0 + m * (N / E);
+      const int r = sidx(n, N);
+      V v = czero<V>();
+      if (bvalid && kept(g, kx, q, r)) {
+        const V* pm = in + ybase + (long long)rowof(r, a.in.zwrap) * a.in.zs;
+        if (f < 3) {
+          v = ldv(pm + f * a.in.cs);
+          ssq += v.x * v.x + v.y * v.y;
+        } else {
+          const T skz = T(r) * sz;
+          // omega_hat = i k x u_hat
+          if (f == 3) {
+            const V uy = ldv(pm + a.in.cs), uz = ldv(pm + 2 * a.in.cs);
+            v = cmul_i(csub(cscale(uz, sky), cscale(uy, skz)));
+          } else if (f == 4) {
+            const V ux = ldv(pm), uz = ldv(pm + 2 * a.in.cs);
+            v = cmul_i(csub(cscale(ux, skz), cscale(uz, skx)));
+          } else {
+            const V ux = ldv(pm), uy = ldv(pm + a.in.cs);
+            v = cmul_i(csub(cscale(uy, skx), cscale(ux, sky)));
+          }
+        }
+      }
+      x[m] = v;
+    }
+    if (f < 3) esum += (double)ssq;
+    line_fft<N, E, +1>(x, j0, tw, ex);
+    if (bvalid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int n = j0 + m * (N / E);
+        out[f * fstride + n * zstride + (long long)iy * g.kxp + kx] = x[m];
+      }
+    }
+  }
+  if (a.e_part) {
+    // energy 1/2 sum w |u|^2, w = 1 on the kx = 0 plane, else 2
+    const double t = block_sum(esum * (kx == 0 ? 0.5 : 1.0), red);
+    if (threadIdx.x == 0) a.e_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// yinv: backward transform along y of 6 fields.  CTA = TX columns x NB z planes.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N>::v) k_yinv(const PassArgs a) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const Geo& g = a.g;
+  const int tid = threadIdx.x;
+  const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
+  const int iz = blockIdx.y * NB + bb;
+  const bool bvalid = iz < g.nz;
+  const int kx = blockIdx.x * TX + line;
+  const int f = blockIdx.z;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
+  V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
+  V x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = j0 + m * (N / E);
+    const int q = sidx(n, N);
+    V v = czero<V>();
+    if (bvalid && q <= g.Ky && q >= -g.Ky) v = ldv(in + (long long)rowof(q, g.cy) * g.kxp);
+    x[m] = v;
+  }
+  line_fft<N, E, +1>(x, j0, static_cast<const V*>(a.tw_y), ex);
+  if (bvalid) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) out[(long long)(j0 + m * (N / E)) * g.kxp] = x[m];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// xpass: per physical (z, y) row.  Thread j0 of the row's group holds the
+// points n = j0 + m N/E.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v)) k_xpass(const PassArgs a) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, RPC = RPCOf<T, N>::v;
+  constexpr int PSH = ilog2<Sched<N, E>::R0>::v;
+  constexpr int LEN = N + (N >> PSH);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const Geo& g = a.g;
+  const int tid = threadIdx.x;
+  const int j0 = tid % G, rl = tid / G;
+  const long long rows = (long long)g.nz * g.ny;
+  const long long row = (long long)blockIdx.x * RPC + rl;
+  const bool rvalid = row < rows;
+  const long long rrow = rvalid ? row : 0;
+  RowExchange<V, PSH> ex{sm + rl * LEN, RPC * LEN, 0};
+  const V* tw = static_cast<const V*>(a.tw_x);
+  const V* B = static_cast<const V*>(a.b6);
+  V U[3][E];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const V* pu = B + ((long long)c * rows + rrow) * g.kxp;
+    const V* pw = B + ((long long)(c + 3) * rows + rrow) * g.kxp;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = j0 + m * (N / E);
+      // full spectrum C[n] = u_hat[n] + i w_hat[n]; for n > N/2 the entries
+      // are conj(u_hat[N-n]) + i conj(w_hat[N-n]) (real u and w)
+      const bool hi = n > N / 2;
+      const int p = hi ? N - n : n;
+      V v = czero<V>();
+      if (rvalid && p <= g.Kx) {
+        V X = ldv(pu + p), W = ldv(pw + p);
+        if (hi) { X = cconj(X); W = cconj(W); }
+        v = mk<V>(X.x - W.y, X.y + W.x);
+      }
+      U[c][m] = v;
+    }
+    line_fft<N, E, +1>(U[c], j0, tw, ex);
+  }
+  // n = u x omega at the thread's points; u_c = Re U[c], omega_c = Im U[c]
+  T umax2 = 0;
+  V F1[E], F2[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
+    const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
+    umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
+    F1[m] = mk<V>(uy * wz - uz * wy, uz * wx - ux * wz);
+    F2[m] = mk<V>(ux * wy - uy * wx, T(0));
+  }
+  if (a.umax2) {
+    const double t = block_max(rvalid ? (double)umax2 : 0.0, red);
+    if (threadIdx.x == 0) atomicMax(a.umax2, (unsigned long long)__double_as_longlong(t));
+  }
+  if (a.xdiag) return;  // uniform across the grid
+  line_fft<N, E, -1>(F1, j0, tw, ex);
+  line_fft<N, E, -1>(F2, j0, tw, ex);
+  V* C = static_cast<V*>(a.a6);
+  V* cx = C + (0 * rows + rrow) * g.kxp;
+  V* cy = C + (1 * rows + rrow) * g.kxp;
+  V* cz = C + (2 * rows + rrow) * g.kxp;
+  // split F1 = DFT(n_x) + i DFT(n_y) using the mirrored entry F1[N-k]
+#pragma unroll
+  for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F1[m]);
+  ex.sync();
+  const int kend = g.kxp < N / 2 + 1 ? g.kxp : N / 2 + 1;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = j0 + m * (N / E);
+    if (rvalid && k < kend) {
+      V nx = czero<V>(), ny = czero<V>(), nz = czero<V>();
+      if (k <= g.Kx) {
+        const V Fk = F1[m];
+        const V Fm = cconj(ex.get((N - k) & (N - 1)));
+        nx = cscale(cadd(Fk, Fm), T(0.5));
+        ny = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
+        nz = F2[m];
+      }
+      cx[k] = nx;
+      cy[k] = ny;
+      cz[k] = nz;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// yfwd: forward transform along y of 3 fields, keep |ky| <= Ky.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const Geo& g = a.g;
+  const int tid = threadIdx.x;
+  const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
+  const int iz = blockIdx.y * NB + bb;
+  const bool bvalid = iz < g.nz;
+  const int kx = blockIdx.x * TX + line;
+  const int f = blockIdx.z;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
+  V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
+  V x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = bvalid ? ldv(in + (long long)(j0 + m * (N / E)) * g.kxp) : czero<V>();
+  line_fft<N, E, -1>(x, j0, static_cast<const V*>(a.tw_y), ex);
+  if (bvalid) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int q = sidx(j0 + m * (N / E), N);
+      if (q <= g.Ky && q >= -g.Ky) out[(long long)rowof(q, g.cy) * g.kxp] = x[m];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// zfwd: forward transform along z of 3 fields, then per retained mode
+//   v = D P(N/(Nx Ny Nz) + f),  and the output of the selected mode.
+// full != 0: the grid covers every (ky, kx < nh) of the caller's layout and
+// writes zeros outside the retained set; otherwise only retained modes of the
+// compact stage buffers are written.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N>::v) k_zfwd(const PassArgs a, const int full) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const Geo& g = a.g;
+  const int tid = threadIdx.x;
+  const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
+  const int bidx = blockIdx.y * NB + bb;
+  const int kx = blockIdx.x * TX + line;
+  int q, iy;
+  bool bvalid, bret;
+  if (full) {
+    bvalid = bidx < g.ny;
+    q = sidx(bidx, g.ny);
+    bret = bvalid && q <= g.Ky && q >= -g.Ky;
+    iy = rowof(q, g.cy);
+  } else {
+    bvalid = bret = bidx < g.cy;
+    iy = bidx;
+    q = iy <= g.Ky ? iy : iy - g.cy;
+  }
+  const bool colin = bret && kx < g.kxp;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  const V* tw = static_cast<const V*>(a.tw_z);
+  const long long cs_in = (long long)g.nz * g.cy * g.kxp;
+  const V* in = static_cast<const V*>(a.b6) + (long long)(colin ? iy : 0) * g.kxp + (colin ? kx : 0);
+  V X[3][E];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const long long n = j0 + m * (N / E);
+      X[c][m] = colin ? ldv(in + c * cs_in + n * g.cy * g.kxp) : czero<V>();
+    }
+    line_fft<N, E, -1>(X[c], j0, tw, ex);
+  }
+  const T inv = T(1.0 / ((double)g.nx * g.ny * g.nz));
+  const T kxv = T(kx) * T(g.sx), kyv = T(q) * T(g.sy), sz = T(g.sz);
+  const V* un = static_cast<const V*>(a.u_n.p);
+  const V* fb = static_cast<const V*>(a.fbox);
+  const T* ifx = static_cast<const T*>(a.ifx);
+  const T* ify = static_cast<const T*>(a.ify);
+  const T* ifz = static_cast<const T*>(a.ifz);
+  const T dt = T(a.dt), nu = T(a.nu);
+  const T ey = (a.mode != ZF_RHS && bret) ? ify[iy] : T(0);
+  const T exx = (a.mode != ZF_RHS && kx <= g.Kx) ? ifx[kx] : T(0);
+  const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
+  const long long fcs = (long long)g.nz * g.ny * g.nh;   // caller layout component stride
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = j0 + m * (N / E);
+    const int r = sidx(n, N);
+    const bool keep = bret && kept(g, kx, q, r);
+    V o[3] = {czero<V>(), czero<V>(), czero<V>()};
+    V v0 = czero<V>(), v1 = czero<V>(), v2 = czero<V>();
+    long long ci = 0;
+    if (keep) {
+      const int iz = rowof(r, g.cz);
+      ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
+      v0 = cscale(X[0][m], inv);
+      v1 = cscale(X[1][m], inv);
+      v2 = cscale(X[2][m], inv);
+      if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
+        const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
+        const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
+        const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
+        v0 = cadd(v0, ldv(fb + fo));
+        v1 = cadd(v1, ldv(fb + fo + fcs2));
+        v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
+      }
+      const T kzv = T(r) * sz;
+      const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+      if (k2 > T(0)) {
+        // Leray projection v - k (k.v)/|k|^2
+        const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
+        const T ik2 = T(1) / k2;
+        v0 = csub(v0, cscale(kd, kxv * ik2));
+        v1 = csub(v1, cscale(kd, kyv * ik2));
+        v2 = csub(v2, cscale(kd, kzv * ik2));
+      } else {
+        v0 = v1 = v2 = czero<V>();
+      }
+      if (a.mode == ZF_RHS) {
+        const V* pu = un + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs + (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
+        const T vk = nu * k2;
+        o[0] = csub(v0, cscale(ldv(pu), vk));
+        o[1] = csub(v1, cscale(ldv(pu + a.u_n.cs), vk));
+        o[2] = csub(v2, cscale(ldv(pu + 2 * a.u_n.cs), vk));
+      } else {
+        // Lawson RK with E = exp(-nu |k|^2 dt/2) = ex(p) ey(q) ez(r)
+        const T Ef = exx * ey * ifz[iz];
+        const T E2 = Ef * Ef;
+        const V* pu = un + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs + (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
+        V* acc = static_cast<V*>(a.acc) + ci;
+        V* nxt = static_cast<V*>(a.nxt) + ci;
+        const V kk[3] = {v0, v1, v2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const V u = ldv(pu + c * a.u_n.cs);
+          const V k = kk[c];
+          switch (a.mode) {
+            case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
+              acc[c * ccs] = cscale(k, E2);
+              nxt[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), Ef);
+              break;
+            case ZF_RK4_2: {  // acc += 2 E k2 ; next = E u + dt/2 k2
+              const V ac = acc[c * ccs];
+              acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
+              nxt[c * ccs] = cadd(cscale(u, Ef), cscale(k, T(0.5) * dt));
+              break;
+            }
+            case ZF_RK4_3: {  // acc += 2 E k3 ; next = E^2 u + dt E k3
+              const V ac = acc[c * ccs];
+              acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
+              nxt[c * ccs] = cadd(cscale(u, E2), cscale(k, dt * Ef));
+              break;
+            }
+            case ZF_RK4_4: {  // u+ = E^2 u + dt/6 (acc + k4)
+              const V ac = acc[c * ccs];
+              o[c] = cadd(cscale(u, E2), cscale(cadd(ac, k), dt / T(6)));
+              break;
+            }
+            case ZF_RK2_1:  // next = E^2 (u + dt k1) ; acc = E^2 (u + dt/2 k1)
+              nxt[c * ccs] = cscale(cadd(u, cscale(k, dt)), E2);
+              acc[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), E2);
+              break;
+            case ZF_RK2_2: {  // u+ = acc + dt/2 k2
+              const V ac = acc[c * ccs];
+              o[c] = cadd(ac, cscale(k, T(0.5) * dt));
+              break;
+            }
+            default: break;
+          }
+        }
+      }
+    }
+    if (full && bvalid && kx < g.nh) {
+      V* po = static_cast<V*>(a.out_full) + ((long long)n * g.ny + bidx) * g.nh + kx;
+      po[0] = o[0];
+      po[fcs] = o[1];
+      po[2 * fcs] = o[2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <typename T, int N>
+cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
+  using V = typename cplx<T>::type;
+  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  cudaError_t e = prep(k_zinv<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB);
+  if (nb) *nb = grid.x * grid.y;
+  k_zinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
+  using V = typename cplx<T>::type;
+  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  cudaError_t e = prep(k_yinv<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 6);
+  k_yinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EOf<T, N>::v, G = N / E, RPC = RPCOf<T, N>::v;
+  constexpr int LEN = N + (N >> ilog2<Sched<N, E>::R0>::v);
+  const size_t smem = 2ull * RPC * LEN * sizeof(V);
+  cudaError_t e = prep(k_xpass<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  const long long rows = (long long)a.g.nz * a.g.ny;
+  dim3 grid((unsigned)((rows + RPC - 1) / RPC));
+  k_xpass<T, N><<<grid, RPC * G, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
+  using V = typename cplx<T>::type;
+  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  cudaError_t e = prep(k_yfwd<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 3);
+  k_yfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
+  using V = typename cplx<T>::type;
+  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  cudaError_t e = prep(k_zfwd<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
+  dim3 grid(full ? (a.g.nh + TX - 1) / TX : a.g.kxp / TX, full ? (a.g.ny + NB - 1) / NB : (a.g.cy + NB - 1) / NB);
+  k_zfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a, full);
+  return cudaGetLastError();
+}
+
+#define PS_DISPATCH_N(n, CALL)                     \
+  switch (n) {                                     \
+    case 8: return CALL(8);                        \
+    case 16: return CALL(16);                      \
+    case 32: return CALL(32);                      \
+    case 64: return CALL(64);                      \
+    case 128: return CALL(128);                    \
+    case 256: return CALL(256);                    \
+    case 512: return CALL(512);                    \
+    case 1024: return CALL(1024);                  \
+    default: return cudaErrorInvalidValue;         \
+  }
+
+}  // namespace ps

@@ -1,0 +1,612 @@
+// Plan layer and C ABI (include/ps.h): validation, scratch ownership, twiddle
+// tables, forcing box, and the launch sequence of one right-hand side and of
+// one integrating-factor Runge-Kutta step.
+#include <cmath>
+#include <new>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ps.h"
+#include "ps_kernels.h"
+
+using namespace ps;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ps_status fail(ps_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ps_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA;
+}
+
+#define PS_CU(call, where)                      \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+
+int halfwidth(int n, ps_dealias d) {
+  if (d == PS_DEALIAS_NONE) return n / 2 - 1;
+  return (n + 2) / 3 - 1;  // largest integer strictly below n/3
+}
+
+ps_status validate(const ps_config* c) {
+  if (!c) return fail(PS_ERR_INVALID_ARG, "config is NULL");
+  if (!pow2_in_range(c->nx) || !pow2_in_range(c->ny) || !pow2_in_range(c->nz))
+    return fail(PS_ERR_INVALID_ARG, "nx, ny, nz must be powers of two in [8, 1024]");
+  if (!(std::isfinite(c->lx) && std::isfinite(c->ly) && std::isfinite(c->lz) && c->lx > 0 && c->ly > 0 && c->lz > 0))
+    return fail(PS_ERR_INVALID_ARG, "box lengths must be finite and positive");
+  if (c->prec != PS_FP32 && c->prec != PS_FP64) return fail(PS_ERR_INVALID_ARG, "unknown precision");
+  if (c->eq != PS_HD && c->eq != PS_MHD) return fail(PS_ERR_INVALID_ARG, "unknown equation set");
+  if (c->eq == PS_MHD) return fail(PS_ERR_UNSUPPORTED, "MHD is not implemented in this build");
+  if (c->dealias != PS_DEALIAS_CUBIC && c->dealias != PS_DEALIAS_SPHERICAL && c->dealias != PS_DEALIAS_NONE)
+    return fail(PS_ERR_INVALID_ARG, "unknown dealias rule");
+  if (c->rk_order != 2 && c->rk_order != 4) return fail(PS_ERR_INVALID_ARG, "rk_order must be 2 or 4");
+  if (!(std::isfinite(c->nu) && c->nu >= 0)) return fail(PS_ERR_INVALID_ARG, "nu must be finite and >= 0");
+  return PS_OK;
+}
+
+Geo make_geo(const ps_config* c) {
+  Geo g{};
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nz = c->nz;
+  g.nh = c->nx / 2 + 1;
+  g.Kx = halfwidth(c->nx, c->dealias);
+  g.Ky = halfwidth(c->ny, c->dealias);
+  g.Kz = halfwidth(c->nz, c->dealias);
+  g.cx = g.Kx + 1;
+  g.cy = 2 * g.Ky + 1;
+  g.cz = 2 * g.Kz + 1;
+  g.kxp = (g.cx + 15) / 16 * 16;
+  g.sphere = c->dealias == PS_DEALIAS_SPHERICAL ? 1 : 0;
+  const double two_pi = 6.283185307179586476925286766559;
+  g.sx = two_pi / c->lx;
+  g.sy = two_pi / c->ly;
+  g.sz = two_pi / c->lz;
+  return g;
+}
+
+struct Sizes {
+  size_t vb;       // bytes per complex element
+  size_t a6, b6;   // intermediate buffers (elements)
+  size_t cmp;      // compact 3-field buffer (elements)
+  size_t state;    // caller-layout field (elements)
+};
+
+Sizes sizes(const Geo& g, ps_precision p) {
+  Sizes s{};
+  s.vb = p == PS_FP32 ? 8 : 16;
+  const size_t kxp = g.kxp;
+  const size_t a1 = 6ull * g.nz * g.cy * kxp, a2 = 3ull * g.nz * g.ny * kxp;
+  const size_t b1 = 6ull * g.nz * g.ny * kxp, b2 = 3ull * g.nz * g.cy * kxp;
+  s.a6 = a1 > a2 ? a1 : a2;
+  s.b6 = b1 > b2 ? b1 : b2;
+  s.cmp = 3ull * g.cz * g.cy * kxp;
+  s.state = 3ull * g.nz * g.ny * g.nh;
+  return s;
+}
+
+int nshells_of(const Geo& g) {
+  const double kx = g.Kx * g.sx, ky = g.Ky * g.sy, kz = g.Kz * g.sz;
+  return (int)std::floor(std::sqrt(kx * kx + ky * ky + kz * kz) + 0.5) + 1;
+}
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct ps_plan {
+  ps_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Geo g{};
+  Sizes sz{};
+  void* a6 = nullptr;
+  void* b6 = nullptr;
+  void* nxt = nullptr;
+  void* acc = nullptr;
+  void* tw = nullptr;         // [nx | ny | nz] twiddles
+  void* iftab = nullptr;      // [cx | cy | cz] integrating factors
+  double if_dt = NAN;
+  void* fbox = nullptr;
+  int Fx = -1, Fy = -1, Fz = -1;
+  double* e_part = nullptr;
+  int n_epart = 0;
+  double* stats = nullptr;                 // [energy]
+  unsigned long long* umax2 = nullptr;     // max |u|^2 bits
+  int* ext = nullptr;
+  int nshells = 0;
+  double* dpart = nullptr;                 // diagnostics partials
+  double* dout = nullptr;                  // diagnostics result (device)
+  void* hstate = nullptr;                  // device state for ps_rk_step_host
+  double time = 0.0;
+  long long launches = 0;
+  bool timing = false;
+  std::vector<TimedLaunch> tl;
+  std::vector<cudaEvent_t> pool;
+  double ms_acc[PS_NKINDS] = {0};
+  long long n_acc[PS_NKINDS] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cudaEvent_t take_event(ps_plan* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Wraps one kernel launch: counts it and, with timing on, brackets it with
+// events on the plan stream.
+template <class F>
+ps_status launch(ps_plan* p, int kind, F&& f, const char* what) {
+  TimedLaunch t{kind, nullptr, nullptr};
+  if (p->timing) {
+    t.a = take_event(p);
+    t.b = take_event(p);
+    cudaEventRecord(t.a, p->stream);
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (p->timing) {
+    cudaEventRecord(t.b, p->stream);
+    p->tl.push_back(t);
+  }
+  p->launches++;
+  return PS_OK;
+}
+
+ps_status collect_timing(ps_plan* p) {
+  if (p->tl.empty()) return PS_OK;
+  PS_CU(cudaStreamSynchronize(p->stream), "timing sync");
+  for (auto& t : p->tl) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    p->ms_acc[t.kind] += ms;
+    p->n_acc[t.kind] += 1;
+    p->pool.push_back(t.a);
+    p->pool.push_back(t.b);
+  }
+  p->tl.clear();
+  return PS_OK;
+}
+
+Spec caller_spec(const Geo& g, const void* ptr) {
+  Spec s;
+  s.p = ptr;
+  s.ys = g.nh;
+  s.zs = (long long)g.ny * g.nh;
+  s.cs = (long long)g.nz * g.ny * g.nh;
+  s.zwrap = g.nz;
+  s.ywrap = g.ny;
+  return s;
+}
+
+Spec compact_spec(const Geo& g, const void* ptr) {
+  Spec s;
+  s.p = ptr;
+  s.ys = g.kxp;
+  s.zs = (long long)g.cy * g.kxp;
+  s.cs = (long long)g.cz * g.cy * g.kxp;
+  s.zwrap = g.cz;
+  s.ywrap = g.cy;
+  return s;
+}
+
+PassArgs base_args(ps_plan* p) {
+  PassArgs a{};
+  a.g = p->g;
+  a.a6 = p->a6;
+  a.b6 = p->b6;
+  const size_t vb = p->sz.vb;
+  a.tw_x = p->tw;
+  a.tw_y = static_cast<char*>(p->tw) + vb * p->g.nx;
+  a.tw_z = static_cast<char*>(p->tw) + vb * (p->g.nx + p->g.ny);
+  a.nu = p->cfg.nu;
+  a.fbox = p->fbox;
+  a.Fx = p->Fx;
+  a.Fy = p->Fy;
+  a.Fz = p->Fz;
+  const size_t tb = p->cfg.prec == PS_FP32 ? 4 : 8;
+  a.ifx = p->iftab;
+  a.ify = static_cast<char*>(p->iftab) + tb * p->g.cx;
+  a.ifz = static_cast<char*>(p->iftab) + tb * (p->g.cx + p->g.cy);
+  a.nxt = p->nxt;
+  a.acc = p->acc;
+  return a;
+}
+
+template <typename T>
+ps_status run_inverse_and_x(ps_plan* p, PassArgs& a) {
+  ps_status s;
+  int nb = 0;
+  if ((s = launch(p, 0, [&] { return launch_zinv<T>(a, p->stream, &nb); }, "z-inverse pass")) != PS_OK) return s;
+  if ((s = launch(p, 1, [&] { return launch_yinv<T>(a, p->stream); }, "y-inverse pass")) != PS_OK) return s;
+  if ((s = launch(p, 2, [&] { return launch_xpass<T>(a, p->stream); }, "x pass")) != PS_OK) return s;
+  return PS_OK;
+}
+
+// One evaluation of D P(N + f) followed by the selected z-forward epilogue.
+template <typename T>
+ps_status run_rhs_passes(ps_plan* p, PassArgs& a) {
+  ps_status s;
+  if ((s = run_inverse_and_x<T>(p, a)) != PS_OK) return s;
+  if (a.e_part) {
+    if ((s = launch(p, 5, [&] { return launch_sum_partials(p->e_part, p->n_epart, p->stats, p->stream); },
+                    "energy reduction")) != PS_OK)
+      return s;
+  }
+  if ((s = launch(p, 3, [&] { return launch_yfwd<T>(a, p->stream); }, "y-forward pass")) != PS_OK) return s;
+  if ((s = launch(p, 4, [&] { return launch_zfwd<T>(a, p->stream); }, "z-forward pass")) != PS_OK) return s;
+  return PS_OK;
+}
+
+template <typename T>
+ps_status do_rhs(ps_plan* p, const void* uhat, void* out) {
+  PassArgs a = base_args(p);
+  a.in = caller_spec(p->g, uhat);
+  a.u_n = a.in;
+  a.out_full = out;
+  a.mode = ZF_RHS;
+  return run_rhs_passes<T>(p, a);
+}
+
+template <typename T>
+ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
+  ps_status s;
+  if (!(p->if_dt == dt)) {
+    if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, p->cfg.nu, dt, p->iftab, p->stream); },
+                    "integrating-factor tables")) != PS_OK)
+      return s;
+    p->if_dt = dt;
+  }
+  PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "reset max|u|");
+  const int nst = p->cfg.rk_order == 4 ? 4 : 2;
+  for (int st = 0; st < nst; ++st) {
+    PassArgs a = base_args(p);
+    a.in = st == 0 ? caller_spec(p->g, uhat) : compact_spec(p->g, p->nxt);
+    a.u_n = caller_spec(p->g, uhat);
+    a.out_full = uhat;
+    a.dt = dt;
+    a.e_part = st == 0 ? p->e_part : nullptr;
+    a.umax2 = st == 0 ? p->umax2 : nullptr;
+    a.mode = nst == 4 ? ZF_RK4_1 + st : ZF_RK2_1 + st;
+    if ((s = run_rhs_passes<T>(p, a)) != PS_OK) return s;
+  }
+  return PS_OK;
+}
+
+template <typename T>
+ps_status do_diag(ps_plan* p, const void* uhat, double* host_out) {
+  ps_status s;
+  const int w = 4 + p->nshells;
+  PS_CU(cudaMemsetAsync(p->dpart, 0, sizeof(double) * (size_t)p->g.cz * w, p->stream), "diag reset");
+  PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "diag reset");
+  const Spec u = caller_spec(p->g, uhat);
+  if ((s = launch(p, 5, [&] { return launch_diag_spectral<T>(p->g, u, p->dpart, p->nshells, p->stream); },
+                  "spectral diagnostics")) != PS_OK)
+    return s;
+  if ((s = launch(p, 5, [&] { return launch_diag_final(p->dpart, p->g.cz, p->nshells, p->dout, p->stream); },
+                  "diagnostics reduction")) != PS_OK)
+    return s;
+  PassArgs a = base_args(p);
+  a.in = u;
+  a.umax2 = p->umax2;
+  a.xdiag = 1;
+  if ((s = run_inverse_and_x<T>(p, a)) != PS_OK) return s;
+  PS_CU(cudaMemcpyAsync(host_out, p->dout, sizeof(double) * w, cudaMemcpyDeviceToHost, p->stream), "diag copy");
+  unsigned long long bits = 0;
+  PS_CU(cudaMemcpyAsync(&bits, p->umax2, sizeof(bits), cudaMemcpyDeviceToHost, p->stream), "diag copy");
+  PS_CU(cudaStreamSynchronize(p->stream), "diag sync");
+  double m2;
+  std::memcpy(&m2, &bits, sizeof(m2));
+  host_out[w] = std::sqrt(m2);
+  return PS_OK;
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t n) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + n && y < x + n;
+}
+
+// Twiddles exp(-2 pi i m/n), m < n, evaluated in long double and rounded.
+template <typename V>
+void fill_twiddles(std::vector<V>& out, int n) {
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int m = 0; m < n; ++m) {
+    const long double ang = two_pi * (long double)m / (long double)n;
+    V v;
+    v.x = (decltype(v.x))std::cos(ang);
+    v.y = (decltype(v.x))(-std::sin(ang));
+    out.push_back(v);
+  }
+}
+
+template <typename V>
+ps_status upload_twiddles(ps_plan* p) {
+  std::vector<V> h;
+  fill_twiddles(h, p->g.nx);
+  fill_twiddles(h, p->g.ny);
+  fill_twiddles(h, p->g.nz);
+  PS_CU(cudaMemcpy(p->tw, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice), "twiddle upload");
+  return PS_OK;
+}
+
+template <typename T>
+ps_status setup_forcing(ps_plan* p) {
+  const Spec f = caller_spec(p->g, p->cfg.forcing);
+  PS_CU(cudaMemsetAsync(p->ext, 0xff, 3 * sizeof(int), p->stream), "forcing extent");
+  PS_CU(launch_forcing_extent<T>(p->g, f, p->ext, p->stream), "forcing extent");
+  int ext[3];
+  PS_CU(cudaMemcpyAsync(ext, p->ext, sizeof(ext), cudaMemcpyDeviceToHost, p->stream), "forcing extent");
+  PS_CU(cudaStreamSynchronize(p->stream), "forcing extent");
+  if (ext[0] < 0) return PS_OK;  // no retained forcing mode
+  p->Fx = ext[0];
+  p->Fy = ext[1];
+  p->Fz = ext[2];
+  const size_t n = 3ull * (p->Fx + 1) * (2 * p->Fy + 1) * (2 * p->Fz + 1);
+  PS_CU(cudaMalloc(&p->fbox, n * p->sz.vb), "forcing box");
+  PS_CU(launch_forcing_gather<T>(p->g, f, p->Fx, p->Fy, p->Fz, p->fbox, p->stream), "forcing gather");
+  PS_CU(cudaStreamSynchronize(p->stream), "forcing gather");
+  return PS_OK;
+}
+
+void release(ps_plan* p) {
+  void* bufs[] = {p->a6, p->b6, p->nxt, p->acc, p->tw, p->iftab, p->fbox, p->e_part, p->stats,
+                  p->umax2, p->ext, p->dpart, p->dout, p->hstate};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto& t : p->tl) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : p->pool) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ps_status_string(ps_status s) {
+  switch (s) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID_ARG: return "invalid argument";
+    case PS_ERR_UNSUPPORTED: return "unsupported";
+    case PS_ERR_OOM: return "out of device memory";
+    case PS_ERR_CUDA: return "CUDA error";
+    case PS_ERR_NONFINITE: return "non-finite result";
+    case PS_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+const char* ps_last_error(void) { return g_last_error.c_str(); }
+
+const char* ps_kind_name(int kind) {
+  static const char* names[PS_NKINDS] = {"z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward_rk", "aux"};
+  return (kind >= 0 && kind < PS_NKINDS) ? names[kind] : "?";
+}
+
+ps_status ps_plan_workspace_bytes(const ps_config* cfg, size_t* bytes) {
+  ps_status s = validate(cfg);
+  if (s != PS_OK) return s;
+  if (!bytes) return fail(PS_ERR_INVALID_ARG, "bytes is NULL");
+  const Geo g = make_geo(cfg);
+  const Sizes z = sizes(g, cfg->prec);
+  const size_t tb = cfg->prec == PS_FP32 ? 4 : 8;
+  *bytes = z.vb * (z.a6 + z.b6 + 2 * z.cmp + (size_t)(g.nx + g.ny + g.nz)) + tb * (g.cx + g.cy + g.cz) +
+           sizeof(double) * (size_t)(g.cz * (g.kxp + 4 + nshells_of(g)) + 16);
+  return PS_OK;
+}
+
+ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out) {
+  if (!out) return fail(PS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ps_status s = validate(cfg);
+  if (s != PS_OK) return s;
+  ps_plan* p = new (std::nothrow) ps_plan();
+  if (!p) return fail(PS_ERR_OOM, "host allocation failed");
+  p->cfg = *cfg;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  p->g = make_geo(cfg);
+  p->sz = sizes(p->g, cfg->prec);
+  p->nshells = nshells_of(p->g);
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  auto bail = [&](ps_status st) {
+    release(p);
+    delete p;
+    return st;
+  };
+  const size_t vb = p->sz.vb, tb = cfg->prec == PS_FP32 ? 4 : 8;
+#define ALLOC(ptr, bytes, what)                          \
+  do {                                                   \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes)); \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, what)); \
+  } while (0)
+  ALLOC(p->a6, p->sz.a6 * vb, "scratch a");
+  ALLOC(p->b6, p->sz.b6 * vb, "scratch b");
+  ALLOC(p->nxt, p->sz.cmp * vb, "stage input");
+  ALLOC(p->acc, p->sz.cmp * vb, "stage accumulator");
+  ALLOC(p->tw, vb * (size_t)(p->g.nx + p->g.ny + p->g.nz), "twiddles");
+  ALLOC(p->iftab, tb * (size_t)(p->g.cx + p->g.cy + p->g.cz), "integrating factors");
+  int nb = cfg->prec == PS_FP32 ? zinv_blocks<float>(p->g) : zinv_blocks<double>(p->g);
+  p->n_epart = nb;
+  ALLOC(p->e_part, sizeof(double) * (size_t)(nb > 0 ? nb : 1), "energy partials");
+  ALLOC(p->stats, sizeof(double) * 4, "stats");
+  ALLOC(p->umax2, sizeof(unsigned long long), "max|u|");
+  ALLOC(p->ext, sizeof(int) * 4, "forcing extent");
+  ALLOC(p->dpart, sizeof(double) * (size_t)p->g.cz * (4 + p->nshells), "diagnostic partials");
+  ALLOC(p->dout, sizeof(double) * (size_t)(4 + p->nshells), "diagnostics");
+#undef ALLOC
+  // Clean scratch once so that padding columns never hold uninitialised bits.
+  e = cudaMemsetAsync(p->a6, 0, p->sz.a6 * vb, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->b6, 0, p->sz.b6 * vb, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->nxt, 0, p->sz.cmp * vb, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->acc, 0, p->sz.cmp * vb, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->stats, 0, sizeof(double) * 4, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "scratch clear"));
+  s = cfg->prec == PS_FP32 ? upload_twiddles<float2>(p) : upload_twiddles<double2>(p);
+  if (s != PS_OK) return bail(s);
+  if (cfg->forcing) {
+    s = cfg->prec == PS_FP32 ? setup_forcing<float>(p) : setup_forcing<double>(p);
+    if (s != PS_OK) return bail(s);
+  }
+  e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "plan create sync"));
+  *out = p;
+  return PS_OK;
+}
+
+ps_status ps_plan_destroy(ps_plan* p) {
+  if (!p) return PS_OK;
+  DeviceGuard dg(p->device);
+  cudaStreamSynchronize(p->stream);
+  release(p);
+  delete p;
+  return PS_OK;
+}
+
+ps_status ps_rhs(ps_plan* p, const void* uhat, void* rhs_out, double t) {
+  (void)t;
+  if (!p || !uhat || !rhs_out) return fail(PS_ERR_INVALID_ARG, "NULL plan or buffer");
+  if (ranges_overlap(uhat, rhs_out, p->sz.state * p->sz.vb))
+    return fail(PS_ERR_INVALID_ARG, "rhs_out overlaps uhat");
+  DeviceGuard dg(p->device);
+  return p->cfg.prec == PS_FP32 ? do_rhs<float>(p, uhat, rhs_out) : do_rhs<double>(p, uhat, rhs_out);
+}
+
+ps_status ps_rk_step(ps_plan* p, void* uhat, double dt, double t) {
+  if (!p || !uhat) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
+  if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
+  DeviceGuard dg(p->device);
+  ps_status s = p->cfg.prec == PS_FP32 ? do_rk_step<float>(p, uhat, dt) : do_rk_step<double>(p, uhat, dt);
+  if (s == PS_OK) p->time = t + dt;
+  return s;
+}
+
+ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int nsteps) {
+  if (!p || !uhat_host) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
+  if (nsteps < 0) return fail(PS_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
+  DeviceGuard dg(p->device);
+  const size_t bytes = p->sz.state * p->sz.vb;
+  if (!p->hstate) PS_CU(cudaMalloc(&p->hstate, bytes), "host-path state");
+  PS_CU(cudaMemcpyAsync(p->hstate, uhat_host, bytes, cudaMemcpyHostToDevice, p->stream), "state upload");
+  for (int i = 0; i < nsteps; ++i) {
+    ps_status s = ps_rk_step(p, p->hstate, dt, t + i * dt);
+    if (s != PS_OK) return s;
+  }
+  PS_CU(cudaMemcpyAsync(uhat_host, p->hstate, bytes, cudaMemcpyDeviceToHost, p->stream), "state download");
+  PS_CU(cudaStreamSynchronize(p->stream), "host-path sync");
+  return PS_OK;
+}
+
+ps_status ps_step_stats(ps_plan* p, double* energy, double* max_u) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  DeviceGuard dg(p->device);
+  double e = 0;
+  unsigned long long bits = 0;
+  PS_CU(cudaMemcpyAsync(&e, p->stats, sizeof(e), cudaMemcpyDeviceToHost, p->stream), "stats copy");
+  PS_CU(cudaMemcpyAsync(&bits, p->umax2, sizeof(bits), cudaMemcpyDeviceToHost, p->stream), "stats copy");
+  PS_CU(cudaStreamSynchronize(p->stream), "stats sync");
+  double m2;
+  std::memcpy(&m2, &bits, sizeof(m2));
+  if (energy) *energy = e;
+  if (max_u) *max_u = std::sqrt(m2);
+  return PS_OK;
+}
+
+ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out) {
+  if (!p || !uhat || !out) return fail(PS_ERR_INVALID_ARG, "NULL plan, state or output");
+  if (!std::isfinite(cfl)) return fail(PS_ERR_INVALID_ARG, "cfl must be finite");
+  if (out->spectrum && out->nshells < 0) return fail(PS_ERR_INVALID_ARG, "negative spectrum capacity");
+  DeviceGuard dg(p->device);
+  std::vector<double> h(5 + p->nshells);
+  ps_status s = p->cfg.prec == PS_FP32 ? do_diag<float>(p, uhat, h.data()) : do_diag<double>(p, uhat, h.data());
+  if (s != PS_OK) return s;
+  out->energy = h[0];
+  out->enstrophy = h[1];
+  out->helicity = h[2];
+  out->max_div = h[3];
+  out->max_u = h[4 + p->nshells];
+  const double dmin = std::fmin(p->cfg.lx / p->cfg.nx, std::fmin(p->cfg.ly / p->cfg.ny, p->cfg.lz / p->cfg.nz));
+  out->cfl_dt = out->max_u > 0 ? cfl * dmin / out->max_u : INFINITY;
+  out->time = p->time;
+  if (out->spectrum) {
+    const int n = out->nshells < p->nshells ? out->nshells : p->nshells;
+    for (int i = 0; i < n; ++i) out->spectrum[i] = h[4 + i];
+  }
+  out->nshells = p->nshells;
+  for (int i = 0; i < 5 + p->nshells; ++i)
+    if (!std::isfinite(h[i])) return fail(PS_ERR_NONFINITE, "non-finite diagnostic");
+  return PS_OK;
+}
+
+ps_status ps_plan_set_timing(ps_plan* p, int enable) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  DeviceGuard dg(p->device);
+  ps_status s = collect_timing(p);
+  if (s != PS_OK) return s;
+  for (int k = 0; k < PS_NKINDS; ++k) {
+    p->ms_acc[k] = 0;
+    p->n_acc[k] = 0;
+  }
+  p->timing = enable != 0;
+  return PS_OK;
+}
+
+ps_status ps_plan_get_timing(ps_plan* p, ps_timing* out) {
+  if (!p || !out) return fail(PS_ERR_INVALID_ARG, "NULL plan or output");
+  DeviceGuard dg(p->device);
+  ps_status s = collect_timing(p);
+  if (s != PS_OK) return s;
+  for (int k = 0; k < PS_NKINDS; ++k) {
+    out->ms[k] = p->ms_acc[k];
+    out->launches[k] = p->n_acc[k];
+  }
+  return PS_OK;
+}
+
+ps_status ps_plan_launch_count(ps_plan* p, long long* launches) {
+  if (!p || !launches) return fail(PS_ERR_INVALID_ARG, "NULL plan or output");
+  *launches = p->launches;
+  return PS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+"""ctypes binding of libps.so (include/ps.h): argument marshalling only.
+
+Every step of the right-hand side and of the Runge-Kutta step runs in the
+library's CUDA kernels; torch is used for device buffers and streams.  If the
+library is missing the import fails: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import enum
+import math
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libps.so")
+
+
+class PsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Precision(enum.IntEnum):
+    FP32 = 0
+    FP64 = 1
+
+
+class Equations(enum.IntEnum):
+    HD = 0
+    MHD = 1
+
+
+class Dealias(enum.IntEnum):
+    CUBIC = 0
+    SPHERICAL = 1
+    NONE = 2
+
+
+PS_OK, PS_ERR_INVALID_ARG, PS_ERR_UNSUPPORTED, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_NONFINITE, PS_ERR_TIMEOUT = range(7)
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
+           5: "non-finite", 6: "timeout"}
+PS_NKINDS = 6
+
+# Exported symbols and their signatures (kept in step with include/ps.h).
+SYMBOLS = (
+    "ps_plan_create", "ps_plan_destroy", "ps_plan_workspace_bytes", "ps_rhs", "ps_rk_step",
+    "ps_rk_step_host", "ps_step_stats", "ps_diagnostics", "ps_plan_set_timing",
+    "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
+    "ps_last_error",
+)
+
+
+class PsConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("prec", ctypes.c_int), ("eq", ctypes.c_int), ("dealias", ctypes.c_int),
+        ("rk_order", ctypes.c_int),
+        ("nu", ctypes.c_double), ("eta", ctypes.c_double),
+        ("forcing", ctypes.c_void_p),
+    ]
+
+
+class PsDiag(ctypes.Structure):
+    _fields_ = [
+        ("energy", ctypes.c_double), ("enstrophy", ctypes.c_double), ("helicity", ctypes.c_double),
+        ("max_div", ctypes.c_double), ("max_u", ctypes.c_double), ("cfl_dt", ctypes.c_double),
+        ("time", ctypes.c_double),
+        ("spectrum", ctypes.POINTER(ctypes.c_double)), ("nshells", ctypes.c_int),
+    ]
+
+
+class PsTiming(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * PS_NKINDS), ("launches", ctypes.c_longlong * PS_NKINDS)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libps.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(the CUDA path has no fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.ps_plan_create.argtypes = [ctypes.POINTER(PsConfig), P, ctypes.POINTER(P)]
+    lib.ps_plan_destroy.argtypes = [P]
+    lib.ps_plan_workspace_bytes.argtypes = [ctypes.POINTER(PsConfig), ctypes.POINTER(ctypes.c_size_t)]
+    lib.ps_rhs.argtypes = [P, P, P, ctypes.c_double]
+    lib.ps_rk_step.argtypes = [P, P, ctypes.c_double, ctypes.c_double]
+    lib.ps_rk_step_host.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.ps_step_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.ps_diagnostics.argtypes = [P, P, ctypes.c_double, ctypes.POINTER(PsDiag)]
+    lib.ps_plan_set_timing.argtypes = [P, ctypes.c_int]
+    lib.ps_plan_get_timing.argtypes = [P, ctypes.POINTER(PsTiming)]
+    lib.ps_plan_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    for name in SYMBOLS:
+        fn = getattr(lib, name)
+        if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
+            fn.restype = ctypes.c_char_p
+        else:
+            fn.restype = ctypes.c_int
+    lib.ps_kind_name.argtypes = [ctypes.c_int]
+    lib.ps_status_string.argtypes = [ctypes.c_int]
+    lib.ps_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != PS_OK:
+        msg = load().ps_last_error().decode(errors="replace")
+        raise PsError(status, msg)
+
+
+def make_config(nx, ny=None, nz=None, *, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi,
+                prec=Precision.FP32, eq=Equations.HD, dealias=Dealias.CUBIC, rk_order=4,
+                nu=0.0, eta=0.0, forcing=None) -> PsConfig:
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    fptr = None
+    if forcing is not None:
+        fptr = forcing.data_ptr() if hasattr(forcing, "data_ptr") else int(forcing)
+    return PsConfig(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz), int(prec), int(eq),
+                    int(dealias), int(rk_order), float(nu), float(eta), fptr)
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- functions with the C names -------------------------------------------------
+
+def ps_plan_create(cfg: PsConfig, stream=None) -> ctypes.c_void_p:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.ps_plan_create(ctypes.byref(cfg), _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def ps_plan_destroy(plan) -> None:
+    _check(load().ps_plan_destroy(plan))
+
+
+def ps_plan_workspace_bytes(cfg: PsConfig) -> int:
+    n = ctypes.c_size_t()
+    _check(load().ps_plan_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def ps_rhs(plan, uhat, rhs_out, t: float = 0.0) -> None:
+    _check(load().ps_rhs(plan, _ptr(uhat), _ptr(rhs_out), float(t)))
+
+
+def ps_rk_step(plan, uhat, dt: float, t: float = 0.0) -> None:
+    _check(load().ps_rk_step(plan, _ptr(uhat), float(dt), float(t)))
+
+
+def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
+    _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_step_stats(plan) -> tuple[float, float]:
+    e, m = ctypes.c_double(), ctypes.c_double()
+    _check(load().ps_step_stats(plan, ctypes.byref(e), ctypes.byref(m)))
+    return e.value, m.value
+
+
+def ps_diagnostics(plan, uhat, cfl: float = 0.5, nshells: int = 4096) -> dict:
+    spec = (ctypes.c_double * max(nshells, 1))()
+    d = PsDiag()
+    d.spectrum = ctypes.cast(spec, ctypes.POINTER(ctypes.c_double))
+    d.nshells = nshells
+    st = load().ps_diagnostics(plan, _ptr(uhat), float(cfl), ctypes.byref(d))
+    out = dict(energy=d.energy, enstrophy=d.enstrophy, helicity=d.helicity, max_div=d.max_div,
+               max_u=d.max_u, cfl_dt=d.cfl_dt, time=d.time,
+               spectrum=[spec[i] for i in range(min(d.nshells, nshells))], status=st)
+    if st not in (PS_OK, PS_ERR_NONFINITE):
+        _check(st)
+    return out
+
+
+def ps_plan_set_timing(plan, enable: bool) -> None:
+    _check(load().ps_plan_set_timing(plan, 1 if enable else 0))
+
+
+def ps_plan_get_timing(plan) -> dict:
+    t = PsTiming()
+    _check(load().ps_plan_get_timing(plan, ctypes.byref(t)))
+    lib = load()
+    return {lib.ps_kind_name(k).decode(): (t.ms[k], t.launches[k]) for k in range(PS_NKINDS)}
+
+
+def ps_plan_launch_count(plan) -> int:
+    n = ctypes.c_longlong()
+    _check(load().ps_plan_launch_count(plan, ctypes.byref(n)))
+    return n.value
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+
+class Plan:
+    """Owns one ps_plan; fields are torch tensors of shape (3, nz, ny, nx//2+1),
+    complex64 (FP32) or complex128 (FP64), contiguous, on the plan's device."""
+
+    def __init__(self, nx, ny=None, nz=None, *, stream=None, **kw):
+        self.cfg = make_config(nx, ny, nz, **kw)
+        self._forcing = kw.get("forcing")  # keep alive until creation copied it
+        self.stream = stream
+        self.handle = ps_plan_create(self.cfg, stream)
+
+    @property
+    def shape(self):
+        c = self.cfg
+        return (3, c.nz, c.ny, c.nx // 2 + 1)
+
+    def _check_field(self, t):
+        import torch
+        want = torch.complex64 if self.cfg.prec == Precision.FP32 else torch.complex128
+        if tuple(t.shape) != self.shape or t.dtype != want or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"field must be a contiguous CUDA {want} tensor of shape {self.shape}")
+
+    def rhs(self, uhat, out=None, t=0.0):
+        import torch
+        self._check_field(uhat)
+        if out is None:
+            out = torch.empty_like(uhat)
+        self._check_field(out)
+        ps_rhs(self.handle, uhat, out, t)
+        return out
+
+    def rk_step(self, uhat, dt, t=0.0):
+        self._check_field(uhat)
+        ps_rk_step(self.handle, uhat, dt, t)
+        return uhat
+
+    def diagnostics(self, uhat, cfl=0.5):
+        self._check_field(uhat)
+        return ps_diagnostics(self.handle, uhat, cfl)
+
+    def step_stats(self):
+        return ps_step_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ps_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

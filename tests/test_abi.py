@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads and exports every symbol include/ps.h
+declares; host-side argument checks return the documented status without
+touching a GPU."""
+
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import ps as _ps
+    return _ps
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ps.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ps_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_path():
+    names = header_functions()
+    for n in ("ps_plan_create", "ps_plan_destroy", "ps_rhs", "ps_rk_step", "ps_diagnostics"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(ps):
+    lib = ps.load()
+    for name in header_functions():
+        assert hasattr(lib, name), name
+    assert set(header_functions()) <= set(ps.SYMBOLS)
+
+
+def test_status_strings(ps):
+    lib = ps.load()
+    assert lib.ps_status_string(0) == b"ok"
+    assert lib.ps_status_string(1) == b"invalid argument"
+    assert lib.ps_kind_name(2) == b"x_fused"
+    assert lib.ps_kind_name(99) == b"?"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=12), dict(nx=4), dict(ny=2048), dict(nz=0), dict(lx=0.0), dict(ly=-1.0),
+    dict(lz=math.inf), dict(rk_order=3), dict(nu=-1e-3), dict(nu=math.nan),
+    dict(dealias=7), dict(prec=5),
+])
+def test_invalid_configs_are_rejected_before_any_cuda_call(ps, bad):
+    kw = dict(nx=32, ny=32, nz=32)
+    kw.update(bad)
+    nx, ny, nz = kw.pop("nx"), kw.pop("ny"), kw.pop("nz")
+    cfg = ps.make_config(nx, ny, nz, **kw)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_plan_create(cfg)
+    assert e.value.status == ps.PS_ERR_INVALID_ARG
+    with pytest.raises(ps.PsError):
+        ps.ps_plan_workspace_bytes(cfg)
+
+
+def test_mhd_is_reported_unsupported(ps):
+    cfg = ps.make_config(32, eq=ps.Equations.MHD)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_plan_create(cfg)
+    assert e.value.status == ps.PS_ERR_UNSUPPORTED
+
+
+def test_null_arguments(ps):
+    lib = ps.load()
+    assert lib.ps_rhs(None, None, None, 0.0) == ps.PS_ERR_INVALID_ARG
+    assert lib.ps_rk_step(None, None, 0.1, 0.0) == ps.PS_ERR_INVALID_ARG
+    assert lib.ps_plan_destroy(None) == ps.PS_OK
+    assert lib.ps_plan_create(None, None, None) == ps.PS_ERR_INVALID_ARG
+
+
+def test_workspace_bytes_scale_with_the_retained_cube(ps):
+    b32 = ps.ps_plan_workspace_bytes(ps.make_config(32))
+    b64 = ps.ps_plan_workspace_bytes(ps.make_config(64))
+    b64d = ps.ps_plan_workspace_bytes(ps.make_config(64, prec=ps.Precision.FP64))
+    assert 6 < b64 / b32 < 10
+    assert 1.9 < b64d / b64 < 2.1
+    # 512^3 FP32: two 6-field intermediates and two compact 3-field stage buffers
+    b512 = ps.ps_plan_workspace_bytes(ps.make_config(512))
+    assert 4.0e9 < b512 < 5.5e9
