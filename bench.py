@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the pseudospectral Navier-Stokes hot path on GB300.
+
+One step = one integrating-factor RK4 step (ps_rk_step): four right-hand-side
+evaluations (curl, backward transforms, u x omega, forward transforms, 2/3
+dealiasing, Leray projection, forcing) with the stage updates and the FP64
+energy / max|u| reductions fused in.  Workload: 512^3 forced hydrodynamics,
+seeded solenoidal field with E(K) ~ K^4 exp(-2 (K/4)^2) normalised to 0.5,
+forcing on shells 2 <= |k| <= 3, nu = 2e-3, dt = 1e-3, FP32 bulk with FP64
+reductions.  The state (1.6 GB) is larger than L2, so no flush is needed.
+
+Metric: RHS Gpoints/s = 4 N^3 / (time per RK4 step) over all ranks, and ms per
+RK step.  The FP64 path and the FP32/FP64 speed ratio are reported alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(the single-field solve is not sharded); value sums the ranks' points.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS Gpoints/s and time/RK step at 512^3, FP32 vs FP64 on GPU, % HBM roofline"
+UNIT = "Gpoints/s"
+FALLBACK_HBM_GBS = 6800.0
+KIND_FILES = {
+    "z_inverse": ["ps_passes.cuh", "ps_fft.cuh", "k_zinv_f32.cu"],
+    "y_inverse": ["ps_passes.cuh", "ps_fft.cuh", "k_yinv_f32.cu"],
+    "x_fused": ["ps_passes.cuh", "ps_fft.cuh", "k_xpass_f32.cu"],
+    "y_forward": ["ps_passes.cuh", "ps_fft.cuh", "k_yfwd_f32.cu"],
+    "z_forward_rk": ["ps_passes.cuh", "ps_fft.cuh", "k_zfwd_f32.cu"],
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(files) -> str:
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(ROOT, "paper_1808_01309_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kind: str, n: int):
+    """DRAM bytes per launch of `kind` at n^3 FP32 from the committed ncu
+    summary, or None if absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    if not os.path.exists(path):
+        return None
+    want = source_hash(KIND_FILES[kind])
+    pat = re.compile(r"^traffic\s+(\S+)\s+n=(\d+)\s+fp32\s+src=(\w+)\s+bytes_per_launch=([0-9.eE+]+)")
+    for line in open(path):
+        m = pat.match(line.strip())
+        if m and m.group(1) == kind and int(m.group(2)) == n and m.group(3) == want:
+            return float(m.group(4))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n: int, vb: int):
+    """Compulsory HBM bytes per launch of each kernel kind for one RHS stage of
+    an IF-RK4 step on an n^3 grid with the cubic 2/3 rule (vb bytes per complex
+    value).  Retained counts: cx = K+1, cy = cz = 2K+1, K = ceil(n/3) - 1."""
+    K = (n + 2) // 3 - 1
+    cx, c2 = K + 1, 2 * K + 1
+    modes = c2 * c2 * cx
+    b = {
+        "z_inverse": (3 * modes + 6 * n * c2 * cx) * vb,
+        "y_inverse": (6 * n * c2 * cx + 6 * n * n * cx) * vb,
+        "x_fused": (6 * n * n * cx + 3 * n * n * cx) * vb,
+        "y_forward": (3 * n * n * cx + 3 * n * c2 * cx) * vb,
+    }
+    # z-forward of an RK4 step, averaged over its four stages: reads the 3
+    # y-forward fields and the state; stages 1-3 write stage input and
+    # accumulator (2-3 also read the accumulator), stage 4 writes the full state
+    nh = n // 2 + 1
+    zf = [3 * n * c2 * cx + 3 * modes + 2 * 3 * modes,
+          3 * n * c2 * cx + 3 * modes + 3 * 3 * modes,
+          3 * n * c2 * cx + 3 * modes + 3 * 3 * modes,
+          3 * n * c2 * cx + 3 * modes + 3 * modes + 3 * n * n * nh]
+    b["z_forward_rk"] = sum(zf) / 4 * vb
+    return b
+
+
+def make_inputs(n: int):
+    from paper_1808_01309_gb300 import inputs
+    u = inputs.random_solenoidal_field(n, n, n, seed=1)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    return u, f
+
+
+def time_steps(plan, ud, dt, steps, warmup, stream, world, ps):
+    import torch
+    for i in range(warmup):
+        plan.rk_step(ud, dt, t=i * dt)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = ps.ps_plan_launch_count(plan.handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        plan.rk_step(ud, dt, t=(warmup + i) * dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier(world)
+    torch.cuda.synchronize()
+    return ms, ps.ps_plan_launch_count(plan.handle) - l0
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import ps
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nu, dt = args.n, 2e-3, 1e-3
+    u, f = make_inputs(n)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    # ---- FP32 (headline) -------------------------------------------------
+    ud = torch.from_numpy(u).to(dev, torch.complex64)
+    fd = torch.from_numpy(f).to(dev, torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=fd, stream=stream)
+    ps.ps_plan_set_timing(plan.handle, False)
+    for i in range(args.warmup):
+        plan.rk_step(ud, dt)
+    torch.cuda.synchronize()
+    ps.ps_plan_set_timing(plan.handle, True)
+    with ClockSampler(local) as clk:
+        ms, launches = time_steps(plan, ud, dt, args.steps, 0, stream, world, ps)
+    kt = ps.ps_plan_get_timing(plan.handle)
+    ps.ps_plan_set_timing(plan.handle, False)
+    ms_max = reduce_max(ms, world)
+    ms_step = ms_max / args.steps
+    e_step, umax_step = plan.step_stats()
+
+    # ---- per-kernel roofline of the dominant kernel -------------------------
+    hbm, peak_src = measured_peaks()
+    alg = algorithmic_bytes(n, 8)
+    kinds = {k: v for k, v in kt.items() if k in alg and v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    avg_ms = kinds[dom][0] / kinds[dom][1]
+    achieved = alg[dom] / (avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom, n)
+    kernel_share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
+    kernel_gbs = {k: round(alg[k] / (v[0] / v[1] * 1e-3) / 1e9, 1) for k, v in kinds.items()}
+    step_bytes = sum(alg[k] * kinds[k][1] for k in kinds) / args.steps
+    plan.close()
+
+    # ---- end to end: host buffers through the C ABI -------------------------
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(u.astype(np.complex64)).pin_memory()
+        plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=fd, stream=stream)
+        for _ in range(max(1, args.warmup // 2)):
+            ps.ps_rk_step_host(plan.handle, host, dt, 0.0, 1)
+        ksteps = max(3, args.steps // 2)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ksteps):
+            ps.ps_rk_step_host(plan.handle, host, dt, i * dt, 1)
+        t1 = time.perf_counter()
+        e2e_ms = reduce_max((t1 - t0) * 1e3, world) / ksteps
+        nbytes = host.numel() * host.element_size()
+        e2e = {"value": round(world * 4 * n ** 3 / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+               "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": ksteps, "api": "ps_rk_step_host (pinned host state, 1 step per call)"}
+        plan.close()
+        del host
+    del ud, fd
+    torch.cuda.empty_cache()
+
+    # ---- FP64 ------------------------------------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        ud = torch.from_numpy(u).to(dev, torch.complex128)
+        fd = torch.from_numpy(f).to(dev, torch.complex128)
+        plan = ps.Plan(n, prec=ps.Precision.FP64, nu=nu, rk_order=4, forcing=fd, stream=stream)
+        ms64, _ = time_steps(plan, ud, dt, args.fp64_steps, 3, stream, world, ps)
+        ms64 = reduce_max(ms64, world) / args.fp64_steps
+        fp64 = {"ms_per_step": round(ms64, 3), "value": round(world * 4 * n ** 3 / (ms64 * 1e-3) / 1e9, 3),
+                "unit": UNIT, "steps": args.fp64_steps, "fp32_speedup": round(ms64 / ms_step, 2),
+                "bound": "fp64 alu (GB300 FP64 ~1.06 TFLOP/s measured by an FMA probe)"}
+        plan.close()
+        del ud, fd
+        torch.cuda.empty_cache()
+
+    out.update(ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
+               achieved=achieved, hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
+               kernel_gbs=kernel_gbs, step_bytes=step_bytes, e2e=e2e, fp64=fp64, energy=e_step,
+               max_u=umax_step, alg=alg)
+    return out, u, f
+
+
+CPU_N = 256  # the oracle's sample grid: one 256^3 RHS takes ~7 s, a 512^3 one ~1 min
+
+
+def oracle_rhs_sample(u, f, n):
+    """Times one FP64 oracle right-hand side on the full n^3 field."""
+    import oracle
+    cfg = oracle.Config(n, n, n, nu=2e-3, rk_order=4)
+    t0 = time.perf_counter()
+    oracle.rhs(u, cfg, forcing=f)
+    return time.perf_counter() - t0
+
+
+def cpu_sample_desc(n_cpu, n, secs):
+    return (f"one FP64 oracle RHS of the same recipe (seeded field + forcing, nu=2e-3) on a {n_cpu}^3 grid "
+            f"instead of {n}^3 ({secs:.1f} s; numpy FFT, single thread), throughput per grid point")
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    n = args.n
+
+    if args.impl == "reference":
+        # the oracle, timed as it stands on this host (rank 0 only)
+        if rank != 0:
+            return
+        nc = min(n, CPU_N)
+        u, f = make_inputs(nc)
+        for _ in range(min(args.warmup, 1)):
+            oracle_rhs_sample(u, f, nc)
+        times = [oracle_rhs_sample(u, f, nc) for _ in range(args.steps)]
+        t = statistics.median(times)
+        value = nc ** 3 / t / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(4 * t * 1e3, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{n}^3 forced HD, IF-RK4, nu=2e-3, dt=1e-3 (FP64 numpy oracle)",
+                           "n": n},
+                "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "each step: " + cpu_sample_desc(nc, n, t)
+                                           + "; ms_per_step = 4 RHS at that size"},
+                "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    res, u, f = run_ours(args, world, rank, local)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        nc = min(n, CPU_N)
+        uc, fc = (u, f) if nc == n else make_inputs(nc)
+        t = min(oracle_rhs_sample(uc, fc, nc) for _ in range(2))
+        cpu = {"value": round(nc ** 3 / t / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "best of two: " + cpu_sample_desc(nc, n, t)}
+    ms = res["ms_step"]
+    value = world * 4 * n ** 3 / (ms * 1e-3) / 1e9
+    frac = res["achieved"] / res["hbm"]
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 forced HD: seeded E(K)~K^4 exp(-2(K/4)^2) field (E=0.5), forcing on "
+                               f"2<=|k|<=3, nu=2e-3, dt=1e-3, IF-RK4, cubic 2/3 dealias, FP32 bulk + FP64 "
+                               f"reductions; step = one RK4 step = 4 RHS", "n": n, "rk_order": 4,
+                   "l2": f"inputs larger than L2 (state {3 * n * n * (n // 2 + 1) * 8 / 1e9:.2f} GB, "
+                         f"129 MB L2), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": res["dom"], "achieved": round(res["achieved"], 1),
+                     "peak": res["hbm"], "unit": "GB/s", "frac": round(frac, 4),
+                     "peak_source": f"{res['peak_src']} (MEASURED_PEAKS.json hbm_gbs)" if res["peak_src"] == "measured"
+                     else "fallback 6800 GB/s",
+                     "traffic": res["traffic"], "algorithmic_bytes": res["alg"][res["dom"]],
+                     "avg_launch_ms": round(res["avg_ms"], 4),
+                     "kernel_share": res["kernel_share"], "kernel_alg_gbs": res["kernel_gbs"],
+                     "step_alg_bytes": res["step_bytes"],
+                     "step_frac": round(res["step_bytes"] / (ms * 1e-3) / 1e9 / res["hbm"], 4)},
+        "cpu_baseline": cpu,
+        "e2e": res["e2e"],
+        "fp64": res["fp64"],
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
+        "stats": {"energy_at_last_step_start": res["energy"], "max_u": res["max_u"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
