@@ -170,6 +170,29 @@ ps_status ps_plan_launch_count(ps_plan* plan, long long* launches);
 /* Name of a kernel kind of ps_timing (0..PS_NKINDS-1), or "?". */
 const char* ps_kind_name(int kind);
 
+/* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
+#define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* Right-hand side like ps_rhs, but without a plan and without allocating any
+ * memory, for callers that cannot allocate: a program that has handed the
+ * device to its own pool allocator, a plugin or callback that must keep the
+ * memory footprint fixed, or code that cannot accept the synchronisation
+ * cudaMalloc/cudaFree may cause.  The paper has no counterpart of this call.
+ *   cfg         : as for ps_plan_create (the forcing pointer, if any, is read
+ *                 during the call)
+ *   cuda_stream : cudaStream_t the kernels run on (NULL = legacy default)
+ *   uhat, rhs_out, t : as for ps_rhs (device buffers, must not overlap)
+ * Scratch: one file-scope __device__ array of PS_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library holds until exit (enough for a 64^3 grid in
+ * FP32 or FP64, with forcing).  A grid needing more returns
+ * PS_ERR_INVALID_ARG, with the sizes in ps_last_error(), before any launch.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each overwrites it, nothing in
+ * it needs to start at zero, and calls whose kernels overlap on the GPU race
+ * on it: serialise them (one stream, or events).  Asynchronous. */
+ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, const void* uhat, void* rhs_out, double t);
+
 const char* ps_status_string(ps_status s);
 const char* ps_last_error(void);
 

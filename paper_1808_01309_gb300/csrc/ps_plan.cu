@@ -109,6 +109,11 @@ struct TimedLaunch {
 
 }  // namespace
 
+namespace ps {
+// Lets other translation units of the library report through ps_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ps
+
 struct ps_plan {
   ps_config cfg{};
   cudaStream_t stream = nullptr;

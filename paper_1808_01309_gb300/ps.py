@@ -48,8 +48,9 @@ SYMBOLS = (
     "ps_plan_create", "ps_plan_destroy", "ps_plan_workspace_bytes", "ps_rhs", "ps_rk_step",
     "ps_rk_step_host", "ps_step_stats", "ps_diagnostics", "ps_plan_set_timing",
     "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
-    "ps_last_error",
+    "ps_last_error", "ps_rhs_noalloc",
 )
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class PsConfig(ctypes.Structure):
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.ps_plan_get_timing.argtypes = [P, ctypes.POINTER(PsTiming)]
     lib.ps_plan_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.ps_rhs_noalloc.argtypes = [ctypes.POINTER(PsConfig), P, P, P, ctypes.c_double]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -164,6 +166,11 @@ def ps_plan_workspace_bytes(cfg: PsConfig) -> int:
 
 def ps_rhs(plan, uhat, rhs_out, t: float = 0.0) -> None:
     _check(load().ps_rhs(plan, _ptr(uhat), _ptr(rhs_out), float(t)))
+
+
+def ps_rhs_noalloc(cfg: PsConfig, uhat, rhs_out, t: float = 0.0, stream=None) -> None:
+    """Right-hand side without a plan and without allocating (static scratch)."""
+    _check(load().ps_rhs_noalloc(ctypes.byref(cfg), _stream_handle(stream), _ptr(uhat), _ptr(rhs_out), float(t)))
 
 
 def ps_rk_step(plan, uhat, dt: float, t: float = 0.0) -> None:
