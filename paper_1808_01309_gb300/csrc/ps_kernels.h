@@ -57,6 +57,7 @@ struct PassArgs {
   const void* fbox;  // forcing box [3][2Fz+1][2Fy+1][Fx+1] or null
   int Fx, Fy, Fz;
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
+  int* err;          // device error word (bounded waits that gave up), never null
 };
 
 // Launchers (one per pass and precision); return the launch error.

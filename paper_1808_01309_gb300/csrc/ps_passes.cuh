@@ -19,6 +19,7 @@
 // transformed where the input is known to vanish elsewhere (pruned transforms);
 // the result is identical to full transforms of the masked field.
 #pragma once
+#include "ps_async.cuh"
 #include "ps_fft.cuh"
 #include "ps_kernels.h"
 
@@ -39,6 +40,20 @@ template <typename T, int N> struct ColThreads {
 template <typename T, int N> struct RPCOf {
   static constexpr int G = N / EOf<T, N>::v;
   static constexpr int v = G >= 256 ? 1 : 256 / G;
+};
+
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef PS_MINB_ZINV
+#define PS_MINB_ZINV 2
+#endif
+#ifndef PS_MINB_XPASS
+#define PS_MINB_XPASS 2
+#endif
+#ifndef PS_MINB_ZFWD
+#define PS_MINB_ZFWD 2
+#endif
+template <typename T, int N> struct MinB {
+  static constexpr int zinv = PS_MINB_ZINV, xpass = PS_MINB_XPASS, zfwd = PS_MINB_ZFWD;
 };
 
 __device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -90,7 +105,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // ky rows; thread (line, j0, bb) holds kz indices n = j0 + m N/E.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N>::v) k_zinv(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -196,93 +211,150 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yinv(const PassArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// xpass: per physical (z, y) row.  Thread j0 of the row's group holds the
-// points n = j0 + m N/E.
+// xpass: per physical (z, y) row.  Persistent CTAs loop over groups of rpc
+// consecutive rows; the six input rows of the next group are brought into a
+// second shared-memory stage by TMA bulk copies while the current group is
+// transformed.  Thread j0 of a row's group of G threads holds the points
+// n = j0 + m N/E.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v)) k_xpass(const PassArgs a) {
+__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N>::xpass)
+    k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, RPC = RPCOf<T, N>::v;
+  constexpr int E = EOf<T, N>::v, G = N / E;
   constexpr int PSH = ilog2<Sched<N, E>::R0>::v;
   constexpr int LEN = N + (N >> PSH);
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
-  V* sm = reinterpret_cast<V*>(smraw);
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int abort_flag;
   const Geo& g = a.g;
+  const int kxp = g.kxp;
   const int tid = threadIdx.x;
   const int j0 = tid % G, rl = tid / G;
   const long long rows = (long long)g.nz * g.ny;
-  const long long row = (long long)blockIdx.x * RPC + rl;
-  const bool rvalid = row < rows;
-  const long long rrow = rvalid ? row : 0;
-  RowExchange<V, PSH> ex{sm + rl * LEN, RPC * LEN, 0};
+  const long long ngroups = (rows + rpc - 1) / rpc;
+  const int stage_elems = 6 * rpc * kxp;
+  V* stage = reinterpret_cast<V*>(smraw);
+  V* exbuf = stage + 2 * stage_elems;
+  RowExchange<V, PSH> ex{exbuf + rl * LEN, rpc * LEN, 0};
   const V* tw = static_cast<const V*>(a.tw_x);
   const V* B = static_cast<const V*>(a.b6);
-  V U[3][E];
+  V* C = static_cast<V*>(a.a6);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // stage s <- the six input fields of row group grp (rpc contiguous rows each)
+  auto issue = [&](long long grp, int s) {
+    const long long r0 = grp * rpc;
+    const long long nr = rows - r0 < rpc ? rows - r0 : rpc;
+    const uint32_t bytes = (uint32_t)(nr * kxp * sizeof(V));
+    mbar_arrive_expect_tx(&bar[s], 6u * bytes);
+    for (int c = 0; c < 6; ++c)
+      bulk_g2s(stage + s * stage_elems + c * rpc * kxp, B + ((long long)c * rows + r0) * kxp, bytes, &bar[s]);
+  };
+  uint32_t ph0 = 0u, ph1 = 0u;  // completed-phase parity of each stage barrier
+  long long it = blockIdx.x;
+  int s = 0;
+  if (tid == 0 && it < ngroups) issue(it, 0);
+  T umax2 = 0;
+  while (it < ngroups) {
+    const long long nxt = it + gridDim.x;
+    if (tid == 0 && nxt < ngroups) {
+      fence_proxy_async();
+      issue(nxt, s ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[s], s ? ph1 : ph0);
+    if (s) ph1 ^= 1u; else ph0 ^= 1u;
+    if (!ok) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      if (tid == 0) {
+        atomicExch(a.err, PS_DEV_TIMEOUT_XPASS);
+        if (nxt < ngroups) mbar_wait(&bar[s ^ 1], s ? ph0 : ph1);  // let the prefetch land
+      }
+      break;
+    }
+    const long long row = it * rpc + rl;
+    const bool rvalid = row < rows;
+    const V* st = stage + s * stage_elems + rl * kxp;
+    V U[3][E];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const V* pu = B + ((long long)c * rows + rrow) * g.kxp;
-    const V* pw = B + ((long long)(c + 3) * rows + rrow) * g.kxp;
+    for (int c = 0; c < 3; ++c) {
+      const V* pu = st + c * rpc * kxp;
+      const V* pw = st + (c + 3) * rpc * kxp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int n = j0 + m * (N / E);
+        // full spectrum C[n] = u_hat[n] + i w_hat[n]; for n > N/2 the entries
+        // are conj(u_hat[N-n]) + i conj(w_hat[N-n]) (real u and w)
+        const bool hi = n > N / 2;
+        const int p = hi ? N - n : n;
+        V v = czero<V>();
+        if (rvalid && p <= g.Kx) {
+          V X = pu[p], W = pw[p];
+          if (hi) {
+            X = cconj(X);
+            W = cconj(W);
+          }
+          v = mk<V>(X.x - W.y, X.y + W.x);
+        }
+        U[c][m] = v;
+      }
+      line_fft<N, E, +1>(U[c], j0, tw, ex);
+    }
+    // n = u x omega at the thread's points; u_c = Re U[c], omega_c = Im U[c]
+    V F1[E], F2[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const int n = j0 + m * (N / E);
-      // full spectrum C[n] = u_hat[n] + i w_hat[n]; for n > N/2 the entries
-      // are conj(u_hat[N-n]) + i conj(w_hat[N-n]) (real u and w)
-      const bool hi = n > N / 2;
-      const int p = hi ? N - n : n;
-      V v = czero<V>();
-      if (rvalid && p <= g.Kx) {
-        V X = ldv(pu + p), W = ldv(pw + p);
-        if (hi) { X = cconj(X); W = cconj(W); }
-        v = mk<V>(X.x - W.y, X.y + W.x);
-      }
-      U[c][m] = v;
+      const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
+      const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
+      umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
+      F1[m] = mk<V>(uy * wz - uz * wy, uz * wx - ux * wz);
+      F2[m] = mk<V>(ux * wy - uy * wx, T(0));
     }
-    line_fft<N, E, +1>(U[c], j0, tw, ex);
-  }
-  // n = u x omega at the thread's points; u_c = Re U[c], omega_c = Im U[c]
-  T umax2 = 0;
-  V F1[E], F2[E];
+    if (!a.xdiag) {  // uniform across the grid
+      line_fft<N, E, -1>(F1, j0, tw, ex);
+      line_fft<N, E, -1>(F2, j0, tw, ex);
+      const long long rrow = rvalid ? row : 0;
+      V* cx = C + (0 * rows + rrow) * kxp;
+      V* cy = C + (1 * rows + rrow) * kxp;
+      V* cz = C + (2 * rows + rrow) * kxp;
+      // split F1 = DFT(n_x) + i DFT(n_y) using the mirrored entry F1[N-k]
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
-    const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
-    umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
-    F1[m] = mk<V>(uy * wz - uz * wy, uz * wx - ux * wz);
-    F2[m] = mk<V>(ux * wy - uy * wx, T(0));
+      for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F1[m]);
+      ex.sync();
+      const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = j0 + m * (N / E);
+        if (rvalid && k < kend) {
+          V nx = czero<V>(), ny = czero<V>(), nz = czero<V>();
+          if (k <= g.Kx) {
+            const V Fk = F1[m];
+            const V Fm = cconj(ex.get((N - k) & (N - 1)));
+            nx = cscale(cadd(Fk, Fm), T(0.5));
+            ny = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
+            nz = F2[m];
+          }
+          cx[k] = nx;
+          cy[k] = ny;
+          cz[k] = nz;
+        }
+      }
+      ex.flip();
+    }
+    __syncthreads();  // stage s and the exchange buffers are free again
+    s ^= 1;
+    it = nxt;
   }
   if (a.umax2) {
-    const double t = block_max(rvalid ? (double)umax2 : 0.0, red);
+    const double t = block_max((double)umax2, red);
     if (threadIdx.x == 0) atomicMax(a.umax2, (unsigned long long)__double_as_longlong(t));
-  }
-  if (a.xdiag) return;  // uniform across the grid
-  line_fft<N, E, -1>(F1, j0, tw, ex);
-  line_fft<N, E, -1>(F2, j0, tw, ex);
-  V* C = static_cast<V*>(a.a6);
-  V* cx = C + (0 * rows + rrow) * g.kxp;
-  V* cy = C + (1 * rows + rrow) * g.kxp;
-  V* cz = C + (2 * rows + rrow) * g.kxp;
-  // split F1 = DFT(n_x) + i DFT(n_y) using the mirrored entry F1[N-k]
-#pragma unroll
-  for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F1[m]);
-  ex.sync();
-  const int kend = g.kxp < N / 2 + 1 ? g.kxp : N / 2 + 1;
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int k = j0 + m * (N / E);
-    if (rvalid && k < kend) {
-      V nx = czero<V>(), ny = czero<V>(), nz = czero<V>();
-      if (k <= g.Kx) {
-        const V Fk = F1[m];
-        const V Fm = cconj(ex.get((N - k) & (N - 1)));
-        nx = cscale(cadd(Fk, Fm), T(0.5));
-        ny = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
-        nz = F2[m];
-      }
-      cx[k] = nx;
-      cy[k] = ny;
-      cz[k] = nz;
-    }
   }
 }
 
@@ -326,7 +398,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) 
 // compact stage buffers are written.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N>::v) k_zfwd(const PassArgs a, const int full) {
+__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a, const int full) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -504,19 +576,37 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
   k_yinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
+// Shared memory of the x pass for rpc rows: two input stages of 6 rows each
+// and the double-buffered exchange.
+template <typename T, int N>
+size_t xpass_smem(const Geo& g, int rpc) {
+  using V = typename cplx<T>::type;
+  constexpr int LEN = N + (N >> ilog2<Sched<N, EOf<T, N>::v>::R0>::v);
+  return (2ull * 6 * rpc * g.kxp + 2ull * rpc * LEN) * sizeof(V);
+}
+
 template <typename T, int N>
 cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
-  using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, RPC = RPCOf<T, N>::v;
-  constexpr int LEN = N + (N >> ilog2<Sched<N, E>::R0>::v);
-  const size_t smem = 2ull * RPC * LEN * sizeof(V);
-  cudaError_t e = prep(k_xpass<T, N>, smem);
+  constexpr int E = EOf<T, N>::v, G = N / E;
+  // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
+  int rpc = RPCOf<T, N>::v;
+  while (rpc > 1 && xpass_smem<T, N>(a.g, rpc) > 113 * 1024) rpc /= 2;
+  const size_t smem = xpass_smem<T, N>(a.g, rpc);
+  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, N>, rpc * G, smem)) != cudaSuccess)
+    return e;
   const long long rows = (long long)a.g.nz * a.g.ny;
-  dim3 grid((unsigned)((rows + RPC - 1) / RPC));
-  k_xpass<T, N><<<grid, RPC * G, smem, s>>>(a);
+  const long long groups = (rows + rpc - 1) / rpc;
+  long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
+  if (grid > groups) grid = groups;
+  k_xpass<T, N><<<(unsigned)grid, rpc * G, smem, s>>>(a, rpc);
   return cudaGetLastError();
 }
+
 template <typename T, int N>
 cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   using V = typename cplx<T>::type;

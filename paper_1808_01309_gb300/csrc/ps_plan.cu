@@ -134,6 +134,7 @@ struct ps_plan {
   double* stats = nullptr;                 // [energy]
   unsigned long long* umax2 = nullptr;     // max |u|^2 bits
   int* ext = nullptr;
+  int* err = nullptr;                      // device error word of bounded waits
   int nshells = 0;
   double* dpart = nullptr;                 // diagnostics partials
   double* dout = nullptr;                  // diagnostics result (device)
@@ -248,7 +249,17 @@ PassArgs base_args(ps_plan* p) {
   a.ifz = static_cast<char*>(p->iftab) + tb * (p->g.cx + p->g.cy);
   a.nxt = p->nxt;
   a.acc = p->acc;
+  a.err = p->err;
   return a;
+}
+
+// Reads the device error word (after a stream synchronisation).
+ps_status check_device_error(ps_plan* p) {
+  int e = 0;
+  PS_CU(cudaMemcpyAsync(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream), "error word");
+  PS_CU(cudaStreamSynchronize(p->stream), "error word");
+  if (e != 0) return fail(PS_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy never completed)");
+  return PS_OK;
 }
 
 template <typename T>
@@ -389,7 +400,7 @@ ps_status setup_forcing(ps_plan* p) {
 
 void release(ps_plan* p) {
   void* bufs[] = {p->a6, p->b6, p->nxt, p->acc, p->tw, p->iftab, p->fbox, p->e_part, p->stats,
-                  p->umax2, p->ext, p->dpart, p->dout, p->hstate};
+                  p->umax2, p->ext, p->err, p->dpart, p->dout, p->hstate};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& t : p->tl) {
@@ -475,6 +486,7 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   ALLOC(p->stats, sizeof(double) * 4, "stats");
   ALLOC(p->umax2, sizeof(unsigned long long), "max|u|");
   ALLOC(p->ext, sizeof(int) * 4, "forcing extent");
+  ALLOC(p->err, sizeof(int), "error word");
   ALLOC(p->dpart, sizeof(double) * (size_t)p->g.cz * (4 + p->nshells), "diagnostic partials");
   ALLOC(p->dout, sizeof(double) * (size_t)(4 + p->nshells), "diagnostics");
 #undef ALLOC
@@ -485,6 +497,7 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   if (e == cudaSuccess) e = cudaMemsetAsync(p->acc, 0, p->sz.cmp * vb, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->stats, 0, sizeof(double) * 4, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) return bail(cuda_fail(e, "scratch clear"));
   s = cfg->prec == PS_FP32 ? upload_twiddles<float2>(p) : upload_twiddles<double2>(p);
   if (s != PS_OK) return bail(s);
@@ -539,7 +552,7 @@ ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int 
   }
   PS_CU(cudaMemcpyAsync(uhat_host, p->hstate, bytes, cudaMemcpyDeviceToHost, p->stream), "state download");
   PS_CU(cudaStreamSynchronize(p->stream), "host-path sync");
-  return PS_OK;
+  return check_device_error(p);
 }
 
 ps_status ps_step_stats(ps_plan* p, double* energy, double* max_u) {
@@ -554,7 +567,7 @@ ps_status ps_step_stats(ps_plan* p, double* energy, double* max_u) {
   std::memcpy(&m2, &bits, sizeof(m2));
   if (energy) *energy = e;
   if (max_u) *max_u = std::sqrt(m2);
-  return PS_OK;
+  return check_device_error(p);
 }
 
 ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out) {
@@ -565,6 +578,7 @@ ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out)
   std::vector<double> h(5 + p->nshells);
   ps_status s = p->cfg.prec == PS_FP32 ? do_diag<float>(p, uhat, h.data()) : do_diag<double>(p, uhat, h.data());
   if (s != PS_OK) return s;
+  if ((s = check_device_error(p)) != PS_OK) return s;
   out->energy = h[0];
   out->enstrophy = h[1];
   out->helicity = h[2];

@@ -120,7 +120,8 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   const size_t b_b = up256((b1 > b2 ? b1 : b2) * vb);
   const size_t tw_b = up256((size_t)(g.nx + g.ny + g.nz) * vb);
   const size_t box_b = c->forcing ? up256(3ull * g.cz * g.cy * g.cx * vb) : 0;
-  const size_t need = a_b + b_b + tw_b + box_b;
+  const size_t err_b = 256;  // error word of bounded device waits (written, never read here)
+  const size_t need = a_b + b_b + tw_b + box_b + err_b;
   if (need > (size_t)PS_NOALLOC_SCRATCH_BYTES) {
     char msg[256];
     std::snprintf(msg, sizeof msg,
@@ -143,6 +144,7 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   a.tw_y = tw + g.nx;
   a.tw_z = tw + g.nx + g.ny;
   a.nu = c->nu;
+  a.err = reinterpret_cast<int*>(p + a_b + b_b + tw_b + box_b);
   a.Fx = a.Fy = a.Fz = -1;
   Spec in;
   in.p = uhat;
