@@ -42,6 +42,34 @@ template <typename V> __device__ __forceinline__ V czero() { return mk<V>(0, 0);
 template <typename V> __device__ __forceinline__ V cmul_i(V a) { return mk<V>(-a.y, a.x); }
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mk<V>(a.y, -a.x); }
 
+// FP32 complex add, subtract and real scaling as packed two-lane FP32
+// instructions (add/sub/mul.rn.f32x2 of sm_100 and later): one instruction per
+// complex operation instead of two.
+#ifndef PS_F32X2
+#define PS_F32X2 1
+#endif
+#if PS_F32X2
+union F2U {
+  float2 f;
+  unsigned long long u;
+};
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  F2U x{a}, y{b}, r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+  return r.f;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  F2U x{a}, y{b}, r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+  return r.f;
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+  F2U x{a}, y{make_float2(s, s)}, r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+  return r.f;
+}
+#endif
+
 // Multiply by exp(DIR * 2 pi i * s/16) for a compile-time s in [0, 8).
 // cos(pi/8), sin(pi/8) and sqrt(1/2) are the exact mathematical constants,
 // rounded by the compiler to the working precision.
@@ -167,13 +195,13 @@ __device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ t
       for (int r = 0; r < R; ++r) a[b + r * NB] = x[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) ex.put((j - k) * R + k + r * NS, x[r]);
+      for (int r = 0; r < R; ++r) ex.template put<NS, R>((j - k) * R + k + r * NS, x[r]);
     }
   }
   if constexpr (!LAST) {
     ex.sync();
 #pragma unroll
-    for (int m = 0; m < E; ++m) a[m] = ex.get(j0 + m * (N / E));
+    for (int m = 0; m < E; ++m) a[m] = ex.template get<NS, R>(j0 + m * (N / E));
     ex.flip();
   }
 }
@@ -200,12 +228,13 @@ __device__ __forceinline__ void line_fft(V (&a)[E], int j0, const V* __restrict_
 }
 
 // Shared-memory exchange for lines laid out as columns: element n of line l
-// at buf[row(n) * LP + l], two buffers used alternately so that one barrier per
-// exchange suffices (a buffer is rewritten only after the barrier of the
-// following exchange, which every thread passes after finishing its reads).
-// row(n) flips the lowest bit when bit SW of n is set: the first exchange
-// writes rows R1 apart, and this keeps them on alternate bank halves.
-template <typename V, int SW>
+// at buf[row(n) * LP + l].  With NBUF = 2 two buffers are used alternately so
+// that one barrier per exchange suffices (a buffer is rewritten only after the
+// barrier of the following exchange, which every thread passes after finishing
+// its reads); with NBUF = 1 a second barrier after the reads frees the single
+// buffer.  row(n) flips the lowest bit when bit SW of n is set: the first
+// exchange writes rows R1 apart, and this keeps them on alternate bank halves.
+template <typename V, int SW, int NBUF = 2>
 struct ColumnExchange {
   V* buf;
   int bufsz;
@@ -213,23 +242,48 @@ struct ColumnExchange {
   int l;
   int par;
   __device__ __forceinline__ int row(int n) const { return n ^ ((n >> SW) & 1); }
+  template <int NS = 0, int R = 0>
   __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + row(n) * lp + l] = v; }
+  template <int NS = 0, int R = 0>
   __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + row(n) * lp + l]; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
-  __device__ __forceinline__ void flip() { par ^= 1; }
+  __device__ __forceinline__ void flip() {
+    if constexpr (NBUF == 2) par ^= 1;
+    else __syncthreads();
+  }
 };
 
-// Shared-memory exchange for a line stored as a row: element n at
-// buf[n + (n >> PS)] (one pad slot every 2^PS elements breaks the stride-R
-// bank pattern of the first exchange).
-template <typename V, int PS>
+// Shared-memory exchange for a line stored as a row of N 8- or 16-byte
+// elements.  Element n of the exchange written by a stage with previous radix
+// product NS and radix R sits at pos<NS, R>(n) = n XOR swz(n): the swizzle only
+// permutes the lowest four bits (one 16-slot window), so the contiguous reads
+// of the next stage stay conflict-free, while the strided writes
+// (j - k) R + k + r NS of consecutive butterflies j spread over all 16 bank
+// pairs:
+//   NS = 1       : writes R apart  -> mix bits 4..7 into bits 0..3
+//   1 < NS < 16  : writes in runs of NS, runs NS R apart -> mix the run index
+//                  into the bits above log2(NS)
+//   NS >= 16 or 0: runs of >= 16 consecutive slots, identity (0 = natural order)
+template <typename V, int PS_UNUSED = 0>
 struct RowExchange {
   V* buf;
   int bufsz;
   int par;
-  __device__ __forceinline__ int pos(int n) const { return n + (n >> PS); }
-  __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + pos(n)] = v; }
-  __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + pos(n)]; }
+  template <int NS, int R>
+  __device__ __forceinline__ static int pos(int n) {
+    if constexpr (NS == 1) {
+      return n ^ ((n >> 4) & 15);
+    } else if constexpr (NS > 1 && NS < 16) {
+      constexpr int LNS = ilog2<NS>::v, LRUN = ilog2<NS * R>::v;
+      return n ^ (((n >> LRUN) & (16 / NS - 1)) << LNS);
+    } else {
+      return n;
+    }
+  }
+  template <int NS = 0, int R = 0>
+  __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + pos<NS, R>(n)] = v; }
+  template <int NS = 0, int R = 0>
+  __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + pos<NS, R>(n)]; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ void flip() { par ^= 1; }
 };

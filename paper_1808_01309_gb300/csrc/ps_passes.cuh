@@ -102,30 +102,54 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // ---------------------------------------------------------------------------
 // zinv: curl + backward transform along z.  CTA = TX kx columns x NB retained
-// ky rows; thread (line, j0, bb) holds kz indices n = j0 + m N/E.
+// ky rows.  The CTA first copies its three input columns (retained kz rows
+// only) into shared memory with cp.async, so that all its HBM reads are in
+// flight at once; the six transforms then read the tile from shared memory.
+// Thread (line, j0, bb) holds kz indices n = j0 + m N/E.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int NTH = ColThreads<T, N>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
+  V* xbuf = reinterpret_cast<V*>(smraw);     // exchange: NB lines x N x TX (single buffer)
+  V* tile = xbuf + NB * N * TX;              // input: [3][NB][cz][TX]
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
   const int iy = blockIdx.y * NB + bb;
   const bool bvalid = iy < g.cy;
   const int kx = blockIdx.x * TX + line;
   const int q = iy <= g.Ky ? iy : iy - g.cy;
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* in = static_cast<const V*>(a.in.p);
+  // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i)
+  {
+    const int per_c = NB * g.cz * TX;
+    for (int e = tid; e < 3 * per_c; e += NTH) {
+      const int col = e % TX, i = (e / TX) % g.cz, b = (e / (TX * g.cz)) % NB, c = e / per_c;
+      const int iyb = blockIdx.y * NB + b, kxc = blockIdx.x * TX + col;
+      if (iyb >= g.cy || kxc > g.Kx) continue;
+      const int qb = iyb <= g.Ky ? iyb : iyb - g.cy;
+      const int r = i <= g.Kz ? i : i - g.cz;
+      const V* src = in + c * a.in.cs + (long long)rowof(r, a.in.zwrap) * a.in.zs +
+                     (long long)rowof(qb, a.in.ywrap) * a.in.ys + kxc;
+      if constexpr (sizeof(V) == 8) cp_async8(tile + e, src);
+      else cp_async16(tile + e, src);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
   const V* tw = static_cast<const V*>(a.tw_z);
   V* out = static_cast<V*>(a.a6);
-  const long long ybase = (long long)rowof(q, a.in.ywrap) * a.in.ys + kx;
   const T skx = T(kx) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
   const long long fstride = (long long)g.nz * g.cy * g.kxp;
   const long long zstride = (long long)g.cy * g.kxp;
+  const int cst = NB * g.cz * TX;                 // component stride in the tile
+  const V* tb = tile + bb * g.cz * TX + line;     // this thread's column
   double esum = 0.0;
 #pragma unroll 1
   for (int f = 0; f < 6; ++f) {
@@ -137,21 +161,21 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
       const int r = sidx(n, N);
       V v = czero<V>();
       if (bvalid && kept(g, kx, q, r)) {
-        const V* pm = in + ybase + (long long)rowof(r, a.in.zwrap) * a.in.zs;
+        const V* pm = tb + rowof(r, g.cz) * TX;
         if (f < 3) {
-          v = ldv(pm + f * a.in.cs);
+          v = pm[f * cst];
           ssq += v.x * v.x + v.y * v.y;
         } else {
           const T skz = T(r) * sz;
           // omega_hat = i k x u_hat
           if (f == 3) {
-            const V uy = ldv(pm + a.in.cs), uz = ldv(pm + 2 * a.in.cs);
+            const V uy = pm[cst], uz = pm[2 * cst];
             v = cmul_i(csub(cscale(uz, sky), cscale(uy, skz)));
           } else if (f == 4) {
-            const V ux = ldv(pm), uz = ldv(pm + 2 * a.in.cs);
+            const V ux = pm[0], uz = pm[2 * cst];
             v = cmul_i(csub(cscale(ux, skz), cscale(uz, skx)));
           } else {
-            const V ux = ldv(pm), uy = ldv(pm + a.in.cs);
+            const V ux = pm[0], uy = pm[cst];
             v = cmul_i(csub(cscale(uy, skx), cscale(ux, sky)));
           }
         }
@@ -222,8 +246,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
     k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E;
-  constexpr int PSH = ilog2<Sched<N, E>::R0>::v;
-  constexpr int LEN = N + (N >> PSH);
+  constexpr int LEN = N;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ __align__(8) uint64_t bar[2];
@@ -237,7 +260,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
   const int stage_elems = 6 * rpc * kxp;
   V* stage = reinterpret_cast<V*>(smraw);
   V* exbuf = stage + 2 * stage_elems;
-  RowExchange<V, PSH> ex{exbuf + rl * LEN, rpc * LEN, 0};
+  RowExchange<V> ex{exbuf + rl * LEN, rpc * LEN, 0};
   const V* tw = static_cast<const V*>(a.tw_x);
   const V* B = static_cast<const V*>(a.b6);
   V* C = static_cast<V*>(a.a6);
@@ -557,7 +580,7 @@ template <typename T, int N>
 cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  const size_t smem = (1ull * NB * N * TX + 3ull * NB * a.g.cz * TX) * sizeof(V);
   cudaError_t e = prep(k_zinv<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB);
@@ -581,8 +604,7 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
 template <typename T, int N>
 size_t xpass_smem(const Geo& g, int rpc) {
   using V = typename cplx<T>::type;
-  constexpr int LEN = N + (N >> ilog2<Sched<N, EOf<T, N>::v>::R0>::v);
-  return (2ull * 6 * rpc * g.kxp + 2ull * rpc * LEN) * sizeof(V);
+  return (2ull * 6 * rpc * g.kxp + 2ull * rpc * N) * sizeof(V);
 }
 
 template <typename T, int N>
