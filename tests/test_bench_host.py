@@ -1,0 +1,70 @@
+"""Host-side logic of bench.py, without a GPU: the max-over-ranks reduction
+over two gloo ranks, the roofline byte model and the traffic lookup."""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        v = bench.reduce_max(float(10 + 5 * rank), world)
+        bench.barrier(world)
+        q.put((rank, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 15.0, 1: 15.0}
+
+
+def test_single_rank_reduction_is_identity():
+    assert bench.reduce_max(3.5, 1) == 3.5
+
+
+def test_algorithmic_bytes_model():
+    b = bench.algorithmic_bytes(512, 8)
+    K, cx, c2 = 170, 171, 341
+    assert b["x_fused"] == 9 * 512 * 512 * cx * 8
+    assert b["z_inverse"] == (3 * c2 * c2 * cx + 6 * 512 * c2 * cx) * 8
+    # one RK4 step moves about 52.7 GB at 512^3 FP32
+    step = 4 * sum(v for k, v in b.items())
+    assert 50e9 < step < 56e9
+
+
+def test_traffic_lookup_requires_matching_sources(tmp_path, monkeypatch):
+    assert bench.ncu_traffic("x_fused", 999) is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("x_fused", 512) is None
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    c = bench.ClockSampler(0)
+    c.lines = ["1965, 2070, 900.1, Not Active, Not Active, Not Active, Active",
+               "1980, 2070, 950.0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s["sm_mhz"] == 1972.5 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]

@@ -1,0 +1,111 @@
+"""Parity at the benchmark's own sizes and launch configuration, and the
+100-step energy criterion.
+
+* 512^3 FP32 RHS of the seeded random field and forcing (the bench workload,
+  same plan configuration) against the FP64 oracle, relative L2 <= 2e-6.
+* 512^3 Taylor-Green: every mode of the RHS against the exact rational
+  tendency -P[(u.grad)u] (no oracle run needed at that size).
+* 512^3 ABC flow: the nonlinear term vanishes identically.
+* 100 IF-RK4 steps in FP32: total energy within 1e-4 of the FP64 oracle
+  (64^3, oracle run in full) and of the FP64 CUDA path (256^3, whose every
+  RHS is itself held to 1e-12 of the oracle by test_gpu_parity).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_01309_gb300 import inputs
+
+from . import exact_fourier as xf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import ps as _ps
+    return _ps
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_bench_workload_rhs_512_matches_oracle(ps):
+    n, nu = 512, 2e-3
+    u = inputs.random_solenoidal_field(n, n, n, seed=1)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    ud = torch.from_numpy(u).to("cuda", torch.complex64)
+    fd = torch.from_numpy(f).to("cuda", torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=fd)
+    out = plan.rhs(ud)
+    got = out.cpu().numpy()
+    plan.close()
+    del ud, fd, out
+    torch.cuda.empty_cache()
+    ref = oracle.rhs(u, oracle.Config(n, n, n, nu=nu), forcing=f)
+    assert relerr(got.astype(np.complex128), ref) < 2e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_taylor_green_512_matches_exact_tendency(ps, prec):
+    n = 512
+    P, dt = (ps.Precision.FP32, torch.complex64) if prec == "fp32" else (ps.Precision.FP64, torch.complex128)
+    ud = torch.from_numpy(inputs.taylor_green(n, n, n)).to("cuda", dt)
+    plan = ps.Plan(n, prec=P, nu=0.0)
+    out = plan.rhs(ud).cpu().numpy().astype(np.complex128)
+    plan.close()
+    exact = np.zeros_like(out)
+    for (p, q, r), v in xf.euler_rate(xf.trig_modes([(0, 1, ("s", 1), ("c", 1), ("c", 1)),
+                                                      (1, -1, ("c", 1), ("s", 1), ("c", 1))])).items():
+        if p >= 0:
+            exact[:, r % n, q % n, p] = [complex(c) for c in v]
+    tol = 2e-6 if prec == "fp32" else 1e-12
+    assert np.max(np.abs(out - exact)) < tol * np.max(np.abs(exact))
+
+
+def test_abc_512_nonlinear_term_vanishes(ps):
+    n = 512
+    ud = torch.from_numpy(inputs.abc_flow(n, n, n)).to("cuda", torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=0.0)
+    out = plan.rhs(ud)
+    assert float(out.abs().max()) < 2e-6
+    plan.close()
+
+
+def _energy_after(ps, n, prec, steps, dt=1e-3, nu=2e-3):
+    P, dtype = (ps.Precision.FP32, torch.complex64) if prec == "fp32" else (ps.Precision.FP64, torch.complex128)
+    u = inputs.random_solenoidal_field(n, n, n, seed=1)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    ud = torch.from_numpy(u).to("cuda", dtype)
+    plan = ps.Plan(n, prec=P, nu=nu, rk_order=4, forcing=torch.from_numpy(f).to("cuda", dtype))
+    for i in range(steps):
+        plan.rk_step(ud, dt, t=i * dt)
+    e = plan.diagnostics(ud)["energy"]
+    plan.close()
+    return e
+
+
+def test_fp32_energy_after_100_steps_matches_oracle_64(ps):
+    n, dt, nu = 64, 1e-3, 2e-3
+    u = inputs.random_solenoidal_field(n, n, n, seed=1)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    cfg = oracle.Config(n, n, n, nu=nu, rk_order=4)
+    for _ in range(100):
+        u = oracle.rk_step(u, dt, cfg, forcing=f)
+    e_ref = oracle.diagnostics(u, cfg)["energy"]
+    e32 = _energy_after(ps, n, "fp32", 100, dt, nu)
+    assert abs(e32 - e_ref) <= 1e-4 * e_ref
+
+
+def test_fp32_energy_after_100_steps_256(ps):
+    e32 = _energy_after(ps, 256, "fp32", 100)
+    e64 = _energy_after(ps, 256, "fp64", 100)
+    assert abs(e32 - e64) <= 1e-4 * e64
+    assert math.isfinite(e32) and 0.3 < e32 < 0.7
