@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
 
@@ -310,7 +312,12 @@ def run_ours(args, world, rank, local):
         del ud, fd
         torch.cuda.empty_cache()
 
-    out.update(ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
+    ens = None
+    if not args.no_ensemble:
+        ens = run_ensemble(args, dev, stream)
+        torch.cuda.empty_cache()
+
+    out.update(ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
                achieved=achieved, hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
                kernel_gbs=kernel_gbs, step_bytes=step_bytes, e2e=e2e, fp64=fp64, energy=e_step,
                max_u=umax_step, alg=alg)
@@ -318,6 +325,48 @@ def run_ours(args, world, rank, local):
 
 
 CPU_N = 256  # the oracle's sample grid: one 256^3 RHS takes ~7 s, a 512^3 one ~1 min
+
+
+ENSEMBLE_SIZES = [64] * 16 + [96] * 16 + [128] * 16
+
+
+def run_ensemble(args, dev, stream):
+    """48 independent unforced solves (16 each at 64^3, 96^3, 128^3), seeds
+    1000+i, nu_i = 1e-3 + 4e-3 U(seed 2000+i), FP32, IF-RK4, dt = 1e-3:
+    member-by-member launches vs one CUDA graph of all steps (autotuned)."""
+    import torch
+    from paper_1808_01309_gb300 import inputs, ps
+    cfgs, host = [], []
+    for i, n in enumerate(ENSEMBLE_SIZES):
+        cfgs.append(ps.make_config(n, prec=ps.Precision.FP32, nu=inputs.ensemble_viscosity(i), rk_order=4))
+        host.append(torch.from_numpy(inputs.random_solenoidal_field(n, n, n, seed=1000 + i)).to(dev, torch.complex64))
+    ens = ps.ps_ensemble_create(cfgs, stream)
+    K, dt = args.ensemble_steps, 1e-3
+    points = 4 * sum(n ** 3 for n in ENSEMBLE_SIZES) * K
+    t0 = time.perf_counter()
+    tuning = ps.ps_ensemble_tune(ens, host, dt)
+    tune_s = time.perf_counter() - t0
+    out = {"members": len(cfgs), "sizes": "16x64^3 + 16x96^3 + 16x128^3", "steps": K, "prec": "fp32",
+           "tuning": tuning, "tune_s": round(tune_s, 2)}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for mode, name in ((ps.ENS_SEQUENTIAL, "sequential"), (ps.ENS_GRAPH, "graph")):
+        states = [h.clone() for h in host]
+        # warm-up (for the graph: captures and instantiates the K-step graph)
+        t1 = time.perf_counter()
+        ps.ps_ensemble_rk_steps(ens, states, dt, 0.0, K, mode)
+        torch.cuda.synchronize()
+        first = time.perf_counter() - t1
+        e0.record(stream)
+        ps.ps_ensemble_rk_steps(ens, states, dt, 0.0, K, mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": round(ms, 3), "ms_per_step": round(ms / K, 4),
+                     "gpoints_s": round(points / (ms * 1e-3) / 1e9, 3), "first_call_s": round(first, 3)}
+    out["graph_speedup"] = round(out["sequential"]["ms"] / out["graph"]["ms"], 3)
+    ps.ps_ensemble_destroy(ens)
+    return out
 
 
 def oracle_rhs_sample(u, f, n):
@@ -404,6 +453,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": res["e2e"],
         "fp64": res["fp64"],
+        "ensemble": res["ens"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "stats": {"energy_at_last_step_start": res["energy"], "max_u": res["max_u"]},

@@ -75,7 +75,7 @@ typedef enum { PS_DEALIAS_CUBIC = 0, PS_DEALIAS_SPHERICAL = 1, PS_DEALIAS_NONE =
 typedef struct ps_plan ps_plan;
 
 /* One solve (Sec. 2: grid and box may differ per axis).
- *   nx, ny, nz : powers of two in [8, 1024]
+ *   nx, ny, nz : powers of two in [8, 1024], or 48, 96, 192 (radix-3 lines)
  *   lx, ly, lz : box lengths, finite and > 0
  *   prec       : arithmetic and storage precision of all fields
  *   eq         : PS_HD (PS_MHD returns PS_ERR_UNSUPPORTED)
@@ -169,6 +169,52 @@ ps_status ps_plan_launch_count(ps_plan* plan, long long* launches);
 
 /* Name of a kernel kind of ps_timing (0..PS_NKINDS-1), or "?". */
 const char* ps_kind_name(int kind);
+
+/* ---- Ensembles of independent solves ------------------------------------
+ * Many independent solves of possibly different sizes and viscosities, each
+ * with its own state, stepped together.  The paper's solver runs one field per
+ * MPI task; this is the single-GPU way to keep a GB300 busy with many small
+ * problems.  One plan per member; no data is shared between members. */
+typedef struct ps_ensemble ps_ensemble;
+#define PS_ENS_MAX_MEMBERS 1024
+#define PS_ENS_MAX_SIZES 8
+
+/* PS_ENS_SEQUENTIAL: member after member, every kernel launched separately on
+ * the ensemble stream.  PS_ENS_GRAPH: all nsteps steps of all members as one
+ * CUDA graph launch; each member's launch chain is a branch, branches run
+ * concurrently (number of branches chosen by ps_ensemble_tune, default
+ * min(members, 16)).  The graph is captured on the first call with a given
+ * (states, dt, t, nsteps) and replayed by later identical calls. */
+typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1 } ps_ens_mode;
+
+/* Result of ps_ensemble_tune: concurrent branches, and per distinct grid
+ * (first nsizes entries, n = nx of the grid) the x-pass rows per CTA chosen
+ * (0 = the automatic maximum); step_ms = graph time of one step of all
+ * members with the chosen shapes. */
+typedef struct {
+  int branches;
+  int nsizes;
+  int n[PS_ENS_MAX_SIZES];
+  int xrpc[PS_ENS_MAX_SIZES];
+  double step_ms;
+} ps_ens_tuning;
+
+/* Create count (1..PS_ENS_MAX_MEMBERS) member plans from cfgs[i] (each as for
+ * ps_plan_create) on the current device; cuda_stream is the ensemble stream. */
+ps_status ps_ensemble_create(const ps_config* cfgs, int count, void* cuda_stream, ps_ensemble** out);
+ps_status ps_ensemble_destroy(ps_ensemble* e);
+
+/* nsteps IF-RK steps of every member, in place on uhats[i] (device state of
+ * member i, layout of its config), starting at time t.  Asynchronous on the
+ * ensemble stream.  Results are identical in both modes. */
+ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, double t, int nsteps,
+                               ps_ens_mode mode);
+
+/* Autotuner: times, on device copies of uhats (left unchanged), the x-pass
+ * rows per CTA for each distinct grid and the number of concurrent graph
+ * branches, keeps the fastest and reports them.  Allocates temporary copies
+ * of the states.  Synchronises the ensemble stream. */
+ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
 
 /* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
 #define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -15,7 +15,7 @@ int zinv_blocks<float>(const Geo& g) {
   int nb = 0;
   switch (g.nz) {
 #define CASE(N) case N: nb = NBOf<float, N>::v; break;
-    CASE(8) CASE(16) CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024)
+    CASE(8) CASE(16) CASE(32) CASE(48) CASE(64) CASE(96) CASE(128) CASE(192) CASE(256) CASE(512) CASE(1024)
 #undef CASE
     default: return 0;
   }

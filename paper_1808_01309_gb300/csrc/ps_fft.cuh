@@ -105,10 +105,11 @@ __host__ __device__ constexpr int bitrev(int x, int bits) {
   return r;
 }
 
-// In-register DFT of size R in {2,4,8,16}: radix-2 decimation in time over a
-// bit-reversed copy; all indices are compile-time after unrolling.
+// In-register DFT of a power-of-two size R in {2,4,8,16}: radix-2 decimation
+// in time over a bit-reversed copy; all indices are compile-time after
+// unrolling.
 template <int R, int DIR, typename V>
-__device__ __forceinline__ void dft(V (&x)[R]) {
+__device__ __forceinline__ void dft_pow2(V (&x)[R]) {
   constexpr int L = ilog2<R>::v;
   V y[R];
 #pragma unroll
@@ -141,6 +142,46 @@ __device__ __forceinline__ void dft(V (&x)[R]) {
   for (int i = 0; i < R; ++i) x[i] = y[i];
 }
 
+// 3-point DFT: with s = DIR sqrt(3)/2,
+//   y0 = x0 + x1 + x2,  y1,2 = x0 - (x1 + x2)/2 +- i s (x1 - x2).
+template <int DIR, typename V>
+__device__ __forceinline__ void dft3(V& a, V& b, V& c) {
+  using T = decltype(V::x);
+  constexpr double S3 = 0.86602540378443864676372317075293618347;  // sqrt(3)/2
+  const V t1 = cadd(b, c);
+  const V t2 = csub(a, cscale(t1, T(0.5)));
+  const V d = cscale(csub(b, c), T(DIR * S3));
+  a = cadd(a, t1);
+  b = cadd(t2, cmul_i(d));
+  c = csub(t2, cmul_i(d));
+}
+
+// In-register DFT of size R in {2,3,4,6,8,16}.  R = 6 = 2 x 3: two 3-point
+// DFTs of the even and odd samples, then X[k] = A0[k] + w6^k A1[k] and
+// X[k+3] = A0[k] - w6^k A1[k], w6 = exp(DIR i pi/3).
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void dft(V (&x)[R]) {
+  if constexpr (R == 3) {
+    dft3<DIR>(x[0], x[1], x[2]);
+  } else if constexpr (R == 6) {
+    using T = decltype(V::x);
+    constexpr double S3 = 0.86602540378443864676372317075293618347;
+    V e0 = x[0], e1 = x[2], e2 = x[4], o0 = x[1], o1 = x[3], o2 = x[5];
+    dft3<DIR>(e0, e1, e2);
+    dft3<DIR>(o0, o1, o2);
+    o1 = cmul(o1, mk<V>(T(0.5), T(DIR * S3)));   // w6
+    o2 = cmul(o2, mk<V>(T(-0.5), T(DIR * S3)));  // w6^2
+    x[0] = cadd(e0, o0);
+    x[3] = csub(e0, o0);
+    x[1] = cadd(e1, o1);
+    x[4] = csub(e1, o1);
+    x[2] = cadd(e2, o2);
+    x[5] = csub(e2, o2);
+  } else {
+    dft_pow2<R, DIR>(x);
+  }
+}
+
 // Radix schedule per length N and registers per thread E: stage radices
 // R0..R3 (1 = no stage).  E = 16 shortens the wider FP32 transforms by one
 // shared-memory exchange; E = 8 keeps FP64 within the register file.
@@ -157,10 +198,15 @@ template <> struct Sched<256, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R
 template <> struct Sched<512, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 8, R3 = 1; };
 template <> struct Sched<1024, 16> { static constexpr int S = 3, R0 = 16, R1 = 8, R2 = 8, R3 = 1; };
 template <> struct Sched<1024, 8> { static constexpr int S = 4, R0 = 8, R1 = 8, R2 = 8, R3 = 2; };
+// lengths with a factor 3 (E = 12)
+template <> struct Sched<48, 12> { static constexpr int S = 3, R0 = 6, R1 = 4, R2 = 2, R3 = 1; };
+template <> struct Sched<96, 12> { static constexpr int S = 3, R0 = 6, R1 = 4, R2 = 4, R3 = 1; };
+template <> struct Sched<192, 12> { static constexpr int S = 4, R0 = 6, R1 = 4, R2 = 4, R3 = 2; };
 
 // Registers per thread for a length-N line in precision T.
 template <typename T, int N> struct EOf {
-  static constexpr int v = (sizeof(T) == 4 && (N == 16 || N == 128 || N == 256 || N == 1024)) ? 16 : 8;
+  static constexpr int v = (N % 3 == 0) ? 12
+                           : (sizeof(T) == 4 && (N == 16 || N == 128 || N == 256 || N == 1024)) ? 16 : 8;
 };
 
 // Twiddle exp(DIR 2 pi i m/N) from the table tw[m] = exp(-2 pi i m/N).
@@ -181,7 +227,7 @@ __device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ t
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = j0 + b * (N / E);
-    const int k = j & (NS - 1);
+    const int k = j % NS;
     V x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = a[b + r * NB];

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct ps_plan;
+
 namespace ps {
 
 // Grid geometry and the retained (2/3-rule) cube.
@@ -57,6 +59,7 @@ struct PassArgs {
   const void* fbox;  // forcing box [3][2Fz+1][2Fy+1][Fx+1] or null
   int Fx, Fy, Fz;
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
+  int xrpc;          // x pass rows per CTA (0 = largest that keeps two CTAs per SM)
   int* err;          // device error word (bounded waits that gave up), never null
 };
 
@@ -80,5 +83,13 @@ cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, 
 template <typename T>
 cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, cudaStream_t s);
 cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double* out, cudaStream_t s);
+
+// Plan internals used by the ensemble layer (ps_plan.cu).
+void plan_set_stream(struct ::ps_plan* p, cudaStream_t s);
+cudaStream_t plan_stream(const struct ::ps_plan* p);
+void plan_set_xrpc(struct ::ps_plan* p, int rpc);
+// Forget the cached integrating-factor tables so the next step recomputes them
+// (a captured graph must contain that launch).
+void plan_invalidate_tables(struct ::ps_plan* p);
 
 }  // namespace ps

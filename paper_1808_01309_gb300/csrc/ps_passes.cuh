@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
           V nx = czero<V>(), ny = czero<V>(), nz = czero<V>();
           if (k <= g.Kx) {
             const V Fk = F1[m];
-            const V Fm = cconj(ex.get((N - k) & (N - 1)));
+            const V Fm = cconj(ex.get(k == 0 ? 0 : N - k));
             nx = cscale(cadd(Fk, Fm), T(0.5));
             ny = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
             nz = F2[m];
@@ -613,6 +613,7 @@ cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
   // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
   int rpc = RPCOf<T, N>::v;
   while (rpc > 1 && xpass_smem<T, N>(a.g, rpc) > 113 * 1024) rpc /= 2;
+  if (a.xrpc > 0 && a.xrpc < rpc) rpc = a.xrpc;  // tuned (smaller) row groups
   const size_t smem = xpass_smem<T, N>(a.g, rpc);
   cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -658,8 +659,11 @@ cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
     case 8: return CALL(8);                        \
     case 16: return CALL(16);                      \
     case 32: return CALL(32);                      \
+    case 48: return CALL(48);                      \
     case 64: return CALL(64);                      \
+    case 96: return CALL(96);                      \
     case 128: return CALL(128);                    \
+    case 192: return CALL(192);                    \
     case 256: return CALL(256);                    \
     case 512: return CALL(512);                    \
     case 1024: return CALL(1024);                  \

@@ -33,7 +33,10 @@ ps_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
 
-bool pow2_in_range(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+// Supported line lengths: powers of two from 8 to 1024, and 48, 96, 192.
+bool pow2_in_range(int n) {
+  return (n >= 8 && n <= 1024 && (n & (n - 1)) == 0) || n == 48 || n == 96 || n == 192;
+}
 
 int halfwidth(int n, ps_dealias d) {
   if (d == PS_DEALIAS_NONE) return n / 2 - 1;
@@ -43,7 +46,7 @@ int halfwidth(int n, ps_dealias d) {
 ps_status validate(const ps_config* c) {
   if (!c) return fail(PS_ERR_INVALID_ARG, "config is NULL");
   if (!pow2_in_range(c->nx) || !pow2_in_range(c->ny) || !pow2_in_range(c->nz))
-    return fail(PS_ERR_INVALID_ARG, "nx, ny, nz must be powers of two in [8, 1024]");
+    return fail(PS_ERR_INVALID_ARG, "nx, ny, nz must be powers of two in [8, 1024] or 48, 96, 192");
   if (!(std::isfinite(c->lx) && std::isfinite(c->ly) && std::isfinite(c->lz) && c->lx > 0 && c->ly > 0 && c->lz > 0))
     return fail(PS_ERR_INVALID_ARG, "box lengths must be finite and positive");
   if (c->prec != PS_FP32 && c->prec != PS_FP64) return fail(PS_ERR_INVALID_ARG, "unknown precision");
@@ -118,6 +121,7 @@ struct ps_plan {
   ps_config cfg{};
   cudaStream_t stream = nullptr;
   int device = 0;
+  int xrpc = 0;  // x-pass rows per CTA override (0 = automatic)
   Geo g{};
   Sizes sz{};
   void* a6 = nullptr;
@@ -250,6 +254,7 @@ PassArgs base_args(ps_plan* p) {
   a.nxt = p->nxt;
   a.acc = p->acc;
   a.err = p->err;
+  a.xrpc = p->xrpc;
   return a;
 }
 
@@ -411,6 +416,13 @@ void release(ps_plan* p) {
 }
 
 }  // namespace
+
+namespace ps {
+void plan_set_stream(ps_plan* p, cudaStream_t s) { p->stream = s; }
+cudaStream_t plan_stream(const ps_plan* p) { return p->stream; }
+void plan_set_xrpc(ps_plan* p, int rpc) { p->xrpc = rpc; }
+void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
+}  // namespace ps
 
 extern "C" {
 

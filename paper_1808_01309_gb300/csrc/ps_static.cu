@@ -80,7 +80,10 @@ size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
 int halfwidth(int n, ps_dealias d) { return d == PS_DEALIAS_NONE ? n / 2 - 1 : (n + 2) / 3 - 1; }
 
-bool pow2_in_range(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+// Supported line lengths: powers of two from 8 to 1024, and 48, 96, 192.
+bool pow2_in_range(int n) {
+  return (n >= 8 && n <= 1024 && (n & (n - 1)) == 0) || n == 48 || n == 96 || n == 192;
+}
 
 ps_status bad(ps_status s, const std::string& m) {
   set_last_error(m);
@@ -187,7 +190,7 @@ extern "C" ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, con
   (void)t;
   if (!cfg || !uhat || !rhs_out) return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: NULL config or buffer");
   if (!pow2_in_range(cfg->nx) || !pow2_in_range(cfg->ny) || !pow2_in_range(cfg->nz))
-    return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: nx, ny, nz must be powers of two in [8, 1024]");
+    return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: nx, ny, nz must be powers of two in [8, 1024] or 48, 96, 192");
   if (!(std::isfinite(cfg->lx) && std::isfinite(cfg->ly) && std::isfinite(cfg->lz) && cfg->lx > 0 &&
         cfg->ly > 0 && cfg->lz > 0))
     return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: box lengths must be finite and positive");

@@ -48,8 +48,11 @@ SYMBOLS = (
     "ps_plan_create", "ps_plan_destroy", "ps_plan_workspace_bytes", "ps_rhs", "ps_rk_step",
     "ps_rk_step_host", "ps_step_stats", "ps_diagnostics", "ps_plan_set_timing",
     "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
-    "ps_last_error", "ps_rhs_noalloc",
+    "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
+    "ps_ensemble_rk_steps", "ps_ensemble_tune",
 )
+ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
+ENS_MAX_SIZES = 8
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -71,6 +74,11 @@ class PsDiag(ctypes.Structure):
         ("time", ctypes.c_double),
         ("spectrum", ctypes.POINTER(ctypes.c_double)), ("nshells", ctypes.c_int),
     ]
+
+
+class PsEnsTuning(ctypes.Structure):
+    _fields_ = [("branches", ctypes.c_int), ("nsizes", ctypes.c_int), ("n", ctypes.c_int * 8),
+                ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double)]
 
 
 class PsTiming(ctypes.Structure):
@@ -102,6 +110,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_get_timing.argtypes = [P, ctypes.POINTER(PsTiming)]
     lib.ps_plan_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.ps_rhs_noalloc.argtypes = [ctypes.POINTER(PsConfig), P, P, P, ctypes.c_double]
+    lib.ps_ensemble_create.argtypes = [ctypes.POINTER(PsConfig), ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.ps_ensemble_destroy.argtypes = [P]
+    lib.ps_ensemble_rk_steps.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int]
+    lib.ps_ensemble_tune.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(PsEnsTuning)]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -216,6 +229,32 @@ def ps_plan_launch_count(plan) -> int:
     n = ctypes.c_longlong()
     _check(load().ps_plan_launch_count(plan, ctypes.byref(n)))
     return n.value
+
+
+def ps_ensemble_create(cfgs, stream=None) -> ctypes.c_void_p:
+    arr = (PsConfig * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    _check(load().ps_ensemble_create(arr, len(cfgs), _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def ps_ensemble_destroy(ens) -> None:
+    _check(load().ps_ensemble_destroy(ens))
+
+
+def _ptr_array(states):
+    return (ctypes.c_void_p * len(states))(*[_ptr(s) for s in states])
+
+
+def ps_ensemble_rk_steps(ens, states, dt: float, t: float = 0.0, nsteps: int = 1, mode: int = ENS_GRAPH) -> None:
+    _check(load().ps_ensemble_rk_steps(ens, _ptr_array(states), float(dt), float(t), int(nsteps), int(mode)))
+
+
+def ps_ensemble_tune(ens, states, dt: float) -> dict:
+    t = PsEnsTuning()
+    _check(load().ps_ensemble_tune(ens, _ptr_array(states), float(dt), ctypes.byref(t)))
+    return {"branches": t.branches, "step_ms": t.step_ms,
+            "xrpc": {int(t.n[i]): int(t.xrpc[i]) for i in range(t.nsizes)}}
 
 
 # ---- convenience wrapper ------------------------------------------------------------

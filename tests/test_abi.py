@@ -47,7 +47,7 @@ def test_status_strings(ps):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(nx=12), dict(nx=4), dict(ny=2048), dict(nz=0), dict(lx=0.0), dict(ly=-1.0),
+    dict(nx=12), dict(nx=4), dict(ny=2048), dict(nz=0), dict(nx=24), dict(nx=384), dict(lx=0.0), dict(ly=-1.0),
     dict(lz=math.inf), dict(rk_order=3), dict(nu=-1e-3), dict(nu=math.nan),
     dict(dealias=7), dict(prec=5),
 ])

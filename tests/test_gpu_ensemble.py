@@ -1,0 +1,112 @@
+"""Ensembles of independent solves of uneven sizes (one CUDA graph vs
+member-by-member launches), and the radix-3 grid lengths they need."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_01309_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import ps as _ps
+    return _ps
+
+
+SIZES = [32, 48, 64, 32, 48, 64, 96]
+
+
+def _members(ps, prec="fp32"):
+    P, dt = (ps.Precision.FP32, torch.complex64) if prec == "fp32" else (ps.Precision.FP64, torch.complex128)
+    cfgs, states, host = [], [], []
+    for i, n in enumerate(SIZES):
+        nu = inputs.ensemble_viscosity(i)
+        cfgs.append(ps.make_config(n, prec=P, nu=nu, rk_order=4))
+        u = inputs.random_solenoidal_field(n, n, n, seed=1000 + i) * 2.0
+        host.append(u)
+        states.append(torch.from_numpy(u).to("cuda", dt))
+    return cfgs, states, host
+
+
+def test_graph_and_sequential_are_identical_and_match_single_plans(ps):
+    cfgs, s_graph, host = _members(ps)
+    s_seq = [s.clone() for s in s_graph]
+    s_one = [s.clone() for s in s_graph]
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, s_graph, 2e-3, 0.0, 3, ps.ENS_GRAPH)
+    ps.ps_ensemble_rk_steps(ens, s_seq, 2e-3, 0.0, 3, ps.ENS_SEQUENTIAL)
+    torch.cuda.synchronize()
+    for i, c in enumerate(cfgs):
+        plan = ps.Plan(c.nx, prec=ps.Precision.FP32, nu=c.nu, rk_order=4)
+        for k in range(3):
+            plan.rk_step(s_one[i], 2e-3, t=k * 2e-3)
+        torch.cuda.synchronize()
+        assert torch.equal(s_graph[i], s_seq[i])
+        assert torch.equal(s_graph[i], s_one[i])
+        plan.close()
+    # replaying the captured graph continues the same trajectory
+    ps.ps_ensemble_rk_steps(ens, s_graph, 2e-3, 0.0, 3, ps.ENS_GRAPH)
+    ps.ps_ensemble_rk_steps(ens, s_seq, 2e-3, 0.0, 3, ps.ENS_SEQUENTIAL)
+    torch.cuda.synchronize()
+    for a, b in zip(s_graph, s_seq):
+        assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+@pytest.mark.parametrize("member", [1, 6])
+def test_ensemble_member_matches_oracle(ps, member):
+    cfgs, states, host = _members(ps, "fp64")
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_GRAPH)
+    torch.cuda.synchronize()
+    n = SIZES[member]
+    ref = host[member]
+    cfg = oracle.Config(n, n, n, nu=cfgs[member].nu, rk_order=4)
+    for _ in range(2):
+        ref = oracle.rk_step(ref, 2e-3, cfg)
+    got = states[member].cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_tuner_keeps_states_and_results(ps):
+    cfgs, states, _ = _members(ps)
+    before = [s.clone() for s in states]
+    ens = ps.ps_ensemble_create(cfgs)
+    tuning = ps.ps_ensemble_tune(ens, states, 2e-3)
+    torch.cuda.synchronize()
+    for a, b in zip(states, before):
+        assert torch.equal(a, b)
+    assert 1 <= tuning["branches"] <= len(SIZES) and tuning["step_ms"] > 0
+    assert set(tuning["xrpc"]) == {32, 48, 64, 96}
+    ref = [s.clone() for s in states]
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_GRAPH)
+    ps.ps_ensemble_rk_steps(ens, ref, 2e-3, 0.0, 2, ps.ENS_SEQUENTIAL)
+    torch.cuda.synchronize()
+    for a, b in zip(states, ref):
+        assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(96, 96, 96), (48, 192, 96), (192, 48, 64)])
+def test_radix3_lengths_rhs_matches_oracle(ps, prec, shape):
+    nx, ny, nz = shape
+    u = inputs.random_solenoidal_field(nx, ny, nz, seed=3, kmax=(nx, ny, nz), ly=4.0)
+    f = inputs.forcing_field(nx, ny, nz, seed=2, ly=4.0)
+    cfg = oracle.Config(nx, ny, nz, ly=4.0, nu=2e-3)
+    ref = oracle.rhs(u, cfg, forcing=f)
+    P, dt = (ps.Precision.FP32, torch.complex64) if prec == "fp32" else (ps.Precision.FP64, torch.complex128)
+    plan = ps.Plan(nx, ny, nz, ly=4.0, prec=P, nu=2e-3, forcing=torch.from_numpy(f).to("cuda", dt))
+    got = plan.rhs(torch.from_numpy(u).to("cuda", dt)).cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+    plan.close()
