@@ -40,4 +40,8 @@ from .spectral import (  # noqa: F401
     rhs,
     rk_step,
     diagnostics,
+    mhd_nonlinear,
+    mhd_rhs,
+    mhd_rk_step,
+    mhd_diagnostics,
 )

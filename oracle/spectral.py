@@ -37,7 +37,8 @@ Readings of the paper (each one is repeated where it is used):
   R7 (nonlinear term, "computed in physical space"): rotational form
      n = u x omega; the gradient part of the advection is absorbed by P.
   R8 (Sec. 2, "explicit Runge-Kutta of 2nd-4th order"): Lawson (integrating
-     factor) RK2 (Heun) and RK4 (classical) with E = exp(-nu |k|^2 dt/2).
+     factor) RK2 (Heun) and RK4 (classical) with E = exp(-nu |k|^2 dt/2)
+     (exp(-eta |k|^2 dt/2) for the magnetic field).
   R9 (diagnostics, not in the paper): Hermitian weight w = 1 on the planes
      kx = 0 and kx = Nx/2, else 2; shells K = floor(|k| + 1/2).
 """
@@ -66,6 +67,7 @@ class Config:
     nu: float = 0.0
     dealias: int = CUBIC
     rk_order: int = 4
+    eta: float = 0.0  # magnetic diffusivity (MHD)
 
     @property
     def nh(self) -> int:
@@ -192,11 +194,11 @@ def rhs(uh: np.ndarray, cfg: Config, forcing=None, nonlinear_on: bool = True) ->
     return _nonviscous(uh, cfg, forcing, nonlinear_on) - cfg.nu * k2 * (uh * D)
 
 
-def rk_step(uh: np.ndarray, dt: float, cfg: Config, forcing=None,
-            nonlinear_on: bool = True) -> np.ndarray:
+def _lawson_step(u, E, R, dt: float, order: int):
     """One explicit Runge-Kutta step (Sec. 2, 2nd or 4th order) in Lawson
-    (integrating-factor) form, reading R8.  With E = exp(-nu |k|^2 dt/2) and
-    R the right-hand side without viscosity:
+    (integrating-factor) form, reading R8.  u and E are arrays of the same
+    shape (E the per-mode half-step factor exp(-rate |k|^2 dt/2)), R the
+    right-hand side without the linear damping:
 
       RK4: k1 = R(u), k2 = R(E (u + dt/2 k1)), k3 = R(E u + dt/2 k2),
            k4 = R(E^2 u + dt E k3),
@@ -204,25 +206,98 @@ def rk_step(uh: np.ndarray, dt: float, cfg: Config, forcing=None,
       RK2: k1 = R(u), k2 = R(E^2 (u + dt k1)),
            u+ = E^2 (u + dt/2 k1) + dt/2 k2
     """
-    kx, ky, kz = wavenumbers(cfg)
-    k2 = kx * kx + ky * ky + kz * kz
-    E = np.exp(-cfg.nu * k2 * dt / 2.0)
-    u = uh * dealias_mask(cfg)
-
-    def R(v):
-        return _nonviscous(v, cfg, forcing, nonlinear_on)
-
-    if cfg.rk_order == 4:
+    if order == 4:
         k1 = R(u)
         k2_ = R(E * (u + 0.5 * dt * k1))
         k3 = R(E * u + 0.5 * dt * k2_)
         k4 = R(E * E * u + dt * E * k3)
         return E * E * u + (dt / 6.0) * (E * E * k1 + 2.0 * E * (k2_ + k3) + k4)
-    if cfg.rk_order == 2:
+    if order == 2:
         k1 = R(u)
         k2_ = R(E * E * (u + dt * k1))
         return E * E * (u + 0.5 * dt * k1) + 0.5 * dt * k2_
     raise ValueError("rk_order must be 2 or 4")
+
+
+def rk_step(uh: np.ndarray, dt: float, cfg: Config, forcing=None,
+            nonlinear_on: bool = True) -> np.ndarray:
+    """One IF-RK step of the HD system (Sec. 2; reading R8, see _lawson_step)
+    with E = exp(-nu |k|^2 dt/2)."""
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    E = np.exp(-cfg.nu * k2 * dt / 2.0) + np.zeros_like(uh, dtype=np.float64)
+    u = uh * dealias_mask(cfg)
+    return _lawson_step(u, E, lambda v: _nonviscous(v, cfg, forcing, nonlinear_on), dt, cfg.rk_order)
+
+
+# --------------------------------------------------------------------------
+# MHD (Eqs. uMHD, bMHD): state = 6 components (u_x, u_y, u_z, B_x, B_y, B_z)
+# --------------------------------------------------------------------------
+
+def mhd_nonlinear(ub: np.ndarray, cfg: Config):
+    """Masked nonlinear terms of the MHD system in rotational form:
+    N_u = D F[u x omega + j x B] (pressure and magnetic pressure gradients
+    are removed by the projection) and N_B = D (i k x F[u x B]) = F[curl(u x B)]
+    (Eqs. uMHD, bMHD with j = curl B; readings R4, R5, R7)."""
+    D = dealias_mask(cfg)
+    u_hat, b_hat = ub[:3] * D, ub[3:] * D
+    u = inverse(u_hat, cfg)
+    om = inverse(curl_hat(u_hat, cfg), cfg)
+    b = inverse(b_hat, cfg)
+    j = inverse(curl_hat(b_hat, cfg), cfg)
+    nu_ = forward(np.cross(u, om, axis=0) + np.cross(j, b, axis=0)) * D
+    nb = curl_hat(forward(np.cross(u, b, axis=0)), cfg) * D
+    return nu_, nb
+
+
+def _mhd_nonviscous(ub, cfg: Config, forcing, nonlinear_on=True):
+    D = dealias_mask(cfg)
+    nu_ = _forcing_or_zero(forcing, cfg, ub[:3])
+    nb = np.zeros_like(ub[3:])
+    if nonlinear_on:
+        n1, n2 = mhd_nonlinear(ub, cfg)
+        nu_ = nu_ + n1
+        nb = n2
+    return np.concatenate([project(nu_, cfg) * D, nb * D])
+
+
+def mhd_rhs(ub: np.ndarray, cfg: Config, forcing=None) -> np.ndarray:
+    """d/dt of (u_hat, B_hat): D P(N_u + f) - nu |k|^2 D u_hat and
+    N_B - eta |k|^2 D B_hat (Eqs. uMHD, bMHD, divergence-free u and B)."""
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    D = dealias_mask(cfg)
+    lin = np.concatenate([cfg.nu * k2 * ub[:3] * D, cfg.eta * k2 * ub[3:] * D])
+    return _mhd_nonviscous(ub, cfg, forcing) - lin
+
+
+def mhd_rk_step(ub: np.ndarray, dt: float, cfg: Config, forcing=None) -> np.ndarray:
+    """One IF-RK step of the MHD system: the same Lawson scheme with
+    E = exp(-nu |k|^2 dt/2) on u and exp(-eta |k|^2 dt/2) on B."""
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz + np.zeros(ub.shape[1:])
+    E = np.concatenate([np.broadcast_to(np.exp(-cfg.nu * k2 * dt / 2.0), (3,) + k2.shape),
+                        np.broadcast_to(np.exp(-cfg.eta * k2 * dt / 2.0), (3,) + k2.shape)])
+    u = ub * dealias_mask(cfg)
+    return _lawson_step(u, E, lambda v: _mhd_nonviscous(v, cfg, forcing), dt, cfg.rk_order)
+
+
+def mhd_diagnostics(ub: np.ndarray, cfg: Config, cfl: float = 0.5) -> dict:
+    """HD diagnostics of u plus magnetic energy 1/2 sum w |B|^2, cross helicity
+    sum w Re(u* . B) and magnetic helicity sum w Re(A* . B), A = i k x B / |k|^2
+    the Coulomb-gauge vector potential (reading R9)."""
+    d = diagnostics(ub[:3], cfg, cfl)
+    D = dealias_mask(cfg)
+    u, b = ub[:3] * D, ub[3:] * D
+    w = hermitian_weight(cfg)
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = np.where(k2 > 0, curl_hat(b, cfg) / np.where(k2 > 0, k2, 1.0), 0.0)
+    d["magnetic_energy"] = float(np.sum(0.5 * w * np.sum(np.abs(b) ** 2, axis=0)))
+    d["cross_helicity"] = float(np.sum(w * np.real(np.sum(np.conj(u) * b, axis=0))))
+    d["magnetic_helicity"] = float(np.sum(w * np.real(np.sum(np.conj(a) * b, axis=0))))
+    return d
 
 
 def diagnostics(uh: np.ndarray, cfg: Config, cfl: float = 0.5) -> dict:
