@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--mhd-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
@@ -312,12 +313,32 @@ def run_ours(args, world, rank, local):
         del ud, fd
         torch.cuda.empty_cache()
 
+    # ---- MHD variant (u and B, twice the transforms per RHS) -----------------
+    mhd = None
+    if args.mhd_steps > 0:
+        from paper_1808_01309_gb300 import inputs
+        b = inputs.random_solenoidal_field(n, n, n, seed=51)
+        ub = torch.from_numpy(np.concatenate([u, b])).to(dev, torch.complex64)
+        del b
+        fd = torch.from_numpy(f).to(dev, torch.complex64)
+        plan = ps.Plan(n, prec=ps.Precision.FP32, eq=ps.Equations.MHD, nu=nu, eta=nu, rk_order=4,
+                       forcing=fd, stream=stream)
+        msm, _ = time_steps(plan, ub, dt, args.mhd_steps, 3, stream, world, ps)
+        msm = reduce_max(msm, world) / args.mhd_steps
+        mhd = {"ms_per_step": round(msm, 3), "value": round(world * 4 * n ** 3 / (msm * 1e-3) / 1e9, 3),
+               "unit": UNIT, "steps": args.mhd_steps, "prec": "fp32",
+               "workload": f"{n}^3 MHD, u and B seeded with the same spectrum (seeds 1, 51), eta = nu",
+               "vs_hd_step": round(msm / ms_step, 2)}
+        plan.close()
+        del ub, fd
+        torch.cuda.empty_cache()
+
     ens = None
     if not args.no_ensemble:
         ens = run_ensemble(args, dev, stream)
         torch.cuda.empty_cache()
 
-    out.update(ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
+    out.update(mhd=mhd, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
                achieved=achieved, hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
                kernel_gbs=kernel_gbs, step_bytes=step_bytes, e2e=e2e, fp64=fp64, energy=e_step,
                max_u=umax_step, alg=alg)
@@ -453,6 +474,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": res["e2e"],
         "fp64": res["fp64"],
+        "mhd": res["mhd"],
         "ensemble": res["ens"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],

@@ -31,10 +31,11 @@
  *
  * Data layout of every spectral vector field (state, right-hand side,
  * forcing): interleaved complex (float2 for PS_FP32, double2 for PS_FP64),
- * C order [component 0..2][kz 0..nz-1][ky 0..ny-1][kx 0..nx/2], kx fastest,
+ * C order [component][kz 0..nz-1][ky 0..ny-1][kx 0..nx/2], kx fastest,
  * ky and kz in FFT order (0..n/2-1, -n/2..-1).  This is the layout of
  * torch.fft.rfftn / numpy.fft.rfftn of a real (nz, ny, nx) array per
- * component.  Field bytes: 3 * nz * ny * (nx/2+1) * (8 or 16).
+ * component.  Components: 3 (u) for PS_HD, 6 (u, B) for PS_MHD.  Field
+ * bytes: ncomp * nz * ny * (nx/2+1) * (8 or 16).
  *
  * Ownership: the caller owns the state, right-hand-side and forcing buffers.
  * The plan owns its scratch (intermediate fields, twiddles, stage registers).
@@ -78,13 +79,16 @@ typedef struct ps_plan ps_plan;
  *   nx, ny, nz : powers of two in [8, 1024], or 48, 96, 192 (radix-3 lines)
  *   lx, ly, lz : box lengths, finite and > 0
  *   prec       : arithmetic and storage precision of all fields
- *   eq         : PS_HD (PS_MHD returns PS_ERR_UNSUPPORTED)
+ *   eq         : PS_HD, or PS_MHD (Eqs. uMHD, bMHD: the state then has six
+ *                components u_x, u_y, u_z, B_x, B_y, B_z; the magnetic
+ *                field advances with dB/dt = curl(u x B) - eta |k|^2 B)
  *   dealias    : truncation rule
  *   rk_order   : 2 or 4
- *   nu         : kinematic viscosity >= 0;  eta: magnetic diffusivity (MHD, unused)
- *   forcing    : device pointer to a constant-in-time forcing field in the
- *                state layout and precision, or NULL.  Its retained modes are
- *                copied at plan creation; later changes are not seen. */
+ *   nu         : kinematic viscosity >= 0;  eta: magnetic diffusivity >= 0 (MHD)
+ *   forcing    : device pointer to a constant-in-time forcing of the
+ *                velocity (three components, state layout and precision), or
+ *                NULL.  Its retained modes are copied at plan creation; later
+ *                changes are not seen. */
 typedef struct {
   int nx, ny, nz;
   double lx, ly, lz;
@@ -104,11 +108,16 @@ typedef struct {
  *   spectrum  : caller-owned host array of capacity nshells (or NULL); shell
  *               K holds 1/2 sum w |u_hat|^2 over modes with floor(|k|+1/2) = K
  *   nshells   : in: capacity of spectrum; out: number of shells of this grid
- *   time      : t + dt of the last ps_rk_step on this plan (0 if none) */
+ *   time      : t + dt of the last ps_rk_step on this plan (0 if none)
+ *   MHD only (0 for HD): magnetic_energy = 1/2 sum w |B_hat|^2,
+ *   cross_helicity = sum w Re(u_hat* . B_hat), magnetic_helicity =
+ *   sum w Re(A_hat* . B_hat) with A_hat = i k x B_hat/|k|^2 (Coulomb gauge);
+ *   the velocity entries above describe u only. */
 typedef struct {
   double energy, enstrophy, helicity, max_div, max_u, cfl_dt, time;
   double* spectrum;
   int nshells;
+  double magnetic_energy, cross_helicity, magnetic_helicity;
 } ps_diag;
 
 #define PS_NKINDS 6
@@ -149,8 +158,8 @@ ps_status ps_rk_step(ps_plan* plan, void* uhat, double dt, double t);
  * back and synchronises.  uhat_host should be page-locked for full speed. */
 ps_status ps_rk_step_host(ps_plan* plan, void* uhat_host, double dt, double t, int nsteps);
 
-/* Energy and max |u(x)| (FP64) of the state at the start of the last
- * ps_rk_step.  Synchronises the plan stream. */
+/* Energy (kinetic + magnetic for MHD) and max |u(x)| (FP64) of the state at
+ * the start of the last ps_rk_step.  Synchronises the plan stream. */
 ps_status ps_step_stats(ps_plan* plan, double* energy, double* max_u);
 
 /* Diagnostics of the device state uhat (see ps_diag).  Runs the backward

@@ -102,16 +102,17 @@ cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, 
 }
 
 // Spectral diagnostics, one CTA per retained kz plane; row blk of `part`
-// holds [E, Omega, H, max|k.u|, spectrum(0..nshells-1)] of that plane.
+// holds [E, Omega, H, max|k.u|, E_B, H_c, H_m, 0, spectrum(0..nshells-1)] of
+// that plane (the magnetic entries only for mhd != 0: B = components 3..5).
 template <typename T>
-__global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nshells) {
+__global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nshells, int mhd) {
   using V = typename cplx<T>::type;
   __shared__ double red[32];
   const int iz = blockIdx.x;
   const int r = iz <= g.Kz ? iz : iz - g.cz;
   const V* up = static_cast<const V*>(u.p);
-  double* row = part + (long long)blockIdx.x * (4 + nshells);
-  double e = 0, om = 0, h = 0, md = 0;
+  double* row = part + (long long)blockIdx.x * (DIAG_HEAD + nshells);
+  double e = 0, om = 0, h = 0, md = 0, eb = 0, hc = 0, hm = 0;
   const int per = g.cy * g.cx;
   for (int i = threadIdx.x; i < per; i += blockDim.x) {
     const int iy = i / g.cx, p = i % g.cx;
@@ -128,36 +129,58 @@ __global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nsh
     const double cyr = kz * ux - kx * uz, cyi = kz * uxi - kx * uzi;
     const double czr = kx * uy - ky * ux, czi = kx * uyi - ky * uxi;
     const double o2 = cxr * cxr + cxi * cxi + cyr * cyr + cyi * cyi + czr * czr + czi * czi;
-    // Re(conj(u) . i c) = Re(u)Im... : Re(conj(a) i b) = a.x (-b.y) + a.y b.x
+    // Re(conj(a) i b) = -a.x b.y + a.y b.x, summed over components
     const double hel = -(ux * cxi) + uxi * cxr - (uy * cyi) + uyi * cyr - (uz * czi) + uzi * czr;
     const double dr = kx * ux + ky * uy + kz * uz, di = kx * uxi + ky * uyi + kz * uzi;
     e += 0.5 * w * u2;
     om += 0.5 * w * o2;
     h += w * hel;
     md = fmax(md, sqrt(dr * dr + di * di));
+    if (mhd) {
+      const V b0 = pm[3 * u.cs], b1 = pm[4 * u.cs], b2 = pm[5 * u.cs];
+      const double bx = b0.x, bxi = b0.y, by = b1.x, byi = b1.y, bz = b2.x, bzi = b2.y;
+      eb += 0.5 * w * (bx * bx + bxi * bxi + by * by + byi * byi + bz * bz + bzi * bzi);
+      hc += w * (ux * bx + uxi * bxi + uy * by + uyi * byi + uz * bz + uzi * bzi);
+      const double k2 = kx * kx + ky * ky + kz * kz;
+      if (k2 > 0) {
+        // A = i d/|k|^2 with d = k x B; Re(conj(i d) . B) = d.re . B.im - d.im . B.re
+        const double dxr = ky * bz - kz * by, dxi = ky * bzi - kz * byi;
+        const double dyr = kz * bx - kx * bz, dyi = kz * bxi - kx * bzi;
+        const double dzr = kx * by - ky * bx, dzi = kx * byi - ky * bxi;
+        const double re = (dxr * bxi - dxi * bx) + (dyr * byi - dyi * by) + (dzr * bzi - dzi * bz);
+        hm += w * re / k2;
+      }
+    }
     const int sh = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
-    if (sh < nshells) atomicAdd(row + 4 + sh, 0.5 * w * u2);
+    if (sh < nshells) atomicAdd(row + DIAG_HEAD + sh, 0.5 * w * u2);
   }
   const double te = block_sum(e, red);
   const double to = block_sum(om, red);
   const double th = block_sum(h, red);
   const double tm = block_max(md, red);
+  const double teb = block_sum(eb, red);
+  const double thc = block_sum(hc, red);
+  const double thm = block_sum(hm, red);
   if (threadIdx.x == 0) {
     row[0] = te;
     row[1] = to;
     row[2] = th;
     row[3] = tm;
+    row[4] = teb;
+    row[5] = thc;
+    row[6] = thm;
+    row[7] = 0.0;
   }
 }
 
 template <typename T>
-cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, cudaStream_t s) {
-  k_diag_spectral<T><<<g.cz, 256, 0, s>>>(g, u, part, nshells);
+cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int mhd, cudaStream_t s) {
+  k_diag_spectral<T><<<g.cz, 256, 0, s>>>(g, u, part, nshells, mhd);
   return cudaGetLastError();
 }
 
 __global__ void k_diag_final(const double* __restrict__ part, int nblk, int nshells, double* out) {
-  const int w = 4 + nshells;
+  const int w = DIAG_HEAD + nshells;
   for (int j = threadIdx.x; j < w; j += blockDim.x) {
     double v = 0.0;
     for (int b = 0; b < nblk; ++b) {
@@ -179,7 +202,7 @@ template cudaError_t launch_forcing_extent<float>(const Geo&, Spec, int*, cudaSt
 template cudaError_t launch_forcing_extent<double>(const Geo&, Spec, int*, cudaStream_t);
 template cudaError_t launch_forcing_gather<float>(const Geo&, Spec, int, int, int, void*, cudaStream_t);
 template cudaError_t launch_forcing_gather<double>(const Geo&, Spec, int, int, int, void*, cudaStream_t);
-template cudaError_t launch_diag_spectral<float>(const Geo&, Spec, double*, int, cudaStream_t);
-template cudaError_t launch_diag_spectral<double>(const Geo&, Spec, double*, int, cudaStream_t);
+template cudaError_t launch_diag_spectral<float>(const Geo&, Spec, double*, int, int, cudaStream_t);
+template cudaError_t launch_diag_spectral<double>(const Geo&, Spec, double*, int, int, cudaStream_t);
 
 }  // namespace ps

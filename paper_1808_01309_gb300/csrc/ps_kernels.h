@@ -38,8 +38,8 @@ struct PassArgs {
   // inverse z pass input (state or stage buffer)
   Spec in;
   // intermediate buffers
-  void* a6;   // [6][nz][cy][kxp]  (z-inverse out) / [3][nz][ny][kxp] (x out)
-  void* b6;   // [6][nz][ny][kxp]  (y-inverse out) / [3][nz][cy][kxp] (y-forward out)
+  void* a6;   // [6 ng][nz][cy][kxp]  (z-inverse out) / [3 ng][nz][ny][kxp] (x out)
+  void* b6;   // [6 ng][nz][ny][kxp]  (y-inverse out) / [3 ng][nz][cy][kxp] (y-forward out)
   const void* tw_x;  // exp(-2 pi i m/nx), m < nx
   const void* tw_y;
   const void* tw_z;
@@ -55,7 +55,11 @@ struct PassArgs {
   const void* ifx;   // exp(-nu kx^2 dt/2) for p <= Kx
   const void* ify;   // ... per retained ky index
   const void* ifz;   // ... per retained kz index
-  double dt, nu;
+  double dt, nu, eta;
+  int ng;            // 3-component groups: 1 (HD: u) or 2 (MHD: u, B)
+  const void* jfx;   // exp(-eta k^2 dt/2) tables of the magnetic group
+  const void* jfy;
+  const void* jfz;
   const void* fbox;  // forcing box [3][2Fz+1][2Fy+1][Fx+1] or null
   int Fx, Fy, Fz;
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
@@ -80,8 +84,10 @@ template <typename T>
 cudaError_t launch_forcing_extent(const Geo& g, Spec f, int* ext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, void* box, cudaStream_t s);
+// Head of one diagnostics row: E, Omega, H, max|k.u|, E_B, H_c, H_m, spare.
+constexpr int DIAG_HEAD = 8;
 template <typename T>
-cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, cudaStream_t s);
+cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int mhd, cudaStream_t s);
 cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double* out, cudaStream_t s);
 
 // Plan internals used by the ensemble layer (ps_plan.cu).

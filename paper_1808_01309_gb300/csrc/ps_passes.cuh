@@ -102,7 +102,8 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // ---------------------------------------------------------------------------
 // zinv: curl + backward transform along z.  CTA = TX kx columns x NB retained
-// ky rows.  The CTA first copies its three input columns (retained kz rows
+// ky rows.  For MHD (a.ng = 2) the velocity group (u, omega) is followed by the
+// magnetic group (B, j = curl B), fields 6..11.  The CTA first copies its three input columns (retained kz rows
 // only) into shared memory with cp.async, so that all its HBM reads are in
 // flight at once; the six transforms then read the tile from shared memory.
 // Thread (line, j0, bb) holds kz indices n = j0 + m N/E.
@@ -123,7 +124,19 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   const bool bvalid = iy < g.cy;
   const int kx = blockIdx.x * TX + line;
   const int q = iy <= g.Ky ? iy : iy - g.cy;
-  const V* in = static_cast<const V*>(a.in.p);
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
+  const V* tw = static_cast<const V*>(a.tw_z);
+  V* out = static_cast<V*>(a.a6);
+  const T skx = T(kx) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
+  const long long fstride = (long long)g.nz * g.cy * g.kxp;
+  const long long zstride = (long long)g.cy * g.kxp;
+  const int cst = NB * g.cz * TX;                 // component stride in the tile
+  const V* tb = tile + bb * g.cz * TX + line;     // this thread's column
+  double esum = 0.0;
+  // one group of three components at a time: u (and then B for MHD)
+#pragma unroll 1
+  for (int grp = 0; grp < a.ng; ++grp) {
+  const V* in = static_cast<const V*>(a.in.p) + 3 * grp * a.in.cs;
   // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i)
   {
     const int per_c = NB * g.cz * TX;
@@ -142,15 +155,6 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
     cp_async_wait<0>();
     __syncthreads();
   }
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
-  const V* tw = static_cast<const V*>(a.tw_z);
-  V* out = static_cast<V*>(a.a6);
-  const T skx = T(kx) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
-  const long long fstride = (long long)g.nz * g.cy * g.kxp;
-  const long long zstride = (long long)g.cy * g.kxp;
-  const int cst = NB * g.cz * TX;                 // component stride in the tile
-  const V* tb = tile + bb * g.cz * TX + line;     // this thread's column
-  double esum = 0.0;
 #pragma unroll 1
   for (int f = 0; f < 6; ++f) {
     V x[E];
@@ -188,12 +192,14 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int n = j0 + m * (N / E);
-        out[f * fstride + n * zstride + (long long)iy * g.kxp + kx] = x[m];
+        out[(6 * grp + f) * fstride + n * zstride + (long long)iy * g.kxp + kx] = x[m];
       }
     }
   }
+  __syncthreads();  // the tile is restaged for the next group
+  }
   if (a.e_part) {
-    // energy 1/2 sum w |u|^2, w = 1 on the kx = 0 plane, else 2
+    // energy 1/2 sum w |u|^2 (+ |B|^2), w = 1 on the kx = 0 plane, else 2
     const double t = block_sum(esum * (kx == 0 ? 0.5 : 1.0), red);
     if (threadIdx.x == 0) a.e_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
@@ -241,12 +247,13 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yinv(const PassArgs a) 
 // transformed.  Thread j0 of a row's group of G threads holds the points
 // n = j0 + m N/E.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N>::xpass)
+template <typename T, int N, int NG>
+__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ? MinB<T, N>::xpass : 1)
     k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E;
   constexpr int LEN = N;
+  constexpr int NF = 6 * NG;  // input fields: u, omega (, B, j)
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ __align__(8) uint64_t bar[2];
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
   const int j0 = tid % G, rl = tid / G;
   const long long rows = (long long)g.nz * g.ny;
   const long long ngroups = (rows + rpc - 1) / rpc;
-  const int stage_elems = 6 * rpc * kxp;
+  const int stage_elems = NF * rpc * kxp;
   V* stage = reinterpret_cast<V*>(smraw);
   V* exbuf = stage + 2 * stage_elems;
   RowExchange<V> ex{exbuf + rl * LEN, rpc * LEN, 0};
@@ -271,13 +278,13 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
     mbar_fence_init();
   }
   __syncthreads();
-  // stage s <- the six input fields of row group grp (rpc contiguous rows each)
+  // stage s <- the NF input fields of row group grp (rpc contiguous rows each)
   auto issue = [&](long long grp, int s) {
     const long long r0 = grp * rpc;
     const long long nr = rows - r0 < rpc ? rows - r0 : rpc;
     const uint32_t bytes = (uint32_t)(nr * kxp * sizeof(V));
-    mbar_arrive_expect_tx(&bar[s], 6u * bytes);
-    for (int c = 0; c < 6; ++c)
+    mbar_arrive_expect_tx(&bar[s], (uint32_t)NF * bytes);
+    for (int c = 0; c < NF; ++c)
       bulk_g2s(stage + s * stage_elems + c * rpc * kxp, B + ((long long)c * rows + r0) * kxp, bytes, &bar[s]);
   };
   uint32_t ph0 = 0u, ph1 = 0u;  // completed-phase parity of each stage barrier
@@ -305,16 +312,18 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
     const long long row = it * rpc + rl;
     const bool rvalid = row < rows;
     const V* st = stage + s * stage_elems + rl * kxp;
-    V U[3][E];
+    // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c
+    V U[3 * NG][E];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const V* pu = st + c * rpc * kxp;
-      const V* pw = st + (c + 3) * rpc * kxp;
+    for (int c = 0; c < 3 * NG; ++c) {
+      const int fr = (c < 3) ? c : 6 + (c - 3);  // real part field
+      const V* pu = st + fr * rpc * kxp;
+      const V* pw = st + (fr + 3) * rpc * kxp;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int n = j0 + m * (N / E);
-        // full spectrum C[n] = u_hat[n] + i w_hat[n]; for n > N/2 the entries
-        // are conj(u_hat[N-n]) + i conj(w_hat[N-n]) (real u and w)
+        // full spectrum C[n] = a_hat[n] + i b_hat[n]; for n > N/2 the entries
+        // are conj(a_hat[N-n]) + i conj(b_hat[N-n]) (real a and b)
         const bool hi = n > N / 2;
         const int p = hi ? N - n : n;
         V v = czero<V>();
@@ -330,46 +339,68 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), MinB<T, N
       }
       line_fft<N, E, +1>(U[c], j0, tw, ex);
     }
-    // n = u x omega at the thread's points; u_c = Re U[c], omega_c = Im U[c]
-    V F1[E], F2[E];
+    // products at the thread's points (real part = field, imaginary = curl)
+    V F[NG == 1 ? 2 : 3][E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
       const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
       umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
-      F1[m] = mk<V>(uy * wz - uz * wy, uz * wx - ux * wz);
-      F2[m] = mk<V>(ux * wy - uy * wx, T(0));
+      T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+      if constexpr (NG == 1) {
+        F[0][m] = mk<V>(nx, ny);
+        F[1][m] = mk<V>(nz, T(0));
+      } else {
+        const T bx = U[3][m].x, by = U[4][m].x, bz = U[5][m].x;
+        const T jx = U[3][m].y, jy = U[4][m].y, jz = U[5][m].y;
+        nx += jy * bz - jz * by;  // + j x B
+        ny += jz * bx - jx * bz;
+        nz += jx * by - jy * bx;
+        const T ex_ = uy * bz - uz * by, ey_ = uz * bx - ux * bz, ez_ = ux * by - uy * bx;  // u x B
+        F[0][m] = mk<V>(nx, ny);
+        F[1][m] = mk<V>(nz, ex_);
+        F[2][m] = mk<V>(ey_, ez_);
+      }
     }
     if (!a.xdiag) {  // uniform across the grid
-      line_fft<N, E, -1>(F1, j0, tw, ex);
-      line_fft<N, E, -1>(F2, j0, tw, ex);
+      constexpr int NFW = NG == 1 ? 2 : 3;
+#pragma unroll
+      for (int w = 0; w < NFW; ++w) line_fft<N, E, -1>(F[w], j0, tw, ex);
       const long long rrow = rvalid ? row : 0;
-      V* cx = C + (0 * rows + rrow) * kxp;
-      V* cy = C + (1 * rows + rrow) * kxp;
-      V* cz = C + (2 * rows + rrow) * kxp;
-      // split F1 = DFT(n_x) + i DFT(n_y) using the mirrored entry F1[N-k]
-#pragma unroll
-      for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F1[m]);
-      ex.sync();
       const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
+      // split each packed transform F = DFT(a) + i DFT(b) of two real fields
+      // with its mirrored entry F[N-k]; for HD the second line has b = 0
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = j0 + m * (N / E);
-        if (rvalid && k < kend) {
-          V nx = czero<V>(), ny = czero<V>(), nz = czero<V>();
-          if (k <= g.Kx) {
-            const V Fk = F1[m];
-            const V Fm = cconj(ex.get(k == 0 ? 0 : N - k));
-            nx = cscale(cadd(Fk, Fm), T(0.5));
-            ny = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
-            nz = F2[m];
-          }
-          cx[k] = nx;
-          cy[k] = ny;
-          cz[k] = nz;
+      for (int w = 0; w < NFW; ++w) {
+        const bool split = (NG == 2) || w == 0;
+        V* ca = C + ((long long)(2 * w) * rows + rrow) * kxp;
+        V* cb = C + ((long long)(2 * w + 1) * rows + rrow) * kxp;
+        if (split) {
+#pragma unroll
+          for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F[w][m]);
+          ex.sync();
         }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int k = j0 + m * (N / E);
+          if (rvalid && k < kend) {
+            V va = czero<V>(), vb = czero<V>();
+            if (k <= g.Kx) {
+              const V Fk = F[w][m];
+              if (split) {
+                const V Fm = cconj(ex.get(k == 0 ? 0 : N - k));
+                va = cscale(cadd(Fk, Fm), T(0.5));
+                vb = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
+              } else {
+                va = Fk;
+              }
+            }
+            ca[k] = va;
+            if (split) cb[k] = vb;
+          }
+        }
+        if (split) ex.flip();
       }
-      ex.flip();
     }
     __syncthreads();  // stage s and the exchange buffers are free again
     s ^= 1;
@@ -447,122 +478,141 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* tw = static_cast<const V*>(a.tw_z);
   const long long cs_in = (long long)g.nz * g.cy * g.kxp;
-  const V* in = static_cast<const V*>(a.b6) + (long long)(colin ? iy : 0) * g.kxp + (colin ? kx : 0);
-  V X[3][E];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const long long n = j0 + m * (N / E);
-      X[c][m] = colin ? ldv(in + c * cs_in + n * g.cy * g.kxp) : czero<V>();
-    }
-    line_fft<N, E, -1>(X[c], j0, tw, ex);
-  }
   const T inv = T(1.0 / ((double)g.nx * g.ny * g.nz));
   const T kxv = T(kx) * T(g.sx), kyv = T(q) * T(g.sy), sz = T(g.sz);
   const V* un = static_cast<const V*>(a.u_n.p);
   const V* fb = static_cast<const V*>(a.fbox);
-  const T* ifx = static_cast<const T*>(a.ifx);
-  const T* ify = static_cast<const T*>(a.ify);
-  const T* ifz = static_cast<const T*>(a.ifz);
-  const T dt = T(a.dt), nu = T(a.nu);
-  const T ey = (a.mode != ZF_RHS && bret) ? ify[iy] : T(0);
-  const T exx = (a.mode != ZF_RHS && kx <= g.Kx) ? ifx[kx] : T(0);
+  const T dt = T(a.dt);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
   const long long fcs = (long long)g.nz * g.ny * g.nh;   // caller layout component stride
+  // group 0: velocity (forcing, Leray projection, viscosity nu)
+  // group 1 (MHD): magnetic field (curl of the transformed u x B, diffusivity eta)
+#pragma unroll 1
+  for (int grp = 0; grp < a.ng; ++grp) {
+    const bool mag = grp == 1;
+    const T* ifx = static_cast<const T*>(mag ? a.jfx : a.ifx);
+    const T* ify = static_cast<const T*>(mag ? a.jfy : a.ify);
+    const T* ifz = static_cast<const T*>(mag ? a.jfz : a.ifz);
+    const T damp = T(mag ? a.eta : a.nu);
+    const V* in = static_cast<const V*>(a.b6) + 3 * grp * cs_in + (long long)(colin ? iy : 0) * g.kxp +
+                  (colin ? kx : 0);
+    V X[3][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int n = j0 + m * (N / E);
-    const int r = sidx(n, N);
-    const bool keep = bret && kept(g, kx, q, r);
-    V o[3] = {czero<V>(), czero<V>(), czero<V>()};
-    V v0 = czero<V>(), v1 = czero<V>(), v2 = czero<V>();
-    long long ci = 0;
-    if (keep) {
-      const int iz = rowof(r, g.cz);
-      ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
-      v0 = cscale(X[0][m], inv);
-      v1 = cscale(X[1][m], inv);
-      v2 = cscale(X[2][m], inv);
-      if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
-        const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
-        const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
-        const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
-        v0 = cadd(v0, ldv(fb + fo));
-        v1 = cadd(v1, ldv(fb + fo + fcs2));
-        v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
-      }
-      const T kzv = T(r) * sz;
-      const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-      if (k2 > T(0)) {
-        // Leray projection v - k (k.v)/|k|^2
-        const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
-        const T ik2 = T(1) / k2;
-        v0 = csub(v0, cscale(kd, kxv * ik2));
-        v1 = csub(v1, cscale(kd, kyv * ik2));
-        v2 = csub(v2, cscale(kd, kzv * ik2));
-      } else {
-        v0 = v1 = v2 = czero<V>();
-      }
-      if (a.mode == ZF_RHS) {
-        const V* pu = un + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs + (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
-        const T vk = nu * k2;
-        o[0] = csub(v0, cscale(ldv(pu), vk));
-        o[1] = csub(v1, cscale(ldv(pu + a.u_n.cs), vk));
-        o[2] = csub(v2, cscale(ldv(pu + 2 * a.u_n.cs), vk));
-      } else {
-        // Lawson RK with E = exp(-nu |k|^2 dt/2) = ex(p) ey(q) ez(r)
-        const T Ef = exx * ey * ifz[iz];
-        const T E2 = Ef * Ef;
-        const V* pu = un + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs + (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
-        V* acc = static_cast<V*>(a.acc) + ci;
-        V* nxt = static_cast<V*>(a.nxt) + ci;
-        const V kk[3] = {v0, v1, v2};
+    for (int c = 0; c < 3; ++c) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const V u = ldv(pu + c * a.u_n.cs);
-          const V k = kk[c];
-          switch (a.mode) {
-            case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
-              acc[c * ccs] = cscale(k, E2);
-              nxt[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), Ef);
-              break;
-            case ZF_RK4_2: {  // acc += 2 E k2 ; next = E u + dt/2 k2
-              const V ac = acc[c * ccs];
-              acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
-              nxt[c * ccs] = cadd(cscale(u, Ef), cscale(k, T(0.5) * dt));
-              break;
+      for (int m = 0; m < E; ++m) {
+        const long long n = j0 + m * (N / E);
+        X[c][m] = colin ? ldv(in + c * cs_in + n * g.cy * g.kxp) : czero<V>();
+      }
+      line_fft<N, E, -1>(X[c], j0, tw, ex);
+    }
+    const T ey = (a.mode != ZF_RHS && bret) ? ify[iy] : T(0);
+    const T exx = (a.mode != ZF_RHS && kx <= g.Kx) ? ifx[kx] : T(0);
+    const int c0 = 3 * grp;  // state component of this group's first field
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = j0 + m * (N / E);
+      const int r = sidx(n, N);
+      const bool keep = bret && kept(g, kx, q, r);
+      V o[3] = {czero<V>(), czero<V>(), czero<V>()};
+      V v0 = czero<V>(), v1 = czero<V>(), v2 = czero<V>();
+      long long ci = 0;
+      if (keep) {
+        const int iz = rowof(r, g.cz);
+        ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
+        v0 = cscale(X[0][m], inv);
+        v1 = cscale(X[1][m], inv);
+        v2 = cscale(X[2][m], inv);
+        const T kzv = T(r) * sz;
+        const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+        if (!mag) {
+          if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
+            const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
+            const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
+            const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
+            v0 = cadd(v0, ldv(fb + fo));
+            v1 = cadd(v1, ldv(fb + fo + fcs2));
+            v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
+          }
+          if (k2 > T(0)) {
+            // Leray projection v - k (k.v)/|k|^2
+            const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
+            const T ik2 = T(1) / k2;
+            v0 = csub(v0, cscale(kd, kxv * ik2));
+            v1 = csub(v1, cscale(kd, kyv * ik2));
+            v2 = csub(v2, cscale(kd, kzv * ik2));
+          } else {
+            v0 = v1 = v2 = czero<V>();
+          }
+        } else {
+          // curl(u x B): i k x v
+          const V w0 = cmul_i(csub(cscale(v2, kyv), cscale(v1, kzv)));
+          const V w1 = cmul_i(csub(cscale(v0, kzv), cscale(v2, kxv)));
+          const V w2 = cmul_i(csub(cscale(v1, kxv), cscale(v0, kyv)));
+          v0 = w0;
+          v1 = w1;
+          v2 = w2;
+        }
+        const V* pu = un + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
+                      (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
+        if (a.mode == ZF_RHS) {
+          const T vk = damp * k2;
+          o[0] = csub(v0, cscale(ldv(pu), vk));
+          o[1] = csub(v1, cscale(ldv(pu + a.u_n.cs), vk));
+          o[2] = csub(v2, cscale(ldv(pu + 2 * a.u_n.cs), vk));
+        } else {
+          // Lawson RK with E = exp(-nu |k|^2 dt/2) = ex(p) ey(q) ez(r)
+          const T Ef = exx * ey * ifz[iz];
+          const T E2 = Ef * Ef;
+          V* acc = static_cast<V*>(a.acc) + c0 * ccs + ci;
+          V* nxt = static_cast<V*>(a.nxt) + c0 * ccs + ci;
+          const V kk[3] = {v0, v1, v2};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const V u = ldv(pu + c * a.u_n.cs);
+            const V k = kk[c];
+            switch (a.mode) {
+              case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
+                acc[c * ccs] = cscale(k, E2);
+                nxt[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), Ef);
+                break;
+              case ZF_RK4_2: {  // acc += 2 E k2 ; next = E u + dt/2 k2
+                const V ac = acc[c * ccs];
+                acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
+                nxt[c * ccs] = cadd(cscale(u, Ef), cscale(k, T(0.5) * dt));
+                break;
+              }
+              case ZF_RK4_3: {  // acc += 2 E k3 ; next = E^2 u + dt E k3
+                const V ac = acc[c * ccs];
+                acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
+                nxt[c * ccs] = cadd(cscale(u, E2), cscale(k, dt * Ef));
+                break;
+              }
+              case ZF_RK4_4: {  // u+ = E^2 u + dt/6 (acc + k4)
+                const V ac = acc[c * ccs];
+                o[c] = cadd(cscale(u, E2), cscale(cadd(ac, k), dt / T(6)));
+                break;
+              }
+              case ZF_RK2_1:  // next = E^2 (u + dt k1) ; acc = E^2 (u + dt/2 k1)
+                nxt[c * ccs] = cscale(cadd(u, cscale(k, dt)), E2);
+                acc[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), E2);
+                break;
+              case ZF_RK2_2: {  // u+ = acc + dt/2 k2
+                const V ac = acc[c * ccs];
+                o[c] = cadd(ac, cscale(k, T(0.5) * dt));
+                break;
+              }
+              default: break;
             }
-            case ZF_RK4_3: {  // acc += 2 E k3 ; next = E^2 u + dt E k3
-              const V ac = acc[c * ccs];
-              acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
-              nxt[c * ccs] = cadd(cscale(u, E2), cscale(k, dt * Ef));
-              break;
-            }
-            case ZF_RK4_4: {  // u+ = E^2 u + dt/6 (acc + k4)
-              const V ac = acc[c * ccs];
-              o[c] = cadd(cscale(u, E2), cscale(cadd(ac, k), dt / T(6)));
-              break;
-            }
-            case ZF_RK2_1:  // next = E^2 (u + dt k1) ; acc = E^2 (u + dt/2 k1)
-              nxt[c * ccs] = cscale(cadd(u, cscale(k, dt)), E2);
-              acc[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), E2);
-              break;
-            case ZF_RK2_2: {  // u+ = acc + dt/2 k2
-              const V ac = acc[c * ccs];
-              o[c] = cadd(ac, cscale(k, T(0.5) * dt));
-              break;
-            }
-            default: break;
           }
         }
       }
-    }
-    if (full && bvalid && kx < g.nh) {
-      V* po = static_cast<V*>(a.out_full) + ((long long)n * g.ny + bidx) * g.nh + kx;
-      po[0] = o[0];
-      po[fcs] = o[1];
-      po[2 * fcs] = o[2];
+      if (full && bvalid && kx < g.nh) {
+        V* po = static_cast<V*>(a.out_full) + c0 * fcs + ((long long)n * g.ny + bidx) * g.nh + kx;
+        po[0] = o[0];
+        po[fcs] = o[1];
+        po[2 * fcs] = o[2];
+      }
     }
   }
 }
@@ -595,39 +645,45 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yinv<T, N>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 6);
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 6 * a.ng);
   k_yinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
-// Shared memory of the x pass for rpc rows: two input stages of 6 rows each
-// and the double-buffered exchange.
+// Shared memory of the x pass for rpc rows: two input stages of 6 ng rows
+// each and the double-buffered exchange.
 template <typename T, int N>
-size_t xpass_smem(const Geo& g, int rpc) {
+size_t xpass_smem(const Geo& g, int rpc, int ng) {
   using V = typename cplx<T>::type;
-  return (2ull * 6 * rpc * g.kxp + 2ull * rpc * N) * sizeof(V);
+  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N) * sizeof(V);
 }
 
-template <typename T, int N>
-cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
+template <typename T, int N, int NG>
+cudaError_t xpass_ng(const PassArgs& a, cudaStream_t s) {
   constexpr int E = EOf<T, N>::v, G = N / E;
   // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
   int rpc = RPCOf<T, N>::v;
-  while (rpc > 1 && xpass_smem<T, N>(a.g, rpc) > 113 * 1024) rpc /= 2;
+  while (rpc > 1 && xpass_smem<T, N>(a.g, rpc, NG) > 113 * 1024) rpc /= 2;
   if (a.xrpc > 0 && a.xrpc < rpc) rpc = a.xrpc;  // tuned (smaller) row groups
-  const size_t smem = xpass_smem<T, N>(a.g, rpc);
-  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = xpass_smem<T, N>(a.g, rpc, NG);
+  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, N>, rpc * G, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, N, NG>, rpc * G, smem)) !=
+      cudaSuccess)
     return e;
   const long long rows = (long long)a.g.nz * a.g.ny;
   const long long groups = (rows + rpc - 1) / rpc;
   long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > groups) grid = groups;
-  k_xpass<T, N><<<(unsigned)grid, rpc * G, smem, s>>>(a, rpc);
+  k_xpass<T, N, NG><<<(unsigned)grid, rpc * G, smem, s>>>(a, rpc);
   return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
+  return a.ng == 2 ? xpass_ng<T, N, 2>(a, s) : xpass_ng<T, N, 1>(a, s);
 }
 
 template <typename T, int N>
@@ -637,7 +693,7 @@ cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 3);
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 3 * a.ng);
   k_yfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
 }

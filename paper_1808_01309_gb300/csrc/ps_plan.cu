@@ -51,7 +51,8 @@ ps_status validate(const ps_config* c) {
     return fail(PS_ERR_INVALID_ARG, "box lengths must be finite and positive");
   if (c->prec != PS_FP32 && c->prec != PS_FP64) return fail(PS_ERR_INVALID_ARG, "unknown precision");
   if (c->eq != PS_HD && c->eq != PS_MHD) return fail(PS_ERR_INVALID_ARG, "unknown equation set");
-  if (c->eq == PS_MHD) return fail(PS_ERR_UNSUPPORTED, "MHD is not implemented in this build");
+  if (c->eq == PS_MHD && !(std::isfinite(c->eta) && c->eta >= 0))
+    return fail(PS_ERR_INVALID_ARG, "eta must be finite and >= 0");
   if (c->dealias != PS_DEALIAS_CUBIC && c->dealias != PS_DEALIAS_SPHERICAL && c->dealias != PS_DEALIAS_NONE)
     return fail(PS_ERR_INVALID_ARG, "unknown dealias rule");
   if (c->rk_order != 2 && c->rk_order != 4) return fail(PS_ERR_INVALID_ARG, "rk_order must be 2 or 4");
@@ -87,18 +88,21 @@ struct Sizes {
   size_t state;    // caller-layout field (elements)
 };
 
-Sizes sizes(const Geo& g, ps_precision p) {
+// ng = number of 3-component groups (1: HD velocity; 2: MHD velocity and field)
+Sizes sizes(const Geo& g, ps_precision p, int ng) {
   Sizes s{};
   s.vb = p == PS_FP32 ? 8 : 16;
   const size_t kxp = g.kxp;
-  const size_t a1 = 6ull * g.nz * g.cy * kxp, a2 = 3ull * g.nz * g.ny * kxp;
-  const size_t b1 = 6ull * g.nz * g.ny * kxp, b2 = 3ull * g.nz * g.cy * kxp;
+  const size_t a1 = 6ull * ng * g.nz * g.cy * kxp, a2 = 3ull * ng * g.nz * g.ny * kxp;
+  const size_t b1 = 6ull * ng * g.nz * g.ny * kxp, b2 = 3ull * ng * g.nz * g.cy * kxp;
   s.a6 = a1 > a2 ? a1 : a2;
   s.b6 = b1 > b2 ? b1 : b2;
-  s.cmp = 3ull * g.cz * g.cy * kxp;
-  s.state = 3ull * g.nz * g.ny * g.nh;
+  s.cmp = 3ull * ng * g.cz * g.cy * kxp;
+  s.state = 3ull * ng * g.nz * g.ny * g.nh;
   return s;
 }
+
+int groups_of(const ps_config* c) { return c->eq == PS_MHD ? 2 : 1; }
 
 int nshells_of(const Geo& g) {
   const double kx = g.Kx * g.sx, ky = g.Ky * g.sy, kz = g.Kz * g.sz;
@@ -122,6 +126,7 @@ struct ps_plan {
   cudaStream_t stream = nullptr;
   int device = 0;
   int xrpc = 0;  // x-pass rows per CTA override (0 = automatic)
+  int ng = 1;    // 3-component groups: 1 HD, 2 MHD
   Geo g{};
   Sizes sz{};
   void* a6 = nullptr;
@@ -251,6 +256,12 @@ PassArgs base_args(ps_plan* p) {
   a.ifx = p->iftab;
   a.ify = static_cast<char*>(p->iftab) + tb * p->g.cx;
   a.ifz = static_cast<char*>(p->iftab) + tb * (p->g.cx + p->g.cy);
+  const size_t half = tb * (p->g.cx + p->g.cy + p->g.cz);
+  a.jfx = static_cast<char*>(p->iftab) + half;
+  a.jfy = static_cast<char*>(p->iftab) + half + tb * p->g.cx;
+  a.jfz = static_cast<char*>(p->iftab) + half + tb * (p->g.cx + p->g.cy);
+  a.ng = p->ng;
+  a.eta = p->cfg.eta;
   a.nxt = p->nxt;
   a.acc = p->acc;
   a.err = p->err;
@@ -309,6 +320,12 @@ ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
     if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, p->cfg.nu, dt, p->iftab, p->stream); },
                     "integrating-factor tables")) != PS_OK)
       return s;
+    if (p->ng == 2) {
+      void* jt = static_cast<char*>(p->iftab) + sizeof(T) * (p->g.cx + p->g.cy + p->g.cz);
+      if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, p->cfg.eta, dt, jt, p->stream); },
+                      "integrating-factor tables")) != PS_OK)
+        return s;
+    }
     p->if_dt = dt;
   }
   PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "reset max|u|");
@@ -330,11 +347,11 @@ ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
 template <typename T>
 ps_status do_diag(ps_plan* p, const void* uhat, double* host_out) {
   ps_status s;
-  const int w = 4 + p->nshells;
+  const int w = DIAG_HEAD + p->nshells;
   PS_CU(cudaMemsetAsync(p->dpart, 0, sizeof(double) * (size_t)p->g.cz * w, p->stream), "diag reset");
   PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "diag reset");
   const Spec u = caller_spec(p->g, uhat);
-  if ((s = launch(p, 5, [&] { return launch_diag_spectral<T>(p->g, u, p->dpart, p->nshells, p->stream); },
+  if ((s = launch(p, 5, [&] { return launch_diag_spectral<T>(p->g, u, p->dpart, p->nshells, p->ng == 2, p->stream); },
                   "spectral diagnostics")) != PS_OK)
     return s;
   if ((s = launch(p, 5, [&] { return launch_diag_final(p->dpart, p->g.cz, p->nshells, p->dout, p->stream); },
@@ -451,10 +468,10 @@ ps_status ps_plan_workspace_bytes(const ps_config* cfg, size_t* bytes) {
   if (s != PS_OK) return s;
   if (!bytes) return fail(PS_ERR_INVALID_ARG, "bytes is NULL");
   const Geo g = make_geo(cfg);
-  const Sizes z = sizes(g, cfg->prec);
+  const Sizes z = sizes(g, cfg->prec, groups_of(cfg));
   const size_t tb = cfg->prec == PS_FP32 ? 4 : 8;
-  *bytes = z.vb * (z.a6 + z.b6 + 2 * z.cmp + (size_t)(g.nx + g.ny + g.nz)) + tb * (g.cx + g.cy + g.cz) +
-           sizeof(double) * (size_t)(g.cz * (g.kxp + 4 + nshells_of(g)) + 16);
+  *bytes = z.vb * (z.a6 + z.b6 + 2 * z.cmp + (size_t)(g.nx + g.ny + g.nz)) + 2 * tb * (g.cx + g.cy + g.cz) +
+           sizeof(double) * (size_t)(g.cz * (g.kxp + DIAG_HEAD + nshells_of(g)) + 16);
   return PS_OK;
 }
 
@@ -468,7 +485,8 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   p->cfg = *cfg;
   p->stream = static_cast<cudaStream_t>(cuda_stream);
   p->g = make_geo(cfg);
-  p->sz = sizes(p->g, cfg->prec);
+  p->ng = groups_of(cfg);
+  p->sz = sizes(p->g, cfg->prec, p->ng);
   p->nshells = nshells_of(p->g);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
@@ -491,7 +509,7 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   ALLOC(p->nxt, p->sz.cmp * vb, "stage input");
   ALLOC(p->acc, p->sz.cmp * vb, "stage accumulator");
   ALLOC(p->tw, vb * (size_t)(p->g.nx + p->g.ny + p->g.nz), "twiddles");
-  ALLOC(p->iftab, tb * (size_t)(p->g.cx + p->g.cy + p->g.cz), "integrating factors");
+  ALLOC(p->iftab, 2 * tb * (size_t)(p->g.cx + p->g.cy + p->g.cz), "integrating factors");
   int nb = cfg->prec == PS_FP32 ? zinv_blocks<float>(p->g) : zinv_blocks<double>(p->g);
   p->n_epart = nb;
   ALLOC(p->e_part, sizeof(double) * (size_t)(nb > 0 ? nb : 1), "energy partials");
@@ -499,8 +517,8 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   ALLOC(p->umax2, sizeof(unsigned long long), "max|u|");
   ALLOC(p->ext, sizeof(int) * 4, "forcing extent");
   ALLOC(p->err, sizeof(int), "error word");
-  ALLOC(p->dpart, sizeof(double) * (size_t)p->g.cz * (4 + p->nshells), "diagnostic partials");
-  ALLOC(p->dout, sizeof(double) * (size_t)(4 + p->nshells), "diagnostics");
+  ALLOC(p->dpart, sizeof(double) * (size_t)p->g.cz * (DIAG_HEAD + p->nshells), "diagnostic partials");
+  ALLOC(p->dout, sizeof(double) * (size_t)(DIAG_HEAD + p->nshells), "diagnostics");
 #undef ALLOC
   // Clean scratch once so that padding columns never hold uninitialised bits.
   e = cudaMemsetAsync(p->a6, 0, p->sz.a6 * vb, p->stream);
@@ -587,7 +605,7 @@ ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out)
   if (!std::isfinite(cfl)) return fail(PS_ERR_INVALID_ARG, "cfl must be finite");
   if (out->spectrum && out->nshells < 0) return fail(PS_ERR_INVALID_ARG, "negative spectrum capacity");
   DeviceGuard dg(p->device);
-  std::vector<double> h(5 + p->nshells);
+  std::vector<double> h(DIAG_HEAD + 1 + p->nshells);
   ps_status s = p->cfg.prec == PS_FP32 ? do_diag<float>(p, uhat, h.data()) : do_diag<double>(p, uhat, h.data());
   if (s != PS_OK) return s;
   if ((s = check_device_error(p)) != PS_OK) return s;
@@ -595,16 +613,19 @@ ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out)
   out->enstrophy = h[1];
   out->helicity = h[2];
   out->max_div = h[3];
-  out->max_u = h[4 + p->nshells];
+  out->max_u = h[DIAG_HEAD + p->nshells];
+  out->magnetic_energy = h[4];
+  out->cross_helicity = h[5];
+  out->magnetic_helicity = h[6];
   const double dmin = std::fmin(p->cfg.lx / p->cfg.nx, std::fmin(p->cfg.ly / p->cfg.ny, p->cfg.lz / p->cfg.nz));
   out->cfl_dt = out->max_u > 0 ? cfl * dmin / out->max_u : INFINITY;
   out->time = p->time;
   if (out->spectrum) {
     const int n = out->nshells < p->nshells ? out->nshells : p->nshells;
-    for (int i = 0; i < n; ++i) out->spectrum[i] = h[4 + i];
+    for (int i = 0; i < n; ++i) out->spectrum[i] = h[DIAG_HEAD + i];
   }
   out->nshells = p->nshells;
-  for (int i = 0; i < 5 + p->nshells; ++i)
+  for (int i = 0; i < DIAG_HEAD + 1 + p->nshells; ++i)
     if (!std::isfinite(h[i])) return fail(PS_ERR_NONFINITE, "non-finite diagnostic");
   return PS_OK;
 }

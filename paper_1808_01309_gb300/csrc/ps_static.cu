@@ -147,6 +147,7 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   a.tw_y = tw + g.nx;
   a.tw_z = tw + g.nx + g.ny;
   a.nu = c->nu;
+  a.ng = 1;  // velocity only (HD)
   a.err = reinterpret_cast<int*>(p + a_b + b_b + tw_b + box_b);
   a.Fx = a.Fy = a.Fz = -1;
   Spec in;

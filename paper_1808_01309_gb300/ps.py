@@ -73,6 +73,8 @@ class PsDiag(ctypes.Structure):
         ("max_div", ctypes.c_double), ("max_u", ctypes.c_double), ("cfl_dt", ctypes.c_double),
         ("time", ctypes.c_double),
         ("spectrum", ctypes.POINTER(ctypes.c_double)), ("nshells", ctypes.c_int),
+        ("magnetic_energy", ctypes.c_double), ("cross_helicity", ctypes.c_double),
+        ("magnetic_helicity", ctypes.c_double),
     ]
 
 
@@ -207,7 +209,8 @@ def ps_diagnostics(plan, uhat, cfl: float = 0.5, nshells: int = 4096) -> dict:
     d.nshells = nshells
     st = load().ps_diagnostics(plan, _ptr(uhat), float(cfl), ctypes.byref(d))
     out = dict(energy=d.energy, enstrophy=d.enstrophy, helicity=d.helicity, max_div=d.max_div,
-               max_u=d.max_u, cfl_dt=d.cfl_dt, time=d.time,
+               max_u=d.max_u, cfl_dt=d.cfl_dt, time=d.time, magnetic_energy=d.magnetic_energy,
+               cross_helicity=d.cross_helicity, magnetic_helicity=d.magnetic_helicity,
                spectrum=[spec[i] for i in range(min(d.nshells, nshells))], status=st)
     if st not in (PS_OK, PS_ERR_NONFINITE):
         _check(st)
@@ -272,7 +275,7 @@ class Plan:
     @property
     def shape(self):
         c = self.cfg
-        return (3, c.nz, c.ny, c.nx // 2 + 1)
+        return (6 if c.eq == Equations.MHD else 3, c.nz, c.ny, c.nx // 2 + 1)
 
     def _check_field(self, t):
         import torch

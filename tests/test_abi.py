@@ -63,11 +63,17 @@ def test_invalid_configs_are_rejected_before_any_cuda_call(ps, bad):
         ps.ps_plan_workspace_bytes(cfg)
 
 
-def test_mhd_is_reported_unsupported(ps):
-    cfg = ps.make_config(32, eq=ps.Equations.MHD)
+def test_mhd_rejects_negative_diffusivity(ps):
+    cfg = ps.make_config(32, eq=ps.Equations.MHD, eta=-1.0)
     with pytest.raises(ps.PsError) as e:
         ps.ps_plan_create(cfg)
-    assert e.value.status == ps.PS_ERR_UNSUPPORTED
+    assert e.value.status == ps.PS_ERR_INVALID_ARG
+
+
+def test_mhd_workspace_is_about_twice_hd(ps):
+    hd = ps.ps_plan_workspace_bytes(ps.make_config(128))
+    mhd = ps.ps_plan_workspace_bytes(ps.make_config(128, eq=ps.Equations.MHD))
+    assert 1.9 < mhd / hd < 2.1
 
 
 def test_null_arguments(ps):
