@@ -209,10 +209,23 @@ template <typename T, int N> struct EOf {
                            : (sizeof(T) == 4 && (N == 16 || N == 128 || N == 256 || N == 1024)) ? 16 : 8;
 };
 
-// Twiddle exp(DIR 2 pi i m/N) from the table tw[m] = exp(-2 pi i m/N).
-template <int DIR, typename V>
-__device__ __forceinline__ V twiddle(const V* __restrict__ tw, int idx) {
-  V w = __ldg(tw + idx);
+// Twiddle tables tw[m] = exp(-2 pi i m/N): read-only global memory (through
+// the non-coherent path) or a copy in shared memory.
+template <typename V>
+struct GlobalTw {
+  const V* __restrict__ p;
+  __device__ __forceinline__ V operator[](int i) const { return __ldg(p + i); }
+};
+template <typename V>
+struct SharedTw {
+  const V* p;
+  __device__ __forceinline__ V operator[](int i) const { return p[i]; }
+};
+
+// Twiddle exp(DIR 2 pi i m/N).
+template <int DIR, typename V, class TW>
+__device__ __forceinline__ V twiddle(const TW& tw, int idx) {
+  V w = tw[idx];
   return DIR > 0 ? cconj(w) : w;
 }
 
@@ -221,8 +234,8 @@ __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int idx) {
 // W_{NS R}^{r k} (k = j mod NS), transforms, and writes y[(j-k) R + k + r NS].
 // Thread j0 owns butterflies j = j0 + b N/E, b < E/R, whose inputs are its
 // registers b + r E/R.  The last stage leaves y[j + r N/R] in the same slots.
-template <int N, int E, int R, int NS, int DIR, bool LAST, typename V, class X>
-__device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ tw, X& ex) {
+template <int N, int E, int R, int NS, int DIR, bool LAST, typename V, class TW, class X>
+__device__ __forceinline__ void stage(V (&a)[E], int j0, const TW& tw, X& ex) {
   constexpr int NB = E / R;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -233,7 +246,7 @@ __device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ t
     for (int r = 0; r < R; ++r) x[r] = a[b + r * NB];
     if constexpr (NS > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<DIR>(tw, r * k * (N / (NS * R))));
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<DIR, V>(tw, r * k * (N / (NS * R))));
     }
     dft<R, DIR>(x);
     if constexpr (LAST) {
@@ -253,8 +266,9 @@ __device__ __forceinline__ void stage(V (&a)[E], int j0, const V* __restrict__ t
 }
 
 // Full length-N line transform on the E registers of thread j0 (see header).
-template <int N, int E, int DIR, typename V, class X>
-__device__ __forceinline__ void line_fft(V (&a)[E], int j0, const V* __restrict__ tw, X& ex) {
+// Full length-N line transform with a twiddle accessor (GlobalTw, SharedTw).
+template <int N, int E, int DIR, typename V, class TW, class X>
+__device__ __forceinline__ void line_fft_tw(V (&a)[E], int j0, const TW& tw, X& ex) {
   using S = Sched<N, E>;
   if constexpr (S::S == 1) {
     stage<N, E, S::R0, 1, DIR, true>(a, j0, tw, ex);
@@ -271,6 +285,13 @@ __device__ __forceinline__ void line_fft(V (&a)[E], int j0, const V* __restrict_
     stage<N, E, S::R2, S::R0 * S::R1, DIR, false>(a, j0, tw, ex);
     stage<N, E, S::R3, S::R0 * S::R1 * S::R2, DIR, true>(a, j0, tw, ex);
   }
+}
+
+// Full length-N line transform with twiddles read from global memory.
+template <int N, int E, int DIR, typename V, class X>
+__device__ __forceinline__ void line_fft(V (&a)[E], int j0, const V* __restrict__ twp, X& ex) {
+  const GlobalTw<V> tw{twp};
+  line_fft_tw<N, E, DIR>(a, j0, tw, ex);
 }
 
 // Shared-memory exchange for lines laid out as columns: element n of line l
@@ -315,6 +336,8 @@ struct RowExchange {
   V* buf;
   int bufsz;
   int par;
+  int bar_id = 0;   // > 0: named barrier of this row's nthr threads
+  int nthr = 0;
   template <int NS, int R>
   __device__ __forceinline__ static int pos(int n) {
     if constexpr (NS == 1) {
@@ -330,7 +353,11 @@ struct RowExchange {
   __device__ __forceinline__ void put(int n, V v) { buf[par * bufsz + pos<NS, R>(n)] = v; }
   template <int NS = 0, int R = 0>
   __device__ __forceinline__ V get(int n) const { return buf[par * bufsz + pos<NS, R>(n)]; }
-  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ void sync() {
+    if (bar_id > 0) asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+    else if (bar_id < 0) __syncwarp();
+    else __syncthreads();
+  }
   __device__ __forceinline__ void flip() { par ^= 1; }
 };
 

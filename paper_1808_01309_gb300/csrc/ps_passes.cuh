@@ -26,7 +26,10 @@
 namespace ps {
 
 // kx columns per CTA in the strided passes: 64-byte row segments
-template <typename T> struct TXOf { static constexpr int v = sizeof(T) == 4 ? 8 : 4; };
+#ifndef PS_TX32
+#define PS_TX32 8
+#endif
+template <typename T> struct TXOf { static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4; };
 // lines batched per CTA in the strided passes (about 256 threads per CTA)
 template <typename T, int N> struct NBOf {
   static constexpr int G = N / EOf<T, N>::v;
@@ -43,6 +46,12 @@ template <typename T, int N> struct RPCOf {
 };
 
 // Minimum resident CTAs per SM requested from the register allocator.
+#ifndef PS_XROWBAR
+#define PS_XROWBAR 1
+#endif
+#ifndef PS_XTWSMEM
+#define PS_XTWSMEM 0
+#endif
 #ifndef PS_MINB_ZINV
 #define PS_MINB_ZINV 2
 #endif
@@ -108,7 +117,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // flight at once; the six transforms then read the tile from shared memory.
 // Thread (line, j0, bb) holds kz indices n = j0 + m N/E.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, int NG>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   double esum = 0.0;
   // one group of three components at a time: u (and then B for MHD)
 #pragma unroll 1
-  for (int grp = 0; grp < a.ng; ++grp) {
+  for (int grp = 0; grp < NG; ++grp) {
   const V* in = static_cast<const V*>(a.in.p) + 3 * grp * a.in.cs;
   // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i)
   {
@@ -268,7 +277,23 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
   V* stage = reinterpret_cast<V*>(smraw);
   V* exbuf = stage + 2 * stage_elems;
   RowExchange<V> ex{exbuf + rl * LEN, rpc * LEN, 0};
-  const V* tw = static_cast<const V*>(a.tw_x);
+#if PS_XROWBAR
+  // rows are independent between the stage barriers: sync only the row's threads
+  if (G >= 32) {
+    ex.bar_id = 1 + rl;
+    ex.nthr = G;
+  } else {
+    ex.bar_id = -1;
+  }
+#endif
+#if PS_XTWSMEM
+  V* tws = exbuf + 2 * rpc * LEN;  // twiddle table copy
+  for (int i = tid; i < N; i += blockDim.x) tws[i] = static_cast<const V*>(a.tw_x)[i];
+  __syncthreads();
+  const SharedTw<V> tw{tws};
+#else
+  const GlobalTw<V> tw{static_cast<const V*>(a.tw_x)};
+#endif
   const V* B = static_cast<const V*>(a.b6);
   V* C = static_cast<V*>(a.a6);
   if (tid == 0) {
@@ -337,7 +362,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
         }
         U[c][m] = v;
       }
-      line_fft<N, E, +1>(U[c], j0, tw, ex);
+      line_fft_tw<N, E, +1>(U[c], j0, tw, ex);
     }
     // products at the thread's points (real part = field, imaginary = curl)
     V F[NG == 1 ? 2 : 3][E];
@@ -365,7 +390,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
     if (!a.xdiag) {  // uniform across the grid
       constexpr int NFW = NG == 1 ? 2 : 3;
 #pragma unroll
-      for (int w = 0; w < NFW; ++w) line_fft<N, E, -1>(F[w], j0, tw, ex);
+      for (int w = 0; w < NFW; ++w) line_fft_tw<N, E, -1>(F[w], j0, tw, ex);
       const long long rrow = rvalid ? row : 0;
       const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
       // split each packed transform F = DFT(a) + i DFT(b) of two real fields
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) 
 // writes zeros outside the retained set; otherwise only retained modes of the
 // compact stage buffers are written.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, int NG>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a, const int full) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
@@ -488,7 +513,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(
   // group 0: velocity (forcing, Leray projection, viscosity nu)
   // group 1 (MHD): magnetic field (curl of the transformed u x B, diffusivity eta)
 #pragma unroll 1
-  for (int grp = 0; grp < a.ng; ++grp) {
+  for (int grp = 0; grp < NG; ++grp) {
     const bool mag = grp == 1;
     const T* ifx = static_cast<const T*>(mag ? a.jfx : a.ifx);
     const T* ify = static_cast<const T*>(mag ? a.jfy : a.ify);
@@ -626,17 +651,21 @@ static cudaError_t prep(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename T, int N>
-cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
+template <typename T, int N, int NG>
+cudaError_t zinv_ng(const PassArgs& a, cudaStream_t s, int* nb) {
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   const size_t smem = (1ull * NB * N * TX + 3ull * NB * a.g.cz * TX) * sizeof(V);
-  cudaError_t e = prep(k_zinv<T, N>, smem);
+  cudaError_t e = prep(k_zinv<T, N, NG>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB);
   if (nb) *nb = grid.x * grid.y;
-  k_zinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  k_zinv<T, N, NG><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
+  return a.ng == 2 ? zinv_ng<T, N, 2>(a, s, nb) : zinv_ng<T, N, 1>(a, s, nb);
 }
 template <typename T, int N>
 cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
@@ -654,7 +683,7 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
 template <typename T, int N>
 size_t xpass_smem(const Geo& g, int rpc, int ng) {
   using V = typename cplx<T>::type;
-  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N) * sizeof(V);
+  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N + (PS_XTWSMEM ? N : 0)) * sizeof(V);
 }
 
 template <typename T, int N, int NG>
@@ -697,17 +726,21 @@ cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   k_yfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
-template <typename T, int N>
-cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
+template <typename T, int N, int NG>
+cudaError_t zfwd_ng(const PassArgs& a, cudaStream_t s) {
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
-  cudaError_t e = prep(k_zfwd<T, N>, smem);
+  cudaError_t e = prep(k_zfwd<T, N, NG>, smem);
   if (e != cudaSuccess) return e;
   const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
   dim3 grid(full ? (a.g.nh + TX - 1) / TX : a.g.kxp / TX, full ? (a.g.ny + NB - 1) / NB : (a.g.cy + NB - 1) / NB);
-  k_zfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a, full);
+  k_zfwd<T, N, NG><<<grid, ColThreads<T, N>::v, smem, s>>>(a, full);
   return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
+  return a.ng == 2 ? zfwd_ng<T, N, 2>(a, s) : zfwd_ng<T, N, 1>(a, s);
 }
 
 #define PS_DISPATCH_N(n, CALL)                     \
