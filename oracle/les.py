@@ -1,0 +1,202 @@
+"""FP64 oracle of the learned large-eddy-simulation (LES) closure.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The closure models the subgrid stress of a filtered velocity field with a
+pointwise multilayer perceptron of the resolved velocity-gradient invariants
+(5 -> 64 -> 64 -> 6, GELU).  Readings (the paper has no LES; these follow the
+workload statement):
+
+  L1 filter: the sharp spectral box |p|, |q|, |r| <= kc; with kc equal to the
+     2/3-rule half-width of the LES grid the filtered field is exactly an LES
+     state (kc = 21 for a 64^3 LES).
+  L2 subgrid stress: tau_ij = F[u_i u_j] - F[u_i] F[u_j] (F the filter), the
+     products formed on the DNS grid, the result sampled on the LES grid.
+  L3 inputs: with A_ij = d u_i / d x_j, S = (A + A^T)/2, R = (A - A^T)/2, the
+     invariants tr(S^2), tr(R^2), tr(S^3), tr(S R^2), tr(S^2 R^2) (the basis of
+     Pope 1975 for a traceless gradient), standardised by fixed per-input
+     scales: x_n = (lambda_n - mean_n) / std_n.
+  L4 outputs: (tau_11, tau_22, tau_33, tau_12, tau_13, tau_23) / s_tau.
+  L5 GELU: the tanh form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+     (Hendrycks and Gimpel 2016).
+  L6 closure term of the momentum equation: -div tau, i.e. -i k_j tau_hat_ij,
+     added to the nonlinear term before the Leray projection.
+  L7 loss: mean over samples and components of (y - t)^2.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import spectral as sp
+
+C_GELU = math.sqrt(2.0 / math.pi)
+SYM = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))  # tau component order (L4)
+
+
+# --------------------------------------------------------------------------
+# Filter and subgrid stress (L1, L2)
+# --------------------------------------------------------------------------
+
+def box_filter(uh: np.ndarray, n_dns: int, n_les: int, kc: int) -> np.ndarray:
+    """Keep |p|, |q|, |r| <= kc of a DNS spectral field (n_dns^3) and return it
+    in the layout of an n_les^3 grid (Fourier coefficients are per unit
+    volume, so they carry over unchanged)."""
+    nh = n_les // 2 + 1
+    out = np.zeros(uh.shape[:-3] + (n_les, n_les, nh), dtype=np.complex128)
+    idx = np.concatenate([np.arange(0, kc + 1), np.arange(-kc, 0)])
+    src = np.where(idx >= 0, idx, idx + n_dns)
+    dst = np.where(idx >= 0, idx, idx + n_les)
+    sel_src = np.ix_(src, src, np.arange(kc + 1))
+    sel_dst = np.ix_(dst, dst, np.arange(kc + 1))
+    for c in range(uh.shape[0]):
+        out[c][sel_dst] = uh[c][sel_src]
+    return out
+
+
+def sgs_stress_true(uh_dns: np.ndarray, n_dns: int, n_les: int, kc: int) -> np.ndarray:
+    """tau_ij = F[u_i u_j] - F[u_i] F[u_j] on the n_les^3 grid, shape
+    (6, n_les, n_les, n_les) in the order of SYM (reading L2)."""
+    cd = sp.Config(n_dns, n_dns, n_dns)
+    cl = sp.Config(n_les, n_les, n_les)
+    u = sp.inverse(uh_dns, cd)
+    ubar = sp.inverse(box_filter(uh_dns, n_dns, n_les, kc), cl)
+    out = np.empty((6, n_les, n_les, n_les))
+    for m, (i, j) in enumerate(SYM):
+        prod = sp.forward(u[i] * u[j])[None]
+        out[m] = sp.inverse(box_filter(prod, n_dns, n_les, kc), cl)[0] - ubar[i] * ubar[j]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Gradient invariants (L3)
+# --------------------------------------------------------------------------
+
+def gradient(uh: np.ndarray, cfg: sp.Config) -> np.ndarray:
+    """A_ij = d u_i/d x_j on the grid, shape (3, 3, nz, ny, nx)."""
+    k = sp.wavenumbers(cfg)
+    D = sp.dealias_mask(cfg)
+    return np.stack([np.stack([sp.inverse((1j * k[j] * uh[i] * D)[None], cfg)[0] for j in range(3)])
+                     for i in range(3)])
+
+
+def invariants(A: np.ndarray) -> np.ndarray:
+    """The five invariants of reading L3, shape (5,) + A.shape[2:]."""
+    At = np.swapaxes(A, 0, 1)
+    S = 0.5 * (A + At)
+    R = 0.5 * (A - At)
+
+    def mm(X, Y):
+        return np.einsum("ik...,kj...->ij...", X, Y)
+
+    def tr(X):
+        return np.einsum("ii...->...", X)
+
+    S2, R2 = mm(S, S), mm(R, R)
+    return np.stack([tr(S2), tr(R2), tr(mm(S2, S)), tr(mm(S, R2)), tr(mm(S2, R2))])
+
+
+# --------------------------------------------------------------------------
+# The network (L4, L5, L7)
+# --------------------------------------------------------------------------
+
+def gelu(x):
+    return 0.5 * x * (1.0 + np.tanh(C_GELU * (x + 0.044715 * x ** 3)))
+
+
+def gelu_grad(x):
+    t = np.tanh(C_GELU * (x + 0.044715 * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * C_GELU * (1.0 + 3.0 * 0.044715 * x * x)
+
+
+def init_params(seed: int = 0, width: int = 64):
+    """W1 (5 x w), b1, W2 (w x w), b2, W3 (w x 6), b3; scaled normal init."""
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.standard_normal((5, width)) / math.sqrt(5.0), "b1": np.zeros(width),
+        "W2": rng.standard_normal((width, width)) / math.sqrt(width), "b2": np.zeros(width),
+        "W3": rng.standard_normal((width, 6)) / math.sqrt(width) * 0.1, "b3": np.zeros(6),
+    }
+
+
+def mlp_forward(p, X, rnd=None):
+    """y = (GELU(GELU(X W1 + b1) W2 + b2)) W3 + b3 for rows of X (B x 5).
+    rnd, if given, rounds the operands of every product the way a BF16
+    tensor-core kernel sees them (inputs, weights, hidden activations)."""
+    r = rnd or (lambda a: a)
+    z1 = r(X) @ r(p["W1"]) + p["b1"]
+    h1 = gelu(z1)
+    z2 = r(h1) @ r(p["W2"]) + p["b2"]
+    h2 = gelu(z2)
+    y = r(h2) @ r(p["W3"]) + p["b3"]
+    return y, (X, z1, h1, z2, h2)
+
+
+def mse_and_grads(p, X, T, rnd=None):
+    """Loss L = mean((y - T)^2) (reading L7) and its gradients with respect to
+    every parameter, by the chain rule written out."""
+    r = rnd or (lambda a: a)
+    y, (X_, z1, h1, z2, h2) = mlp_forward(p, X, rnd)
+    B = X.shape[0]
+    dy = 2.0 * (y - T) / (B * T.shape[1])
+    g = {}
+    g["W3"] = r(h2).T @ r(dy)
+    g["b3"] = dy.sum(0)
+    dh2 = r(dy) @ r(p["W3"]).T
+    dz2 = dh2 * gelu_grad(z2)
+    g["W2"] = r(h1).T @ r(dz2)
+    g["b2"] = dz2.sum(0)
+    dh1 = r(dz2) @ r(p["W2"]).T
+    dz1 = dh1 * gelu_grad(z1)
+    g["W1"] = r(X_).T @ r(dz1)
+    g["b1"] = dz1.sum(0)
+    return float(np.mean((y - T) ** 2)), g
+
+
+def bf16_round(a):
+    """Round float values to bfloat16 (8-bit mantissa, round to nearest even),
+    returned as float64; used to feed the oracle the operands a BF16 kernel
+    multiplies."""
+    f = np.asarray(a, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# Closure term and LES right-hand side (L6)
+# --------------------------------------------------------------------------
+
+def model_stress(uh, cfg: sp.Config, p, norm):
+    """Model stress tau (6, nz, ny, nx) of the state: invariants of its
+    gradient, standardised (norm = dict(mean, std, s_tau)), through the MLP."""
+    lam = invariants(gradient(uh, cfg))
+    X = ((lam.reshape(5, -1).T - norm["mean"]) / norm["std"])
+    y, _ = mlp_forward(p, X)
+    return (y.T * norm["s_tau"]).reshape((6,) + lam.shape[1:])
+
+
+def closure_term(uh, cfg: sp.Config, p, norm):
+    """-i k_j tau_hat_ij, masked (reading L6)."""
+    tau = model_stress(uh, cfg, p, norm)
+    th = sp.forward(tau)
+    k = sp.wavenumbers(cfg)
+    full = {}
+    for m, (i, j) in enumerate(SYM):
+        full[(i, j)] = th[m]
+        full[(j, i)] = th[m]
+    div = np.stack([sum(1j * k[j] * full[(i, j)] for j in range(3)) for i in range(3)])
+    return -div * sp.dealias_mask(cfg)
+
+
+def les_rhs(uh, cfg: sp.Config, p, norm, forcing=None):
+    """RHS of the LES: D P(N + f - div tau) - nu |k|^2 D u."""
+    kx, ky, kz = sp.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    D = sp.dealias_mask(cfg)
+    v = sp.nonlinear(uh, cfg) + closure_term(uh, cfg, p, norm)
+    if forcing is not None:
+        v = v + np.asarray(forcing) * D
+    return sp.project(v, cfg) * D - cfg.nu * k2 * uh * D

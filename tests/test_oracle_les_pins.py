@@ -1,0 +1,136 @@
+"""Pins of the LES-closure oracle (oracle/les.py); CPU only."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import les
+from oracle.spectral import Config
+from paper_1808_01309_gb300 import inputs
+
+
+def test_gelu_derivative_matches_finite_differences():
+    x = np.linspace(-5, 5, 41)
+    h = 1e-6
+    fd = (les.gelu(x + h) - les.gelu(x - h)) / (2 * h)
+    assert np.max(np.abs(fd - les.gelu_grad(x))) < 1e-8
+    # limits: gelu(x) -> x for large x, -> 0 for very negative x
+    assert abs(les.gelu(10.0) - 10.0) < 1e-12 and abs(les.gelu(-10.0)) < 1e-12
+
+
+def test_mlp_gradients_match_central_differences():
+    rng = np.random.default_rng(3)
+    p = les.init_params(seed=1)
+    for k in p:
+        p[k] = p[k] + 0.1 * rng.standard_normal(p[k].shape)
+    X = rng.standard_normal((37, 5))
+    T = rng.standard_normal((37, 6))
+    _, g = les.mse_and_grads(p, X, T)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = les.mse_and_grads(p, X, T)
+            flat[idx] = old - h
+            lm, _ = les.mse_and_grads(p, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx)
+
+
+def _inv(A):
+    return les.invariants(np.asarray(A, dtype=np.float64)[:, :, None])[:, 0]
+
+
+def test_invariants_closed_forms():
+    a, b = 0.7, -0.3
+    lam = _inv(np.diag([a, b, -a - b]))
+    assert np.allclose(lam, [a * a + b * b + (a + b) ** 2, 0, a ** 3 + b ** 3 - (a + b) ** 3, 0, 0], atol=1e-15)
+    w = 1.3
+    lam = _inv([[0, -w, 0], [w, 0, 0], [0, 0, 0]])
+    assert np.allclose(lam, [0, -2 * w * w, 0, 0, 0], atol=1e-15)
+    g = 0.9
+    lam = _inv([[0, g, 0], [0, 0, 0], [0, 0, 0]])
+    assert np.allclose(lam, [g * g / 2, -g * g / 2, 0, 0, -g ** 4 / 8], atol=1e-15)
+
+
+def test_gradient_of_taylor_green_is_analytic():
+    n = 16
+    cfg = Config(n, n, n)
+    A = les.gradient(inputs.taylor_green(n, n, n), cfg)
+    z, y, x = np.meshgrid(*(np.arange(n) * 2 * math.pi / n,) * 3, indexing="ij")
+    exp = np.zeros_like(A)
+    exp[0, 0] = np.cos(x) * np.cos(y) * np.cos(z)
+    exp[0, 1] = -np.sin(x) * np.sin(y) * np.cos(z)
+    exp[0, 2] = -np.sin(x) * np.cos(y) * np.sin(z)
+    exp[1, 0] = np.sin(x) * np.sin(y) * np.cos(z)
+    exp[1, 1] = -np.cos(x) * np.cos(y) * np.cos(z)
+    exp[1, 2] = np.cos(x) * np.sin(y) * np.sin(z)
+    assert np.max(np.abs(A - exp)) < 1e-14
+
+
+def test_subgrid_stress_closed_form():
+    """u_y = cos(2x) + cos(30x) on a 128^3 DNS grid filtered at kc = 21:
+    F[u_y^2] = 1 + cos(4x)/2 and u_y_bar^2 = 1/2 + cos(4x)/2, so tau_yy = 1/2
+    and every other component vanishes."""
+    n, kc, nl = 128, 21, 64
+    uh = inputs.trig_field(n, n, n, [(1, 1.0, ("c", 2), ("1", 0), ("1", 0)),
+                                     (1, 1.0, ("c", 30), ("1", 0), ("1", 0))])
+    tau = les.sgs_stress_true(uh, n, nl, kc)
+    expect = np.zeros_like(tau)
+    expect[1] = 0.5
+    assert np.max(np.abs(tau - expect)) < 1e-14
+
+
+def test_subgrid_stress_vanishes_for_band_limited_fields():
+    n, kc, nl = 64, 21, 64
+    u = inputs.random_solenoidal_field(n, n, n, seed=5, kmax=(10, 10, 10))
+    tau = les.sgs_stress_true(u, n, nl, kc)
+    assert np.max(np.abs(tau)) < 1e-15 * 1e3
+
+
+def test_zero_network_reduces_les_to_the_plain_method():
+    n = 16
+    cfg = Config(n, n, n, nu=1e-2)
+    u = inputs.random_solenoidal_field(n, n, n, seed=7)
+    p = les.init_params(seed=2)
+    p["W3"][:] = 0
+    p["b3"][:] = 0
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0)
+    assert np.max(np.abs(les.closure_term(u, cfg, p, norm))) == 0.0
+    assert np.max(np.abs(les.les_rhs(u, cfg, p, norm) - oracle.rhs(u, cfg))) < 1e-15
+
+
+def test_closure_of_a_constant_stress_field_is_zero_and_linear_in_output():
+    """A network whose output is a constant (W3 = 0, b3 = c) models a uniform
+    stress: its divergence, the closure term, vanishes; doubling W3 and b3
+    doubles the term."""
+    n = 16
+    cfg = Config(n, n, n)
+    u = inputs.random_solenoidal_field(n, n, n, seed=8)
+    norm = dict(mean=np.zeros(5), std=np.ones(5) * 10.0, s_tau=0.01)
+    p = les.init_params(seed=3)
+    q = {k: v.copy() for k, v in p.items()}
+    q["W3"][:] = 0
+    q["b3"][:] = np.arange(6.0)
+    assert np.max(np.abs(les.closure_term(u, cfg, q, norm))) < 1e-16
+    c1 = les.closure_term(u, cfg, p, norm)
+    p2 = {k: v.copy() for k, v in p.items()}
+    p2["W3"] *= 2
+    p2["b3"] *= 2
+    assert np.max(np.abs(les.closure_term(u, cfg, p2, norm) - 2 * c1)) < 1e-15 * np.max(np.abs(c1)) * 10
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.00390625, 1.001953125, 1.0029296875, -3.14159265])
+    r = les.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0  # 1 + 2^-8 is a tie: rounds to the even 1.0
+    # round-to-nearest-even at the midpoint between 1 and 1 + 2^-7
+    assert les.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert les.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    assert abs(r[4] + 3.140625) < 1e-12
