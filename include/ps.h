@@ -225,6 +225,30 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
  * of the states.  Synchronises the ensemble stream. */
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
 
+/* ---- Learned LES closure: pointwise MLP on the BF16 tensor cores --------
+ * A multilayer perceptron 5 -> 64 -> 64 -> 6 with GELU (tanh form) maps the
+ * standardised gradient invariants of a resolved velocity to the subgrid
+ * stress.  Parameters are one FP32 device vector of PS_MLP_NPARAM values:
+ * W1[5][64] | b1[64] | W2[64][64] | b2[64] | W3[64][6] | b3[6], y = x W + b.
+ * Products run on the tensor cores (mma, BF16 operands, FP32 accumulation);
+ * biases, activations and sums stay FP32.  The paper has no closure; the
+ * model follows the LES workload of this library. */
+#define PS_MLP_NPARAM 4934
+
+/* Y[count][6] = MLP(X[count][5]) (device FP32 buffers).  Asynchronous. */
+ps_status ps_mlp_forward(const float* params, const float* X, float* Y, long long count, void* cuda_stream);
+
+/* Mean-squared-error loss L = mean((MLP(X) - T)^2) over count samples and 6
+ * outputs (*loss, device double) and dL/dparams (grad, device FP32, overwritten).
+ * Asynchronous. */
+ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long long count, float* grad,
+                      double* loss, void* cuda_stream);
+
+/* One Adam update (bias-corrected, step >= 1) of params with the moment
+ * buffers m, v (device FP32, PS_MLP_NPARAM each, zero before step 1). */
+ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                      float beta2, float eps, void* cuda_stream);
+
 /* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
 #define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

@@ -143,15 +143,15 @@ def mse_and_grads(p, X, T, rnd=None):
     dy = 2.0 * (y - T) / (B * T.shape[1])
     g = {}
     g["W3"] = r(h2).T @ r(dy)
-    g["b3"] = dy.sum(0)
+    g["b3"] = r(dy).sum(0)
     dh2 = r(dy) @ r(p["W3"]).T
     dz2 = dh2 * gelu_grad(z2)
     g["W2"] = r(h1).T @ r(dz2)
-    g["b2"] = dz2.sum(0)
+    g["b2"] = r(dz2).sum(0)
     dh1 = r(dz2) @ r(p["W2"]).T
     dz1 = dh1 * gelu_grad(z1)
     g["W1"] = r(X_).T @ r(dz1)
-    g["b1"] = dz1.sum(0)
+    g["b1"] = r(dz1).sum(0)
     return float(np.mean((y - T) ** 2)), g
 
 

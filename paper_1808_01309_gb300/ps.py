@@ -49,8 +49,9 @@ SYMBOLS = (
     "ps_rk_step_host", "ps_step_stats", "ps_diagnostics", "ps_plan_set_timing",
     "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
-    "ps_ensemble_rk_steps", "ps_ensemble_tune",
+    "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
 )
+MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
 ENS_MAX_SIZES = 8
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -117,6 +118,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_ensemble_rk_steps.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int]
     lib.ps_ensemble_tune.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(PsEnsTuning)]
+    lib.ps_mlp_forward.argtypes = [P, P, P, ctypes.c_longlong, P]
+    lib.ps_mlp_grad.argtypes = [P, P, P, ctypes.c_longlong, P, P, P]
+    lib.ps_mlp_adam.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, P]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -258,6 +263,20 @@ def ps_ensemble_tune(ens, states, dt: float) -> dict:
     _check(load().ps_ensemble_tune(ens, _ptr_array(states), float(dt), ctypes.byref(t)))
     return {"branches": t.branches, "step_ms": t.step_ms,
             "xrpc": {int(t.n[i]): int(t.xrpc[i]) for i in range(t.nsizes)}}
+
+
+def ps_mlp_forward(params, X, Y, count: int, stream=None) -> None:
+    _check(load().ps_mlp_forward(_ptr(params), _ptr(X), _ptr(Y), int(count), _stream_handle(stream)))
+
+
+def ps_mlp_grad(params, X, T, count: int, grad, loss, stream=None) -> None:
+    _check(load().ps_mlp_grad(_ptr(params), _ptr(X), _ptr(T), int(count), _ptr(grad), _ptr(loss),
+                              _stream_handle(stream)))
+
+
+def ps_mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    _check(load().ps_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+                              float(beta2), float(eps), _stream_handle(stream)))
 
 
 # ---- convenience wrapper ------------------------------------------------------------
