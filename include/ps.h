@@ -249,6 +249,29 @@ ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long 
 ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
                       float beta2, float eps, void* cuda_stream);
 
+/* Attach a trained closure to an FP32 HD plan (cubic or no truncation):
+ * afterwards ps_rhs and ps_rk_step add -div tau to the nonlinear term before
+ * the projection, tau = s_tau MLP((lambda - mean)/std) with lambda the five
+ * invariants tr S^2, tr R^2, tr S^3, tr S R^2, tr S^2 R^2 of the resolved
+ * velocity gradient (S, R its symmetric and antisymmetric parts) and the
+ * outputs ordered tau_11, tau_22, tau_33, tau_12, tau_13, tau_23.
+ *   params : device FP32 vector of PS_MLP_NPARAM values (copied), or NULL to
+ *            detach the closure
+ *   norm11 : host doubles mean[5], std[5], s_tau
+ * Allocates the closure scratch on first use; synchronises the plan stream. */
+ps_status ps_plan_set_closure(ps_plan* plan, const float* params, const double* norm11);
+
+/* Training pairs for the closure from one DNS state (FP32, n_dns^3, 2 pi box,
+ * HD layout): the DNS field is box-filtered to |p|,|q|,|r| <= kc and sampled
+ * on an n_les^3 grid; X[P][5] = standardised invariants of the filtered
+ * velocity gradient (raw invariants if norm11 is NULL), T[P][6] = the subgrid
+ * stress F[u_i u_j] - F[u_i] F[u_j] (P = n_les^3, point order z, y, x).
+ * n_dns, n_les in {16, 32, 48, 64, 96, 128, 192, 256, 512}, n_les <= n_dns,
+ * 1 <= kc <= ceil(n_les/3) - 1.  Allocates and frees its scratch; synchronises
+ * the stream. */
+ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm11, float* X,
+                                 float* T, void* cuda_stream);
+
 /* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
 #define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

@@ -169,18 +169,19 @@ def bf16_round(a):
 # Closure term and LES right-hand side (L6)
 # --------------------------------------------------------------------------
 
-def model_stress(uh, cfg: sp.Config, p, norm):
+def model_stress(uh, cfg: sp.Config, p, norm, rnd=None):
     """Model stress tau (6, nz, ny, nx) of the state: invariants of its
-    gradient, standardised (norm = dict(mean, std, s_tau)), through the MLP."""
+    gradient, standardised (norm = dict(mean, std, s_tau)), through the MLP
+    (rnd as in mlp_forward)."""
     lam = invariants(gradient(uh, cfg))
     X = ((lam.reshape(5, -1).T - norm["mean"]) / norm["std"])
-    y, _ = mlp_forward(p, X)
+    y, _ = mlp_forward(p, X, rnd)
     return (y.T * norm["s_tau"]).reshape((6,) + lam.shape[1:])
 
 
-def closure_term(uh, cfg: sp.Config, p, norm):
+def closure_term(uh, cfg: sp.Config, p, norm, rnd=None):
     """-i k_j tau_hat_ij, masked (reading L6)."""
-    tau = model_stress(uh, cfg, p, norm)
+    tau = model_stress(uh, cfg, p, norm, rnd)
     th = sp.forward(tau)
     k = sp.wavenumbers(cfg)
     full = {}
@@ -191,12 +192,28 @@ def closure_term(uh, cfg: sp.Config, p, norm):
     return -div * sp.dealias_mask(cfg)
 
 
-def les_rhs(uh, cfg: sp.Config, p, norm, forcing=None):
+def _les_nonviscous(uh, cfg: sp.Config, p, norm, forcing, rnd):
+    """D P(N + f - div tau): the LES right-hand side without the viscous term."""
+    D = sp.dealias_mask(cfg)
+    v = sp.nonlinear(uh, cfg) + closure_term(uh, cfg, p, norm, rnd)
+    if forcing is not None:
+        v = v + np.asarray(forcing) * D
+    return sp.project(v, cfg) * D
+
+
+def les_rhs(uh, cfg: sp.Config, p, norm, forcing=None, rnd=None):
     """RHS of the LES: D P(N + f - div tau) - nu |k|^2 D u."""
     kx, ky, kz = sp.wavenumbers(cfg)
     k2 = kx * kx + ky * ky + kz * kz
     D = sp.dealias_mask(cfg)
-    v = sp.nonlinear(uh, cfg) + closure_term(uh, cfg, p, norm)
-    if forcing is not None:
-        v = v + np.asarray(forcing) * D
-    return sp.project(v, cfg) * D - cfg.nu * k2 * uh * D
+    return _les_nonviscous(uh, cfg, p, norm, forcing, rnd) - cfg.nu * k2 * uh * D
+
+
+def les_rk_step(uh, dt: float, cfg: sp.Config, p, norm, forcing=None, rnd=None):
+    """One IF-RK step of the LES: the scheme of the HD step (Sec. 2) with the
+    closure term inside every stage's nonlinear term."""
+    kx, ky, kz = sp.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    E = np.exp(-cfg.nu * k2 * dt / 2.0) + np.zeros_like(uh, dtype=np.float64)
+    u = uh * sp.dealias_mask(cfg)
+    return sp._lawson_step(u, E, lambda v: _les_nonviscous(v, cfg, p, norm, forcing, rnd), dt, cfg.rk_order)

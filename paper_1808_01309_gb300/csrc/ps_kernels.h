@@ -65,6 +65,7 @@ struct PassArgs {
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
   int xrpc;          // x pass rows per CTA (0 = largest that keeps two CTAs per SM)
   int* err;          // device error word (bounded waits that gave up), never null
+  const void* extra; // compact closure term added to the velocity group before projection, or null
 };
 
 // Launchers (one per pass and precision); return the launch error.
@@ -89,6 +90,20 @@ constexpr int DIAG_HEAD = 8;
 template <typename T>
 cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int mhd, cudaStream_t s);
 cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double* out, cudaStream_t s);
+
+// LES closure (ps_les.cu): -i k_j tau_hat_ij of the model stress of the state
+// `in`, written to the compact buffer s.extra ([3][cz][cy][kxp], FP32).
+struct LesScratch {
+  const float* params;  // MLP parameters (PS_MLP_NPARAM)
+  const float* norm;    // mean[5], 1/std[5], s_tau (device)
+  float2* spec;         // [9][nz][ny][nh]
+  float* phys;          // [9][nz][ny][nx]
+  float* X;             // [P][5]
+  float* Y;             // [P][6]
+  float2* extra;        // compact closure term
+};
+cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void* twy, const void* twz,
+                             const LesScratch& s, cudaStream_t st);
 
 // Plan internals used by the ensemble layer (ps_plan.cu).
 void plan_set_stream(struct ::ps_plan* p, cudaStream_t s);

@@ -1,0 +1,533 @@
+// Learned LES closure on the CUDA path (include/ps.h: ps_plan_set_closure,
+// ps_les_training_sample): plain (unpruned) 3D transforms of any number of
+// fields, the resolved velocity-gradient invariants, the MLP of ps_mlp.cu, and
+// the divergence of the modelled stress that the z-forward pass adds to the
+// nonlinear term before the projection.  FP32.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ps.h"
+#include "ps_passes.cuh"
+
+namespace ps {
+void set_last_error(const std::string& msg);
+
+namespace les {
+
+using V = float2;
+constexpr int TXG = 8;  // columns per CTA of the strided transform
+
+__global__ void k_tw(V* tw, int n) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s, c;
+  sincospi(2.0 * m / n, &s, &c);
+  tw[m] = make_float2((float)c, (float)(-s));
+}
+
+// In-place C2C transform along an axis of length N: element n of line
+// (b, col) at (b / nb2) s1 + (b % nb2) s2 + n es + col, col < ncols.
+template <int N, int DIR>
+__global__ void k_c2c(V* data, const V* __restrict__ tw, int ncols, int nb2, long long s1, long long s2,
+                      long long es, int nbatch) {
+  constexpr int E = EOf<float, N>::v, G = N / E;
+  constexpr int NBG = 256 / (TXG * G) > 0 ? 256 / (TXG * G) : 1;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int tid = threadIdx.x;
+  const int line = tid % TXG, rest = tid / TXG, j0 = rest % G, bb = rest / G;
+  const int b = blockIdx.y * NBG + bb;
+  const int col = blockIdx.x * TXG + line;
+  const bool ok = b < nbatch && col < ncols;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TXG, NBG * N * TXG, TXG, line, 0};
+  V* base = data + (ok ? (long long)(b / nb2) * s1 + (long long)(b % nb2) * s2 + col : 0);
+  V x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = ok ? base[(long long)(j0 + m * (N / E)) * es] : czero<V>();
+  line_fft<N, E, DIR>(x, j0, tw, ex);
+  if (ok) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) base[(long long)(j0 + m * (N / E)) * es] = x[m];
+  }
+}
+
+// x rows: spectra of fields 2p and 2p+1 (nh = N/2+1 entries each) <-> real
+// rows of N points.  One row group of G threads per (pair, row).
+template <int N>
+__global__ void k_c2r(const V* __restrict__ spec, float* __restrict__ phys, const V* __restrict__ tw, int F,
+                      long long rows) {
+  constexpr int E = EOf<float, N>::v, G = N / E, NH = N / 2 + 1;
+  constexpr int RPC = 256 / G > 0 ? 256 / G : 1;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int j0 = threadIdx.x % G, rl = threadIdx.x / G;
+  const long long row = (long long)blockIdx.x * RPC + rl;
+  const int f0 = 2 * blockIdx.y, f1 = f0 + 1;
+  const bool ok = row < rows, has1 = f1 < F;
+  RowExchange<V> ex{sm + rl * N, RPC * N, 0};
+  const V* pa = spec + ((long long)f0 * rows + (ok ? row : 0)) * NH;
+  const V* pb = spec + ((long long)(has1 ? f1 : f0) * rows + (ok ? row : 0)) * NH;
+  V x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = j0 + m * (N / E);
+    const bool hi = n > N / 2;
+    const int p = hi ? N - n : n;
+    V A = ok ? pa[p] : czero<V>(), B = (ok && has1) ? pb[p] : czero<V>();
+    if (hi) {
+      A = cconj(A);
+      B = cconj(B);
+    }
+    x[m] = mk<V>(A.x - B.y, A.y + B.x);  // A + i B
+  }
+  line_fft<N, E, +1>(x, j0, tw, ex);
+  if (ok) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = j0 + m * (N / E);
+      phys[((long long)f0 * rows + row) * N + n] = x[m].x;
+      if (has1) phys[((long long)f1 * rows + row) * N + n] = x[m].y;
+    }
+  }
+}
+
+template <int N>
+__global__ void k_r2c(const float* __restrict__ phys, V* __restrict__ spec, const V* __restrict__ tw, int F,
+                      long long rows, float scale) {
+  constexpr int E = EOf<float, N>::v, G = N / E, NH = N / 2 + 1;
+  constexpr int RPC = 256 / G > 0 ? 256 / G : 1;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int j0 = threadIdx.x % G, rl = threadIdx.x / G;
+  const long long row = (long long)blockIdx.x * RPC + rl;
+  const int f0 = 2 * blockIdx.y, f1 = f0 + 1;
+  const bool ok = row < rows, has1 = f1 < F;
+  RowExchange<V> ex{sm + rl * N, RPC * N, 0};
+  V x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = j0 + m * (N / E);
+    const float a = ok ? phys[((long long)f0 * rows + row) * N + n] : 0.f;
+    const float b = (ok && has1) ? phys[((long long)f1 * rows + row) * N + n] : 0.f;
+    x[m] = make_float2(a, b);
+  }
+  line_fft<N, E, -1>(x, j0, tw, ex);
+#pragma unroll
+  for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), x[m]);
+  ex.sync();
+  if (ok) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = j0 + m * (N / E);
+      if (k < NH) {
+        const V Fk = x[m];
+        const V Fm = cconj(ex.get(k == 0 ? 0 : N - k));
+        spec[((long long)f0 * rows + row) * NH + k] = cscale(cadd(Fk, Fm), 0.5f * scale);
+        if (has1) spec[((long long)f1 * rows + row) * NH + k] = cscale(cmul_mi(csub(Fk, Fm)), 0.5f * scale);
+      }
+    }
+  }
+}
+
+template <int N, int DIR>
+cudaError_t c2c_n(V* data, const V* tw, int ncols, int nb2, long long s1, long long s2, long long es, int nbatch,
+                  cudaStream_t s) {
+  constexpr int E = EOf<float, N>::v, G = N / E;
+  constexpr int NBG = 256 / (TXG * G) > 0 ? 256 / (TXG * G) : 1;
+  const size_t smem = 2ull * NBG * N * TXG * sizeof(V);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_c2c<N, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((ncols + TXG - 1) / TXG, (nbatch + NBG - 1) / NBG);
+  k_c2c<N, DIR><<<grid, TXG * G * NBG, smem, s>>>(data, tw, ncols, nb2, s1, s2, es, nbatch);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t c2r_n(const V* spec, float* phys, const V* tw, int F, long long rows, cudaStream_t s) {
+  constexpr int E = EOf<float, N>::v, G = N / E;
+  constexpr int RPC = 256 / G > 0 ? 256 / G : 1;
+  const size_t smem = 2ull * RPC * N * sizeof(V);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((rows + RPC - 1) / RPC), (F + 1) / 2);
+  k_c2r<N><<<grid, RPC * G, smem, s>>>(spec, phys, tw, F, rows);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t r2c_n(const float* phys, V* spec, const V* tw, int F, long long rows, float scale, cudaStream_t s) {
+  constexpr int E = EOf<float, N>::v, G = N / E;
+  constexpr int RPC = 256 / G > 0 ? 256 / G : 1;
+  const size_t smem = 2ull * RPC * N * sizeof(V);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((rows + RPC - 1) / RPC), (F + 1) / 2);
+  k_r2c<N><<<grid, RPC * G, smem, s>>>(phys, spec, tw, F, rows, scale);
+  return cudaGetLastError();
+}
+
+#define LES_DISPATCH(n, CALL)                  \
+  switch (n) {                                 \
+    case 16: return CALL(16);                  \
+    case 32: return CALL(32);                  \
+    case 48: return CALL(48);                  \
+    case 64: return CALL(64);                  \
+    case 96: return CALL(96);                  \
+    case 128: return CALL(128);                \
+    case 192: return CALL(192);                \
+    case 256: return CALL(256);                \
+    case 512: return CALL(512);                \
+    default: return cudaErrorInvalidValue;     \
+  }
+
+cudaError_t c2c(int n, int dir, V* d, const V* tw, int ncols, int nb2, long long s1, long long s2, long long es,
+                int nbatch, cudaStream_t s) {
+  if (dir > 0) {
+#define CALL(N) c2c_n<N, +1>(d, tw, ncols, nb2, s1, s2, es, nbatch, s)
+    LES_DISPATCH(n, CALL)
+#undef CALL
+  } else {
+#define CALL(N) c2c_n<N, -1>(d, tw, ncols, nb2, s1, s2, es, nbatch, s)
+    LES_DISPATCH(n, CALL)
+#undef CALL
+  }
+}
+cudaError_t c2r(int n, const V* spec, float* phys, const V* tw, int F, long long rows, cudaStream_t s) {
+#define CALL(N) c2r_n<N>(spec, phys, tw, F, rows, s)
+  LES_DISPATCH(n, CALL)
+#undef CALL
+}
+cudaError_t r2c(int n, const float* phys, V* spec, const V* tw, int F, long long rows, float scale,
+                cudaStream_t s) {
+#define CALL(N) r2c_n<N>(phys, spec, tw, F, rows, scale, s)
+  LES_DISPATCH(n, CALL)
+#undef CALL
+}
+
+// Spectral [F][nz][ny][nh] (overwritten by the z and y passes) -> physical
+// [F][nz][ny][nx], unnormalised backward sum.
+cudaError_t spec2phys(const Geo& g, int F, V* spec, float* phys, const V* twx, const V* twy, const V* twz,
+                      cudaStream_t s) {
+  const long long plane = (long long)g.ny * g.nh, fs = (long long)g.nz * plane;
+  cudaError_t e = c2c(g.nz, +1, spec, twz, g.nh, g.ny, fs, g.nh, plane, F * g.ny, s);
+  if (e == cudaSuccess) e = c2c(g.ny, +1, spec, twy, g.nh, g.nz, fs, plane, g.nh, F * g.nz, s);
+  if (e == cudaSuccess) e = c2r(g.nx, spec, phys, twx, F, (long long)g.nz * g.ny, s);
+  return e;
+}
+
+// Physical -> spectral with the 1/(nx ny nz) of the forward transform.
+cudaError_t phys2spec(const Geo& g, int F, const float* phys, V* spec, const V* twx, const V* twy, const V* twz,
+                      cudaStream_t s) {
+  const long long plane = (long long)g.ny * g.nh, fs = (long long)g.nz * plane;
+  const float scale = (float)(1.0 / ((double)g.nx * g.ny * g.nz));
+  cudaError_t e = r2c(g.nx, phys, spec, twx, F, (long long)g.nz * g.ny, scale, s);
+  if (e == cudaSuccess) e = c2c(g.ny, -1, spec, twy, g.nh, g.nz, fs, plane, g.nh, F * g.nz, s);
+  if (e == cudaSuccess) e = c2c(g.nz, -1, spec, twz, g.nh, g.ny, fs, g.nh, plane, F * g.ny, s);
+  return e;
+}
+
+// A_ij = i k_j u_i for kept modes (0 elsewhere), 9 fields [i][j] in the full
+// spectral layout.
+__global__ void k_grad(const Geo g, const Spec u, V* out) {
+  const long long total = (long long)g.nz * g.ny * g.nh;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int p = (int)(i % g.nh), qi = (int)((i / g.nh) % g.ny), ri = (int)(i / ((long long)g.nh * g.ny));
+  const int q = sidx(qi, g.ny), r = sidx(ri, g.nz);
+  V uu[3] = {czero<V>(), czero<V>(), czero<V>()};
+  if (kept(g, p, q, r)) {
+    const V* pm = static_cast<const V*>(u.p) + (long long)rowof(r, u.zwrap) * u.zs +
+                  (long long)rowof(q, u.ywrap) * u.ys + p;
+    uu[0] = pm[0];
+    uu[1] = pm[u.cs];
+    uu[2] = pm[2 * u.cs];
+  }
+  const float k[3] = {float(p * g.sx), float(q * g.sy), float(r * g.sz)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) out[(3 * a + b) * total + i] = cmul_i(cscale(uu[a], k[b]));
+}
+
+// Invariants tr S^2, tr R^2, tr S^3, tr S R^2, tr S^2 R^2 of A (9 physical
+// fields), standardised: X[p][n] = (lambda_n - mean_n) * invstd_n.
+__global__ void k_features(const float* __restrict__ A, float* __restrict__ X, long long P,
+                           const float* __restrict__ norm) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float a[3][3], S[3][3], R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a[i][j] = A[(3 * i + j) * P + p];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      S[i][j] = 0.5f * (a[i][j] + a[j][i]);
+      R[i][j] = 0.5f * (a[i][j] - a[j][i]);
+    }
+  float S2[3][3], R2[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float s = 0, r = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        s += S[i][k] * S[k][j];
+        r += R[i][k] * R[k][j];
+      }
+      S2[i][j] = s;
+      R2[i][j] = r;
+    }
+  float l1 = 0, l2 = 0, l3 = 0, l4 = 0, l5 = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    l1 += S2[i][i];
+    l2 += R2[i][i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      l3 += S2[i][k] * S[k][i];
+      l4 += S[i][k] * R2[k][i];
+      l5 += S2[i][k] * R2[k][i];
+    }
+  }
+  const float lam[5] = {l1, l2, l3, l4, l5};
+#pragma unroll
+  for (int n = 0; n < 5; ++n) X[p * 5 + n] = (lam[n] - norm[n]) * norm[5 + n];
+}
+
+// tau_m = s_tau Y[p][m] (physical, 6 fields) and its optional difference.
+__global__ void k_stress(const float* __restrict__ Y, float* __restrict__ tau, long long P, const float* norm) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) tau[m * P + p] = norm[10] * Y[p * 6 + m];
+}
+
+// extra_c = -i sum_j k_j tau_hat_cj for kept modes, compact layout.
+__global__ void k_div(const Geo g, const V* __restrict__ th, V* __restrict__ extra) {
+  const long long total = (long long)g.cz * g.cy * g.cx;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int p = (int)(i % g.cx), iy = (int)((i / g.cx) % g.cy), iz = (int)(i / ((long long)g.cx * g.cy));
+  const int q = iy <= g.Ky ? iy : iy - g.cy, r = iz <= g.Kz ? iz : iz - g.cz;
+  const long long ci = ((long long)iz * g.cy + iy) * g.kxp + p, cs = (long long)g.cz * g.cy * g.kxp;
+  if (!kept(g, p, q, r)) {
+    for (int c = 0; c < 3; ++c) extra[c * cs + ci] = czero<V>();
+    return;
+  }
+  const long long fs = (long long)g.nz * g.ny * g.nh;
+  const long long fi = ((long long)rowof(r, g.nz) * g.ny + rowof(q, g.ny)) * g.nh + p;
+  const float k[3] = {float(p * g.sx), float(q * g.sy), float(r * g.sz)};
+  // symmetric components in the order 11, 22, 33, 12, 13, 23
+  const int idx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    V s = czero<V>();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s = cadd(s, cscale(th[idx[c][j] * fs + fi], k[j]));
+    extra[c * cs + ci] = cmul_mi(s);  // -i s
+  }
+}
+
+}  // namespace les
+
+cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void* twy, const void* twz,
+                             const LesScratch& s, cudaStream_t st) {
+  using namespace les;
+  const long long P = (long long)g.nx * g.ny * g.nz;
+  const long long M = (long long)g.nz * g.ny * g.nh;
+  const V *tx = static_cast<const V*>(twx), *ty = static_cast<const V*>(twy), *tz = static_cast<const V*>(twz);
+  k_grad<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(g, in, s.spec);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = spec2phys(g, 9, s.spec, s.phys, tx, ty, tz, st);
+  if (e == cudaSuccess) {
+    k_features<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.X, P, s.norm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const ps_status ms = ps_mlp_forward(s.params, s.X, s.Y, P, st);
+    if (ms != PS_OK) return cudaErrorLaunchFailure;
+  }
+  if (e == cudaSuccess) {
+    k_stress<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.Y, s.phys, P, s.norm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = phys2spec(g, 6, s.phys, s.spec, tx, ty, tz, st);
+  if (e == cudaSuccess) {
+    const long long C = (long long)g.cz * g.cy * g.cx;
+    k_div<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(g, s.spec, s.extra);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+namespace les {
+
+// tau_m = F[u_i u_j] - ubar_i ubar_j on the LES grid (physical fields).
+__global__ void k_tau_true(const float* __restrict__ fuu, const float* __restrict__ ub, float* __restrict__ T,
+                           long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int m = 0; m < 6; ++m) T[p * 6 + m] = fuu[m * P + p] - ub[ii[m] * P + p] * ub[jj[m] * P + p];
+}
+
+__global__ void k_products(const float* u, float* uu, long long P) {  // in place: no __restrict__
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float a = u[p], b = u[P + p], c = u[2 * P + p];
+  uu[p] = a * a;
+  uu[P + p] = b * b;
+  uu[2 * P + p] = c * c;
+  uu[3 * P + p] = a * b;
+  uu[4 * P + p] = a * c;
+  uu[5 * P + p] = b * c;
+}
+
+// Copy the modes |p|,|q|,|r| <= kc of F full-layout fields on grid gs into
+// grid gd (zeros elsewhere).
+__global__ void k_truncate(const V* __restrict__ src, const Geo gs, V* __restrict__ dst, const Geo gd, int kc, int F) {
+  const long long td = (long long)gd.nz * gd.ny * gd.nh;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= td * F) return;
+  const int f = (int)(i / td);
+  const long long j = i % td;
+  const int p = (int)(j % gd.nh), qi = (int)((j / gd.nh) % gd.ny), ri = (int)(j / ((long long)gd.nh * gd.ny));
+  const int q = sidx(qi, gd.ny), r = sidx(ri, gd.nz);
+  V v = czero<V>();
+  if (p <= kc && q <= kc && q >= -kc && r <= kc && r >= -kc) {
+    const long long ts = (long long)gs.nz * gs.ny * gs.nh;
+    v = src[f * ts + ((long long)rowof(r, gs.nz) * gs.ny + rowof(q, gs.ny)) * gs.nh + p];
+  }
+  dst[i] = v;
+}
+
+Geo cube_geo(int n) {
+  Geo g{};
+  g.nx = g.ny = g.nz = n;
+  g.nh = n / 2 + 1;
+  g.Kx = g.Ky = g.Kz = (n + 2) / 3 - 1;
+  g.cx = g.Kx + 1;
+  g.cy = g.cz = 2 * g.Kx + 1;
+  g.kxp = (g.cx + 15) / 16 * 16;
+  g.sx = g.sy = g.sz = 1.0;  // 2 pi box
+  return g;
+}
+
+}  // namespace les
+}  // namespace ps
+
+extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm11,
+                                            float* X, float* T, void* cuda_stream) {
+  using namespace ps;
+  using namespace ps::les;
+  auto bad = [](const char* m) {
+    set_last_error(m);
+    return PS_ERR_INVALID_ARG;
+  };
+  auto ok_n = [](int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512; };
+  if (!uhat_dns || !X || !T) return bad("ps_les_training_sample: NULL buffer");
+  if (!ok_n(n_dns) || !ok_n(n_les) || n_les > n_dns) return bad("ps_les_training_sample: unsupported grid sizes");
+  if (kc < 1 || kc > (n_les + 2) / 3 - 1) return bad("ps_les_training_sample: kc must be in 1..ceil(n_les/3)-1");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const Geo gd = cube_geo(n_dns), gl = cube_geo(n_les);
+  const long long Md = (long long)gd.nz * gd.ny * gd.nh, Pd = (long long)n_dns * n_dns * n_dns;
+  const long long Ml = (long long)gl.nz * gl.ny * gl.nh, Pl = (long long)n_les * n_les * n_les;
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  V* twd = static_cast<V*>(alloc(sizeof(V) * n_dns));
+  V* twl = static_cast<V*>(alloc(sizeof(V) * n_les));
+  V* sd = static_cast<V*>(alloc(sizeof(V) * 6 * Md));      // DNS spectra (6 fields)
+  float* pd = static_cast<float*>(alloc(sizeof(float) * 6 * Pd));  // DNS physical (6 fields)
+  V* sl = static_cast<V*>(alloc(sizeof(V) * 6 * Ml));      // LES spectra (6 fields)
+  V* sg = static_cast<V*>(alloc(sizeof(V) * 9 * Ml));      // LES gradient spectra
+  float* pl = static_cast<float*>(alloc(sizeof(float) * 9 * Pl));  // LES physical (9 fields)
+  float* ub = static_cast<float*>(alloc(sizeof(float) * 3 * Pl));
+  float* nrm = static_cast<float*>(alloc(sizeof(float) * 11));
+  ps_status st = PS_OK;
+  if (!twd || !twl || !sd || !pd || !sl || !sg || !pl || !ub || !nrm) {
+    set_last_error("ps_les_training_sample: device allocation failed");
+    st = PS_ERR_OOM;
+  }
+  cudaError_t e = cudaSuccess;
+  const unsigned bd = (unsigned)((Pd + 255) / 256), bl = (unsigned)((Pl + 255) / 256);
+  if (st == PS_OK) {
+    float h[11];
+    for (int i = 0; i < 5; ++i) {
+      h[i] = norm11 ? (float)norm11[i] : 0.f;
+      h[5 + i] = norm11 ? (float)(1.0 / norm11[5 + i]) : 1.f;
+    }
+    h[10] = norm11 ? (float)norm11[10] : 1.f;
+    e = cudaMemcpyAsync(nrm, h, sizeof(h), cudaMemcpyHostToDevice, s);
+    k_tw<<<(n_dns + 255) / 256, 256, 0, s>>>(twd, n_dns);
+    k_tw<<<(n_les + 255) / 256, 256, 0, s>>>(twl, n_les);
+    // 1. DNS velocity on its grid (fields 3..5 of pd), products u_i u_j in
+    //    place (each point reads its three values before writing six)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, sizeof(V) * 3 * Md, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = spec2phys(gd, 3, sd, pd + 3 * Pd, twd, twd, twd, s);
+    if (e == cudaSuccess) {
+      k_products<<<bd, 256, 0, s>>>(pd + 3 * Pd, pd, Pd);
+      e = cudaGetLastError();
+    }
+    // 2. F[u_i u_j] on the LES grid
+    if (e == cudaSuccess) e = phys2spec(gd, 6, pd, sd, twd, twd, twd, s);
+    if (e == cudaSuccess) {
+      k_truncate<<<(unsigned)((6 * Ml + 255) / 256), 256, 0, s>>>(sd, gd, sl, gl, kc, 6);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = spec2phys(gl, 6, sl, pl, twl, twl, twl, s);
+    // 3. filtered velocity, its gradient spectra, and ubar on the LES grid
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, sizeof(V) * 3 * Md, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+      k_truncate<<<(unsigned)((3 * Ml + 255) / 256), 256, 0, s>>>(sd, gd, sl, gl, kc, 3);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      Spec in;
+      in.p = sl;
+      in.ys = gl.nh;
+      in.zs = (long long)gl.ny * gl.nh;
+      in.cs = (long long)gl.nz * gl.ny * gl.nh;
+      in.zwrap = gl.nz;
+      in.ywrap = gl.ny;
+      Geo gk = gl;
+      gk.Kx = gk.Ky = gk.Kz = kc;
+      k_grad<<<(unsigned)((Ml + 255) / 256), 256, 0, s>>>(gk, in, sg);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = spec2phys(gl, 3, sl, ub, twl, twl, twl, s);
+    // 4. tau = F[u_i u_j] - ubar_i ubar_j, then the invariants of grad ubar
+    if (e == cudaSuccess) {
+      k_tau_true<<<bl, 256, 0, s>>>(pl, ub, T, Pl);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = spec2phys(gl, 9, sg, pl, twl, twl, twl, s);
+    if (e == cudaSuccess) {
+      k_features<<<bl, 256, 0, s>>>(pl, X, Pl, nrm);
+      e = cudaGetLastError();
+    }
+  }
+  if (st == PS_OK && e != cudaSuccess) {
+    set_last_error(std::string("ps_les_training_sample: ") + cudaGetErrorString(e));
+    st = PS_ERR_CUDA;
+  }
+  cudaStreamSynchronize(s);
+  for (void* b : bufs) cudaFree(b);
+  return st;
+}

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   constexpr int NTH = ColThreads<T, N>::v;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   const Geo& g = a.g;
   V* xbuf = reinterpret_cast<V*>(smraw);     // exchange: NB lines x N x TX (single buffer)
@@ -221,7 +221,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
   const int tid = threadIdx.x;
@@ -444,7 +444,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
   const int tid = threadIdx.x;
@@ -480,7 +480,7 @@ template <typename T, int N, int NG>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a, const int full) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
   const int tid = threadIdx.x;
@@ -551,6 +551,12 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(
         const T kzv = T(r) * sz;
         const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
         if (!mag) {
+          if (a.extra) {  // closure term (LES), compact layout
+            const V* ex0 = static_cast<const V*>(a.extra) + ci;
+            v0 = cadd(v0, ldv(ex0));
+            v1 = cadd(v1, ldv(ex0 + ccs));
+            v2 = cadd(v2, ldv(ex0 + 2 * ccs));
+          }
           if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
             const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
             const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;

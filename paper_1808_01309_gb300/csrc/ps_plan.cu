@@ -126,6 +126,10 @@ struct ps_plan {
   cudaStream_t stream = nullptr;
   int device = 0;
   int xrpc = 0;  // x-pass rows per CTA override (0 = automatic)
+  // learned LES closure (ps_plan_set_closure)
+  bool les_on = false;
+  ps::LesScratch les{};
+  void* les_mem[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int ng = 1;    // 3-component groups: 1 HD, 2 MHD
   Geo g{};
   Sizes sz{};
@@ -299,6 +303,14 @@ ps_status run_rhs_passes(ps_plan* p, PassArgs& a) {
       return s;
   }
   if ((s = launch(p, 3, [&] { return launch_yfwd<T>(a, p->stream); }, "y-forward pass")) != PS_OK) return s;
+  if (p->les_on) {
+    // closure term of the stage input, added by the z-forward pass
+    if ((s = launch(p, 5, [&] { return les_closure_term(p->g, a.in, a.tw_x, a.tw_y, a.tw_z, p->les, p->stream); },
+                    "LES closure")) != PS_OK)
+      return s;
+    p->launches += 10;  // the closure is 11 kernels
+    a.extra = p->les.extra;
+  }
   if ((s = launch(p, 4, [&] { return launch_zfwd<T>(a, p->stream); }, "z-forward pass")) != PS_OK) return s;
   return PS_OK;
 }
@@ -422,7 +434,8 @@ ps_status setup_forcing(ps_plan* p) {
 
 void release(ps_plan* p) {
   void* bufs[] = {p->a6, p->b6, p->nxt, p->acc, p->tw, p->iftab, p->fbox, p->e_part, p->stats,
-                  p->umax2, p->ext, p->err, p->dpart, p->dout, p->hstate};
+                  p->umax2, p->ext, p->err, p->dpart, p->dout, p->hstate, p->les_mem[0], p->les_mem[1],
+                  p->les_mem[2], p->les_mem[3], p->les_mem[4], p->les_mem[5], p->les_mem[6]};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& t : p->tl) {
@@ -652,6 +665,52 @@ ps_status ps_plan_get_timing(ps_plan* p, ps_timing* out) {
     out->ms[k] = p->ms_acc[k];
     out->launches[k] = p->n_acc[k];
   }
+  return PS_OK;
+}
+
+ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* norm11) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  if (!params) {
+    p->les_on = false;
+    return PS_OK;
+  }
+  if (!norm11) return fail(PS_ERR_INVALID_ARG, "NULL normalisation");
+  for (int i = 0; i < 11; ++i)
+    if (!std::isfinite(norm11[i]) || (i >= 5 && i < 10 && !(norm11[i] > 0)))
+      return fail(PS_ERR_INVALID_ARG, "normalisation: finite values and positive scales required");
+  if (p->cfg.prec != PS_FP32 || p->ng != 1 || p->cfg.dealias == PS_DEALIAS_SPHERICAL)
+    return fail(PS_ERR_UNSUPPORTED, "the LES closure needs an FP32 HD plan with the cubic or no truncation");
+  const auto les_n = [](int n) { return n >= 16 && n <= 512 && (n % 16 == 0) && ((n & (n - 1)) == 0 || n % 48 == 0); };
+  if (!les_n(p->g.nx) || !les_n(p->g.ny) || !les_n(p->g.nz))
+    return fail(PS_ERR_UNSUPPORTED, "the LES closure supports grid sizes 16..512");
+  DeviceGuard dg(p->device);
+  const ps::Geo& g = p->g;
+  const size_t P = (size_t)g.nx * g.ny * g.nz, M = (size_t)g.nz * g.ny * g.nh;
+  if (!p->les_mem[0]) {
+    const size_t sizes[7] = {sizeof(float) * PS_MLP_NPARAM, sizeof(float) * 16, sizeof(float2) * 9 * M,
+                             sizeof(float) * 9 * P, sizeof(float) * 5 * P, sizeof(float) * 6 * P,
+                             sizeof(float2) * p->sz.cmp};
+    for (int i = 0; i < 7; ++i) PS_CU(cudaMalloc(&p->les_mem[i], sizes[i]), "closure scratch");
+    PS_CU(cudaMemsetAsync(p->les_mem[6], 0, sizes[6], p->stream), "closure scratch");
+  }
+  float h[11];
+  for (int i = 0; i < 5; ++i) {
+    h[i] = (float)norm11[i];
+    h[5 + i] = (float)(1.0 / norm11[5 + i]);
+  }
+  h[10] = (float)norm11[10];
+  PS_CU(cudaMemcpyAsync(p->les_mem[0], params, sizeof(float) * PS_MLP_NPARAM, cudaMemcpyDeviceToDevice, p->stream),
+        "closure parameters");
+  PS_CU(cudaMemcpyAsync(p->les_mem[1], h, sizeof(h), cudaMemcpyHostToDevice, p->stream), "closure scales");
+  PS_CU(cudaStreamSynchronize(p->stream), "closure setup");
+  p->les.params = static_cast<const float*>(p->les_mem[0]);
+  p->les.norm = static_cast<const float*>(p->les_mem[1]);
+  p->les.spec = static_cast<float2*>(p->les_mem[2]);
+  p->les.phys = static_cast<float*>(p->les_mem[3]);
+  p->les.X = static_cast<float*>(p->les_mem[4]);
+  p->les.Y = static_cast<float*>(p->les_mem[5]);
+  p->les.extra = static_cast<float2*>(p->les_mem[6]);
+  p->les_on = true;
   return PS_OK;
 }
 

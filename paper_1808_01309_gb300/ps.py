@@ -50,6 +50,7 @@ SYMBOLS = (
     "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
+    "ps_plan_set_closure", "ps_les_training_sample",
 )
 MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
@@ -122,6 +123,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_mlp_grad.argtypes = [P, P, P, ctypes.c_longlong, P, P, P]
     lib.ps_mlp_adam.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, P]
+    lib.ps_plan_set_closure.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
+    lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), P, P, P]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -279,6 +283,33 @@ def ps_mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999
                               float(beta2), float(eps), _stream_handle(stream)))
 
 
+def _norm11(norm):
+    """(mean[5], std[5], s_tau) as a ctypes double[11], or None."""
+    if norm is None:
+        return None
+    if isinstance(norm, dict):
+        vals = list(norm["mean"]) + list(norm["std"]) + [norm["s_tau"]]
+    else:
+        vals = list(norm)
+    if len(vals) != 11:
+        raise ValueError("normalisation needs mean[5], std[5] and s_tau")
+    return (ctypes.c_double * 11)(*[float(v) for v in vals])
+
+
+def ps_plan_set_closure(plan, params, norm) -> None:
+    """Attach the closure (params: device FP32 vector, norm: mean, std, s_tau);
+    params None detaches it."""
+    if params is None:
+        _check(load().ps_plan_set_closure(plan, None, None))
+        return
+    _check(load().ps_plan_set_closure(plan, _ptr(params), _norm11(norm)))
+
+
+def ps_les_training_sample(n_dns: int, uhat_dns, n_les: int, kc: int, norm, X, T, stream=None) -> None:
+    _check(load().ps_les_training_sample(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _norm11(norm),
+                                         _ptr(X), _ptr(T), _stream_handle(stream)))
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Plan:
@@ -322,6 +353,10 @@ class Plan:
 
     def step_stats(self):
         return ps_step_stats(self.handle)
+
+    def set_closure(self, params, norm=None):
+        """Attach a trained LES closure (see ps_plan_set_closure); None detaches."""
+        ps_plan_set_closure(self.handle, params, norm)
 
     def close(self):
         if self.handle:

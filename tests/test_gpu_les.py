@@ -1,0 +1,213 @@
+"""Learned LES closure on the CUDA path against the FP64 oracle (oracle/les.py).
+
+The closure runs the BF16 tensor-core MLP, so its parity reference is the
+oracle fed the same BF16 operand rounding (bf16_round on the network inputs,
+weights and hidden activations); the rest of the path (gradients, invariants,
+transforms, divergence, projection, RK) is FP32 against FP64.
+
+Tolerances (relative L2 over the field):
+  closure term -div tau          1e-3  (BF16-rounded oracle), 3e-2 (unrounded)
+  LES right-hand side / RK step  2e-4  (BF16-rounded oracle)
+  training sample T (stress)     1e-4 of the RMS of F[u_i u_j]
+  training sample X (invariants) 1e-4 per invariant
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import les
+from paper_1808_01309_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import ps as _ps
+    return _ps
+
+
+def pack(p):
+    return np.concatenate([p[k].reshape(-1) for k in ORDER]).astype(np.float32)
+
+
+def fp32_params(seed):
+    """Random network (nonzero biases, sizeable output layer) and the FP64
+    copy of its FP32 values that the oracle uses."""
+    rng = np.random.default_rng(seed)
+    p = les.init_params(seed=seed)
+    for k in p:
+        p[k] = p[k] + 0.1 * rng.standard_normal(p[k].shape)
+    p["W3"] *= 5.0
+    v = pack(p)
+    out, o = {}, 0
+    for k in ORDER:
+        n = p[k].size
+        out[k] = v[o:o + n].reshape(p[k].shape).astype(np.float64)
+        o += n
+    return v, out
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def to_dev(x, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype)
+
+
+def to_np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def norm_of(u, cfg, s_tau):
+    lam = les.invariants(les.gradient(u, cfg)).reshape(5, -1)
+    return dict(mean=lam.mean(1), std=lam.std(1), s_tau=s_tau)
+
+
+LES_CASES = [
+    # (nx, ny, nz, lx, ly, lz)
+    (32, 32, 32, 2 * math.pi, 2 * math.pi, 2 * math.pi),
+    (64, 64, 64, 2 * math.pi, 2 * math.pi, 2 * math.pi),
+    (48, 48, 48, 2 * math.pi, 2 * math.pi, 2 * math.pi),
+    (32, 64, 16, 3.0, 7.0, 2 * math.pi),
+]
+
+
+@pytest.mark.parametrize("case", LES_CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}")
+def test_les_rhs_matches_oracle(ps, case):
+    nx, ny, nz, lx, ly, lz = case
+    nu = 5e-3
+    u = inputs.random_solenoidal_field(nx, ny, nz, seed=11, kmax=(nx, ny, nz), lx=lx, ly=ly, lz=lz)
+    cfg = oracle.Config(nx, ny, nz, lx=lx, ly=ly, lz=lz, nu=nu)
+    v, p = fp32_params(3)
+    norm = norm_of(u, cfg, 0.05)
+    plan = ps.Plan(nx, ny, nz, lx=lx, ly=ly, lz=lz, prec=ps.Precision.FP32, nu=nu)
+    ud = to_dev(u)
+    plain = to_np(plan.rhs(ud))
+    plan.set_closure(torch.from_numpy(v).cuda(), norm)
+    got = to_np(plan.rhs(ud))
+    ref = les.les_rhs(u, cfg, p, norm, rnd=les.bf16_round)
+    base = oracle.rhs(u, cfg)
+    # the closure is a visible part of the right-hand side in this test
+    term = ref - base
+    assert np.linalg.norm(term) > 0.05 * np.linalg.norm(base)
+    assert relerr(got, ref) < 2e-4
+    # the closure term alone: projected -div tau
+    assert relerr(got - plain, term) < 1e-3
+    ref64 = les.les_rhs(u, cfg, p, norm) - base
+    assert relerr(got - plain, ref64) < 3e-2
+    mask = oracle.dealias_mask(cfg)
+    assert np.all(got[:, ~mask] == 0)
+    # detaching restores the plain method exactly
+    plan.set_closure(None)
+    assert np.array_equal(to_np(plan.rhs(ud)), plain)
+    plan.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_les_rk_steps_match_oracle(ps, order):
+    n, nu, dt = 32, 1e-2, 5e-3
+    u = 2.0 * inputs.random_solenoidal_field(n, n, n, seed=12)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    cfg = oracle.Config(n, n, n, nu=nu, rk_order=order)
+    v, p = fp32_params(4)
+    norm = norm_of(u, cfg, 0.05)
+    ref = u
+    for _ in range(3):
+        ref = les.les_rk_step(ref, dt, cfg, p, norm, forcing=f, rnd=les.bf16_round)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=order, forcing=to_dev(f))
+    plan.set_closure(torch.from_numpy(v).cuda(), norm)
+    ud = to_dev(u)
+    for i in range(3):
+        plan.rk_step(ud, dt, t=i * dt)
+    got = to_np(ud)
+    assert relerr(got, ref) < 2e-4
+    # the closure moved the state: the plain step differs by much more than the tolerance
+    plain = u
+    for _ in range(3):
+        plain = oracle.rk_step(plain, dt, cfg, forcing=f)
+    assert relerr(plain, ref) > 20 * 2e-4
+    plan.close()
+
+
+def test_closure_rejects_unsupported_plans(ps):
+    v, _ = fp32_params(1)
+    dv = torch.from_numpy(v).cuda()
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0)
+    for kw in (dict(prec=ps.Precision.FP64), dict(eq=ps.Equations.MHD, eta=1e-2),
+               dict(dealias=ps.Dealias.SPHERICAL)):
+        plan = ps.Plan(32, **kw)
+        with pytest.raises(ps.PsError):
+            plan.set_closure(dv, norm)
+        plan.close()
+    plan = ps.Plan(32)
+    with pytest.raises(ps.PsError):
+        plan.set_closure(dv, dict(mean=np.zeros(5), std=np.zeros(5), s_tau=1.0))
+    plan.close()
+
+
+TRAIN_CASES = [(64, 32, 10), (128, 64, 21), (96, 48, 15), (64, 64, 21)]
+
+
+@pytest.mark.parametrize("case", TRAIN_CASES, ids=lambda c: f"{c[0]}to{c[1]}kc{c[2]}")
+def test_training_sample_matches_oracle(ps, case):
+    n_dns, n_les, kc = case
+    # spectrum peaked at the filter width: a sizeable subgrid stress
+    u = inputs.random_solenoidal_field(n_dns, n_dns, n_dns, seed=13, kmax=(n_dns // 3,) * 3, k_peak=float(kc))
+    P = n_les ** 3
+    X = torch.empty((P, 5), device="cuda", dtype=torch.float32)
+    T = torch.empty((P, 6), device="cuda", dtype=torch.float32)
+    ps.ps_les_training_sample(n_dns, to_dev(u), n_les, kc, None, X, T)
+    torch.cuda.synchronize()
+    tau = les.sgs_stress_true(u, n_dns, n_les, kc)
+    got_t = T.cpu().numpy().reshape(n_les, n_les, n_les, 6).transpose(3, 0, 1, 2).astype(np.float64)
+    ud = oracle.spectral.inverse(u, oracle.Config(n_dns, n_dns, n_dns))
+    scale = math.sqrt(np.mean(ud ** 2)) ** 2
+    assert np.max(np.abs(got_t - tau)) < 1e-4 * scale * 10
+    assert np.linalg.norm(got_t - tau) / math.sqrt(tau.size) < 1e-4 * scale
+    assert np.linalg.norm(tau) > 1e-2 * scale * math.sqrt(tau.size)  # a nontrivial stress
+    cl = oracle.Config(n_les, n_les, n_les)
+    lam = les.invariants(les.gradient(les.box_filter(u, n_dns, n_les, kc), cl)).reshape(5, -1).T
+    got_x = X.cpu().numpy().astype(np.float64)
+    for i in range(5):
+        assert relerr(got_x[:, i], lam[:, i]) < 1e-4, i
+    # with a normalisation the features are standardised on the device
+    mean, std = lam.mean(0), lam.std(0)
+    ps.ps_les_training_sample(n_dns, to_dev(u), n_les, kc, dict(mean=mean, std=std, s_tau=1.0), X, T)
+    torch.cuda.synchronize()
+    assert relerr(X.cpu().numpy(), (lam - mean) / std) < 1e-4
+
+
+def test_training_sample_closed_form(ps):
+    """u_y = cos(2x) + cos(30x) on 128^3 filtered at kc = 21 onto 64^3:
+    tau_yy = 1/2 exactly, every other component zero."""
+    n, nl, kc = 128, 64, 21
+    uh = inputs.trig_field(n, n, n, [(1, 1.0, ("c", 2), ("1", 0), ("1", 0)),
+                                     (1, 1.0, ("c", 30), ("1", 0), ("1", 0))])
+    P = nl ** 3
+    X = torch.empty((P, 5), device="cuda", dtype=torch.float32)
+    T = torch.empty((P, 6), device="cuda", dtype=torch.float32)
+    ps.ps_les_training_sample(n, to_dev(uh), nl, kc, None, X, T)
+    got = T.cpu().numpy()
+    expect = np.zeros((P, 6))
+    expect[:, 1] = 0.5
+    assert np.max(np.abs(got - expect)) < 2e-6
+
+
+def test_training_sample_rejects_bad_sizes(ps):
+    u = torch.zeros((3, 32, 32, 17), device="cuda", dtype=torch.complex64)
+    X = torch.empty((32 ** 3, 5), device="cuda")
+    T = torch.empty((32 ** 3, 6), device="cuda")
+    for args in ((32, 64, 10), (32, 32, 11), (32, 32, 0), (40, 32, 5)):
+        with pytest.raises(ps.PsError):
+            ps.ps_les_training_sample(args[0], u, args[1], args[2], None, X, T)

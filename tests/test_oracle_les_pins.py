@@ -134,3 +134,23 @@ def test_bf16_rounding():
     assert les.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
     assert les.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
     assert abs(r[4] + 3.140625) < 1e-12
+
+
+def test_les_step_with_a_zero_network_is_the_plain_step():
+    n = 16
+    cfg = Config(n, n, n, nu=2e-2)
+    u = inputs.random_solenoidal_field(n, n, n, seed=9)
+    p = les.init_params(seed=4)
+    p["W3"][:] = 0
+    p["b3"][:] = 0
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0)
+    a = les.les_rk_step(u, 1e-2, cfg, p, norm)
+    b = oracle.rk_step(u, 1e-2, cfg)
+    assert np.max(np.abs(a - b)) < 1e-15
+    # a nonzero network changes the step by dt times the projected closure (to first order)
+    p = les.init_params(seed=4)
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=0.05)
+    dt = 1e-4
+    d = les.les_rk_step(u, dt, cfg, p, norm) - oracle.rk_step(u, dt, cfg)
+    c = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg)
+    assert np.linalg.norm(d - dt * c) < 1e-3 * np.linalg.norm(dt * c)
