@@ -4,24 +4,41 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The closure models the subgrid stress of a filtered velocity field with a
 pointwise multilayer perceptron of the resolved velocity-gradient invariants
-(5 -> 64 -> 64 -> 6, GELU).  Readings (the paper has no LES; these follow the
-workload statement):
+(5 -> 64 -> 64 -> 6, GELU) whose outputs weight a tensor basis.  Readings
+(the paper has no LES; these follow the workload statement):
 
   L1 filter: the sharp spectral box |p|, |q|, |r| <= kc; with kc equal to the
      2/3-rule half-width of the LES grid the filtered field is exactly an LES
      state (kc = 21 for a 64^3 LES).
-  L2 subgrid stress: tau_ij = F[u_i u_j] - F[u_i] F[u_j] (F the filter), the
-     products formed on the DNS grid, the result sampled on the LES grid.
+  L2 subgrid stress: tau_ij = F[u_i u_j] - F[ubar_i ubar_j] (F the filter,
+     ubar = F[u]), the products u_i u_j formed on the DNS grid, the result
+     sampled on the LES grid.  The LES forms its own nonlinear term from ubar
+     and truncates it at kc, so this is exactly the part of the filtered
+     momentum flux that it misses (for the sharp filter, F[ubar ubar] differs
+     from ubar ubar only above kc, where the closure term is discarded).
   L3 inputs: with A_ij = d u_i / d x_j, S = (A + A^T)/2, R = (A - A^T)/2, the
      invariants tr(S^2), tr(R^2), tr(S^3), tr(S R^2), tr(S^2 R^2) (the basis of
      Pope 1975 for a traceless gradient), standardised by fixed per-input
      scales: x_n = (lambda_n - mean_n) / std_n.
-  L4 outputs: (tau_11, tau_22, tau_33, tau_12, tau_13, tau_23) / s_tau.
+  L4 outputs: coefficients g_1..g_6 of the first six tensors of the same
+     integrity basis (Pope 1975), built from the scaled S' = S / s_A,
+     R' = R / s_A:
+        T1 = S', T2 = S'R' - R'S', T3 = S'^2 - tr(S'^2) I/3,
+        T4 = R'^2 - tr(R'^2) I/3, T5 = R'S'^2 - S'^2R',
+        T6 = R'^2 S' + S'R'^2 - 2 tr(S'R'^2) I/3,
+     tau = s_tau sum_n g_n T_n, components ordered 11, 22, 33, 12, 13, 23.
+     Every T_n is symmetric, traceless and rotates with the flow, so the
+     model stress does too.  (Taking the six stress components directly as
+     outputs of rotation-invariant inputs is not equivariant: for isotropic
+     data the mean-square-optimal such map is isotropic, a pure pressure that
+     the projection removes.)
   L5 GELU: the tanh form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
      (Hendrycks and Gimpel 2016).
   L6 closure term of the momentum equation: -div tau, i.e. -i k_j tau_hat_ij,
      added to the nonlinear term before the Leray projection.
-  L7 loss: mean over samples and components of (y - t)^2.
+  L7 loss: mean over samples and the six components of (y - t)^2, where y is
+     the network output (plain fit) or the model stress in units of s_tau,
+     sum_n g_n T_n (tensor-basis fit).
 """
 
 from __future__ import annotations
@@ -57,16 +74,18 @@ def box_filter(uh: np.ndarray, n_dns: int, n_les: int, kc: int) -> np.ndarray:
 
 
 def sgs_stress_true(uh_dns: np.ndarray, n_dns: int, n_les: int, kc: int) -> np.ndarray:
-    """tau_ij = F[u_i u_j] - F[u_i] F[u_j] on the n_les^3 grid, shape
-    (6, n_les, n_les, n_les) in the order of SYM (reading L2)."""
+    """tau_ij = F[u_i u_j] - F[ubar_i ubar_j] on the n_les^3 grid, shape
+    (6, n_les, n_les, n_les) in the order of SYM (reading L2).  Both products
+    are formed on the DNS grid, where neither aliases."""
     cd = sp.Config(n_dns, n_dns, n_dns)
     cl = sp.Config(n_les, n_les, n_les)
     u = sp.inverse(uh_dns, cd)
-    ubar = sp.inverse(box_filter(uh_dns, n_dns, n_les, kc), cl)
+    # ubar on the DNS grid: the filtered field, zero-padded
+    ubar = sp.inverse(box_filter(uh_dns, n_dns, n_dns, kc), cd)
     out = np.empty((6, n_les, n_les, n_les))
     for m, (i, j) in enumerate(SYM):
-        prod = sp.forward(u[i] * u[j])[None]
-        out[m] = sp.inverse(box_filter(prod, n_dns, n_les, kc), cl)[0] - ubar[i] * ubar[j]
+        full = sp.forward(u[i] * u[j]) - sp.forward(ubar[i] * ubar[j])
+        out[m] = sp.inverse(box_filter(full[None], n_dns, n_les, kc), cl)[0]
     return out
 
 
@@ -96,6 +115,30 @@ def invariants(A: np.ndarray) -> np.ndarray:
 
     S2, R2 = mm(S, S), mm(R, R)
     return np.stack([tr(S2), tr(R2), tr(mm(S2, S)), tr(mm(S, R2)), tr(mm(S2, R2))])
+
+
+def tensor_basis(A: np.ndarray, s_A: float = 1.0) -> np.ndarray:
+    """T_1..T_6 of reading L4 for the gradient A (3, 3, ...), shape
+    (6 tensors, 6 components) + A.shape[2:]."""
+    At = np.swapaxes(A, 0, 1)
+    S = 0.5 * (A + At) / s_A
+    R = 0.5 * (A - At) / s_A
+
+    def mm(X, Y):
+        return np.einsum("ik...,kj...->ij...", X, Y)
+
+    def tr(X):
+        return np.einsum("ii...->...", X)
+
+    eye = np.eye(3).reshape((3, 3) + (1,) * (A.ndim - 2))
+    S2, R2 = mm(S, S), mm(R, R)
+    T = [S,
+         mm(S, R) - mm(R, S),
+         S2 - tr(S2) * eye / 3.0,
+         R2 - tr(R2) * eye / 3.0,
+         mm(R, S2) - mm(S2, R),
+         mm(R2, S) + mm(S, R2) - 2.0 * tr(mm(S, R2)) * eye / 3.0]
+    return np.stack([np.stack([t[i, j] for (i, j) in SYM]) for t in T])
 
 
 # --------------------------------------------------------------------------
@@ -137,10 +180,28 @@ def mlp_forward(p, X, rnd=None):
 def mse_and_grads(p, X, T, rnd=None):
     """Loss L = mean((y - T)^2) (reading L7) and its gradients with respect to
     every parameter, by the chain rule written out."""
-    r = rnd or (lambda a: a)
-    y, (X_, z1, h1, z2, h2) = mlp_forward(p, X, rnd)
+    y, cache = mlp_forward(p, X, rnd)
     B = X.shape[0]
     dy = 2.0 * (y - T) / (B * T.shape[1])
+    return float(np.mean((y - T) ** 2)), _backward(p, cache, dy, rnd)
+
+
+def mse_and_grads_tb(p, X, Bas, T, rnd=None):
+    """Tensor-basis fit (readings L4, L7): model stress m = Bas y per sample
+    (Bas of shape (B, 6 components, 6 tensors)), L = mean((m - T)^2) with T
+    in units of s_tau; returns L and the parameter gradients."""
+    y, cache = mlp_forward(p, X, rnd)
+    m = np.einsum("bmn,bn->bm", Bas, y)
+    e = m - T
+    B = X.shape[0]
+    dy = np.einsum("bmn,bm->bn", Bas, e) * (2.0 / (B * T.shape[1]))
+    return float(np.mean(e ** 2)), _backward(p, cache, dy, rnd)
+
+
+def _backward(p, cache, dy, rnd):
+    """Parameter gradients given the output delta dy = dL/dy."""
+    r = rnd or (lambda a: a)
+    X_, z1, h1, z2, h2 = cache
     g = {}
     g["W3"] = r(h2).T @ r(dy)
     g["b3"] = r(dy).sum(0)
@@ -152,7 +213,7 @@ def mse_and_grads(p, X, T, rnd=None):
     dz1 = dh1 * gelu_grad(z1)
     g["W1"] = r(X_).T @ r(dz1)
     g["b1"] = r(dz1).sum(0)
-    return float(np.mean((y - T) ** 2)), g
+    return g
 
 
 def bf16_round(a):
@@ -171,12 +232,15 @@ def bf16_round(a):
 
 def model_stress(uh, cfg: sp.Config, p, norm, rnd=None):
     """Model stress tau (6, nz, ny, nx) of the state: invariants of its
-    gradient, standardised (norm = dict(mean, std, s_tau)), through the MLP
-    (rnd as in mlp_forward)."""
-    lam = invariants(gradient(uh, cfg))
+    gradient, standardised (norm = dict(mean, std, s_tau, s_A)), through the
+    MLP (rnd as in mlp_forward), weighting the tensor basis (reading L4)."""
+    A = gradient(uh, cfg)
+    lam = invariants(A)
     X = ((lam.reshape(5, -1).T - norm["mean"]) / norm["std"])
     y, _ = mlp_forward(p, X, rnd)
-    return (y.T * norm["s_tau"]).reshape((6,) + lam.shape[1:])
+    Tb = tensor_basis(A, norm["s_A"]).reshape(6, 6, -1)
+    tau = np.einsum("nmp,pn->mp", Tb, y)
+    return (tau * norm["s_tau"]).reshape((6,) + lam.shape[1:])
 
 
 def closure_term(uh, cfg: sp.Config, p, norm, rnd=None):

@@ -87,6 +87,16 @@ def test_subgrid_stress_closed_form():
     assert np.max(np.abs(tau - expect)) < 1e-14
 
 
+def test_subgrid_stress_of_a_resolved_mode_is_zero():
+    """u_x = cos(12 y), a single mode inside the filter: F[u u] = F[ubar ubar]
+    exactly, so tau vanishes (the product ubar ubar itself has a cos(24 y)
+    part above kc that the LES truncates too)."""
+    n, kc, nl = 128, 21, 64
+    uh = inputs.trig_field(n, n, n, [(0, 1.0, ("1", 0), ("c", 12), ("1", 0))])
+    tau = les.sgs_stress_true(uh, n, nl, kc)
+    assert np.max(np.abs(tau)) < 1e-15
+
+
 def test_subgrid_stress_vanishes_for_band_limited_fields():
     n, kc, nl = 64, 21, 64
     u = inputs.random_solenoidal_field(n, n, n, seed=5, kmax=(10, 10, 10))
@@ -101,29 +111,116 @@ def test_zero_network_reduces_les_to_the_plain_method():
     p = les.init_params(seed=2)
     p["W3"][:] = 0
     p["b3"][:] = 0
-    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0)
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0, s_A=1.0)
     assert np.max(np.abs(les.closure_term(u, cfg, p, norm))) == 0.0
     assert np.max(np.abs(les.les_rhs(u, cfg, p, norm) - oracle.rhs(u, cfg))) < 1e-15
 
 
-def test_closure_of_a_constant_stress_field_is_zero_and_linear_in_output():
-    """A network whose output is a constant (W3 = 0, b3 = c) models a uniform
-    stress: its divergence, the closure term, vanishes; doubling W3 and b3
-    doubles the term."""
+def test_constant_strain_coefficient_is_an_eddy_viscosity():
+    """g = (c, 0, ..., 0) for every input gives tau = s_tau c S / s_A; for a
+    solenoidal field div S = (1/2) lap u, so the closure term is
+    (s_tau c / (2 s_A)) |k|^2 u_hat on the retained modes."""
     n = 16
-    cfg = Config(n, n, n)
-    u = inputs.random_solenoidal_field(n, n, n, seed=8)
-    norm = dict(mean=np.zeros(5), std=np.ones(5) * 10.0, s_tau=0.01)
+    cfg = Config(n, n, n, lx=2 * math.pi, ly=5.0, lz=3.0)
+    u = inputs.random_solenoidal_field(n, n, n, seed=8, lx=2 * math.pi, ly=5.0, lz=3.0)
+    norm = dict(mean=np.zeros(5), std=np.ones(5) * 10.0, s_tau=0.03, s_A=2.5)
     p = les.init_params(seed=3)
-    q = {k: v.copy() for k, v in p.items()}
-    q["W3"][:] = 0
-    q["b3"][:] = np.arange(6.0)
-    assert np.max(np.abs(les.closure_term(u, cfg, q, norm))) < 1e-16
-    c1 = les.closure_term(u, cfg, p, norm)
-    p2 = {k: v.copy() for k, v in p.items()}
+    p["W3"][:] = 0
+    p["b3"][:] = [-0.7, 0, 0, 0, 0, 0]
+    kx, ky, kz = oracle.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    expect = (0.03 * -0.7 / (2 * 2.5)) * k2 * u * oracle.dealias_mask(cfg)
+    got = les.closure_term(u, cfg, p, norm)
+    assert np.max(np.abs(got - expect)) < 1e-14 * np.max(np.abs(expect))
+    # linear in the output layer
+    p2 = les.init_params(seed=3)
+    c1 = les.closure_term(u, cfg, p2, norm)
     p2["W3"] *= 2
     p2["b3"] *= 2
-    assert np.max(np.abs(les.closure_term(u, cfg, p2, norm) - 2 * c1)) < 1e-15 * np.max(np.abs(c1)) * 10
+    assert np.max(np.abs(les.closure_term(u, cfg, p2, norm) - 2 * c1)) < 1e-14 * np.max(np.abs(c1))
+
+
+def _tb(A, s_A=1.0):
+    return les.tensor_basis(np.asarray(A, dtype=np.float64)[:, :, None], s_A)[:, :, 0]
+
+
+def test_tensor_basis_closed_forms():
+    """Hand-derived basis tensors for a simple shear and for a diagonal strain
+    with a rotation about z (components 11, 22, 33, 12, 13, 23)."""
+    g = 1.7
+    T = _tb([[0, g, 0], [0, 0, 0], [0, 0, 0]])
+    assert np.allclose(T[0], [0, 0, 0, g / 2, 0, 0], atol=1e-15)
+    assert np.allclose(T[1], [-g * g / 2, g * g / 2, 0, 0, 0, 0], atol=1e-15)
+    assert np.allclose(T[2], [g * g / 12, g * g / 12, -g * g / 6, 0, 0, 0], atol=1e-15)
+    assert np.allclose(T[3], [-g * g / 12, -g * g / 12, g * g / 6, 0, 0, 0], atol=1e-15)
+    assert np.allclose(T[4], 0, atol=1e-15)
+    assert np.allclose(T[5], [0, 0, 0, -g ** 3 / 4, 0, 0], atol=1e-15)
+    # the scale s_A divides S and R
+    assert np.allclose(_tb([[0, g, 0], [0, 0, 0], [0, 0, 0]], 2.0), _tb([[0, g / 2, 0], [0, 0, 0], [0, 0, 0]]),
+                       atol=1e-15)
+    a, b, w = 0.8, -0.3, 1.1
+    c = -a - b
+    T = _tb([[a, -w, 0], [w, b, 0], [0, 0, c]])
+    assert np.allclose(T[1], [0, 0, 0, w * (b - a), 0, 0], atol=1e-15)
+    assert np.allclose(T[4], [0, 0, 0, w * (a * a - b * b), 0, 0], atol=1e-15)
+    s6 = 2 * (a + b) / 3
+    assert np.allclose(T[5], [w * w * (-2 * a + s6), w * w * (-2 * b + s6), w * w * s6, 0, 0, 0], atol=1e-15)
+
+
+def test_tensor_basis_gradient_model_identity_and_equivariance():
+    """-T2 + T3 - T4 is the deviatoric part of A A^T (the gradient model), and
+    every basis tensor rotates with A while the invariants do not change."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((3, 3, 50))
+    A -= np.einsum("ii...->...", A) / 3 * np.eye(3)[:, :, None]  # traceless
+    T = les.tensor_basis(A)
+    AAt = np.einsum("ik...,jk...->ij...", A, A)
+    dev = AAt - np.einsum("ii...->...", AAt) / 3 * np.eye(3)[:, :, None]
+    expect = np.stack([dev[i, j] for (i, j) in les.SYM])
+    assert np.max(np.abs(-T[1] + T[2] - T[3] - expect)) < 1e-13
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Ar = np.einsum("ik,kl...,jl->ij...", Q, A, Q)
+    Tr = les.tensor_basis(Ar)
+
+    def full(t):
+        F = np.zeros((3, 3) + t.shape[1:])
+        for m, (i, j) in enumerate(les.SYM):
+            F[i, j] = F[j, i] = t[m]
+        return F
+
+    for n in range(6):
+        rot = np.einsum("ik,kl...,jl->ij...", Q, full(T[n]), Q)
+        assert np.max(np.abs(full(Tr[n]) - rot)) < 1e-12, n
+    assert np.max(np.abs(les.invariants(Ar) - les.invariants(A))) < 1e-12
+
+
+def test_tensor_basis_fit_gradients_match_central_differences():
+    rng = np.random.default_rng(6)
+    p = les.init_params(seed=5)
+    for k in p:
+        p[k] = p[k] + 0.1 * rng.standard_normal(p[k].shape)
+    X = rng.standard_normal((29, 5))
+    Bas = rng.standard_normal((29, 6, 6))
+    T = rng.standard_normal((29, 6))
+    _, g = les.mse_and_grads_tb(p, X, Bas, T)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = les.mse_and_grads_tb(p, X, Bas, T)
+            flat[idx] = old - h
+            lm, _ = les.mse_and_grads_tb(p, X, Bas, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx)
+    # with the identity basis the fit is the plain fit
+    eye = np.broadcast_to(np.eye(6), (29, 6, 6))
+    l1, g1 = les.mse_and_grads_tb(p, X, eye, T)
+    l2, g2 = les.mse_and_grads(p, X, T)
+    assert abs(l1 - l2) < 1e-14 and all(np.allclose(g1[k], g2[k], rtol=1e-13, atol=1e-15) for k in p)
 
 
 def test_bf16_rounding():
@@ -143,14 +240,14 @@ def test_les_step_with_a_zero_network_is_the_plain_step():
     p = les.init_params(seed=4)
     p["W3"][:] = 0
     p["b3"][:] = 0
-    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0)
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=1.0, s_A=1.0)
     a = les.les_rk_step(u, 1e-2, cfg, p, norm)
     b = oracle.rk_step(u, 1e-2, cfg)
     assert np.max(np.abs(a - b)) < 1e-15
     # a nonzero network changes the step by dt times the projected closure (to first order)
     p = les.init_params(seed=4)
-    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=0.05)
-    dt = 1e-4
+    norm = dict(mean=np.zeros(5), std=np.ones(5), s_tau=0.05, s_A=1.0)
+    dt = 1e-6
     d = les.les_rk_step(u, dt, cfg, p, norm) - oracle.rk_step(u, dt, cfg)
     c = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg)
     assert np.linalg.norm(d - dt * c) < 1e-3 * np.linalg.norm(dt * c)
