@@ -244,6 +244,13 @@ ps_status ps_mlp_forward(const float* params, const float* X, float* Y, long lon
 ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long long count, float* grad,
                       double* loss, void* cuda_stream);
 
+/* Tensor-basis fit: loss L = mean over count samples and 6 components of
+ * (sum_n y_n T_n(A/s_A) - T/s_tau)^2 with y = MLP(X), A[count][9] the
+ * gradients of the samples and T_n the basis of ps_plan_set_closure; *loss
+ * (device double) and dL/dparams (grad, overwritten).  Asynchronous. */
+ps_status ps_mlp_grad_tb(const float* params, const float* X, const float* A, const float* T, long long count,
+                         double s_A, double s_tau, float* grad, double* loss, void* cuda_stream);
+
 /* One Adam update (bias-corrected, step >= 1) of params with the moment
  * buffers m, v (device FP32, PS_MLP_NPARAM each, zero before step 1). */
 ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
@@ -251,26 +258,42 @@ ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int 
 
 /* Attach a trained closure to an FP32 HD plan (cubic or no truncation):
  * afterwards ps_rhs and ps_rk_step add -div tau to the nonlinear term before
- * the projection, tau = s_tau MLP((lambda - mean)/std) with lambda the five
- * invariants tr S^2, tr R^2, tr S^3, tr S R^2, tr S^2 R^2 of the resolved
- * velocity gradient (S, R its symmetric and antisymmetric parts) and the
- * outputs ordered tau_11, tau_22, tau_33, tau_12, tau_13, tau_23.
+ * the projection (every RK stage), with the model stress
+ *   tau = s_tau sum_{n=1..6} g_n T_n(S/s_A, R/s_A),
+ *   g = MLP((lambda - mean)/std),
+ * lambda the five invariants tr S^2, tr R^2, tr S^3, tr S R^2, tr S^2 R^2 of
+ * the resolved velocity gradient A_ij = du_i/dx_j (S, R its symmetric and
+ * antisymmetric parts) and T_1..T_6 the first six tensors of Pope's (1975)
+ * integrity basis: S, SR - RS, S^2 - tr(S^2) I/3, R^2 - tr(R^2) I/3,
+ * RS^2 - S^2 R, R^2 S + S R^2 - 2 tr(S R^2) I/3.
  *   params : device FP32 vector of PS_MLP_NPARAM values (copied), or NULL to
  *            detach the closure
- *   norm11 : host doubles mean[5], std[5], s_tau
- * Allocates the closure scratch on first use; synchronises the plan stream. */
-ps_status ps_plan_set_closure(ps_plan* plan, const float* params, const double* norm11);
+ *   norm12 : host doubles mean[5], std[5], s_tau, s_A (std, s_tau, s_A > 0)
+ * Grid sizes 16..512 (powers of two, 48, 96, 192).  Allocates the closure
+ * scratch on first use (about 29 floats per grid point); synchronises the
+ * plan stream.  PS_ERR_UNSUPPORTED for FP64, MHD or spherical truncation. */
+ps_status ps_plan_set_closure(ps_plan* plan, const float* params, const double* norm12);
 
-/* Training pairs for the closure from one DNS state (FP32, n_dns^3, 2 pi box,
- * HD layout): the DNS field is box-filtered to |p|,|q|,|r| <= kc and sampled
- * on an n_les^3 grid; X[P][5] = standardised invariants of the filtered
- * velocity gradient (raw invariants if norm11 is NULL), T[P][6] = the subgrid
- * stress F[u_i u_j] - F[u_i] F[u_j] (P = n_les^3, point order z, y, x).
+/* Training data for the closure from one DNS state (FP32, n_dns^3, 2 pi box,
+ * HD layout, device): with F the box filter |p|,|q|,|r| <= kc and ubar = F[u]
+ * sampled on an n_les^3 grid (P = n_les^3 points, order z, y, x):
+ *   X[P][5] : standardised invariants of grad ubar (raw if norm12 is NULL;
+ *             only mean and std of norm12 are used)
+ *   A[P][9] : grad ubar, A_ij at 3i+j (optional, NULL to skip)
+ *   T[P][6] : subgrid stress F[u_i u_j] - F[ubar_i ubar_j], order 11, 22,
+ *             33, 12, 13, 23 (the part of the filtered momentum flux that an
+ *             LES truncated at kc does not form itself)
  * n_dns, n_les in {16, 32, 48, 64, 96, 128, 192, 256, 512}, n_les <= n_dns,
- * 1 <= kc <= ceil(n_les/3) - 1.  Allocates and frees its scratch; synchronises
- * the stream. */
-ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm11, float* X,
-                                 float* T, void* cuda_stream);
+ * 1 <= kc <= ceil(n_les/3) - 1.  Allocates and frees its scratch (about 60
+ * bytes per DNS point); synchronises the stream. */
+ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm12, float* X,
+                                 float* A, float* T, void* cuda_stream);
+
+/* Box filter of an FP32 HD state: uhat_les (n_les^3 layout, device) receives
+ * the modes |p|, |q|, |r| <= kc of uhat_dns (n_dns^3) and zeros elsewhere.
+ * Even sizes 8..1024, n_les <= n_dns, 0 <= kc < n_les/2, no aliasing of the
+ * two buffers.  Asynchronous. */
+ps_status ps_les_filter(int n_dns, const void* uhat_dns, int n_les, int kc, void* uhat_les, void* cuda_stream);
 
 /* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
 #define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -9,6 +9,7 @@
 
 #include "ps.h"
 #include "ps_passes.cuh"
+#include "ps_tb.cuh"
 
 namespace ps {
 void set_last_error(const std::string& msg);
@@ -257,9 +258,11 @@ __global__ void k_grad(const Geo g, const Spec u, V* out) {
 }
 
 // Invariants tr S^2, tr R^2, tr S^3, tr S R^2, tr S^2 R^2 of A (9 physical
-// fields), standardised: X[p][n] = (lambda_n - mean_n) * invstd_n.
-__global__ void k_features(const float* __restrict__ A, float* __restrict__ X, long long P,
-                           const float* __restrict__ norm) {
+// fields), standardised: X[p][n] = (lambda_n - mean_n) * invstd_n, with
+// norm = [mean 5 | invstd 5 | s_tau | 1/s_A].  Aout (optional) receives the
+// gradient as rows [p][9].
+__global__ void k_features(const float* __restrict__ A, float* __restrict__ X, float* __restrict__ Aout,
+                           long long P, const float* __restrict__ norm) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
   float a[3][3], S[3][3], R[3][3];
@@ -267,6 +270,10 @@ __global__ void k_features(const float* __restrict__ A, float* __restrict__ X, l
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) a[i][j] = A[(3 * i + j) * P + p];
+  if (Aout) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Aout[p * 9 + k] = a[k / 3][k % 3];
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -275,19 +282,8 @@ __global__ void k_features(const float* __restrict__ A, float* __restrict__ X, l
       R[i][j] = 0.5f * (a[i][j] - a[j][i]);
     }
   float S2[3][3], R2[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float s = 0, r = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        s += S[i][k] * S[k][j];
-        r += R[i][k] * R[k][j];
-      }
-      S2[i][j] = s;
-      R2[i][j] = r;
-    }
+  matmul3(S, S, S2);
+  matmul3(R, R, R2);
   float l1 = 0, l2 = 0, l3 = 0, l4 = 0, l5 = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -305,12 +301,30 @@ __global__ void k_features(const float* __restrict__ A, float* __restrict__ X, l
   for (int n = 0; n < 5; ++n) X[p * 5 + n] = (lam[n] - norm[n]) * norm[5 + n];
 }
 
-// tau_m = s_tau Y[p][m] (physical, 6 fields) and its optional difference.
-__global__ void k_stress(const float* __restrict__ Y, float* __restrict__ tau, long long P, const float* norm) {
+// Model stress tau = s_tau sum_n Y[p][n] T_n(A/s_A), written over fields 0..5
+// of the gradient buffer G (9 planar fields; each point reads its own nine
+// values before writing six, so no __restrict__).
+__global__ void k_stress(float* G, const float* __restrict__ Y, long long P, const float* __restrict__ norm) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
+  float a[3][3];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) tau[m * P + p] = norm[10] * Y[p * 6 + m];
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a[i][j] = G[(3 * i + j) * P + p];
+  float Tb[6][6];
+  tensor_basis(a, norm[11], Tb);
+  float g[6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) g[n] = Y[p * 6 + n];
+  const float st = norm[10];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    float t = 0.f;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) t += g[n] * Tb[n][m];
+    G[m * P + p] = st * t;
+  }
 }
 
 // extra_c = -i sum_j k_j tau_hat_cj for kept modes, compact layout.
@@ -351,7 +365,7 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = spec2phys(g, 9, s.spec, s.phys, tx, ty, tz, st);
   if (e == cudaSuccess) {
-    k_features<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.X, P, s.norm);
+    k_features<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.X, nullptr, P, s.norm);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
@@ -359,7 +373,7 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
     if (ms != PS_OK) return cudaErrorLaunchFailure;
   }
   if (e == cudaSuccess) {
-    k_stress<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.Y, s.phys, P, s.norm);
+    k_stress<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.Y, P, s.norm);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = phys2spec(g, 6, s.phys, s.spec, tx, ty, tz, st);
@@ -373,17 +387,17 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
 
 namespace les {
 
-// tau_m = F[u_i u_j] - ubar_i ubar_j on the LES grid (physical fields).
-__global__ void k_tau_true(const float* __restrict__ fuu, const float* __restrict__ ub, float* __restrict__ T,
-                           long long P) {
+// Rows T[p][m] of 6 planar physical fields.
+__global__ void k_rows6(const float* __restrict__ f, float* __restrict__ T, long long P) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-  for (int m = 0; m < 6; ++m) T[p * 6 + m] = fuu[m * P + p] - ub[ii[m] * P + p] * ub[jj[m] * P + p];
+  for (int m = 0; m < 6; ++m) T[p * 6 + m] = f[m * P + p];
 }
 
-__global__ void k_products(const float* u, float* uu, long long P) {  // in place: no __restrict__
+// u_i u_j (order 11, 22, 33, 12, 13, 23) of 3 planar fields u into 6 fields uu;
+// may run in place with u = uu + 3P (each point reads its three values first).
+__global__ void k_products(const float* u, float* uu, long long P) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
   const float a = u[p], b = u[P + p], c = u[2 * P + p];
@@ -413,6 +427,12 @@ __global__ void k_truncate(const V* __restrict__ src, const Geo gs, V* __restric
   dst[i] = v;
 }
 
+// a <- a - b on F fields of one grid (full layout).
+__global__ void k_sub(V* __restrict__ a, const V* __restrict__ b, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = csub(a[i], b[i]);
+}
+
 Geo cube_geo(int n) {
   Geo g{};
   g.nx = g.ny = g.nz = n;
@@ -425,21 +445,28 @@ Geo cube_geo(int n) {
   return g;
 }
 
+unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
+
 }  // namespace les
 }  // namespace ps
 
-extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm11,
-                                            float* X, float* T, void* cuda_stream) {
+extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int kc, const double* norm12,
+                                            float* X, float* A, float* T, void* cuda_stream) {
   using namespace ps;
   using namespace ps::les;
   auto bad = [](const char* m) {
     set_last_error(m);
     return PS_ERR_INVALID_ARG;
   };
-  auto ok_n = [](int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512; };
+  auto ok_n = [](int n) {
+    return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512;
+  };
   if (!uhat_dns || !X || !T) return bad("ps_les_training_sample: NULL buffer");
   if (!ok_n(n_dns) || !ok_n(n_les) || n_les > n_dns) return bad("ps_les_training_sample: unsupported grid sizes");
   if (kc < 1 || kc > (n_les + 2) / 3 - 1) return bad("ps_les_training_sample: kc must be in 1..ceil(n_les/3)-1");
+  if (norm12)
+    for (int i = 5; i < 10; ++i)
+      if (!(norm12[i] > 0) || !std::isfinite(norm12[i])) return bad("ps_les_training_sample: std must be positive");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const Geo gd = cube_geo(n_dns), gl = cube_geo(n_les);
   const long long Md = (long long)gd.nz * gd.ny * gd.nh, Pd = (long long)n_dns * n_dns * n_dns;
@@ -453,49 +480,74 @@ extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int
   };
   V* twd = static_cast<V*>(alloc(sizeof(V) * n_dns));
   V* twl = static_cast<V*>(alloc(sizeof(V) * n_les));
-  V* sd = static_cast<V*>(alloc(sizeof(V) * 6 * Md));      // DNS spectra (6 fields)
+  V* sd = static_cast<V*>(alloc(sizeof(V) * 6 * Md));              // DNS spectra (6 fields)
   float* pd = static_cast<float*>(alloc(sizeof(float) * 6 * Pd));  // DNS physical (6 fields)
-  V* sl = static_cast<V*>(alloc(sizeof(V) * 6 * Ml));      // LES spectra (6 fields)
-  V* sg = static_cast<V*>(alloc(sizeof(V) * 9 * Ml));      // LES gradient spectra
+  V* sl = static_cast<V*>(alloc(sizeof(V) * 6 * Ml));              // LES spectra (6 fields)
+  V* sg = static_cast<V*>(alloc(sizeof(V) * 9 * Ml));              // LES spectra (9 fields)
   float* pl = static_cast<float*>(alloc(sizeof(float) * 9 * Pl));  // LES physical (9 fields)
-  float* ub = static_cast<float*>(alloc(sizeof(float) * 3 * Pl));
-  float* nrm = static_cast<float*>(alloc(sizeof(float) * 11));
+  float* nrm = static_cast<float*>(alloc(sizeof(float) * 12));
   ps_status st = PS_OK;
-  if (!twd || !twl || !sd || !pd || !sl || !sg || !pl || !ub || !nrm) {
+  if (!twd || !twl || !sd || !pd || !sl || !sg || !pl || !nrm) {
     set_last_error("ps_les_training_sample: device allocation failed");
     st = PS_ERR_OOM;
   }
   cudaError_t e = cudaSuccess;
-  const unsigned bd = (unsigned)((Pd + 255) / 256), bl = (unsigned)((Pl + 255) / 256);
+  const unsigned bd = blocks(Pd), bl = blocks(Pl);
+  const size_t ubytes = sizeof(V) * 3 * Md;
   if (st == PS_OK) {
-    float h[11];
+    float h[12];
     for (int i = 0; i < 5; ++i) {
-      h[i] = norm11 ? (float)norm11[i] : 0.f;
-      h[5 + i] = norm11 ? (float)(1.0 / norm11[5 + i]) : 1.f;
+      h[i] = norm12 ? (float)norm12[i] : 0.f;
+      h[5 + i] = norm12 ? (float)(1.0 / norm12[5 + i]) : 1.f;
     }
-    h[10] = norm11 ? (float)norm11[10] : 1.f;
+    h[10] = h[11] = 1.f;
     e = cudaMemcpyAsync(nrm, h, sizeof(h), cudaMemcpyHostToDevice, s);
     k_tw<<<(n_dns + 255) / 256, 256, 0, s>>>(twd, n_dns);
     k_tw<<<(n_les + 255) / 256, 256, 0, s>>>(twl, n_les);
-    // 1. DNS velocity on its grid (fields 3..5 of pd), products u_i u_j in
-    //    place (each point reads its three values before writing six)
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, sizeof(V) * 3 * Md, cudaMemcpyDeviceToDevice, s);
+    // 1. F[u_i u_j] on the LES grid: DNS velocity (fields 3..5 of pd), the
+    //    products in place, forward, truncate
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, ubytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = spec2phys(gd, 3, sd, pd + 3 * Pd, twd, twd, twd, s);
     if (e == cudaSuccess) {
       k_products<<<bd, 256, 0, s>>>(pd + 3 * Pd, pd, Pd);
       e = cudaGetLastError();
     }
-    // 2. F[u_i u_j] on the LES grid
     if (e == cudaSuccess) e = phys2spec(gd, 6, pd, sd, twd, twd, twd, s);
     if (e == cudaSuccess) {
-      k_truncate<<<(unsigned)((6 * Ml + 255) / 256), 256, 0, s>>>(sd, gd, sl, gl, kc, 6);
+      k_truncate<<<blocks(6 * Ml), 256, 0, s>>>(sd, gd, sl, gl, kc, 6);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = spec2phys(gl, 6, sl, pl, twl, twl, twl, s);
-    // 3. filtered velocity, its gradient spectra, and ubar on the LES grid
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, sizeof(V) * 3 * Md, cudaMemcpyDeviceToDevice, s);
+    // 2. F[ubar_i ubar_j]: ubar on the LES grid (3 < 2/3 of the grid, so its
+    //    products do not alias below kc), products, forward, truncate
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, ubytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
-      k_truncate<<<(unsigned)((3 * Ml + 255) / 256), 256, 0, s>>>(sd, gd, sl, gl, kc, 3);
+      k_truncate<<<blocks(3 * Ml), 256, 0, s>>>(sd, gd, sg, gl, kc, 3);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = spec2phys(gl, 3, sg, pl + 3 * Pl, twl, twl, twl, s);
+    if (e == cudaSuccess) {
+      k_products<<<bl, 256, 0, s>>>(pl + 3 * Pl, pl, Pl);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = phys2spec(gl, 6, pl, sg, twl, twl, twl, s);
+    if (e == cudaSuccess) {
+      k_sub<<<blocks(6 * Ml), 256, 0, s>>>(sl, sg, 6 * Ml);
+      e = cudaGetLastError();
+    }
+    // 3. tau = F[uu] - F[ubar ubar]: truncate the difference, back to the LES grid
+    if (e == cudaSuccess) {
+      k_truncate<<<blocks(6 * Ml), 256, 0, s>>>(sl, gl, sg, gl, kc, 6);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = spec2phys(gl, 6, sg, pl, twl, twl, twl, s);
+    if (e == cudaSuccess) {
+      k_rows6<<<bl, 256, 0, s>>>(pl, T, Pl);
+      e = cudaGetLastError();
+    }
+    // 4. features of grad ubar
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, uhat_dns, ubytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+      k_truncate<<<blocks(3 * Ml), 256, 0, s>>>(sd, gd, sl, gl, kc, 3);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -508,18 +560,12 @@ extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int
       in.ywrap = gl.ny;
       Geo gk = gl;
       gk.Kx = gk.Ky = gk.Kz = kc;
-      k_grad<<<(unsigned)((Ml + 255) / 256), 256, 0, s>>>(gk, in, sg);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = spec2phys(gl, 3, sl, ub, twl, twl, twl, s);
-    // 4. tau = F[u_i u_j] - ubar_i ubar_j, then the invariants of grad ubar
-    if (e == cudaSuccess) {
-      k_tau_true<<<bl, 256, 0, s>>>(pl, ub, T, Pl);
+      k_grad<<<blocks(Ml), 256, 0, s>>>(gk, in, sg);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = spec2phys(gl, 9, sg, pl, twl, twl, twl, s);
     if (e == cudaSuccess) {
-      k_features<<<bl, 256, 0, s>>>(pl, X, Pl, nrm);
+      k_features<<<bl, 256, 0, s>>>(pl, X, A, Pl, nrm);
       e = cudaGetLastError();
     }
   }
@@ -530,4 +576,33 @@ extern "C" ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int
   cudaStreamSynchronize(s);
   for (void* b : bufs) cudaFree(b);
   return st;
+}
+
+extern "C" ps_status ps_les_filter(int n_dns, const void* uhat_dns, int n_les, int kc, void* uhat_les,
+                                   void* cuda_stream) {
+  using namespace ps;
+  using namespace ps::les;
+  if (!uhat_dns || !uhat_les) {
+    set_last_error("ps_les_filter: NULL buffer");
+    return PS_ERR_INVALID_ARG;
+  }
+  const auto ok_n = [](int n) { return n >= 8 && n <= 1024 && n % 2 == 0; };
+  if (!ok_n(n_dns) || !ok_n(n_les) || n_les > n_dns || kc < 0 || 2 * kc >= n_les) {
+    set_last_error("ps_les_filter: need even sizes 8..1024, n_les <= n_dns and 0 <= kc < n_les/2");
+    return PS_ERR_INVALID_ARG;
+  }
+  if (uhat_dns == uhat_les) {
+    set_last_error("ps_les_filter: input and output may not alias");
+    return PS_ERR_INVALID_ARG;
+  }
+  const Geo gd = cube_geo(n_dns), gl = cube_geo(n_les);
+  const long long Ml = (long long)gl.nz * gl.ny * gl.nh;
+  k_truncate<<<blocks(3 * Ml), 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+      static_cast<const V*>(uhat_dns), gd, static_cast<V*>(uhat_les), gl, kc, 3);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("ps_les_filter: ") + cudaGetErrorString(e));
+    return PS_ERR_CUDA;
+  }
+  return PS_OK;
 }

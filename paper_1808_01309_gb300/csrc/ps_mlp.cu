@@ -18,6 +18,7 @@
 #include <string>
 
 #include "ps.h"
+#include "ps_tb.cuh"
 
 namespace ps {
 void set_last_error(const std::string& msg);
@@ -94,6 +95,7 @@ struct Smem {
   float z1[CH][H], z2[CH][H];
   bf dy[CH][16];  // output deltas padded to 16 (columns 6..15 zero)
   bf dz1[CH][H], dz2[CH][H];
+  float yf[CH][8];  // network outputs (tensor-basis fit)
 };
 
 __device__ void load_weights(Smem& s, const float* __restrict__ p) {
@@ -198,9 +200,13 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p
 }
 
 // Forward + backward of the mean-squared error over B samples; gradients and
-// loss accumulate (atomically) into grad[NPARAM] and *loss.
+// loss accumulate (atomically) into grad[NPARAM] and *loss.  TB: the fitted
+// quantity is the model stress sum_n y_n T_n(A/s_A) (T_n the tensor basis of
+// the gradient rows Ag[B][9]) against T/s_tau; otherwise y against T.
+template <bool TB>
 __global__ void __launch_bounds__(128) k_mlp_grad(const float* __restrict__ p, const float* __restrict__ X,
-                                                  const float* __restrict__ T, long long B, float* grad,
+                                                  const float* __restrict__ Ag, const float* __restrict__ T,
+                                                  long long B, float inv_sA, float inv_stau, float* grad,
                                                   double* loss) {
   extern __shared__ __align__(16) unsigned char raw[];
   Smem& s = *reinterpret_cast<Smem*>(raw);
@@ -225,20 +231,53 @@ __global__ void __launch_bounds__(128) k_mlp_grad(const float* __restrict__ p, c
     __syncthreads();
     float yreg[2][4];
     forward_tiles(s, count, nullptr, yreg);
-    // output delta dy = 2 (y - t)/(B * 6); loss terms
+    if constexpr (!TB) {
+      // output delta dy = 2 (y - t)/(B * 6); loss terms
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int r0 = 32 * w + 16 * t;
-      for_acc(r0, 0, [&](int r, int c, int i) {
-        float dy = 0.f;
-        if (c < NO && r < count) {
-          const float e = yreg[t][i] - T[(c0 + r) * NO + c];
+      for (int t = 0; t < 2; ++t) {
+        const int r0 = 32 * w + 16 * t;
+        for_acc(r0, 0, [&](int r, int c, int i) {
+          float dy = 0.f;
+          if (c < NO && r < count) {
+            const float e = yreg[t][i] - T[(c0 + r) * NO + c];
+            lsum += (double)e * e;
+            dy = scale * e;
+          }
+          s.dy[r][c] = __float2bfloat16(dy);
+          s.dy[r][c + 8] = __float2bfloat16(0.f);
+        });
+      }
+    } else {
+      // gather each sample's six outputs, then one lane per sample:
+      // m = Tb^T y, e = m - t/s_tau, dy = 2/(B*6) Tb e
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        for_acc(32 * w + 16 * t, 0, [&](int r, int c, int i) { s.yf[r][c] = yreg[t][i]; });
+      __syncwarp();
+      const int r = 32 * w + lane;
+      float dy[NO] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (r < count) {
+        float a[3][3];
+        const float* ar = Ag + (c0 + r) * 9;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) a[i][j] = ar[3 * i + j];
+        float Tb[6][6];
+        ps::tensor_basis(a, inv_sA, Tb);
+#pragma unroll
+        for (int m = 0; m < NO; ++m) {
+          float mv = 0.f;
+#pragma unroll
+          for (int n = 0; n < NO; ++n) mv += Tb[n][m] * s.yf[r][n];
+          const float e = mv - T[(c0 + r) * NO + m] * inv_stau;
           lsum += (double)e * e;
-          dy = scale * e;
+#pragma unroll
+          for (int n = 0; n < NO; ++n) dy[n] += scale * Tb[n][m] * e;
         }
-        s.dy[r][c] = __float2bfloat16(dy);
-        s.dy[r][c + 8] = __float2bfloat16(0.f);
-      });
+      }
+#pragma unroll
+      for (int n = 0; n < 16; ++n) s.dy[r][n] = __float2bfloat16(n < NO ? dy[n] : 0.f);
     }
     __syncwarp();
     // dh2 = dy W3^T, dz2 = dh2 * gelu'(z2)
@@ -400,10 +439,31 @@ ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long 
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    e = cudaFuncSetAttribute(k_mlp_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return cuerr(e, "ps_mlp_grad");
-  k_mlp_grad<<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, T, count, grad, loss);
+  k_mlp_grad<false><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, nullptr, T, count, 1.f, 1.f, grad, loss);
   return cuerr(cudaGetLastError(), "ps_mlp_grad");
+}
+
+ps_status ps_mlp_grad_tb(const float* params, const float* X, const float* A, const float* T, long long count,
+                         double s_A, double s_tau, float* grad, double* loss, void* stream) {
+  if (!params || !X || !A || !T || !grad || !loss || count <= 0) {
+    ps::set_last_error("ps_mlp_grad_tb: NULL buffer or non-positive count");
+    return PS_ERR_INVALID_ARG;
+  }
+  if (!(s_A > 0) || !(s_tau > 0) || !std::isfinite(s_A) || !std::isfinite(s_tau)) {
+    ps::set_last_error("ps_mlp_grad_tb: scales must be positive and finite");
+    return PS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return cuerr(e, "ps_mlp_grad_tb");
+  k_mlp_grad<true><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, A, T, count, (float)(1.0 / s_A),
+                                                              (float)(1.0 / s_tau), grad, loss);
+  return cuerr(cudaGetLastError(), "ps_mlp_grad_tb");
 }
 
 ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,

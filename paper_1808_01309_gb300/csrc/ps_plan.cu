@@ -668,16 +668,16 @@ ps_status ps_plan_get_timing(ps_plan* p, ps_timing* out) {
   return PS_OK;
 }
 
-ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* norm11) {
+ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* norm12) {
   if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
   if (!params) {
     p->les_on = false;
     return PS_OK;
   }
-  if (!norm11) return fail(PS_ERR_INVALID_ARG, "NULL normalisation");
-  for (int i = 0; i < 11; ++i)
-    if (!std::isfinite(norm11[i]) || (i >= 5 && i < 10 && !(norm11[i] > 0)))
-      return fail(PS_ERR_INVALID_ARG, "normalisation: finite values and positive scales required");
+  if (!norm12) return fail(PS_ERR_INVALID_ARG, "NULL normalisation");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(norm12[i]) || (i >= 5 && !(norm12[i] > 0)))
+      return fail(PS_ERR_INVALID_ARG, "normalisation: finite values, positive std, s_tau and s_A required");
   if (p->cfg.prec != PS_FP32 || p->ng != 1 || p->cfg.dealias == PS_DEALIAS_SPHERICAL)
     return fail(PS_ERR_UNSUPPORTED, "the LES closure needs an FP32 HD plan with the cubic or no truncation");
   const auto les_n = [](int n) { return n >= 16 && n <= 512 && (n % 16 == 0) && ((n & (n - 1)) == 0 || n % 48 == 0); };
@@ -693,12 +693,13 @@ ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* nor
     for (int i = 0; i < 7; ++i) PS_CU(cudaMalloc(&p->les_mem[i], sizes[i]), "closure scratch");
     PS_CU(cudaMemsetAsync(p->les_mem[6], 0, sizes[6], p->stream), "closure scratch");
   }
-  float h[11];
+  float h[12];
   for (int i = 0; i < 5; ++i) {
-    h[i] = (float)norm11[i];
-    h[5 + i] = (float)(1.0 / norm11[5 + i]);
+    h[i] = (float)norm12[i];
+    h[5 + i] = (float)(1.0 / norm12[5 + i]);
   }
-  h[10] = (float)norm11[10];
+  h[10] = (float)norm12[10];
+  h[11] = (float)(1.0 / norm12[11]);
   PS_CU(cudaMemcpyAsync(p->les_mem[0], params, sizeof(float) * PS_MLP_NPARAM, cudaMemcpyDeviceToDevice, p->stream),
         "closure parameters");
   PS_CU(cudaMemcpyAsync(p->les_mem[1], h, sizeof(h), cudaMemcpyHostToDevice, p->stream), "closure scales");

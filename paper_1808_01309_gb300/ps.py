@@ -50,7 +50,8 @@ SYMBOLS = (
     "ps_plan_get_timing", "ps_plan_launch_count", "ps_kind_name", "ps_status_string",
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
-    "ps_plan_set_closure", "ps_les_training_sample",
+    "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
+    "ps_les_filter",
 )
 MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
@@ -125,7 +126,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.c_float, P]
     lib.ps_plan_set_closure.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
     lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
-                                           ctypes.POINTER(ctypes.c_double), P, P, P]
+                                           ctypes.POINTER(ctypes.c_double), P, P, P, P]
+    lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.ps_mlp_grad_tb.argtypes = [P, P, P, P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, P, P, P]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -283,31 +286,41 @@ def ps_mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999
                               float(beta2), float(eps), _stream_handle(stream)))
 
 
-def _norm11(norm):
-    """(mean[5], std[5], s_tau) as a ctypes double[11], or None."""
+def _norm12(norm):
+    """(mean[5], std[5], s_tau, s_A) as a ctypes double[12], or None."""
     if norm is None:
         return None
     if isinstance(norm, dict):
-        vals = list(norm["mean"]) + list(norm["std"]) + [norm["s_tau"]]
+        vals = list(norm["mean"]) + list(norm["std"]) + [norm.get("s_tau", 1.0), norm.get("s_A", 1.0)]
     else:
         vals = list(norm)
-    if len(vals) != 11:
-        raise ValueError("normalisation needs mean[5], std[5] and s_tau")
-    return (ctypes.c_double * 11)(*[float(v) for v in vals])
+    if len(vals) != 12:
+        raise ValueError("normalisation needs mean[5], std[5], s_tau and s_A")
+    return (ctypes.c_double * 12)(*[float(v) for v in vals])
 
 
 def ps_plan_set_closure(plan, params, norm) -> None:
-    """Attach the closure (params: device FP32 vector, norm: mean, std, s_tau);
-    params None detaches it."""
+    """Attach the closure (params: device FP32 vector; norm: mean, std, s_tau,
+    s_A); params None detaches it."""
     if params is None:
         _check(load().ps_plan_set_closure(plan, None, None))
         return
-    _check(load().ps_plan_set_closure(plan, _ptr(params), _norm11(norm)))
+    _check(load().ps_plan_set_closure(plan, _ptr(params), _norm12(norm)))
 
 
-def ps_les_training_sample(n_dns: int, uhat_dns, n_les: int, kc: int, norm, X, T, stream=None) -> None:
-    _check(load().ps_les_training_sample(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _norm11(norm),
-                                         _ptr(X), _ptr(T), _stream_handle(stream)))
+def ps_les_training_sample(n_dns: int, uhat_dns, n_les: int, kc: int, norm, X, A, T, stream=None) -> None:
+    _check(load().ps_les_training_sample(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _norm12(norm),
+                                         _ptr(X), None if A is None else _ptr(A), _ptr(T), _stream_handle(stream)))
+
+
+def ps_les_filter(n_dns: int, uhat_dns, n_les: int, kc: int, uhat_les, stream=None) -> None:
+    _check(load().ps_les_filter(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _ptr(uhat_les),
+                                _stream_handle(stream)))
+
+
+def ps_mlp_grad_tb(params, X, A, T, count: int, s_A: float, s_tau: float, grad, loss, stream=None) -> None:
+    _check(load().ps_mlp_grad_tb(_ptr(params), _ptr(X), _ptr(A), _ptr(T), int(count), float(s_A), float(s_tau),
+                                 _ptr(grad), _ptr(loss), _stream_handle(stream)))
 
 
 # ---- convenience wrapper ------------------------------------------------------------

@@ -118,3 +118,24 @@ def test_training_reduces_the_loss(ps):
         if step in (1, 300):
             losses.append(float(L.item()))
     assert losses[1] < 0.1 * losses[0]
+
+
+@pytest.mark.parametrize("B", [100, 40000])
+def test_tensor_basis_gradients_match_oracle(ps, B):
+    p, X, _ = _case(4, B)
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((B, 9)).astype(np.float32)
+    T = rng.standard_normal((B, 6)).astype(np.float32)
+    s_A, s_tau = 1.7, 0.3
+    dev = "cuda"
+    grad = torch.empty(ps.MLP_NPARAM, device=dev, dtype=torch.float32)
+    loss = torch.empty(1, device=dev, dtype=torch.float64)
+    ps.ps_mlp_grad_tb(torch.from_numpy(pack(p)).to(dev), torch.from_numpy(X).to(dev), torch.from_numpy(A).to(dev),
+                      torch.from_numpy(T).to(dev), B, s_A, s_tau, grad, loss)
+    Bas = les.tensor_basis(A.astype(np.float64).T.reshape(3, 3, B), s_A).transpose(2, 1, 0)
+    L_ref, g_ref = les.mse_and_grads_tb(p, X.astype(np.float64), Bas, T.astype(np.float64) / s_tau,
+                                        rnd=les.bf16_round)
+    assert abs(float(loss.item()) - L_ref) < 1e-4 * L_ref
+    g = unpack(grad.cpu().numpy())
+    for k in ORDER:
+        assert relerr(g[k], g_ref[k]) < 2e-2, k
