@@ -39,6 +39,11 @@ pointwise multilayer perceptron of the resolved velocity-gradient invariants
   L7 loss: mean over samples and the six components of (y - t)^2, where y is
      the network output (plain fit) or the model stress in units of s_tau,
      sum_n g_n T_n (tensor-basis fit).
+  L8 force loss: L = sum over the half spectrum of w |r_hat|^2 (w = 1 on the
+     kx = 0 plane, 2 elsewhere; by Parseval the grid mean of |r|^2), with
+     r_hat = D P(closure term) - f_hat the residual against a given projected,
+     band-limited subgrid force f_hat (the filtered DNS right-hand side minus
+     the LES right-hand side of the filtered state).
 """
 
 from __future__ import annotations
@@ -254,6 +259,39 @@ def closure_term(uh, cfg: sp.Config, p, norm, rnd=None):
         full[(j, i)] = th[m]
     div = np.stack([sum(1j * k[j] * full[(i, j)] for j in range(3)) for i in range(3)])
     return -div * sp.dealias_mask(cfg)
+
+
+def force_loss_and_grads(uh, cfg: sp.Config, p, norm, f_hat, rnd=None):
+    """Force loss of reading L8 and its parameter gradients by the adjoint:
+    r(x) is linear in tau through tau -> D P(-div tau), so
+    dL/dtau_ij(x) = (2 / (Nx Ny Nz)) d r_i / d x_j (r already projected and
+    masked), summed over (i, j) and (j, i) for a stored off-diagonal
+    component; dL/dg_n = s_tau sum_m T_n,m dL/dtau_m per point; the network
+    part is the chain rule of mse_and_grads."""
+    D = sp.dealias_mask(cfg)
+    A = gradient(uh, cfg)
+    lam = invariants(A)
+    X = (lam.reshape(5, -1).T - norm["mean"]) / norm["std"]
+    y, cache = mlp_forward(p, X, rnd)
+    Tb = tensor_basis(A, norm["s_A"]).reshape(6, 6, -1)
+    tau = norm["s_tau"] * np.einsum("nmp,pn->mp", Tb, y).reshape((6,) + lam.shape[1:])
+    th = sp.forward(tau)
+    k = sp.wavenumbers(cfg)
+    full = {}
+    for m, (i, j) in enumerate(SYM):
+        full[(i, j)] = th[m]
+        full[(j, i)] = th[m]
+    div = np.stack([sum(1j * k[j] * full[(i, j)] for j in range(3)) for i in range(3)])
+    r_hat = sp.project(-div * D, cfg) * D - np.asarray(f_hat) * D
+    w = sp.hermitian_weight(cfg)
+    L = float(np.sum(w * np.abs(r_hat) ** 2))
+    # d r_i / d x_j on the grid
+    G = np.stack([np.stack([sp.inverse((1j * k[j] * r_hat[i])[None], cfg)[0] for j in range(3)])
+                  for i in range(3)])
+    scale = 2.0 / (cfg.nx * cfg.ny * cfg.nz)
+    dtau = np.stack([scale * (G[i, j] + G[j, i]) if i != j else scale * G[i, i] for (i, j) in SYM])
+    dy = norm["s_tau"] * np.einsum("nmp,mp->pn", Tb, dtau.reshape(6, -1))
+    return L, _backward(p, cache, dy, rnd)
 
 
 def _les_nonviscous(uh, cfg: sp.Config, p, norm, forcing, rnd):

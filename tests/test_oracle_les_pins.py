@@ -251,3 +251,47 @@ def test_les_step_with_a_zero_network_is_the_plain_step():
     d = les.les_rk_step(u, dt, cfg, p, norm) - oracle.rk_step(u, dt, cfg)
     c = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg)
     assert np.linalg.norm(d - dt * c) < 1e-3 * np.linalg.norm(dt * c)
+
+
+def _force_case(seed=10, n=12):
+    cfg = Config(n, n, n, lx=2 * math.pi, ly=4.0, lz=5.0)
+    u = inputs.random_solenoidal_field(n, n, n, seed=seed, lx=2 * math.pi, ly=4.0, lz=5.0)
+    rng = np.random.default_rng(seed)
+    p = les.init_params(seed=seed)
+    for k in p:
+        p[k] = p[k] + 0.1 * rng.standard_normal(p[k].shape)
+    p["W3"] *= 5
+    lam = les.invariants(les.gradient(u, cfg)).reshape(5, -1)
+    norm = dict(mean=lam.mean(1), std=lam.std(1), s_tau=0.05, s_A=3.0)
+    f = oracle.spectral.project(inputs.forcing_field(n, n, n, seed=3, kmax_shell=5.0, rms=0.01, lx=2 * math.pi,
+                                                     ly=4.0, lz=5.0), cfg) * oracle.dealias_mask(cfg)
+    return cfg, u, p, norm, f
+
+
+def test_force_loss_is_the_grid_mean_of_the_residual():
+    cfg, u, p, norm, f = _force_case()
+    L, _ = les.force_loss_and_grads(u, cfg, p, norm, f)
+    r_hat = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg) - f
+    r = oracle.spectral.inverse(r_hat, cfg)
+    assert abs(L - np.mean(np.sum(r * r, axis=0))) < 1e-13 * L
+    assert L > 0
+
+
+def test_force_loss_gradients_match_central_differences():
+    cfg, u, p, norm, f = _force_case()
+    _, g = les.force_loss_and_grads(u, cfg, p, norm, f)
+    rng = np.random.default_rng(12)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = les.force_loss_and_grads(u, cfg, p, norm, f)
+            flat[idx] = old - h
+            lm, _ = les.force_loss_and_grads(u, cfg, p, norm, f)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            scale = max(np.max(np.abs(g[name])), 1e-30)
+            assert abs(fd - an) <= 1e-5 * scale, (name, idx, fd, an)
