@@ -251,6 +251,12 @@ ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long 
 ps_status ps_mlp_grad_tb(const float* params, const float* X, const float* A, const float* T, long long count,
                          double s_A, double s_tau, float* grad, double* loss, void* cuda_stream);
 
+/* Backpropagation only: grad += dL/dparams for given output deltas
+ * dY[count][6] = dL/dy at the samples X[count][5] (device FP32; grad is
+ * accumulated, not overwritten).  Asynchronous. */
+ps_status ps_mlp_backward(const float* params, const float* X, const float* dY, long long count, float* grad,
+                          void* cuda_stream);
+
 /* One Adam update (bias-corrected, step >= 1) of params with the moment
  * buffers m, v (device FP32, PS_MLP_NPARAM each, zero before step 1). */
 ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
@@ -273,6 +279,18 @@ ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int 
  * scratch on first use (about 29 floats per grid point); synchronises the
  * plan stream.  PS_ERR_UNSUPPORTED for FP64, MHD or spherical truncation. */
 ps_status ps_plan_set_closure(ps_plan* plan, const float* params, const double* norm12);
+
+/* Force-matched training of the attached closure (ps_plan_set_closure gives
+ * the normalisation; params here replaces the attached network):
+ *   L = sum over the half spectrum of w |D P(-div tau(ubar)) - f|^2
+ * (w = 1 on the kx = 0 plane, 2 elsewhere; by Parseval the grid mean of the
+ * squared residual), with f a projected, band-limited subgrid force in the
+ * state layout, e.g. the filtered DNS right-hand side minus the LES
+ * right-hand side of the filtered state.  Adds L to *loss (device double) and
+ * dL/dparams to grad (device FP32); accumulate = 0 zeroes both first.
+ * Allocates 9 more floats per grid point on first use.  Asynchronous. */
+ps_status ps_plan_closure_grad(ps_plan* plan, const float* params, const void* ubar, const void* force, float* grad,
+                               double* loss, int accumulate);
 
 /* Training data for the closure from one DNS state (FP32, n_dns^3, 2 pi box,
  * HD layout, device): with F the box filter |p|,|q|,|r| <= kc and ubar = F[u]

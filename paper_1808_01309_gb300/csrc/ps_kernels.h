@@ -95,15 +95,21 @@ cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double*
 // `in`, written to the compact buffer s.extra ([3][cz][cy][kxp], FP32).
 struct LesScratch {
   const float* params;  // MLP parameters (PS_MLP_NPARAM)
-  const float* norm;    // mean[5], 1/std[5], s_tau (device)
+  const float* norm;    // mean[5], 1/std[5], s_tau, 1/s_A (device)
   float2* spec;         // [9][nz][ny][nh]
   float* phys;          // [9][nz][ny][nx]
   float* X;             // [P][5]
   float* Y;             // [P][6]
   float2* extra;        // compact closure term
+  float* Arows;         // [P][9] gradient rows (training only)
 };
 cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void* twy, const void* twz,
                              const LesScratch& s, cudaStream_t st);
+// Force loss (sum over the half spectrum of w |D P(closure) - f|^2) of the
+// state `in` against the subgrid force f (full layout), added to *loss, and
+// its parameter gradient added to grad; params replaces s.params.
+cudaError_t les_closure_grad(const Geo& g, Spec in, Spec f, const void* twx, const void* twy, const void* twz,
+                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st);
 
 // Plan internals used by the ensemble layer (ps_plan.cu).
 void plan_set_stream(struct ::ps_plan* p, cudaStream_t s);

@@ -353,6 +353,78 @@ __global__ void k_div(const Geo g, const V* __restrict__ th, V* __restrict__ ext
   }
 }
 
+// r_hat = D P(extra) - f for the full-layout modes (zero outside the kept
+// set), loss += sum w |r_hat|^2 (w = 1 on the kx = 0 plane, else 2).
+__global__ void k_force_residual(const Geo g, const V* __restrict__ extra, const Spec f, V* __restrict__ rh,
+                                 double* loss) {
+  __shared__ double red[32];
+  const long long total = (long long)g.nz * g.ny * g.nh;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % g.nh), qi = (int)((i / g.nh) % g.ny), ri = (int)(i / ((long long)g.nh * g.ny));
+    const int q = sidx(qi, g.ny), r = sidx(ri, g.nz);
+    V o[3] = {czero<V>(), czero<V>(), czero<V>()};
+    if (kept(g, p, q, r)) {
+      const long long cs = (long long)g.cz * g.cy * g.kxp;
+      const long long ci = ((long long)rowof(r, g.cz) * g.cy + rowof(q, g.cy)) * g.kxp + p;
+      V v[3] = {extra[ci], extra[ci + cs], extra[ci + 2 * cs]};
+      const float kx = float(p * g.sx), ky = float(q * g.sy), kz = float(r * g.sz);
+      const float k2 = kx * kx + ky * ky + kz * kz;
+      if (k2 > 0.f) {
+        const V kd = cadd(cadd(cscale(v[0], kx), cscale(v[1], ky)), cscale(v[2], kz));
+        const float ik2 = 1.f / k2;
+        v[0] = csub(v[0], cscale(kd, kx * ik2));
+        v[1] = csub(v[1], cscale(kd, ky * ik2));
+        v[2] = csub(v[2], cscale(kd, kz * ik2));
+      } else {
+        v[0] = v[1] = v[2] = czero<V>();
+      }
+      const V* fp = static_cast<const V*>(f.p) + (long long)rowof(r, f.zwrap) * f.zs +
+                    (long long)rowof(q, f.ywrap) * f.ys + p;
+      const double w = p == 0 ? 1.0 : 2.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c] = csub(v[c], fp[c * f.cs]);
+        acc += w * ((double)o[c].x * o[c].x + (double)o[c].y * o[c].y);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rh[c * total + i] = o[c];
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(loss, t);
+}
+
+// dL/dg_n = s_tau sum_m T_n,m(A/s_A) dL/dtau_m with dL/dtau_ij = c d r_i/d x_j
+// (both orders for an off-diagonal component); G holds d r_i / d x_j as 9
+// planar fields [3i+j], Arows the gradient of the state.
+__global__ void k_dg(const float* __restrict__ Arows, const float* __restrict__ G, const float* __restrict__ norm,
+                     float c, float* __restrict__ dY, long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float a[3][3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a[k / 3][k % 3] = Arows[p * 9 + k];
+  float Tb[6][6];
+  tensor_basis(a, norm[11], Tb);
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+  float dt[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const float gij = G[(3 * ii[m] + jj[m]) * P + p];
+    dt[m] = c * (m < 3 ? gij : gij + G[(3 * jj[m] + ii[m]) * P + p]);
+  }
+  const float st = norm[10];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    float v = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) v += Tb[n][m] * dt[m];
+    dY[p * 6 + n] = st * v;
+  }
+}
+
 }  // namespace les
 
 cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void* twy, const void* twz,
@@ -382,6 +454,59 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
     k_div<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(g, s.spec, s.extra);
     e = cudaGetLastError();
   }
+  return e;
+}
+
+cudaError_t les_closure_grad(const Geo& g, Spec in, Spec f, const void* twx, const void* twy, const void* twz,
+                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st) {
+  using namespace les;
+  const long long P = (long long)g.nx * g.ny * g.nz;
+  const long long M = (long long)g.nz * g.ny * g.nh;
+  const V *tx = static_cast<const V*>(twx), *ty = static_cast<const V*>(twy), *tz = static_cast<const V*>(twz);
+  // forward: features (keeping the gradient rows), network, stress, its
+  // divergence (compact), as in les_closure_term
+  k_grad<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(g, in, s.spec);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = spec2phys(g, 9, s.spec, s.phys, tx, ty, tz, st);
+  if (e == cudaSuccess) {
+    k_features<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.X, s.Arows, P, s.norm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && ps_mlp_forward(params, s.X, s.Y, P, st) != PS_OK) e = cudaErrorLaunchFailure;
+  if (e == cudaSuccess) {
+    k_stress<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.phys, s.Y, P, s.norm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = phys2spec(g, 6, s.phys, s.spec, tx, ty, tz, st);
+  if (e == cudaSuccess) {
+    const long long C = (long long)g.cz * g.cy * g.cx;
+    k_div<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(g, s.spec, s.extra);
+    e = cudaGetLastError();
+  }
+  // residual and loss; d r_i / d x_j (k_grad reads each mode's three values
+  // before writing its nine, so it runs in place on the spectral buffer)
+  if (e == cudaSuccess) {
+    k_force_residual<<<1024, 256, 0, st>>>(g, s.extra, f, s.spec, loss);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    Spec r;
+    r.p = s.spec;
+    r.ys = g.nh;
+    r.zs = (long long)g.ny * g.nh;
+    r.cs = M;
+    r.zwrap = g.nz;
+    r.ywrap = g.ny;
+    k_grad<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(g, r, s.spec);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = spec2phys(g, 9, s.spec, s.phys, tx, ty, tz, st);
+  // adjoint through the tensor basis, then the network
+  if (e == cudaSuccess) {
+    k_dg<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(s.Arows, s.phys, s.norm, (float)(2.0 / (double)P), s.Y, P);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && ps_mlp_backward(params, s.X, s.Y, P, grad, st) != PS_OK) e = cudaErrorLaunchFailure;
   return e;
 }
 

@@ -199,11 +199,14 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p
   }
 }
 
-// Forward + backward of the mean-squared error over B samples; gradients and
-// loss accumulate (atomically) into grad[NPARAM] and *loss.  TB: the fitted
-// quantity is the model stress sum_n y_n T_n(A/s_A) (T_n the tensor basis of
-// the gradient rows Ag[B][9]) against T/s_tau; otherwise y against T.
-template <bool TB>
+// Forward + backward over B samples; parameter gradients accumulate
+// (atomically) into grad[NPARAM] and the loss into *loss.
+//   MODE_PLAIN: mean-squared error of y against T
+//   MODE_TB   : mean-squared error of the model stress sum_n y_n T_n(A/s_A)
+//               (T_n the tensor basis of the gradient rows Ag[B][9]) against T/s_tau
+//   MODE_DY   : no loss; T holds dL/dy per sample (backpropagation only)
+enum { MODE_PLAIN = 0, MODE_TB = 1, MODE_DY = 2 };
+template <int MODE>
 __global__ void __launch_bounds__(128) k_mlp_grad(const float* __restrict__ p, const float* __restrict__ X,
                                                   const float* __restrict__ Ag, const float* __restrict__ T,
                                                   long long B, float inv_sA, float inv_stau, float* grad,
@@ -231,7 +234,17 @@ __global__ void __launch_bounds__(128) k_mlp_grad(const float* __restrict__ p, c
     __syncthreads();
     float yreg[2][4];
     forward_tiles(s, count, nullptr, yreg);
-    if constexpr (!TB) {
+    if constexpr (MODE == MODE_DY) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int r0 = 32 * w + 16 * t;
+        for_acc(r0, 0, [&](int r, int c, int i) {
+          const float dy = (c < NO && r < count) ? T[(c0 + r) * NO + c] : 0.f;
+          s.dy[r][c] = __float2bfloat16(dy);
+          s.dy[r][c + 8] = __float2bfloat16(0.f);
+        });
+      }
+    } else if constexpr (MODE == MODE_PLAIN) {
       // output delta dy = 2 (y - t)/(B * 6); loss terms
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -381,8 +394,10 @@ __global__ void __launch_bounds__(128) k_mlp_grad(const float* __restrict__ p, c
     if (c < NO) atomicAdd(grad + OFF_B3 + c, bsum2);
   }
   // loss
-  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-  if (lane == 0) atomicAdd(loss, lsum / (double)(B * NO));
+  if constexpr (MODE != MODE_DY) {
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) atomicAdd(loss, lsum / (double)(B * NO));
+  }
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -439,9 +454,9 @@ ps_status ps_mlp_grad(const float* params, const float* X, const float* T, long 
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    e = cudaFuncSetAttribute(k_mlp_grad<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return cuerr(e, "ps_mlp_grad");
-  k_mlp_grad<false><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, nullptr, T, count, 1.f, 1.f, grad, loss);
+  k_mlp_grad<MODE_PLAIN><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, nullptr, T, count, 1.f, 1.f, grad, loss);
   return cuerr(cudaGetLastError(), "ps_mlp_grad");
 }
 
@@ -459,11 +474,27 @@ ps_status ps_mlp_grad_tb(const float* params, const float* X, const float* A, co
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    e = cudaFuncSetAttribute(k_mlp_grad<MODE_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return cuerr(e, "ps_mlp_grad_tb");
-  k_mlp_grad<true><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, A, T, count, (float)(1.0 / s_A),
+  k_mlp_grad<MODE_TB><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, A, T, count, (float)(1.0 / s_A),
                                                               (float)(1.0 / s_tau), grad, loss);
   return cuerr(cudaGetLastError(), "ps_mlp_grad_tb");
+}
+
+ps_status ps_mlp_backward(const float* params, const float* X, const float* dY, long long count, float* grad,
+                          void* stream) {
+  if (!params || !X || !dY || !grad || count < 0) {
+    ps::set_last_error("ps_mlp_backward: NULL buffer or negative count");
+    return PS_ERR_INVALID_ARG;
+  }
+  if (count == 0) return PS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_mlp_grad<MODE_DY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return cuerr(e, "ps_mlp_backward");
+  k_mlp_grad<MODE_DY><<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, nullptr, dY, count, 1.f, 1.f, grad,
+                                                                 nullptr);
+  return cuerr(cudaGetLastError(), "ps_mlp_backward");
 }
 
 ps_status ps_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,

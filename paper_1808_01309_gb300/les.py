@@ -102,6 +102,34 @@ def train(params, X, A, T, norm: dict, iters: int = 2000, lr: float = 2e-3, log_
     return log
 
 
+def train_force(plan, params, norm: dict, snaps, iters: int = 1000, lr: float = 1e-3, log_every: int = 100):
+    """Full-batch Adam on the force loss (ps_plan_closure_grad) summed over
+    the snapshots (ubar, exact force); logs the loss relative to the exact
+    forces' own mean square (Parseval on the LES grid)."""
+    torch = _torch()
+    plan.set_closure(params, norm)
+    grad = torch.empty_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.empty(1, device=params.device, dtype=torch.float64)
+    zero = torch.zeros(ps.MLP_NPARAM, device=params.device, dtype=torch.float32)
+    # the exact forces' mean square: the loss of the zero network
+    z = torch.empty_like(loss)
+    for k, (ub, f) in enumerate(snaps):
+        plan.closure_grad(zero, ub, f, grad, z, accumulate=k > 0)
+    ref = float(z.item())
+    log = []
+    for it in range(1, iters + 1):
+        for k, (ub, f) in enumerate(snaps):
+            plan.closure_grad(params, ub, f, grad, loss, accumulate=k > 0)
+        if it == 1 or it % log_every == 0 or it == iters:
+            log.append((it, float(loss.item()) / ref))
+        rate = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * (it - 1) / max(iters - 1, 1))))
+        ps.ps_mlp_adam(params, grad, m, v, it, rate)
+    plan.set_closure(None)
+    return log
+
+
 def shell_transfer(uhat, force, kc: int) -> np.ndarray:
     """Energy transfer spectrum T(K) = sum over shell K of w Re(conj(u) . f)
     (w = 1 on the kx = 0 plane, 2 elsewhere) for K = 0..kc; host analysis of
@@ -156,7 +184,11 @@ def _timed_steps(plan, u, dt: float, nsteps: int, t0: float) -> float:
 
 
 def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_spin=4.0, t_train=1.0,
-               n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, seed=1, verbose=True) -> dict:
+               n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, fit="both", force_iters=1000,
+               force_lr=1e-3, seed=1, verbose=True) -> dict:
+    """Runs the workflow of the module docstring; fit = "stress" (tensor-basis
+    stress loss), "force" (stress fit refined on the force loss) or "both"
+    (both models evaluated)."""
     torch = _torch()
     dev = "cuda"
     say = print if verbose else (lambda *a, **k: None)
@@ -182,23 +214,29 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     d0 = dns.diagnostics(u)
     say(f"spin-up to t={t:.2f}: E={d0['energy']:.4f} Omega={d0['enstrophy']:.2f} max|u|={d0['max_u']:.3f}")
     out["dns_after_spinup"] = dict(energy=d0["energy"], enstrophy=d0["enstrophy"], max_u=d0["max_u"])
-    # 2. training pairs over the training window
+    # 2. training data over the training window: stress pairs (X, A, T) and,
+    #    for the force fit, the filtered state with its exact subgrid force
+    f_les = torch.from_numpy(inputs.forcing_field(n_les, n_les, n_les, seed=2)).to(dev, torch.complex64)
+    les_plan = ps.Plan(n_les, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=f_les)
     gap = int(round(t_train / n_snap / dt_dns))
     Xr, A, T = training_pairs(u, n_dns, n_les, kc)
     norm = calibrate(Xr, A, T)
     del Xr
-    Xs, As, Ts = [], [], []
+    Xs, As, Ts, snaps = [], [], [], []
     for k in range(n_snap):
         X, A, T = training_pairs(u, n_dns, n_les, kc, norm)
         Xs.append(X)
         As.append(A)
         Ts.append(T)
+        if fit in ("force", "both"):
+            ubar, exact, _ = sgs_force(dns, les_plan, u, n_dns, n_les, kc)
+            snaps.append((ubar, exact))
         _timed_steps(dns, u, dt_dns, gap, t)
         t += gap * dt_dns
     X, A, T = torch.cat(Xs), torch.cat(As), torch.cat(Ts)
     del Xs, As, Ts
     say(f"training pairs: {X.shape[0]} points from {n_snap} snapshots; s_A={norm['s_A']:.3f} s_tau={norm['s_tau']:.4g}")
-    # 3. fit
+    # 3. fit: stress (tensor-basis MSE), then optionally the force loss
     params = torch.from_numpy(init_params(seed)).to(dev)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
@@ -210,20 +248,30 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     tt = (T.double() / norm["s_tau"]).pow(2).mean().item()
     out["fit"] = dict(loss_log=log, target_mean_square=tt, explained=1.0 - log[-1][1] / tt, seconds=t_fit,
                       samples=int(X.shape[0]))
-    say(f"fit: loss {log[0][1]:.4f} -> {log[-1][1]:.4f} (target mean square {tt:.4f}) in {t_fit:.1f} s")
+    say(f"stress fit: loss {log[0][1]:.4f} -> {log[-1][1]:.4f} (target mean square {tt:.4f}) in {t_fit:.1f} s")
     del X, A, T
     out["norm"] = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in norm.items()}
+    models = {"learned_stress": params}
+    if fit in ("force", "both"):
+        pf = params.clone()
+        w0 = time.perf_counter()
+        flog = train_force(les_plan, pf, norm, snaps, iters=force_iters, lr=force_lr)
+        torch.cuda.synchronize()
+        out["force_fit"] = dict(loss_log=flog, seconds=time.perf_counter() - w0)
+        say(f"force fit: relative loss {flog[0][1]:.4f} -> {flog[-1][1]:.4f}")
+        models = {"learned_force": pf} if fit == "force" else {"learned_stress": params, "learned_force": pf}
+    del snaps
     # 4. evaluation window: LES initial state, a-priori energy transfer of
     #    the exact and the modelled subgrid force, DNS spectra
-    f_les = torch.from_numpy(inputs.forcing_field(n_les, n_les, n_les, seed=2)).to(dev, torch.complex64)
-    les_plan = ps.Plan(n_les, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=f_les)
-    les0, exact, model = sgs_force(dns, les_plan, u, n_dns, n_les, kc, closure=(params, norm))
+    les0, exact, _ = sgs_force(dns, les_plan, u, n_dns, n_les, kc)
+    out["transfer"] = dict(exact=shell_transfer(les0, exact, kc).tolist())
+    say("SGS transfer exact: " + " ".join(f"{x:+.2e}" for x in out["transfer"]["exact"][1:]))
+    for name, pm in models.items():
+        _, _, model = sgs_force(dns, les_plan, u, n_dns, n_les, kc, closure=(pm, norm))
+        out["transfer"][name] = shell_transfer(les0, model, kc).tolist()
+        say(f"SGS transfer {name}: " + " ".join(f"{x:+.2e}" for x in out["transfer"][name][1:]))
     les_plan.close()
-    T_exact, T_model = shell_transfer(les0, exact, kc), shell_transfer(les0, model, kc)
-    out["transfer"] = dict(exact=T_exact.tolist(), model=T_model.tolist())
-    say("SGS transfer exact: " + " ".join(f"{x:+.2e}" for x in T_exact[1:]))
-    say("SGS transfer model: " + " ".join(f"{x:+.2e}" for x in T_model[1:]))
-    del exact, model
+    del exact
     t_eval0 = t
     n_dns_eval = int(round(t_eval / dt_dns))
     per = n_dns_eval // n_eval
@@ -242,7 +290,7 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     dns_ms = 1e3 * secs_dns / (per * n_eval)
     les_per = int(round(per * dt_dns / dt_les))
     runs = {}
-    for name, closure in (("learned", params), ("no_model", None)):
+    for name, closure in list(models.items()) + [("no_model", None)]:
         plan = ps.Plan(n_les, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=f_les)
         if closure is not None:
             plan.set_closure(closure, norm)
@@ -271,7 +319,7 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
         else:
             say(f"LES {name}: non-finite state")
         runs[name] = r
-    les_ms = runs["learned"]["ms_per_step"]
+    les_ms = runs[next(iter(models))]["ms_per_step"]
     out["dns"] = dict(ms_per_step=dns_ms, spectrum=np.mean(spec_dns, axis=0)[1:].tolist(), steps=per * n_eval,
                       energy=e_dns)
     out["les"] = runs
@@ -296,11 +344,14 @@ def main(argv=None):
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--fit", choices=("stress", "force", "both"), default="both")
+    ap.add_argument("--force-iters", type=int, default=1000)
+    ap.add_argument("--force-lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None, help="write the result as JSON here")
     a = ap.parse_args(argv)
     r = experiment(n_dns=a.n_dns, n_les=a.n_les, kc=a.kc, nu=a.nu, dt_dns=a.dt_dns, dt_les=a.dt_les,
                    t_spin=a.t_spin, t_train=a.t_train, n_snap=a.n_snap, t_eval=a.t_eval, n_eval=a.n_eval,
-                   iters=a.iters, lr=a.lr)
+                   iters=a.iters, lr=a.lr, fit=a.fit, force_iters=a.force_iters, force_lr=a.force_lr)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(r, fh, indent=1)

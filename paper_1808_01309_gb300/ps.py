@@ -51,7 +51,7 @@ SYMBOLS = (
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
-    "ps_les_filter",
+    "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad",
 )
 MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_set_closure.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
     lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double), P, P, P, P]
+    lib.ps_mlp_backward.argtypes = [P, P, P, ctypes.c_longlong, P, P]
+    lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
     lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
     lib.ps_mlp_grad_tb.argtypes = [P, P, P, P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, P, P, P]
     for name in SYMBOLS:
@@ -313,6 +315,15 @@ def ps_les_training_sample(n_dns: int, uhat_dns, n_les: int, kc: int, norm, X, A
                                          _ptr(X), None if A is None else _ptr(A), _ptr(T), _stream_handle(stream)))
 
 
+def ps_mlp_backward(params, X, dY, count: int, grad, stream=None) -> None:
+    _check(load().ps_mlp_backward(_ptr(params), _ptr(X), _ptr(dY), int(count), _ptr(grad), _stream_handle(stream)))
+
+
+def ps_plan_closure_grad(plan, params, ubar, force, grad, loss, accumulate: bool = False) -> None:
+    _check(load().ps_plan_closure_grad(plan, _ptr(params), _ptr(ubar), _ptr(force), _ptr(grad), _ptr(loss),
+                                       1 if accumulate else 0))
+
+
 def ps_les_filter(n_dns: int, uhat_dns, n_les: int, kc: int, uhat_les, stream=None) -> None:
     _check(load().ps_les_filter(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _ptr(uhat_les),
                                 _stream_handle(stream)))
@@ -370,6 +381,13 @@ class Plan:
     def set_closure(self, params, norm=None):
         """Attach a trained LES closure (see ps_plan_set_closure); None detaches."""
         ps_plan_set_closure(self.handle, params, norm)
+
+    def closure_grad(self, params, ubar, force, grad, loss, accumulate=False):
+        """Force-matched loss and gradient of the attached closure (see
+        ps_plan_closure_grad)."""
+        self._check_field(ubar)
+        self._check_field(force)
+        ps_plan_closure_grad(self.handle, params, ubar, force, grad, loss, accumulate)
 
     def close(self):
         if self.handle:

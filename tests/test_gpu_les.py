@@ -266,12 +266,61 @@ def test_les_workflow_improves_on_the_plain_les(ps):
     the plain solver at the same resolution (which piles energy up at kc)."""
     from paper_1808_01309_gb300 import les as wf
     r = wf.experiment(n_dns=128, n_les=32, kc=10, t_spin=2.0, t_train=0.5, n_snap=4, t_eval=2.0, n_eval=4,
-                      iters=300, verbose=False)
+                      iters=300, fit="both", force_iters=200, verbose=False)
     log = r["fit"]["loss_log"]
     assert log[-1][1] < log[0][1]
-    learned, plain = r["les"]["learned"], r["les"]["no_model"]
-    assert learned["finite"] and plain["finite"]
-    assert learned["max_rel_err"] < 0.5 * plain["max_rel_err"]
+    flog = r["force_fit"]["loss_log"]
+    assert flog[-1][1] < flog[0][1]
+    plain = r["les"]["no_model"]
+    assert plain["finite"]
+    for name in ("learned_stress", "learned_force"):
+        learned = r["les"][name]
+        assert learned["finite"], name
+        assert learned["max_rel_err"] < 0.5 * plain["max_rel_err"], name
     # the exact subgrid force drains energy near the cutoff
     assert r["transfer"]["exact"][-1] < 0
     assert r["cost_ratio"] > 1.0
+
+
+def test_closure_force_gradient_matches_oracle(ps):
+    n = 32
+    lx, ly, lz = 2 * math.pi, 5.0, 2 * math.pi
+    cfg = oracle.Config(n, n, n, lx=lx, ly=ly, lz=lz, nu=1e-3)
+    u = inputs.random_solenoidal_field(n, n, n, seed=16, kmax=(n, n, n), lx=lx, ly=ly, lz=lz)
+    v, p = fp32_params(6)
+    norm = norm_of(u, cfg, 0.05)
+    D = oracle.dealias_mask(cfg)
+    c = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg)
+    f = oracle.spectral.project(inputs.forcing_field(n, n, n, seed=3, kmax_shell=9.0, rms=1.0, lx=lx, ly=ly, lz=lz),
+                                cfg) * D
+    f = f * (0.7 * np.linalg.norm(c) / np.linalg.norm(f))
+    f = f.astype(np.complex64).astype(np.complex128)  # the device sees FP32 values
+    plan = ps.Plan(n, n, n, lx=lx, ly=ly, lz=lz, prec=ps.Precision.FP32, nu=1e-3)
+    dv = torch.from_numpy(v).cuda()
+    plan.set_closure(dv, norm)
+    grad = torch.empty(ps.MLP_NPARAM, device="cuda", dtype=torch.float32)
+    loss = torch.empty(1, device="cuda", dtype=torch.float64)
+    ud, fd = to_dev(u), to_dev(f)
+    plan.closure_grad(dv, ud, fd, grad, loss)
+    L_ref, g_ref = les.force_loss_and_grads(u, cfg, p, norm, f, rnd=les.bf16_round)
+    assert abs(loss.item() - L_ref) < 1e-3 * L_ref
+    g = grad.cpu().numpy().astype(np.float64)
+    o = 0
+    for k in ORDER:
+        sz = p[k].size
+        assert relerr(g[o:o + sz], g_ref[k].reshape(-1)) < 3e-2, k
+        o += sz
+    # accumulation adds a second copy
+    plan.closure_grad(dv, ud, fd, grad, loss, accumulate=True)
+    assert abs(loss.item() - 2 * L_ref) < 2e-3 * L_ref
+    assert relerr(grad.cpu().numpy() / 2, g) < 1e-6
+    # a few Adam steps on the force loss lower it
+    m, vv = torch.zeros_like(dv), torch.zeros_like(dv)
+    first = None
+    for it in range(1, 41):
+        plan.closure_grad(dv, ud, fd, grad, loss)
+        first = first or loss.item()
+        ps.ps_mlp_adam(dv, grad, m, vv, it, 3e-3)
+    plan.closure_grad(dv, ud, fd, grad, loss)
+    assert loss.item() < 0.8 * first
+    plan.close()
