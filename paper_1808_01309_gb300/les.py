@@ -183,7 +183,7 @@ def _timed_steps(plan, u, dt: float, nsteps: int, t0: float) -> float:
     return time.perf_counter() - w0
 
 
-def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_spin=4.0, t_train=1.0,
+def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_spin=8.0, t_train=2.0,
                n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, fit="both", force_iters=1000,
                force_lr=1e-3, seed=1, verbose=True) -> dict:
     """Runs the workflow of the module docstring; fit = "stress" (tensor-basis
@@ -337,8 +337,8 @@ def main(argv=None):
     ap.add_argument("--nu", type=float, default=2e-3)
     ap.add_argument("--dt-dns", type=float, default=1e-3)
     ap.add_argument("--dt-les", type=float, default=5e-3)
-    ap.add_argument("--t-spin", type=float, default=4.0)
-    ap.add_argument("--t-train", type=float, default=1.0)
+    ap.add_argument("--t-spin", type=float, default=8.0)
+    ap.add_argument("--t-train", type=float, default=2.0)
     ap.add_argument("--n-snap", type=int, default=8)
     ap.add_argument("--t-eval", type=float, default=5.0)
     ap.add_argument("--n-eval", type=int, default=10)
