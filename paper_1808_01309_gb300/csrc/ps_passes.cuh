@@ -146,19 +146,43 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
 #pragma unroll 1
   for (int grp = 0; grp < NG; ++grp) {
   const V* in = static_cast<const V*>(a.in.p) + 3 * grp * a.in.cs;
-  // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i)
+  // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i) at
+  // tile[((c NB + b) cz + i) TX + col]; thread tid keeps column tid % TX and
+  // walks the rows (c, b, i) with stride NTH / TX (counters, no division)
   {
-    const int per_c = NB * g.cz * TX;
-    for (int e = tid; e < 3 * per_c; e += NTH) {
-      const int col = e % TX, i = (e / TX) % g.cz, b = (e / (TX * g.cz)) % NB, c = e / per_c;
-      const int iyb = blockIdx.y * NB + b, kxc = blockIdx.x * TX + col;
-      if (iyb >= g.cy || kxc > g.Kx) continue;
-      const int qb = iyb <= g.Ky ? iyb : iyb - g.cy;
-      const int r = i <= g.Kz ? i : i - g.cz;
-      const V* src = in + c * a.in.cs + (long long)rowof(r, a.in.zwrap) * a.in.zs +
-                     (long long)rowof(qb, a.in.ywrap) * a.in.ys + kxc;
-      if constexpr (sizeof(V) == 8) cp_async8(tile + e, src);
-      else cp_async16(tile + e, src);
+    static_assert(NTH % TX == 0, "whole rows per pass");
+    constexpr int RSTEP = NTH / TX;
+    const int col = tid % TX;
+    const int kxc = blockIdx.x * TX + col;
+    if (kxc <= g.Kx) {
+      int i = tid / TX, b = 0, c = 0;
+      while (i >= g.cz) {
+        i -= g.cz;
+        if (++b == NB) {
+          b = 0;
+          ++c;
+        }
+      }
+      V* dst = tile + (tid / TX) * TX + col;
+      for (; c < 3; dst += RSTEP * TX) {
+        const int iyb = blockIdx.y * NB + b;
+        if (iyb < g.cy) {
+          const int qb = iyb <= g.Ky ? iyb : iyb - g.cy;
+          const int r = i <= g.Kz ? i : i - g.cz;
+          const V* src = in + c * a.in.cs + (long long)rowof(r, a.in.zwrap) * a.in.zs +
+                         (long long)rowof(qb, a.in.ywrap) * a.in.ys + kxc;
+          if constexpr (sizeof(V) == 8) cp_async8(dst, src);
+          else cp_async16(dst, src);
+        }
+        i += RSTEP;
+        while (i >= g.cz) {
+          i -= g.cz;
+          if (++b == NB) {
+            b = 0;
+            ++c;
+          }
+        }
+      }
     }
     cp_async_commit();
     cp_async_wait<0>();
