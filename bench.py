@@ -38,12 +38,13 @@ sys.path.insert(0, ROOT)
 METRIC = "RHS Gpoints/s and time/RK step at 512^3, FP32 vs FP64 on GPU, % HBM roofline"
 UNIT = "Gpoints/s"
 FALLBACK_HBM_GBS = 6800.0
+_COMMON = ["ps_passes.cuh", "ps_fft.cuh", "ps_async.cuh", "ps_kernels.h"]
 KIND_FILES = {
-    "z_inverse": ["ps_passes.cuh", "ps_fft.cuh", "k_zinv_f32.cu"],
-    "y_inverse": ["ps_passes.cuh", "ps_fft.cuh", "k_yinv_f32.cu"],
-    "x_fused": ["ps_passes.cuh", "ps_fft.cuh", "k_xpass_f32.cu"],
-    "y_forward": ["ps_passes.cuh", "ps_fft.cuh", "k_yfwd_f32.cu"],
-    "z_forward_rk": ["ps_passes.cuh", "ps_fft.cuh", "k_zfwd_f32.cu"],
+    "z_inverse": _COMMON + ["k_zinv_f32.cu"],
+    "y_inverse": _COMMON + ["k_yinv_f32.cu"],
+    "x_fused": _COMMON + ["k_xpass_f32.cu"],
+    "y_forward": _COMMON + ["k_yfwd_f32.cu"],
+    "z_forward_rk": _COMMON + ["k_zfwd_f32.cu"],
 }
 
 
