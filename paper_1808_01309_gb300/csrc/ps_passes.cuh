@@ -524,6 +524,18 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(
     q = iy <= g.Ky ? iy : iy - g.cy;
   }
   const bool colin = bret && kx < g.kxp;
+  const long long fcs = (long long)g.nz * g.ny * g.nh;   // caller layout component stride
+  if (full && !__syncthreads_or(colin && kx <= g.Kx)) {
+    // the whole tile lies outside the retained set: its modes are zero
+    if (bvalid && kx < g.nh) {
+      V* po = static_cast<V*>(a.out_full) + (long long)bidx * g.nh + kx;
+#pragma unroll 1
+      for (int c = 0; c < 3 * NG; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) po[c * fcs + (long long)(j0 + m * (N / E)) * g.ny * g.nh] = czero<V>();
+    }
+    return;
+  }
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* tw = static_cast<const V*>(a.tw_z);
   const long long cs_in = (long long)g.nz * g.cy * g.kxp;
@@ -533,7 +545,6 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(
   const V* fb = static_cast<const V*>(a.fbox);
   const T dt = T(a.dt);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
-  const long long fcs = (long long)g.nz * g.ny * g.nh;   // caller layout component stride
   // group 0: velocity (forcing, Leray projection, viscosity nu)
   // group 1 (MHD): magnetic field (curl of the transformed u x B, diffusivity eta)
 #pragma unroll 1
