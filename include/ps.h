@@ -153,10 +153,27 @@ ps_status ps_rhs(ps_plan* plan, const void* uhat, void* rhs_out, double t);
  * (ps_step_stats).  dt must be finite.  Asynchronous. */
 ps_status ps_rk_step(ps_plan* plan, void* uhat, double dt, double t);
 
-/* Same as nsteps calls of ps_rk_step on a HOST buffer: copies the state to a
- * plan-owned device buffer (allocated on the first call), steps, copies it
- * back and synchronises.  uhat_host should be page-locked for full speed. */
+/* Same as nsteps calls of ps_rk_step on a HOST buffer, then synchronises
+ * (nsteps = 0 does nothing).  How the state moves (ps_plan_set_host_mode):
+ *   PS_HOST_AUTO   : (default) for a page-locked buffer (cudaHostAlloc /
+ *                    cudaHostRegister) only the retained cube of modes crosses
+ *                    the host link, gathered and scattered by kernels through
+ *                    the buffer's device mapping (NVLink-C2C on Grace
+ *                    systems), while copy engines write the zeros of the
+ *                    masked modes into the host buffer during the steps;
+ *                    pageable memory takes PS_HOST_COPY;
+ *   PS_HOST_COPY   : cudaMemcpyAsync of the whole state to a plan-owned device
+ *                    buffer (allocated on the first call) and back;
+ *   PS_HOST_SMCOPY : the whole state copied by a streaming kernel through the
+ *                    device mapping, and back;
+ *   PS_HOST_MAPPED : the passes use the page-locked buffer in place (the
+ *                    first pass and every stage update read its retained
+ *                    modes, the last stage writes it).
+ * SMCOPY and MAPPED fail with PS_ERR_UNSUPPORTED on pageable memory.  The
+ * modes outside the retained set are zero on return in every mode. */
+enum { PS_HOST_AUTO = 0, PS_HOST_COPY = 1, PS_HOST_MAPPED = 2, PS_HOST_SMCOPY = 3 };
 ps_status ps_rk_step_host(ps_plan* plan, void* uhat_host, double dt, double t, int nsteps);
+ps_status ps_plan_set_host_mode(ps_plan* plan, int mode);
 
 /* Energy (kinetic + magnetic for MHD) and max |u(x)| (FP64) of the state at
  * the start of the last ps_rk_step.  Synchronises the plan stream. */

@@ -196,6 +196,65 @@ cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double*
   return cudaGetLastError();
 }
 
+// Contiguous copy of n bytes by the SMs (16-byte accesses, four in flight
+// per thread); either side may be page-locked host memory addressed through
+// its device mapping.
+__global__ void k_stream_copy(const uint4* __restrict__ src, uint4* __restrict__ dst, long long n16) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = src[i];
+}
+
+__global__ void k_stream_copy8(const uint2* __restrict__ src, uint2* __restrict__ dst, long long n8) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_stream_copy(const void* src, void* dst, size_t bytes, int nsm, cudaStream_t s) {
+  const int blocks = 4 * (nsm > 0 ? nsm : 152);
+  if (((uintptr_t)src | (uintptr_t)dst | bytes) % 16 == 0)
+    k_stream_copy<<<blocks, 256, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst),
+                                        (long long)(bytes / 16));
+  else
+    k_stream_copy8<<<blocks, 256, 0, s>>>(static_cast<const uint2*>(src), static_cast<uint2*>(dst),
+                                         (long long)(bytes / 8));
+  return cudaGetLastError();
+}
+
+// Copy the modes of the retained cube |p| <= Kx, |q| <= Ky, |r| <= Kz of nc
+// caller-layout components from src to dst (either may be the device mapping
+// of page-locked host memory); one kx row segment per group of threads.
+template <typename V>
+__global__ void k_copy_cube(const V* __restrict__ src, V* __restrict__ dst, const Geo g, int nc) {
+  const long long rows = (long long)nc * g.cz * g.cy;
+  const long long fcs = (long long)g.nz * g.ny * g.nh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows * g.cx;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % g.cx);
+    const long long row = i / g.cx;
+    const int iy = (int)(row % g.cy), iz = (int)((row / g.cy) % g.cz), c = (int)(row / ((long long)g.cy * g.cz));
+    const int q = iy <= g.Ky ? iy : iy - g.cy, r = iz <= g.Kz ? iz : iz - g.cz;
+    const long long o = c * fcs + ((long long)rowof(r, g.nz) * g.ny + rowof(q, g.ny)) * g.nh + p;
+    dst[o] = src[o];
+  }
+}
+
+cudaError_t launch_copy_cube(const void* src, void* dst, const Geo& g, int nc, size_t vb, int nsm, cudaStream_t s) {
+  const int blocks = 8 * (nsm > 0 ? nsm : 152);
+  if (vb == 8)
+    k_copy_cube<float2><<<blocks, 256, 0, s>>>(static_cast<const float2*>(src), static_cast<float2*>(dst), g, nc);
+  else
+    k_copy_cube<double2><<<blocks, 256, 0, s>>>(static_cast<const double2*>(src), static_cast<double2*>(dst), g, nc);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_if_tables<float>(const Geo&, double, double, void*, cudaStream_t);
 template cudaError_t launch_if_tables<double>(const Geo&, double, double, void*, cudaStream_t);
 template cudaError_t launch_forcing_extent<float>(const Geo&, Spec, int*, cudaStream_t);

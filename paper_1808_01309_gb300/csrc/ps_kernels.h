@@ -103,6 +103,8 @@ struct LesScratch {
   float2* extra;        // compact closure term
   float* Arows;         // [P][9] gradient rows (training only)
 };
+cudaError_t launch_stream_copy(const void* src, void* dst, size_t bytes, int nsm, cudaStream_t s);
+cudaError_t launch_copy_cube(const void* src, void* dst, const Geo& g, int nc, size_t vb, int nsm, cudaStream_t s);
 cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void* twy, const void* twz,
                              const LesScratch& s, cudaStream_t st);
 // Force loss (sum over the half spectrum of w |D P(closure) - f|^2) of the

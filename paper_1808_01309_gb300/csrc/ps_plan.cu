@@ -1,6 +1,7 @@
 // Plan layer and C ABI (include/ps.h): validation, scratch ownership, twiddle
 // tables, forcing box, and the launch sequence of one right-hand side and of
 // one integrating-factor Runge-Kutta step.
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <cstdio>
@@ -152,6 +153,10 @@ struct ps_plan {
   double* dpart = nullptr;                 // diagnostics partials
   double* dout = nullptr;                  // diagnostics result (device)
   void* hstate = nullptr;                  // device state for ps_rk_step_host
+  int host_mode = PS_HOST_AUTO;            // ps_plan_set_host_mode
+  cudaStream_t side = nullptr;             // zero fill of the host state's masked modes
+  cudaEvent_t side_go = nullptr, side_done = nullptr;
+  void* zbuf = nullptr;                    // zeros, ZBUF_BYTES
   double time = 0.0;
   long long launches = 0;
   bool timing = false;
@@ -443,6 +448,10 @@ void release(ps_plan* p) {
     cudaEventDestroy(t.b);
   }
   for (auto e : p->pool) cudaEventDestroy(e);
+  if (p->zbuf) cudaFree(p->zbuf);
+  if (p->side_go) cudaEventDestroy(p->side_go);
+  if (p->side_done) cudaEventDestroy(p->side_done);
+  if (p->side) cudaStreamDestroy(p->side);
 }
 
 }  // namespace
@@ -581,19 +590,140 @@ ps_status ps_rk_step(ps_plan* p, void* uhat, double dt, double t) {
   return s;
 }
 
+ps_status ps_plan_set_host_mode(ps_plan* p, int mode) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  if (mode < PS_HOST_AUTO || mode > PS_HOST_SMCOPY)
+    return fail(PS_ERR_INVALID_ARG, "unknown host mode");
+  p->host_mode = mode;
+  return PS_OK;
+}
+
+namespace {
+
+constexpr size_t ZBUF_BYTES = 32ull << 20;
+
+// Zeros into the modes of the page-locked host state outside the retained
+// cube, by copy-engine transfers from a zero buffer on the side stream:
+// the planes |r| > Kz, in the other planes the rows |q| > Ky, and in the
+// remaining rows the entries kx > Kx.
+cudaError_t zero_outside_cube(ps_plan* p, char* host) {
+  const ps::Geo& g = p->g;
+  const size_t vb = p->sz.vb, row = (size_t)g.nh * vb, plane = (size_t)g.ny * row;
+  const size_t fcs = (size_t)g.nz * plane;
+  const int nc = 3 * p->ng;
+  cudaStream_t st = p->side;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  const int zr0 = g.Kz + 1, nzr = g.nz - 2 * g.Kz - 1;  // masked planes
+  const int yr0 = g.Ky + 1, nyr = g.ny - 2 * g.Ky - 1;  // masked rows
+  const size_t xw = (size_t)(g.nh - g.cx) * vb;          // masked tail of a row
+  const int zlo[2] = {0, g.nz - g.Kz}, zn[2] = {g.Kz + 1, g.Kz};
+  const int ylo[2] = {0, g.ny - g.Ky}, yn[2] = {g.Ky + 1, g.Ky};
+  for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+    char* base = host + c * fcs;
+    // whole planes
+    for (size_t off = 0, n = (size_t)nzr * plane; off < n && e == cudaSuccess; off += ZBUF_BYTES)
+      e = cudaMemcpyAsync(base + zr0 * plane + off, p->zbuf, std::min(ZBUF_BYTES, n - off), k, st);
+    for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+      if (zn[a] <= 0) continue;
+      // whole rows of the retained planes
+      if (nyr > 0) {
+        const size_t w = (size_t)nyr * row;
+        const int hc = (int)std::max<size_t>(1, ZBUF_BYTES / w);
+        for (int h0 = 0; h0 < zn[a] && e == cudaSuccess; h0 += hc)
+          e = cudaMemcpy2DAsync(base + (size_t)(zlo[a] + h0) * plane + yr0 * row, plane, p->zbuf, w, w,
+                                std::min(hc, zn[a] - h0), k, st);
+      }
+      // row tails of the retained rows
+      for (int b = 0; b < 2 && e == cudaSuccess && xw > 0; ++b) {
+        if (yn[b] <= 0) continue;
+        const int dc = (int)std::max<size_t>(1, ZBUF_BYTES / (xw * yn[b]));
+        for (int d0 = 0; d0 < zn[a] && e == cudaSuccess; d0 += dc) {
+          cudaMemcpy3DParms m{};
+          m.srcPtr = make_cudaPitchedPtr(p->zbuf, xw, xw, yn[b]);
+          m.dstPtr = make_cudaPitchedPtr(base + (size_t)(zlo[a] + d0) * plane + (size_t)ylo[b] * row + g.cx * vb,
+                                         row, row, g.ny);
+          m.extent = make_cudaExtent(xw, yn[b], std::min(dc, zn[a] - d0));
+          m.kind = k;
+          e = cudaMemcpy3DAsync(&m, st);
+        }
+      }
+    }
+  }
+  return e;
+}
+
+}  // namespace
+
 ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int nsteps) {
   if (!p || !uhat_host) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
   if (nsteps < 0) return fail(PS_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
+  if (nsteps == 0) return PS_OK;
   DeviceGuard dg(p->device);
   const size_t bytes = p->sz.state * p->sz.vb;
+  // device address of a page-locked host buffer (NVLink-C2C on Grace systems)
+  void* mapped = nullptr;
+  if (p->host_mode != PS_HOST_COPY) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, uhat_host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+      mapped = at.devicePointer;
+    else
+      (void)cudaGetLastError();  // clear the error of an unregistered pointer
+    if (!mapped && p->host_mode != PS_HOST_AUTO)
+      return fail(PS_ERR_UNSUPPORTED, "this host mode needs page-locked (registered or cudaHostAlloc) memory");
+  }
+  if (mapped && p->host_mode == PS_HOST_MAPPED) {
+    for (int i = 0; i < nsteps; ++i) {
+      ps_status s = ps_rk_step(p, mapped, dt, t + i * dt);
+      if (s != PS_OK) return s;
+    }
+    PS_CU(cudaStreamSynchronize(p->stream), "host-path sync");
+    return check_device_error(p);
+  }
   if (!p->hstate) PS_CU(cudaMalloc(&p->hstate, bytes), "host-path state");
-  PS_CU(cudaMemcpyAsync(p->hstate, uhat_host, bytes, cudaMemcpyHostToDevice, p->stream), "state upload");
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+  const bool cube = mapped && p->host_mode == PS_HOST_AUTO;
+  if (cube) {
+    // only the retained modes cross the host link; the masked modes of the
+    // host state are zeroed by copy engines while the steps run
+    if (!p->side) {
+      PS_CU(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "side stream");
+      PS_CU(cudaEventCreateWithFlags(&p->side_go, cudaEventDisableTiming), "side event");
+      PS_CU(cudaEventCreateWithFlags(&p->side_done, cudaEventDisableTiming), "side event");
+      PS_CU(cudaMalloc(&p->zbuf, ZBUF_BYTES), "zero buffer");
+      PS_CU(cudaMemsetAsync(p->zbuf, 0, ZBUF_BYTES, p->stream), "zero buffer");
+    }
+    PS_CU(cudaEventRecord(p->side_go, p->stream), "side event");
+    PS_CU(cudaStreamWaitEvent(p->side, p->side_go, 0), "side event");
+    PS_CU(zero_outside_cube(p, static_cast<char*>(uhat_host)), "zero fill of the masked modes");
+    PS_CU(cudaEventRecord(p->side_done, p->side), "side event");
+    PS_CU(ps::launch_copy_cube(mapped, p->hstate, p->g, 3 * p->ng, p->sz.vb, nsm, p->stream), "state upload");
+    p->launches++;
+  } else if (mapped) {
+    PS_CU(ps::launch_stream_copy(mapped, p->hstate, bytes, nsm, p->stream), "state upload");
+    p->launches++;
+  } else {
+    PS_CU(cudaMemcpyAsync(p->hstate, uhat_host, bytes, cudaMemcpyHostToDevice, p->stream), "state upload");
+  }
   for (int i = 0; i < nsteps; ++i) {
     ps_status s = ps_rk_step(p, p->hstate, dt, t + i * dt);
-    if (s != PS_OK) return s;
+    if (s != PS_OK) {
+      if (cube) cudaStreamSynchronize(p->side);
+      return s;
+    }
   }
-  PS_CU(cudaMemcpyAsync(uhat_host, p->hstate, bytes, cudaMemcpyDeviceToHost, p->stream), "state download");
+  if (cube) {
+    PS_CU(ps::launch_copy_cube(p->hstate, mapped, p->g, 3 * p->ng, p->sz.vb, nsm, p->stream), "state download");
+    p->launches++;
+    PS_CU(cudaStreamWaitEvent(p->stream, p->side_done, 0), "side event");
+  } else if (mapped) {
+    PS_CU(ps::launch_stream_copy(p->hstate, mapped, bytes, nsm, p->stream), "state download");
+    p->launches++;
+  } else {
+    PS_CU(cudaMemcpyAsync(uhat_host, p->hstate, bytes, cudaMemcpyDeviceToHost, p->stream), "state download");
+  }
   PS_CU(cudaStreamSynchronize(p->stream), "host-path sync");
   return check_device_error(p);
 }

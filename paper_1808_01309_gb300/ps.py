@@ -51,8 +51,9 @@ SYMBOLS = (
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
-    "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad",
+    "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode",
 )
+HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
 ENS_MAX_SIZES = 8
@@ -127,6 +128,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_set_closure.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
     lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double), P, P, P, P]
+    lib.ps_plan_set_host_mode.argtypes = [P, ctypes.c_int]
     lib.ps_mlp_backward.argtypes = [P, P, P, ctypes.c_longlong, P, P]
     lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
     lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
@@ -208,6 +210,10 @@ def ps_rk_step(plan, uhat, dt: float, t: float = 0.0) -> None:
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
     _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_plan_set_host_mode(plan, mode: int) -> None:
+    _check(load().ps_plan_set_host_mode(plan, int(mode)))
 
 
 def ps_step_stats(plan) -> tuple[float, float]:

@@ -30,6 +30,53 @@ def test_host_buffer_steps_equal_device_steps(ps):
     host = torch.from_numpy(u.astype(np.complex64)).pin_memory()
     ps.ps_rk_step_host(plan.handle, host, dt, 0.0, 3)
     assert torch.equal(host, dev.cpu())
+    # pageable memory under the default mode takes the copy-engine path
+    pageable = torch.from_numpy(u.astype(np.complex64))
+    ps.ps_rk_step_host(plan.handle, pageable, dt, 0.0, 3)
+    assert torch.equal(pageable, host)
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", ["auto", "copy", "mapped", "smcopy"])
+def test_host_state_modes_match_device_steps(ps, mode):
+    """Host-buffer stepping copies the state or lets the kernels access the
+    page-locked buffer in place; both give the device result bit for bit."""
+    n, dt = 32, 2e-3
+    # content outside the retained modes: every mode must write its zeros
+    u = 2.0 * inputs.random_solenoidal_field(n, n, n, seed=6, kmax=(n, n, n))
+    f = torch.from_numpy(inputs.forcing_field(n, n, n, seed=2)).to("cuda", torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=3e-3, forcing=f)
+    dev = torch.from_numpy(u.astype(np.complex64)).cuda()
+    for i in range(2):
+        plan.rk_step(dev, dt, t=i * dt)
+    mask = oracle.dealias_mask(oracle.Config(n, n, n))
+    assert np.all(dev.cpu().numpy()[:, ~mask] == 0)
+    ps.ps_plan_set_host_mode(plan.handle, {"auto": ps.HOST_AUTO, "copy": ps.HOST_COPY,
+                                           "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY}[mode])
+    host = torch.from_numpy(u.astype(np.complex64)).pin_memory()
+    for i in range(2):
+        ps.ps_rk_step_host(plan.handle, host, dt, i * dt, 1)
+    assert torch.equal(host, dev.cpu())
+    # several steps per call, and an MHD/FP64 plan (6 components, 16-byte modes)
+    host2 = torch.from_numpy(u.astype(np.complex64)).pin_memory()
+    ps.ps_rk_step_host(plan.handle, host2, dt, 0.0, 2)
+    assert torch.equal(host2, dev.cpu())
+    ub = np.concatenate([u, 0.5 * inputs.random_solenoidal_field(n, n, n, seed=7, kmax=(n, n, n))])
+    pm = ps.Plan(n, prec=ps.Precision.FP64, eq=ps.Equations.MHD, nu=3e-3, eta=2e-3)
+    dm = torch.from_numpy(ub).cuda()
+    pm.rk_step(dm, dt)
+    ps.ps_plan_set_host_mode(pm.handle, {"auto": ps.HOST_AUTO, "copy": ps.HOST_COPY,
+                                         "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY}[mode])
+    hm = torch.from_numpy(ub).pin_memory()
+    ps.ps_rk_step_host(pm.handle, hm, dt, 0.0, 1)
+    assert torch.equal(hm, dm.cpu())
+    pm.close()
+    if mode in ("mapped", "smcopy"):
+        pageable = torch.from_numpy(u.astype(np.complex64))
+        with pytest.raises(ps.PsError):
+            ps.ps_rk_step_host(plan.handle, pageable, dt, 0.0, 1)
+    with pytest.raises(ps.PsError):
+        ps.ps_plan_set_host_mode(plan.handle, 7)
     plan.close()
 
 
