@@ -153,6 +153,14 @@ ps_status ps_rhs(ps_plan* plan, const void* uhat, void* rhs_out, double t);
  * (ps_step_stats).  dt must be finite.  Asynchronous. */
 ps_status ps_rk_step(ps_plan* plan, void* uhat, double dt, double t);
 
+/* nsteps calls of ps_rk_step on the device state uhat, replayed as one CUDA
+ * graph: the first call for a given (uhat, dt, nsteps) captures the steps,
+ * later calls with the same triple launch the captured graph on the plan
+ * stream (for small grids, whose steps are bound by launch latency).  The
+ * result equals nsteps calls of ps_rk_step bit for bit.  With per-kernel
+ * timing on, the steps are launched one by one.  Asynchronous. */
+ps_status ps_rk_steps(ps_plan* plan, void* uhat, double dt, double t, int nsteps);
+
 /* Same as nsteps calls of ps_rk_step on a HOST buffer, then synchronises
  * (nsteps = 0 does nothing).  How the state moves (ps_plan_set_host_mode):
  *   PS_HOST_AUTO   : (default) for a page-locked buffer (cudaHostAlloc /

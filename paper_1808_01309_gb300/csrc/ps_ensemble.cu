@@ -117,7 +117,8 @@ ps_status capture(ps_ensemble* e, void* const* u, double dt, double t, int nstep
 }
 
 ps_status run_graph(ps_ensemble* e, void* const* u, double dt, double t, int nsteps) {
-  const bool same = e->exec && e->key_steps == nsteps && e->key_dt == dt && e->key_t == t &&
+  // t is not part of the key: the right-hand side does not depend on it
+  const bool same = e->exec && e->key_steps == nsteps && e->key_dt == dt &&
                     e->key_branches == e->nbranch &&
                     std::equal(e->key_states.begin(), e->key_states.end(), u);
   if (!same) {
@@ -125,6 +126,7 @@ ps_status run_graph(ps_ensemble* e, void* const* u, double dt, double t, int nst
     if (st != PS_OK) return st;
   }
   ENS_CU(cudaGraphLaunch(e->exec, e->main), "graph launch");
+  for (ps_plan* p : e->plans) plan_set_time(p, t + nsteps * dt);
   return PS_OK;
 }
 

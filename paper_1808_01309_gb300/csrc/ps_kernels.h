@@ -120,5 +120,6 @@ void plan_set_xrpc(struct ::ps_plan* p, int rpc);
 // Forget the cached integrating-factor tables so the next step recomputes them
 // (a captured graph must contain that launch).
 void plan_invalidate_tables(struct ::ps_plan* p);
+void plan_set_time(struct ::ps_plan* p, double t);
 
 }  // namespace ps

@@ -154,6 +154,14 @@ struct ps_plan {
   double* dout = nullptr;                  // diagnostics result (device)
   void* hstate = nullptr;                  // device state for ps_rk_step_host
   int host_mode = PS_HOST_AUTO;            // ps_plan_set_host_mode
+  // ps_rk_steps: captured graph of nsteps steps, keyed by (state, dt, nsteps)
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_u = nullptr;
+  double g_dt = NAN;
+  int g_n = 0;
+  long long g_launches = 0;
   cudaStream_t side = nullptr;             // zero fill of the host state's masked modes
   cudaEvent_t side_go = nullptr, side_done = nullptr;
   void* zbuf = nullptr;                    // zeros, ZBUF_BYTES
@@ -448,6 +456,9 @@ void release(ps_plan* p) {
     cudaEventDestroy(t.b);
   }
   for (auto e : p->pool) cudaEventDestroy(e);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap) cudaStreamDestroy(p->cap);
   if (p->zbuf) cudaFree(p->zbuf);
   if (p->side_go) cudaEventDestroy(p->side_go);
   if (p->side_done) cudaEventDestroy(p->side_done);
@@ -461,6 +472,7 @@ void plan_set_stream(ps_plan* p, cudaStream_t s) { p->stream = s; }
 cudaStream_t plan_stream(const ps_plan* p) { return p->stream; }
 void plan_set_xrpc(ps_plan* p, int rpc) { p->xrpc = rpc; }
 void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
+void plan_set_time(ps_plan* p, double t) { p->time = t; }
 }  // namespace ps
 
 extern "C" {
@@ -654,6 +666,61 @@ cudaError_t zero_outside_cube(ps_plan* p, char* host) {
 }
 
 }  // namespace
+
+ps_status ps_rk_steps(ps_plan* p, void* uhat, double dt, double t, int nsteps) {
+  if (!p || !uhat) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
+  if (nsteps < 0) return fail(PS_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
+  if (nsteps == 0) return PS_OK;
+  DeviceGuard dg(p->device);
+  if (p->timing) {  // per-kernel events: plain launches
+    for (int i = 0; i < nsteps; ++i) {
+      ps_status s = ps_rk_step(p, uhat, dt, t + i * dt);
+      if (s != PS_OK) return s;
+    }
+    return PS_OK;
+  }
+  if (!(p->gexec && p->g_u == uhat && p->g_dt == dt && p->g_n == nsteps)) {
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->gexec = nullptr;
+    p->graph = nullptr;
+    if (!p->cap) PS_CU(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t home = p->stream;
+    const long long l0 = p->launches;
+    // work already queued on the plan stream comes first
+    cudaEvent_t ready = nullptr;
+    PS_CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "capture event");
+    cudaEventRecord(ready, home);
+    cudaStreamWaitEvent(p->cap, ready, 0);
+    cudaEventDestroy(ready);
+    PS_CU(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    p->stream = p->cap;
+    p->if_dt = NAN;  // the factor tables are part of the graph
+    ps_status st = PS_OK;
+    for (int i = 0; i < nsteps && st == PS_OK; ++i) st = ps_rk_step(p, uhat, dt, t + i * dt);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->cap, &g);
+    p->stream = home;
+    if (st != PS_OK) {
+      if (g) cudaGraphDestroy(g);
+      p->if_dt = NAN;
+      return st;
+    }
+    PS_CU(ce, "end capture");
+    p->graph = g;
+    PS_CU(cudaGraphInstantiate(&p->gexec, g, 0), "graph instantiate");
+    p->g_u = uhat;
+    p->g_dt = dt;
+    p->g_n = nsteps;
+    p->g_launches = p->launches - l0;
+    p->launches = l0;
+  }
+  PS_CU(cudaGraphLaunch(p->gexec, p->stream), "graph launch");
+  p->launches += p->g_launches;
+  p->time = t + nsteps * dt;
+  return PS_OK;
+}
 
 ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int nsteps) {
   if (!p || !uhat_host) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");

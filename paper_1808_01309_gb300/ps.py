@@ -51,7 +51,7 @@ SYMBOLS = (
     "ps_last_error", "ps_rhs_noalloc", "ps_ensemble_create", "ps_ensemble_destroy",
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
-    "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode",
+    "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double), P, P, P, P]
     lib.ps_plan_set_host_mode.argtypes = [P, ctypes.c_int]
+    lib.ps_rk_steps.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     lib.ps_mlp_backward.argtypes = [P, P, P, ctypes.c_longlong, P, P]
     lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
     lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
@@ -206,6 +207,10 @@ def ps_rhs_noalloc(cfg: PsConfig, uhat, rhs_out, t: float = 0.0, stream=None) ->
 
 def ps_rk_step(plan, uhat, dt: float, t: float = 0.0) -> None:
     _check(load().ps_rk_step(plan, _ptr(uhat), float(dt), float(t)))
+
+
+def ps_rk_steps(plan, uhat, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
+    _check(load().ps_rk_steps(plan, _ptr(uhat), float(dt), float(t), int(nsteps)))
 
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
@@ -375,6 +380,12 @@ class Plan:
     def rk_step(self, uhat, dt, t=0.0):
         self._check_field(uhat)
         ps_rk_step(self.handle, uhat, dt, t)
+        return uhat
+
+    def rk_steps(self, uhat, dt, nsteps, t=0.0):
+        """nsteps steps replayed as one captured CUDA graph (ps_rk_steps)."""
+        self._check_field(uhat)
+        ps_rk_steps(self.handle, uhat, dt, t, nsteps)
         return uhat
 
     def diagnostics(self, uhat, cfl=0.5):

@@ -80,6 +80,41 @@ def test_host_state_modes_match_device_steps(ps, mode):
     plan.close()
 
 
+def test_graph_replayed_steps_equal_single_steps(ps):
+    """ps_rk_steps captures the steps once per (state, dt, nsteps) and replays
+    them; results equal ps_rk_step calls bit for bit (HD with forcing, MHD)."""
+    n, dt = 32, 2e-3
+    u = inputs.random_solenoidal_field(n, n, n, seed=8)
+    f = torch.from_numpy(inputs.forcing_field(n, n, n, seed=2)).to("cuda", torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=4e-3, forcing=f)
+    a = torch.from_numpy(u.astype(np.complex64)).cuda()
+    b = a.clone()
+    for i in range(6):
+        plan.rk_step(a, dt, t=i * dt)
+    l0 = ps.ps_plan_launch_count(plan.handle)
+    plan.rk_steps(b, dt, 3, t=0.0)
+    plan.rk_steps(b, dt, 3, t=3 * dt)  # replay of the same graph
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert ps.ps_plan_launch_count(plan.handle) - l0 >= 2 * 3 * 21
+    # a different step size re-captures
+    plan.rk_step(a, 1e-3)
+    plan.rk_steps(b, 1e-3, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    plan.close()
+    ub = np.concatenate([u, 0.3 * inputs.random_solenoidal_field(n, n, n, seed=9)])
+    pm = ps.Plan(n, prec=ps.Precision.FP64, eq=ps.Equations.MHD, nu=3e-3, eta=2e-3)
+    a = torch.from_numpy(ub).cuda()
+    b = a.clone()
+    for i in range(2):
+        pm.rk_step(a, dt)
+    pm.rk_steps(b, dt, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    pm.close()
+
+
 def test_timing_and_launch_counts(ps):
     n = 32
     plan = ps.Plan(n, prec=ps.Precision.FP32, nu=1e-3)

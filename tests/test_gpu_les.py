@@ -131,10 +131,15 @@ def test_les_rk_steps_match_oracle(ps, order):
     plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=order, forcing=to_dev(f))
     plan.set_closure(torch.from_numpy(v).cuda(), norm)
     ud = to_dev(u)
+    ug = ud.clone()
     for i in range(3):
         plan.rk_step(ud, dt, t=i * dt)
     got = to_np(ud)
     assert relerr(got, ref) < 2e-4
+    # the closure's launches replay in a captured graph too
+    plan.rk_steps(ug, dt, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(ug, ud)
     # the closure moved the state: the plain step differs by much more than the tolerance
     plain = u
     for _ in range(3):
