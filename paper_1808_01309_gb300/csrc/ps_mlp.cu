@@ -184,18 +184,95 @@ __device__ void stage_inputs(Smem& s, const float* __restrict__ X, int count) {
   }
 }
 
+// Inference: each warp keeps the whole network's BF16 weight fragments and its
+// biases in registers and runs 16-sample tiles through it.  The m16n8
+// accumulator fragments of two neighbouring 8-column tiles of one layer are,
+// after bias, GELU and BF16 packing, exactly the m16n8k16 A fragment of the
+// next layer's 16-column k tile, so activations never leave the registers.
+// Same products, roundings and summation order as forward_tiles.
 __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p, const float* __restrict__ X,
                                                      float* __restrict__ Y, long long B) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  Smem& s = *reinterpret_cast<Smem*>(raw);
-  load_weights(s, p);
-  for (long long c0 = (long long)blockIdx.x * CH; c0 < B; c0 += (long long)gridDim.x * CH) {
-    const int count = (int)(B - c0 < CH ? B - c0 : CH);
-    __syncthreads();
-    stage_inputs(s, X + c0 * NI, count);
-    __syncthreads();
-    float yreg[2][4];
-    forward_tiles(s, count, Y + c0 * NO, yreg);
+  const int lane = threadIdx.x & 31;
+  const int qd = lane & 3, rq = lane >> 2;  // column pair and row within a fragment
+  // B fragments: W[k][n] at k = k0 + 2 qd + {0, 1} (+ 8), n = n0 + rq
+  auto wfrag = [&](int off, int K, int N, int k0, int n0, uint32_t (&b)[2]) {
+    const int n = n0 + rq, k = k0 + 2 * qd;
+    auto w = [&](int kk) { return __float2bfloat16((kk < K && n < N) ? p[off + kk * N + n] : 0.f); };
+    b[0] = pack(w(k), w(k + 1));
+    b[1] = pack(w(k + 8), w(k + 9));
+  };
+  uint32_t w1[H / 8][2], w2[H / 16][H / 8][2], w3[H / 16][2];
+#pragma unroll
+  for (int nt = 0; nt < H / 8; ++nt) wfrag(OFF_W1, NI, H, 0, 8 * nt, w1[nt]);
+#pragma unroll
+  for (int kt = 0; kt < H / 16; ++kt) {
+#pragma unroll
+    for (int nt = 0; nt < H / 8; ++nt) wfrag(OFF_W2, H, H, 16 * kt, 8 * nt, w2[kt][nt]);
+    wfrag(OFF_W3, H, NO, 16 * kt, 0, w3[kt]);
+  }
+  float bb1[H / 8][2], bb2[H / 8][2], bb3[2];
+#pragma unroll
+  for (int nt = 0; nt < H / 8; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      bb1[nt][j] = p[OFF_B1 + 8 * nt + 2 * qd + j];
+      bb2[nt][j] = p[OFF_B2 + 8 * nt + 2 * qd + j];
+    }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) bb3[j] = 2 * qd + j < NO ? p[OFF_B3 + 2 * qd + j] : 0.f;
+  const long long ntiles = (B + 15) / 16;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < ntiles;
+       tile += wstride) {
+    const long long r0 = tile * 16 + rq, r1 = r0 + 8;
+    // layer 1 input fragment: columns 2 qd + {0, 1} of the 5 inputs (k tile 0)
+    auto xin = [&](long long r, int c) { return __float2bfloat16((r < B && c < NI) ? X[r * NI + c] : 0.f); };
+    uint32_t a[4];
+    a[0] = pack(xin(r0, 2 * qd), xin(r0, 2 * qd + 1));
+    a[1] = pack(xin(r1, 2 * qd), xin(r1, 2 * qd + 1));
+    a[2] = a[3] = 0u;
+    // layers 1 and 2
+    uint32_t h[H / 16][4];
+#pragma unroll
+    for (int nt = 0; nt < H / 8; ++nt) {
+      float d[4] = {0, 0, 0, 0};
+      mma16816(d, a, w1[nt]);
+      const bf g0 = __float2bfloat16(gelu(d[0] + bb1[nt][0])), g1 = __float2bfloat16(gelu(d[1] + bb1[nt][1]));
+      const bf g2 = __float2bfloat16(gelu(d[2] + bb1[nt][0])), g3 = __float2bfloat16(gelu(d[3] + bb1[nt][1]));
+      h[nt >> 1][(nt & 1) * 2 + 0] = pack(g0, g1);  // row r0
+      h[nt >> 1][(nt & 1) * 2 + 1] = pack(g2, g3);  // row r1
+    }
+    float acc[H / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < H / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < H / 16; ++kt) {
+      const uint32_t ak[4] = {h[kt][0], h[kt][1], h[kt][2], h[kt][3]};
+#pragma unroll
+      for (int nt = 0; nt < H / 8; ++nt) mma16816(acc[nt], ak, w2[kt][nt]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < H / 8; ++nt) {
+      const bf g0 = __float2bfloat16(gelu(acc[nt][0] + bb2[nt][0])), g1 = __float2bfloat16(gelu(acc[nt][1] + bb2[nt][1]));
+      const bf g2 = __float2bfloat16(gelu(acc[nt][2] + bb2[nt][0])), g3 = __float2bfloat16(gelu(acc[nt][3] + bb2[nt][1]));
+      h[nt >> 1][(nt & 1) * 2 + 0] = pack(g0, g1);
+      h[nt >> 1][(nt & 1) * 2 + 1] = pack(g2, g3);
+    }
+    // layer 3
+    float d[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int kt = 0; kt < H / 16; ++kt) {
+      const uint32_t ak[4] = {h[kt][0], h[kt][1], h[kt][2], h[kt][3]};
+      mma16816(d, ak, w3[kt]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = 2 * qd + j;
+      if (c < NO) {
+        if (r0 < B) Y[r0 * NO + c] = d[j] + bb3[j];
+        if (r1 < B) Y[r1 * NO + c] = d[2 + j] + bb3[j];
+      }
+    }
   }
 }
 
@@ -438,9 +515,7 @@ ps_status ps_mlp_forward(const float* params, const float* X, float* Y, long lon
   }
   if (count == 0) return PS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-  if (e != cudaSuccess) return cuerr(e, "ps_mlp_forward");
-  k_mlp_forward<<<grid_for(count), 128, sizeof(Smem), s>>>(params, X, Y, count);
+  k_mlp_forward<<<grid_for(count), 128, 0, s>>>(params, X, Y, count);
   return cuerr(cudaGetLastError(), "ps_mlp_forward");
 }
 
