@@ -68,3 +68,23 @@ def test_clock_summary_parses_nvidia_smi_lines():
                "1980, 2070, 950.0, Not Active, Not Active, Not Active, Not Active"]
     s = c.summary()
     assert s["sm_mhz"] == 1972.5 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
+
+
+def test_roofline_model_bytes_add_up_to_the_step_model():
+    """Per-launch model bytes of the five passes (42 S per RHS plus the RK
+    updates) sum to the 198 S of one IF-RK4 step; the pruned compulsory bytes
+    of the retained modes are smaller."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    n = 512
+    S = n * n * (n // 2 + 1) * 8
+    model, step = b.model_bytes(n, 8)
+    assert step == 198 * S
+    assert abs(4 * sum(model.values()) - step) < 1e-6 * step
+    assert sum(model[k] for k in model if k != "z_forward_rk") + 6 * S == 42 * S
+    pruned = b.algorithmic_bytes(n, 8)
+    assert all(pruned[k] < model[k] for k in model)
