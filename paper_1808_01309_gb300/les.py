@@ -278,13 +278,14 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     per = n_dns_eval // n_eval
     spec_dns = []
     secs_dns = 0.0
-    e_dns = []
+    e_dns, eps_dns = [], []
     for k in range(n_eval):
         secs_dns += _timed_steps(dns, u, dt_dns, per, t)
         t += per * dt_dns
         s, d = _spectrum(dns, u, kc)
         spec_dns.append(s)
         e_dns.append(d["energy"])
+        eps_dns.append(2.0 * nu * d["enstrophy"])  # dissipation rate of the DNS
     dns.close()
     del u, f_dns
     torch.cuda.empty_cache()
@@ -296,7 +297,7 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
         if closure is not None:
             plan.set_closure(closure, norm)
         ul = les0.clone()
-        spec, en, secs, tl, ok = [], [], 0.0, t_eval0, True
+        spec, en, eps, secs, tl, ok = [], [], [], 0.0, t_eval0, True
         for k in range(n_eval):
             dts = _timed_steps(plan, ul, dt_les, les_per, tl)
             if k > 0:  # the first chunk includes the graph capture
@@ -308,9 +309,20 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
                 break
             spec.append(s)
             en.append(d["energy"])
+            # dissipation: resolved 2 nu Omega plus the energy the closure
+            # removes, -sum_k w Re(u* . f_closure)
+            drain = 0.0
+            if closure is not None:
+                plan.set_closure(None)
+                r0 = plan.rhs(ul)
+                plan.set_closure(closure, norm)
+                drain = -float(shell_transfer(ul, plan.rhs(ul) - r0, ul.shape[1]).sum())
+            eps.append(2.0 * nu * d["enstrophy"] + drain)
         plan.close()
         r = dict(finite=ok, ms_per_step=1e3 * secs / max(les_per * (len(spec) - 1), 1), steps=les_per * n_eval,
-                 energy=en)
+                 energy=en, dissipation=eps)
+        if ok:
+            r["dissipation_rel_err"] = float(abs(np.mean(eps) - np.mean(eps_dns)) / np.mean(eps_dns))
         if ok:
             E_les = np.mean(spec, axis=0)[1:]
             E_dns = np.mean(spec_dns, axis=0)[1:]
@@ -318,13 +330,13 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
             r.update(spectrum=E_les.tolist(), rel_err=rel.tolist(), max_rel_err=float(rel.max()),
                      mean_rel_err=float(rel.mean()))
             say(f"LES {name}: max rel. spectrum error {rel.max():.3f} (mean {rel.mean():.3f}), "
-                f"{r['ms_per_step']:.3f} ms/step")
+                f"dissipation {np.mean(eps):.4f} vs DNS {np.mean(eps_dns):.4f}, {r['ms_per_step']:.3f} ms/step")
         else:
             say(f"LES {name}: non-finite state")
         runs[name] = r
     les_ms = runs[next(iter(models))]["ms_per_step"]
     out["dns"] = dict(ms_per_step=dns_ms, spectrum=np.mean(spec_dns, axis=0)[1:].tolist(), steps=per * n_eval,
-                      energy=e_dns)
+                      energy=e_dns, dissipation=eps_dns)
     out["les"] = runs
     out["cost_ratio"] = (dns_ms / dt_dns) / (les_ms / dt_les) if les_ms > 0 else None
     out["wall_seconds"] = time.perf_counter() - t_wall
