@@ -44,6 +44,11 @@ pointwise multilayer perceptron of the resolved velocity-gradient invariants
      r_hat = D P(closure term) - f_hat the residual against a given projected,
      band-limited subgrid force f_hat (the filtered DNS right-hand side minus
      the LES right-hand side of the filtered state).
+  L9 transfer loss: L = sum over shells K of (T_model(K) - T_exact(K))^2 with
+     T(K) = sum over the modes of shell K (K = floor(|k| + 1/2)) of
+     w Re(u_hat* . f_hat), f_hat the projected closure term (model) or the
+     subgrid force (exact): the energy the closure moves into or out of each
+     shell.
 """
 
 from __future__ import annotations
@@ -286,6 +291,53 @@ def force_loss_and_grads(uh, cfg: sp.Config, p, norm, f_hat, rnd=None):
     w = sp.hermitian_weight(cfg)
     L = float(np.sum(w * np.abs(r_hat) ** 2))
     # d r_i / d x_j on the grid
+    G = np.stack([np.stack([sp.inverse((1j * k[j] * r_hat[i])[None], cfg)[0] for j in range(3)])
+                  for i in range(3)])
+    scale = 2.0 / (cfg.nx * cfg.ny * cfg.nz)
+    dtau = np.stack([scale * (G[i, j] + G[j, i]) if i != j else scale * G[i, i] for (i, j) in SYM])
+    dy = norm["s_tau"] * np.einsum("nmp,mp->pn", Tb, dtau.reshape(6, -1))
+    return L, _backward(p, cache, dy, rnd)
+
+
+def shell_index(cfg: sp.Config) -> np.ndarray:
+    """K = floor(|k| + 1/2) of every stored mode (reading R9)."""
+    kx, ky, kz = sp.wavenumbers(cfg)
+    return np.floor(np.sqrt(kx * kx + ky * ky + kz * kz) + 0.5).astype(int)
+
+
+def transfer_spectrum(uh, f_hat, cfg: sp.Config, nshells: int) -> np.ndarray:
+    """T(K) = sum_{shell K} w Re(u_hat* . f_hat), K = 0..nshells-1 (reading L9)."""
+    w = sp.hermitian_weight(cfg) * sp.dealias_mask(cfg)
+    e = (w * np.real(np.conj(uh) * f_hat).sum(0))
+    return np.bincount(shell_index(cfg).ravel(), weights=e.ravel(), minlength=nshells)[:nshells]
+
+
+def transfer_loss_and_grads(uh, cfg: sp.Config, p, norm, T_exact, rnd=None):
+    """Transfer loss of reading L9 and its parameter gradients.  dL/df_hat
+    has the form of the force-loss gradient with the residual replaced by
+    dT(K(k)) u_hat(k), dT = T_model - T_exact, so the adjoint of
+    force_loss_and_grads applies to that field unchanged."""
+    nsh = len(T_exact)
+    D = sp.dealias_mask(cfg)
+    A = gradient(uh, cfg)
+    lam = invariants(A)
+    X = (lam.reshape(5, -1).T - norm["mean"]) / norm["std"]
+    y, cache = mlp_forward(p, X, rnd)
+    Tb = tensor_basis(A, norm["s_A"]).reshape(6, 6, -1)
+    tau = norm["s_tau"] * np.einsum("nmp,pn->mp", Tb, y).reshape((6,) + lam.shape[1:])
+    th = sp.forward(tau)
+    k = sp.wavenumbers(cfg)
+    full = {}
+    for m, (i, j) in enumerate(SYM):
+        full[(i, j)] = th[m]
+        full[(j, i)] = th[m]
+    div = np.stack([sum(1j * k[j] * full[(i, j)] for j in range(3)) for i in range(3)])
+    f_model = sp.project(-div * D, cfg) * D
+    dT = transfer_spectrum(uh * D, f_model, cfg, nsh) - np.asarray(T_exact)
+    L = float(np.sum(dT * dT))
+    K = shell_index(cfg)
+    dTk = np.where(K < nsh, dT[np.minimum(K, nsh - 1)], 0.0)
+    r_hat = dTk * uh * D
     G = np.stack([np.stack([sp.inverse((1j * k[j] * r_hat[i])[None], cfg)[0] for j in range(3)])
                   for i in range(3)])
     scale = 2.0 / (cfg.nx * cfg.ny * cfg.nz)

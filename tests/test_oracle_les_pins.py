@@ -295,3 +295,35 @@ def test_force_loss_gradients_match_central_differences():
             an = g[name].reshape(-1)[idx]
             scale = max(np.max(np.abs(g[name])), 1e-30)
             assert abs(fd - an) <= 1e-5 * scale, (name, idx, fd, an)
+
+
+def test_transfer_spectrum_sums_to_the_energy_rate():
+    """Summed over all shells, T(K) of a force is sum w Re(u* . f), the rate
+    of change of the energy 1/2 sum w |u|^2 under du/dt = f (Parseval)."""
+    cfg, u, p, norm, f = _force_case()
+    T = les.transfer_spectrum(u, f, cfg, 64)
+    r = oracle.spectral.inverse(u, cfg)
+    q = oracle.spectral.inverse(f, cfg)
+    assert abs(T.sum() - np.mean(np.sum(r * q, axis=0))) < 1e-13 * abs(T.sum())
+
+
+def test_transfer_loss_gradients_match_central_differences():
+    cfg, u, p, norm, f = _force_case()
+    Te = les.transfer_spectrum(u, f, cfg, 12)
+    L, g = les.transfer_loss_and_grads(u, cfg, p, norm, Te)
+    assert L > 0
+    rng = np.random.default_rng(13)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = les.transfer_loss_and_grads(u, cfg, p, norm, Te)
+            flat[idx] = old - h
+            lm, _ = les.transfer_loss_and_grads(u, cfg, p, norm, Te)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            scale = max(np.max(np.abs(g[name])), 1e-30)
+            assert abs(fd - an) <= 1e-5 * scale, (name, idx, fd, an)
