@@ -317,6 +317,14 @@ ps_status ps_plan_set_closure(ps_plan* plan, const float* params, const double* 
 ps_status ps_plan_closure_grad(ps_plan* plan, const float* params, const void* ubar, const void* force, float* grad,
                                double* loss, int accumulate);
 
+/* Same for the energy-transfer loss L = sum_{K < nshells} (T(K) - t_exact[K])^2,
+ * T(K) = sum over the kept modes of shell K = floor(|k| + 1/2) of
+ * w Re(ubar* . D P(-div tau(ubar))): the energy the closure moves into each
+ * shell, against t_exact (host, nshells <= 1024 doubles), e.g. the transfer
+ * of the exact subgrid force.  Synchronises the plan stream. */
+ps_status ps_plan_closure_grad_transfer(ps_plan* plan, const float* params, const void* ubar, const double* t_exact,
+                                        int nshells, float* grad, double* loss, int accumulate);
+
 /* Training data for the closure from one DNS state (FP32, n_dns^3, 2 pi box,
  * HD layout, device): with F the box filter |p|,|q|,|r| <= kc and ubar = F[u]
  * sampled on an n_les^3 grid (P = n_les^3 points, order z, y, x):

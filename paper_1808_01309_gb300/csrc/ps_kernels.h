@@ -110,8 +110,11 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
 // Force loss (sum over the half spectrum of w |D P(closure) - f|^2) of the
 // state `in` against the subgrid force f (full layout), added to *loss, and
 // its parameter gradient added to grad; params replaces s.params.
+// With t_exact (device, nsh shells) the loss is instead sum_K (T(K) - t_exact[K])^2
+// of the shell energy transfer of the projected closure term; bins holds 2 nsh doubles.
 cudaError_t les_closure_grad(const Geo& g, Spec in, Spec f, const void* twx, const void* twy, const void* twz,
-                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st);
+                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st,
+                             const double* t_exact = nullptr, int nsh = 0, double* bins = nullptr);
 
 // Plan internals used by the ensemble layer (ps_plan.cu).
 void plan_set_stream(struct ::ps_plan* p, cudaStream_t s);

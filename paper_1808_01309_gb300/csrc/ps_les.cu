@@ -396,6 +396,86 @@ __global__ void k_force_residual(const Geo g, const V* __restrict__ extra, const
   if (threadIdx.x == 0) atomicAdd(loss, t);
 }
 
+// Shell energy transfer of the projected closure term: bins[K] +=
+// w Re(u* . D P extra) over the kept modes, K = floor(|k| + 1/2) < nsh.
+__global__ void k_transfer_shells(const Geo g, const V* __restrict__ extra, const Spec u, double* bins, int nsh) {
+  extern __shared__ double sb[];
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  const long long total = (long long)g.cz * g.cy * g.cx;
+  const long long cs = (long long)g.cz * g.cy * g.kxp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % g.cx), iy = (int)((i / g.cx) % g.cy), iz = (int)(i / ((long long)g.cx * g.cy));
+    const int q = iy <= g.Ky ? iy : iy - g.cy, r = iz <= g.Kz ? iz : iz - g.cz;
+    if (!kept(g, p, q, r)) continue;
+    const double kx = p * g.sx, ky = q * g.sy, kz = r * g.sz;
+    const int K = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
+    if (K >= nsh) continue;
+    const long long ci = ((long long)iz * g.cy + iy) * g.kxp + p;
+    double v[3][2] = {{extra[ci].x, extra[ci].y}, {extra[ci + cs].x, extra[ci + cs].y},
+                      {extra[ci + 2 * cs].x, extra[ci + 2 * cs].y}};
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (k2 > 0) {
+      const double dr = (kx * v[0][0] + ky * v[1][0] + kz * v[2][0]) / k2;
+      const double di = (kx * v[0][1] + ky * v[1][1] + kz * v[2][1]) / k2;
+      const double kk[3] = {kx, ky, kz};
+      for (int c = 0; c < 3; ++c) {
+        v[c][0] -= kk[c] * dr;
+        v[c][1] -= kk[c] * di;
+      }
+    } else {
+      continue;
+    }
+    const V* up = static_cast<const V*>(u.p) + (long long)rowof(r, u.zwrap) * u.zs + (long long)rowof(q, u.ywrap) * u.ys + p;
+    double e = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const V a = up[c * u.cs];
+      e += (double)a.x * v[c][0] + (double)a.y * v[c][1];
+    }
+    atomicAdd(sb + K, (p == 0 ? 1.0 : 2.0) * e);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) atomicAdd(bins + i, sb[i]);
+}
+
+// dT = bins - T_exact, loss += sum dT^2 (one block).
+__global__ void k_transfer_delta(const double* __restrict__ bins, const double* __restrict__ te, int nsh,
+                                 double* __restrict__ dT, double* loss) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+    const double d = bins[i] - te[i];
+    dT[i] = d;
+    a += d * d;
+  }
+  const double t = block_sum(a, red);
+  if (threadIdx.x == 0) atomicAdd(loss, t);
+}
+
+// r_hat(k) = dT(K(k)) u(k) on the kept modes (full layout, zero elsewhere).
+__global__ void k_transfer_residual(const Geo g, const Spec u, const double* __restrict__ dT, int nsh,
+                                    V* __restrict__ rh) {
+  const long long total = (long long)g.nz * g.ny * g.nh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % g.nh), qi = (int)((i / g.nh) % g.ny), ri = (int)(i / ((long long)g.nh * g.ny));
+    const int q = sidx(qi, g.ny), r = sidx(ri, g.nz);
+    V o[3] = {czero<V>(), czero<V>(), czero<V>()};
+    if (kept(g, p, q, r)) {
+      const double kx = p * g.sx, ky = q * g.sy, kz = r * g.sz;
+      const int K = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
+      if (K < nsh) {
+        const float d = (float)dT[K];
+        const V* up = static_cast<const V*>(u.p) + (long long)rowof(r, u.zwrap) * u.zs +
+                      (long long)rowof(q, u.ywrap) * u.ys + p;
+        for (int c = 0; c < 3; ++c) o[c] = cscale(up[c * u.cs], d);
+      }
+    }
+    for (int c = 0; c < 3; ++c) rh[c * total + i] = o[c];
+  }
+}
+
 // dL/dg_n = s_tau sum_m T_n,m(A/s_A) dL/dtau_m with dL/dtau_ij = c d r_i/d x_j
 // (both orders for an off-diagonal component); G holds d r_i / d x_j as 9
 // planar fields [3i+j], Arows the gradient of the state.
@@ -458,7 +538,8 @@ cudaError_t les_closure_term(const Geo& g, Spec in, const void* twx, const void*
 }
 
 cudaError_t les_closure_grad(const Geo& g, Spec in, Spec f, const void* twx, const void* twy, const void* twz,
-                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st) {
+                             const LesScratch& s, const float* params, float* grad, double* loss, cudaStream_t st,
+                             const double* t_exact, int nsh, double* bins) {
   using namespace les;
   const long long P = (long long)g.nx * g.ny * g.nz;
   const long long M = (long long)g.nz * g.ny * g.nh;
@@ -485,9 +566,25 @@ cudaError_t les_closure_grad(const Geo& g, Spec in, Spec f, const void* twx, con
   }
   // residual and loss; d r_i / d x_j (k_grad reads each mode's three values
   // before writing its nine, so it runs in place on the spectral buffer)
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && !t_exact) {
     k_force_residual<<<1024, 256, 0, st>>>(g, s.extra, f, s.spec, loss);
     e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && t_exact) {
+    // transfer loss: bins = T_model, dT = bins - T_exact (in bins + nsh)
+    e = cudaMemsetAsync(bins, 0, sizeof(double) * nsh, st);
+    if (e == cudaSuccess) {
+      k_transfer_shells<<<256, 256, sizeof(double) * nsh, st>>>(g, s.extra, in, bins, nsh);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_transfer_delta<<<1, 128, 0, st>>>(bins, t_exact, nsh, bins + nsh, loss);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_transfer_residual<<<1024, 256, 0, st>>>(g, in, bins + nsh, nsh, s.spec);
+      e = cudaGetLastError();
+    }
   }
   if (e == cudaSuccess) {
     Spec r;

@@ -130,7 +130,7 @@ struct ps_plan {
   // learned LES closure (ps_plan_set_closure)
   bool les_on = false;
   ps::LesScratch les{};
-  void* les_mem[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* les_mem[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int ng = 1;    // 3-component groups: 1 HD, 2 MHD
   Geo g{};
   Sizes sz{};
@@ -448,7 +448,8 @@ ps_status setup_forcing(ps_plan* p) {
 void release(ps_plan* p) {
   void* bufs[] = {p->a6, p->b6, p->nxt, p->acc, p->tw, p->iftab, p->fbox, p->e_part, p->stats,
                   p->umax2, p->ext, p->err, p->dpart, p->dout, p->hstate, p->les_mem[0], p->les_mem[1],
-                  p->les_mem[2], p->les_mem[3], p->les_mem[4], p->les_mem[5], p->les_mem[6], p->les_mem[7]};
+                  p->les_mem[2], p->les_mem[3], p->les_mem[4], p->les_mem[5], p->les_mem[6], p->les_mem[7],
+                  p->les_mem[8]};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& t : p->tl) {
@@ -930,6 +931,33 @@ ps_status ps_plan_closure_grad(ps_plan* p, const float* params, const void* ubar
                                              static_cast<char*>(p->tw) + sizeof(float2) * (g.nx + g.ny), p->les,
                                              params, grad, loss, p->stream);
   PS_CU(e, "closure gradient");
+  return PS_OK;
+}
+
+ps_status ps_plan_closure_grad_transfer(ps_plan* p, const float* params, const void* ubar, const double* t_exact,
+                                        int nshells, float* grad, double* loss, int accumulate) {
+  if (!p || !params || !ubar || !t_exact || !grad || !loss) return fail(PS_ERR_INVALID_ARG, "NULL plan or buffer");
+  if (nshells < 1 || nshells > 1024) return fail(PS_ERR_INVALID_ARG, "nshells must be in 1..1024");
+  if (!p->les_on) return fail(PS_ERR_INVALID_ARG, "no closure attached (ps_plan_set_closure)");
+  DeviceGuard dg(p->device);
+  const ps::Geo& g = p->g;
+  const size_t P = (size_t)g.nx * g.ny * g.nz;
+  if (!p->les_mem[7]) PS_CU(cudaMalloc(&p->les_mem[7], sizeof(float) * 9 * P), "closure training scratch");
+  if (!p->les_mem[8]) PS_CU(cudaMalloc(&p->les_mem[8], sizeof(double) * 3 * 1024), "closure transfer scratch");
+  p->les.Arows = static_cast<float*>(p->les_mem[7]);
+  double* te = static_cast<double*>(p->les_mem[8]);
+  PS_CU(cudaMemcpyAsync(te, t_exact, sizeof(double) * nshells, cudaMemcpyHostToDevice, p->stream), "transfer target");
+  if (!accumulate) {
+    PS_CU(cudaMemsetAsync(grad, 0, sizeof(float) * PS_MLP_NPARAM, p->stream), "gradient reset");
+    PS_CU(cudaMemsetAsync(loss, 0, sizeof(double), p->stream), "loss reset");
+  }
+  const ps::Spec u = caller_spec(g, ubar);
+  const cudaError_t e = ps::les_closure_grad(g, u, u, p->tw, static_cast<char*>(p->tw) + sizeof(float2) * g.nx,
+                                             static_cast<char*>(p->tw) + sizeof(float2) * (g.nx + g.ny), p->les,
+                                             params, grad, loss, p->stream, te, nshells, te + 1024);
+  PS_CU(e, "closure transfer gradient");
+  // the host target may be released once the copy has run
+  PS_CU(cudaStreamSynchronize(p->stream), "transfer target");
   return PS_OK;
 }
 

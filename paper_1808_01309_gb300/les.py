@@ -130,6 +130,29 @@ def train_force(plan, params, norm: dict, snaps, iters: int = 1000, lr: float = 
     return log
 
 
+def train_transfer(plan, params, norm: dict, snaps, iters: int = 500, lr: float = 1e-3, log_every: int = 50):
+    """Full-batch Adam on the energy-transfer loss (ps_plan_closure_grad_transfer)
+    summed over the snapshots (ubar, exact transfer T(K)); logs the loss
+    relative to that of the zero network."""
+    torch = _torch()
+    plan.set_closure(params, norm)
+    grad = torch.empty_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.empty(1, device=params.device, dtype=torch.float64)
+    ref = sum(float(np.sum(np.asarray(te) ** 2)) for _, te in snaps)
+    log = []
+    for it in range(1, iters + 1):
+        for k, (ub, te) in enumerate(snaps):
+            plan.closure_grad_transfer(params, ub, te, grad, loss, accumulate=k > 0)
+        if it == 1 or it % log_every == 0 or it == iters:
+            log.append((it, float(loss.item()) / ref))
+        rate = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * (it - 1) / max(iters - 1, 1))))
+        ps.ps_mlp_adam(params, grad, m, v, it, rate)
+    plan.set_closure(None)
+    return log
+
+
 def shell_transfer(uhat, force, kc: int) -> np.ndarray:
     """Energy transfer spectrum T(K) = sum over shell K of w Re(conj(u) . f)
     (w = 1 on the kx = 0 plane, 2 elsewhere) for K = 0..kc; host analysis of
@@ -188,8 +211,9 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
                n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, fit="both", force_iters=1000,
                force_lr=1e-3, seed=1, verbose=True) -> dict:
     """Runs the workflow of the module docstring; fit = "stress" (tensor-basis
-    stress loss), "force" (stress fit refined on the force loss) or "both"
-    (both models evaluated)."""
+    stress loss), "force" (stress fit refined on the force loss), "transfer"
+    (stress fit refined on the shell energy-transfer loss) or "both" (all
+    three models evaluated)."""
     torch = _torch()
     dev = "cuda"
     say = print if verbose else (lambda *a, **k: None)
@@ -229,7 +253,7 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
         Xs.append(X)
         As.append(A)
         Ts.append(T)
-        if fit in ("force", "both"):
+        if fit in ("force", "transfer", "both"):
             ubar, exact, _ = sgs_force(dns, les_plan, u, n_dns, n_les, kc)
             snaps.append((ubar, exact))
         _timed_steps(dns, u, dt_dns, gap, t)
@@ -261,6 +285,19 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
         out["force_fit"] = dict(loss_log=flog, seconds=time.perf_counter() - w0)
         say(f"force fit: relative loss {flog[0][1]:.4f} -> {flog[-1][1]:.4f}")
         models = {"learned_force": pf} if fit == "force" else {"learned_stress": params, "learned_force": pf}
+    if fit in ("transfer", "both"):
+        pt = params.clone()
+        nsh = int(math.ceil(math.sqrt(3.0) * kc)) + 1  # every shell of the retained cube
+        tsnaps = [(ub, shell_transfer(ub, ex, nsh)) for ub, ex in snaps]
+        w0 = time.perf_counter()
+        tlog = train_transfer(les_plan, pt, norm, tsnaps, iters=force_iters, lr=force_lr)
+        torch.cuda.synchronize()
+        out["transfer_fit"] = dict(loss_log=tlog, seconds=time.perf_counter() - w0)
+        say(f"transfer fit: relative loss {tlog[0][1]:.4f} -> {tlog[-1][1]:.4f}")
+        if fit == "transfer":
+            models = {"learned_transfer": pt}
+        else:
+            models["learned_transfer"] = pt
     del snaps
     # 4. evaluation window: LES initial state, a-priori energy transfer of
     #    the exact and the modelled subgrid force, DNS spectra
@@ -359,7 +396,7 @@ def main(argv=None):
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--fit", choices=("stress", "force", "both"), default="both")
+    ap.add_argument("--fit", choices=("stress", "force", "transfer", "both"), default="both")
     ap.add_argument("--force-iters", type=int, default=1000)
     ap.add_argument("--force-lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None, help="write the result as JSON here")

@@ -52,6 +52,7 @@ SYMBOLS = (
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
     "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
+    "ps_plan_closure_grad_transfer",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -129,6 +130,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_les_training_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double), P, P, P, P]
     lib.ps_plan_set_host_mode.argtypes = [P, ctypes.c_int]
+    lib.ps_plan_closure_grad_transfer.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, P, P,
+                                                  ctypes.c_int]
     lib.ps_rk_steps.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     lib.ps_mlp_backward.argtypes = [P, P, P, ctypes.c_longlong, P, P]
     lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
@@ -335,6 +338,13 @@ def ps_plan_closure_grad(plan, params, ubar, force, grad, loss, accumulate: bool
                                        1 if accumulate else 0))
 
 
+def ps_plan_closure_grad_transfer(plan, params, ubar, t_exact, grad, loss, accumulate: bool = False) -> None:
+    te = [float(x) for x in t_exact]
+    arr = (ctypes.c_double * len(te))(*te)
+    _check(load().ps_plan_closure_grad_transfer(plan, _ptr(params), _ptr(ubar), arr, len(te), _ptr(grad), _ptr(loss),
+                                                1 if accumulate else 0))
+
+
 def ps_les_filter(n_dns: int, uhat_dns, n_les: int, kc: int, uhat_les, stream=None) -> None:
     _check(load().ps_les_filter(int(n_dns), _ptr(uhat_dns), int(n_les), int(kc), _ptr(uhat_les),
                                 _stream_handle(stream)))
@@ -405,6 +415,12 @@ class Plan:
         self._check_field(ubar)
         self._check_field(force)
         ps_plan_closure_grad(self.handle, params, ubar, force, grad, loss, accumulate)
+
+    def closure_grad_transfer(self, params, ubar, t_exact, grad, loss, accumulate=False):
+        """Energy-transfer loss and gradient of the attached closure (see
+        ps_plan_closure_grad_transfer)."""
+        self._check_field(ubar)
+        ps_plan_closure_grad_transfer(self.handle, params, ubar, t_exact, grad, loss, accumulate)
 
     def close(self):
         if self.handle:

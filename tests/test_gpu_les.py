@@ -278,6 +278,9 @@ def test_les_workflow_improves_on_the_plain_les(ps):
     assert flog[-1][1] < flog[0][1]
     plain = r["les"]["no_model"]
     assert plain["finite"]
+    # the transfer fit matches the a-priori shell transfer; its LES may not stay
+    # bounded (backscatter), so only its fit is checked
+    assert r["transfer_fit"]["loss_log"][-1][1] < 0.5 * r["transfer_fit"]["loss_log"][0][1]
     for name in ("learned_stress", "learned_force"):
         learned = r["les"][name]
         assert learned["finite"], name
@@ -328,4 +331,42 @@ def test_closure_force_gradient_matches_oracle(ps):
         ps.ps_mlp_adam(dv, grad, m, vv, it, 3e-3)
     plan.closure_grad(dv, ud, fd, grad, loss)
     assert loss.item() < 0.8 * first
+    plan.close()
+
+
+def test_closure_transfer_gradient_matches_oracle(ps):
+    n = 32
+    lx, ly, lz = 2 * math.pi, 5.0, 2 * math.pi
+    cfg = oracle.Config(n, n, n, lx=lx, ly=ly, lz=lz, nu=1e-3)
+    u = inputs.random_solenoidal_field(n, n, n, seed=17, lx=lx, ly=ly, lz=lz)
+    v, p = fp32_params(7)
+    norm = norm_of(u, cfg, 0.05)
+    nsh = 20
+    c = oracle.spectral.project(les.closure_term(u, cfg, p, norm), cfg)
+    Tm = les.transfer_spectrum(u, c, cfg, nsh)
+    Te = -0.5 * Tm  # the target pushes every shell's transfer the other way
+    plan = ps.Plan(n, n, n, lx=lx, ly=ly, lz=lz, prec=ps.Precision.FP32, nu=1e-3)
+    dv = torch.from_numpy(v).cuda()
+    plan.set_closure(dv, norm)
+    grad = torch.empty(ps.MLP_NPARAM, device="cuda", dtype=torch.float32)
+    loss = torch.empty(1, device="cuda", dtype=torch.float64)
+    ud = to_dev(u)
+    plan.closure_grad_transfer(dv, ud, Te, grad, loss)
+    L_ref, g_ref = les.transfer_loss_and_grads(u, cfg, p, norm, Te, rnd=les.bf16_round)
+    assert abs(loss.item() - L_ref) < 3e-3 * L_ref
+    g = grad.cpu().numpy().astype(np.float64)
+    o = 0
+    for k in ORDER:
+        sz = p[k].size
+        assert relerr(g[o:o + sz], g_ref[k].reshape(-1)) < 3e-2, k
+        o += sz
+    # Adam on the transfer loss moves the transfer toward the target
+    m, vv = torch.zeros_like(dv), torch.zeros_like(dv)
+    first = None
+    for it in range(1, 31):
+        plan.closure_grad_transfer(dv, ud, Te, grad, loss)
+        first = first or loss.item()
+        ps.ps_mlp_adam(dv, grad, m, vv, it, 3e-3)
+    plan.closure_grad_transfer(dv, ud, Te, grad, loss)
+    assert loss.item() < 0.5 * first
     plan.close()
