@@ -209,7 +209,7 @@ def _timed_steps(plan, u, dt: float, nsteps: int, t0: float) -> float:
 
 def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_spin=8.0, t_train=2.0,
                n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, fit="both", force_iters=1000,
-               force_lr=1e-3, seed=1, verbose=True) -> dict:
+               force_lr=1e-3, drain_only=False, seed=1, verbose=True) -> dict:
     """Runs the workflow of the module docstring; fit = "stress" (tensor-basis
     stress loss), "force" (stress fit refined on the force loss), "transfer"
     (stress fit refined on the shell energy-transfer loss) or "both" (all
@@ -289,6 +289,8 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
         pt = params.clone()
         nsh = int(math.ceil(math.sqrt(3.0) * kc)) + 1  # every shell of the retained cube
         tsnaps = [(ub, shell_transfer(ub, ex, nsh)) for ub, ex in snaps]
+        if drain_only:  # target the drain alone: min(T_exact, 0) per shell
+            tsnaps = [(ub, np.minimum(te, 0.0)) for ub, te in tsnaps]
         w0 = time.perf_counter()
         tlog = train_transfer(les_plan, pt, norm, tsnaps, iters=force_iters, lr=force_lr)
         torch.cuda.synchronize()
@@ -399,11 +401,13 @@ def main(argv=None):
     ap.add_argument("--fit", choices=("stress", "force", "transfer", "both"), default="both")
     ap.add_argument("--force-iters", type=int, default=1000)
     ap.add_argument("--force-lr", type=float, default=1e-3)
+    ap.add_argument("--drain-only", action="store_true", help="transfer fit: target min(T_exact, 0) per shell")
     ap.add_argument("--out", default=None, help="write the result as JSON here")
     a = ap.parse_args(argv)
     r = experiment(n_dns=a.n_dns, n_les=a.n_les, kc=a.kc, nu=a.nu, dt_dns=a.dt_dns, dt_les=a.dt_les,
                    t_spin=a.t_spin, t_train=a.t_train, n_snap=a.n_snap, t_eval=a.t_eval, n_eval=a.n_eval,
-                   iters=a.iters, lr=a.lr, fit=a.fit, force_iters=a.force_iters, force_lr=a.force_lr)
+                   iters=a.iters, lr=a.lr, fit=a.fit, force_iters=a.force_iters, force_lr=a.force_lr,
+                   drain_only=a.drain_only)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(r, fh, indent=1)
