@@ -44,7 +44,8 @@ KIND_FILES = {
     "y_inverse": _COMMON + ["k_yinv_f32.cu"],
     "x_fused": _COMMON + ["k_xpass_f32.cu"],
     "y_forward": _COMMON + ["k_yfwd_f32.cu"],
-    "z_forward_rk": _COMMON + ["k_zfwd_f32.cu"],
+    "z_forward": _COMMON + ["k_zfwd_f32.cu"],
+    "update": _COMMON + ["k_zfwd_f32.cu"],
 }
 
 
@@ -189,16 +190,18 @@ def algorithmic_bytes(n: int, vb: int):
         "y_inverse": (6 * n * c2 * cx + 6 * n * n * cx) * vb,
         "x_fused": (6 * n * n * cx + 3 * n * n * cx) * vb,
         "y_forward": (3 * n * n * cx + 3 * n * c2 * cx) * vb,
+        "z_forward": (3 * n * c2 * cx + 3 * modes) * vb,
     }
-    # z-forward of an RK4 step, averaged over its four stages: reads the 3
-    # y-forward fields and the state; stages 1-3 write stage input and
-    # accumulator (2-3 also read the accumulator), stage 4 writes the full state
+    # per-mode update of an RK4 step, averaged over its four stages: reads the
+    # transformed nonlinear term and the state; stages 1-3 write stage input and
+    # accumulator (2-3 also read the accumulator), stage 4 reads the
+    # accumulator and writes the full state
     nh = n // 2 + 1
-    zf = [3 * n * c2 * cx + 3 * modes + 2 * 3 * modes,
-          3 * n * c2 * cx + 3 * modes + 3 * 3 * modes,
-          3 * n * c2 * cx + 3 * modes + 3 * 3 * modes,
-          3 * n * c2 * cx + 3 * modes + 3 * modes + 3 * n * n * nh]
-    b["z_forward_rk"] = sum(zf) / 4 * vb
+    up = [3 * modes + 3 * modes + 2 * 3 * modes,
+          3 * modes + 3 * modes + 3 * 3 * modes,
+          3 * modes + 3 * modes + 3 * 3 * modes,
+          3 * modes + 3 * modes + 3 * modes + 3 * n * n * nh]
+    b["update"] = sum(up) / 4 * vb
     return b
 
 
@@ -207,10 +210,10 @@ def model_bytes(n: int, vb: int):
     three-passes-per-direction schedule (no pruning): with S = n^2 (n/2+1) vb
     one complex field, an HD RHS reads 3+6+6+3+3 S and writes 6+6+3+3+3 S
     (42 S), an IF-RK4 step moves 4 x 42 S + 30 S = 198 S (the RK stage
-    updates, carried by the z-forward pass)."""
+    updates, carried by the per-mode update kernel, 30 S / 4 per launch)."""
     S = n * n * (n // 2 + 1) * vb
     return {"z_inverse": 9 * S, "y_inverse": 12 * S, "x_fused": 9 * S, "y_forward": 6 * S,
-            "z_forward_rk": 6 * S + 30 * S / 4}, 198 * S
+            "z_forward": 6 * S, "update": 30 * S / 4}, 198 * S
 
 
 def make_inputs(n: int):

@@ -120,10 +120,11 @@ typedef struct {
   double magnetic_energy, cross_helicity, magnetic_helicity;
 } ps_diag;
 
-#define PS_NKINDS 6
+#define PS_NKINDS 7
 /* Per-kernel-kind device time measured with CUDA events on the plan stream
  * while timing is enabled: 0 z-inverse, 1 y-inverse, 2 fused x pass,
- * 3 y-forward, 4 z-forward (+ spectral ops and RK update), 5 auxiliary. */
+ * 3 y-forward, 4 z-forward transform, 5 auxiliary, 6 per-mode update
+ * (forcing, projection, closure, RHS or RK stage update). */
 typedef struct {
   double ms[PS_NKINDS];
   long long launches[PS_NKINDS];

@@ -10,4 +10,9 @@ cudaError_t launch_zfwd<float>(const PassArgs& a, cudaStream_t s) {
 #undef CALL
 }
 
+template <>
+cudaError_t launch_update<float>(const PassArgs& a, cudaStream_t s) {
+  return update_launch<float>(a, s);
+}
+
 }  // namespace ps

@@ -10,4 +10,9 @@ cudaError_t launch_zfwd<double>(const PassArgs& a, cudaStream_t s) {
 #undef CALL
 }
 
+template <>
+cudaError_t launch_update<double>(const PassArgs& a, cudaStream_t s) {
+  return update_launch<double>(a, s);
+}
+
 }  // namespace ps

@@ -210,17 +210,97 @@ template <typename T, int N> struct EOf {
 };
 
 // Twiddle tables tw[m] = exp(-2 pi i m/N): read-only global memory (through
-// the non-coherent path) or a copy in shared memory.
+// the non-coherent path) or a copy in shared memory.  at<NS, R>(r, b, idx)
+// returns the twiddle of input r of the thread's butterfly b in the stage with
+// previous radix product NS, which is tw[idx].
 template <typename V>
 struct GlobalTw {
   const V* __restrict__ p;
   __device__ __forceinline__ V operator[](int i) const { return __ldg(p + i); }
+  template <int NS, int R>
+  __device__ __forceinline__ V at(int, int, int idx) const { return __ldg(p + idx); }
 };
 template <typename V>
 struct SharedTw {
   const V* p;
   __device__ __forceinline__ V operator[](int i) const { return p[i]; }
+  template <int NS, int R>
+  __device__ __forceinline__ V at(int, int, int idx) const { return p[idx]; }
 };
+
+// Per-thread twiddle slots: stage s > 0 of a schedule needs (E/R_s)(R_s - 1)
+// twiddles per thread (inputs r = 1..R_s-1 of each of its butterflies).
+template <int N, int E> struct TwSlots {
+  using S = Sched<N, E>;
+  static constexpr int n1 = S::S > 1 ? (E / S::R1) * (S::R1 - 1) : 0;
+  static constexpr int n2 = S::S > 2 ? (E / S::R2) * (S::R2 - 1) : 0;
+  static constexpr int n3 = S::S > 3 ? (E / S::R3) * (S::R3 - 1) : 0;
+  static constexpr int total = n1 + n2 + n3;
+  __host__ __device__ static constexpr int base(int ns) {
+    return ns == S::R0 ? 0 : ns == S::R0 * S::R1 ? n1 : n1 + n2;
+  }
+};
+
+// Twiddles of one thread position j0 gathered into a table [slot][N/E] (slot
+// = stage base + b (R-1) + r - 1), so that the G threads of a line read G
+// consecutive entries per twiddle: conflict-free shared-memory reads instead of
+// scattered table lookups.  Used by kernels whose threads keep one j0 for many
+// lines (the persistent x pass).
+template <typename V, int N, int E>
+struct ThreadTw {
+  const V* p;
+  int j0;
+  template <int NS, int R>
+  __device__ __forceinline__ V at(int r, int b, int) const {
+    return p[(TwSlots<N, E>::base(NS) + b * (R - 1) + (r - 1)) * (N / E) + j0];
+  }
+};
+
+// The same twiddles held in registers for the whole kernel (kernels that keep
+// one j0 and whose schedule needs few twiddles per thread).
+template <typename V, int N, int E>
+struct RegTw {
+  V w[TwSlots<N, E>::total > 0 ? TwSlots<N, E>::total : 1];
+  template <int NS, int R>
+  __device__ __forceinline__ V at(int r, int b, int) const {
+    return w[TwSlots<N, E>::base(NS) + b * (R - 1) + (r - 1)];
+  }
+  template <int NS, int R>
+  __device__ __forceinline__ void load_stage(const V* __restrict__ tw, int j0) {
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int k = (j0 + b * (N / E)) % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[TwSlots<N, E>::base(NS) + b * (R - 1) + (r - 1)] = __ldg(tw + r * k * (N / (NS * R)));
+    }
+  }
+  __device__ __forceinline__ void load(const V* __restrict__ tw, int j0) {
+    using S = Sched<N, E>;
+    if constexpr (S::S > 1) load_stage<S::R0, S::R1>(tw, j0);
+    if constexpr (S::S > 2) load_stage<S::R0 * S::R1, S::R2>(tw, j0);
+    if constexpr (S::S > 3) load_stage<S::R0 * S::R1 * S::R2, S::R3>(tw, j0);
+  }
+};
+
+template <int N, int E, int NS, int R, typename V>
+__device__ __forceinline__ void fill_stage_tw(V* tab, const V* __restrict__ tw, int j0) {
+  constexpr int NB = E / R;
+  for (int b = 0; b < NB; ++b) {
+    const int k = (j0 + b * (N / E)) % NS;
+    for (int r = 1; r < R; ++r)
+      tab[(TwSlots<N, E>::base(NS) + b * (R - 1) + (r - 1)) * (N / E) + j0] = tw[r * k * (N / (NS * R))];
+  }
+}
+
+// Thread j0 (0 <= j0 < N/E) writes its column of the per-thread table.
+template <int N, int E, typename V>
+__device__ void fill_thread_tw(V* tab, const V* __restrict__ tw, int j0) {
+  using S = Sched<N, E>;
+  if constexpr (S::S > 1) fill_stage_tw<N, E, S::R0, S::R1>(tab, tw, j0);
+  if constexpr (S::S > 2) fill_stage_tw<N, E, S::R0 * S::R1, S::R2>(tab, tw, j0);
+  if constexpr (S::S > 3) fill_stage_tw<N, E, S::R0 * S::R1 * S::R2, S::R3>(tab, tw, j0);
+}
 
 // Twiddle exp(DIR 2 pi i m/N).
 template <int DIR, typename V, class TW>
@@ -246,7 +326,10 @@ __device__ __forceinline__ void stage(V (&a)[E], int j0, const TW& tw, X& ex) {
     for (int r = 0; r < R; ++r) x[r] = a[b + r * NB];
     if constexpr (NS > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<DIR, V>(tw, r * k * (N / (NS * R))));
+      for (int r = 1; r < R; ++r) {
+        const V w = tw.template at<NS, R>(r, b, r * k * (N / (NS * R)));
+        x[r] = cmul(x[r], DIR > 0 ? cconj(w) : w);
+      }
     }
     dft<R, DIR>(x);
     if constexpr (LAST) {

@@ -74,6 +74,8 @@ template <typename T> cudaError_t launch_yinv(const PassArgs& a, cudaStream_t s)
 template <typename T> cudaError_t launch_xpass(const PassArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_yfwd(const PassArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_zfwd(const PassArgs& a, cudaStream_t s);
+// projection, forcing, closure and the ZfwdMode output from the z-forward pass's a6
+template <typename T> cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
 // number of CTAs (energy partials) the z-inverse pass uses for this geometry
 template <typename T> int zinv_blocks(const Geo& g);
 

@@ -19,6 +19,7 @@
 // transformed where the input is known to vanish elsewhere (pruned transforms);
 // the result is identical to full transforms of the masked field.
 #pragma once
+#include <type_traits>
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
 #include "ps_kernels.h"
@@ -29,15 +30,24 @@ namespace ps {
 #ifndef PS_TX32
 #define PS_TX32 8
 #endif
-template <typename T> struct TXOf { static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4; };
+#ifndef PS_TXY32
+#define PS_TXY32 8
+#endif
+#ifndef PS_TXZF32
+#define PS_TXZF32 8
+#endif
+// K: 0 z-inverse, 1 y passes, 2 z-forward
+template <typename T, int K = 0> struct TXOf {
+  static constexpr int v = sizeof(T) == 4 ? (K == 1 ? PS_TXY32 : K == 2 ? PS_TXZF32 : PS_TX32) : 4;
+};
 // lines batched per CTA in the strided passes (about 256 threads per CTA)
-template <typename T, int N> struct NBOf {
+template <typename T, int N, int K = 0> struct NBOf {
   static constexpr int G = N / EOf<T, N>::v;
-  static constexpr int q = 256 / (TXOf<T>::v * G);
+  static constexpr int q = 256 / (TXOf<T, K>::v * G);
   static constexpr int v = q < 1 ? 1 : q;
 };
-template <typename T, int N> struct ColThreads {
-  static constexpr int v = TXOf<T>::v * (N / EOf<T, N>::v) * NBOf<T, N>::v;
+template <typename T, int N, int K = 0> struct ColThreads {
+  static constexpr int v = TXOf<T, K>::v * (N / EOf<T, N>::v) * NBOf<T, N, K>::v;
 };
 // rows per CTA in the x pass
 template <typename T, int N> struct RPCOf {
@@ -45,12 +55,24 @@ template <typename T, int N> struct RPCOf {
   static constexpr int v = G >= 256 ? 1 : 256 / G;
 };
 
+// x pass: per-thread twiddle table in shared memory when it takes at most 8 KB
+template <typename T, int N> struct XTwTable {
+  static constexpr int E = EOf<T, N>::v;
+  static constexpr bool v = (size_t)TwSlots<N, E>::total * (N / E) * sizeof(typename cplx<T>::type) <= 8192;
+};
+
+// x pass: twiddles in registers for the whole kernel when there are few
+#ifndef PS_XTWREG
+#define PS_XTWREG 14
+#endif
+template <typename T, int N> struct XTwReg {
+  static constexpr int E = EOf<T, N>::v;
+  static constexpr bool v = sizeof(T) == 4 && E == 8 && TwSlots<N, E>::total <= PS_XTWREG;
+};
+
 // Minimum resident CTAs per SM requested from the register allocator.
 #ifndef PS_XROWBAR
 #define PS_XROWBAR 1
-#endif
-#ifndef PS_XTWSMEM
-#define PS_XTWSMEM 0
 #endif
 #ifndef PS_MINB_ZINV
 #define PS_MINB_ZINV 2
@@ -58,11 +80,8 @@ template <typename T, int N> struct RPCOf {
 #ifndef PS_MINB_XPASS
 #define PS_MINB_XPASS 2
 #endif
-#ifndef PS_MINB_ZFWD
-#define PS_MINB_ZFWD 2
-#endif
 template <typename T, int N> struct MinB {
-  static constexpr int zinv = PS_MINB_ZINV, xpass = PS_MINB_XPASS, zfwd = PS_MINB_ZFWD;
+  static constexpr int zinv = PS_MINB_ZINV, xpass = PS_MINB_XPASS;
 };
 
 __device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -188,6 +207,10 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
     cp_async_wait<0>();
     __syncthreads();
   }
+  unsigned keepm = 0;  // bit m: mode (kx, q, r(n)) of element m is retained
+#pragma unroll
+  for (int m = 0; m < E; ++m)
+    if (bvalid && kept(g, kx, q, sidx(j0 + m * (N / E), N))) keepm |= 1u << m;
 #pragma unroll 1
   for (int f = 0; f < 6; ++f) {
     V x[E];
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
       const int n = j0 + m * (N / E);
       const int r = sidx(n, N);
       V v = czero<V>();
-      if (bvalid && kept(g, kx, q, r)) {
+      if ((keepm >> m) & 1u) {
         const V* pm = tb + rowof(r, g.cz) * TX;
         if (f < 3) {
           v = pm[f * cst];
@@ -242,9 +265,9 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
 // yinv: backward transform along y of 6 fields.  CTA = TX columns x NB z planes.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N>::v) k_yinv(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -310,14 +333,22 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
     ex.bar_id = -1;
   }
 #endif
-#if PS_XTWSMEM
-  V* tws = exbuf + 2 * rpc * LEN;  // twiddle table copy
-  for (int i = tid; i < N; i += blockDim.x) tws[i] = static_cast<const V*>(a.tw_x)[i];
-  __syncthreads();
-  const SharedTw<V> tw{tws};
-#else
-  const GlobalTw<V> tw{static_cast<const V*>(a.tw_x)};
-#endif
+  // per-thread twiddle table (when it is small): thread j0 of every row reads
+  // its own column, conflict-free; larger tables stay in global memory
+  constexpr bool TR = XTwReg<T, N>::v;
+  constexpr bool TT = !TR && XTwTable<T, N>::v;
+  using TwAcc = typename std::conditional<TR, RegTw<V, N, E>,
+                typename std::conditional<TT, ThreadTw<V, N, E>, GlobalTw<V>>::type>::type;
+  TwAcc tw;
+  if constexpr (TR) {
+    tw.load(static_cast<const V*>(a.tw_x), j0);
+  } else if constexpr (TT) {
+    V* twt = exbuf + 2 * rpc * LEN;
+    if (rl == 0) fill_thread_tw<N, E>(twt, static_cast<const V*>(a.tw_x), j0);
+    tw = TwAcc{twt, j0};
+  } else {
+    tw = TwAcc{static_cast<const V*>(a.tw_x)};
+  }
   const V* B = static_cast<const V*>(a.b6);
   V* C = static_cast<V*>(a.a6);
   if (tid == 0) {
@@ -465,9 +496,9 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
 // yfwd: forward transform along y of 3 fields, keep |ky| <= Ky.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -494,190 +525,185 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v) k_yfwd(const PassArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// zfwd: forward transform along z of 3 fields, then per retained mode
-//   v = D P(N/(Nx Ny Nz) + f),  and the output of the selected mode.
-// full != 0: the grid covers every (ky, kx < nh) of the caller's layout and
-// writes zeros outside the retained set; otherwise only retained modes of the
-// compact stage buffers are written.
+// zfwd: forward transform along z of one field per CTA (blockIdx.z), keep the
+// retained kz rows and scale by 1/(Nx Ny Nz).  Writes the compact transformed
+// nonlinear term [3 ng][cz][cy][kxp] into a6 (zero where the mode is not
+// retained).  The projection, forcing and stage update follow in k_update.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int NG>
-__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a, const int full) {
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
-  const int bidx = blockIdx.y * NB + bb;
+  const int iy = blockIdx.y * NB + bb;
+  const bool bvalid = iy < g.cy;
   const int kx = blockIdx.x * TX + line;
-  int q, iy;
-  bool bvalid, bret;
-  if (full) {
-    bvalid = bidx < g.ny;
-    q = sidx(bidx, g.ny);
-    bret = bvalid && q <= g.Ky && q >= -g.Ky;
-    iy = rowof(q, g.cy);
-  } else {
-    bvalid = bret = bidx < g.cy;
-    iy = bidx;
-    q = iy <= g.Ky ? iy : iy - g.cy;
-  }
-  const bool colin = bret && kx < g.kxp;
-  const long long fcs = (long long)g.nz * g.ny * g.nh;   // caller layout component stride
-  if (full && !__syncthreads_or(colin && kx <= g.Kx)) {
-    // the whole tile lies outside the retained set: its modes are zero
-    if (bvalid && kx < g.nh) {
-      V* po = static_cast<V*>(a.out_full) + (long long)bidx * g.nh + kx;
-#pragma unroll 1
-      for (int c = 0; c < 3 * NG; ++c)
+  const int q = iy <= g.Ky ? iy : iy - g.cy;
+  const int f = blockIdx.z;
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  const long long cs_in = (long long)g.nz * g.cy * g.kxp;
+  const V* in = static_cast<const V*>(a.b6) + f * cs_in + (long long)(bvalid ? iy : 0) * g.kxp + kx;
+  V x[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) po[c * fcs + (long long)(j0 + m * (N / E)) * g.ny * g.nh] = czero<V>();
+  for (int m = 0; m < E; ++m)
+    x[m] = bvalid ? ldv(in + (long long)(j0 + m * (N / E)) * g.cy * g.kxp) : czero<V>();
+  line_fft<N, E, -1>(x, j0, static_cast<const V*>(a.tw_z), ex);
+  if (bvalid) {
+    const T inv = T(1.0 / ((double)g.nx * g.ny * g.nz));
+    V* out = static_cast<V*>(a.a6) + (long long)f * g.cz * g.cy * g.kxp + (long long)iy * g.kxp + kx;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int r = sidx(j0 + m * (N / E), N);
+      if (r <= g.Kz && r >= -g.Kz)
+        out[(long long)rowof(r, g.cz) * g.cy * g.kxp] = kept(g, kx, q, r) ? cscale(x[m], inv) : czero<V>();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// update: per mode, from the compact transformed nonlinear term Nh (a6)
+//   velocity group: v = P(Nh + f + closure), P = I - k k^T/|k|^2, v(0) = 0
+//   magnetic group: v = i k x Nh  (the curl of u x B)
+// then the selected output (ZfwdMode): the right-hand side v - damp |k|^2 u, or
+// a Lawson RK stage update of the compact stage buffers / the caller's state.
+// full != 0: one thread per mode of the caller's layout (modes outside the
+// retained set are written as zero); otherwise one thread per retained mode.
+// Consecutive threads take consecutive kx: every access is a contiguous row.
+// ---------------------------------------------------------------------------
+template <typename T, int NG>
+__global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full) {
+  using V = typename cplx<T>::type;
+  const Geo& g = a.g;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int kx, q, r;
+  long long orow = 0;  // row of the caller layout (z * ny + y)
+  if (full) {
+    if (idx >= (long long)g.nz * g.ny * g.nh) return;
+    kx = (int)(idx % g.nh);
+    orow = idx / g.nh;
+    q = sidx((int)(orow % g.ny), g.ny);
+    r = sidx((int)(orow / g.ny), g.nz);
+  } else {
+    if (idx >= (long long)g.cz * g.cy * g.cx) return;
+    kx = (int)(idx % g.cx);
+    const long long crow = idx / g.cx;
+    const int iy = (int)(crow % g.cy), iz = (int)(crow / g.cy);
+    q = iy <= g.Ky ? iy : iy - g.cy;
+    r = iz <= g.Kz ? iz : iz - g.cz;
+  }
+  const long long fcs = (long long)g.nz * g.ny * g.nh;  // caller layout component stride
+  const bool keep = kept(g, kx, q, r);
+  if (!keep) {
+    if (full) {
+      V* po = static_cast<V*>(a.out_full) + orow * g.nh + kx;
+#pragma unroll
+      for (int c = 0; c < 3 * NG; ++c) po[c * fcs] = czero<V>();
     }
     return;
   }
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
-  const V* tw = static_cast<const V*>(a.tw_z);
-  const long long cs_in = (long long)g.nz * g.cy * g.kxp;
-  const T inv = T(1.0 / ((double)g.nx * g.ny * g.nz));
-  const T kxv = T(kx) * T(g.sx), kyv = T(q) * T(g.sy), sz = T(g.sz);
-  const V* un = static_cast<const V*>(a.u_n.p);
-  const V* fb = static_cast<const V*>(a.fbox);
-  const T dt = T(a.dt);
+  const int iy = rowof(q, g.cy), iz = rowof(r, g.cz);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
-  // group 0: velocity (forcing, Leray projection, viscosity nu)
-  // group 1 (MHD): magnetic field (curl of the transformed u x B, diffusivity eta)
-#pragma unroll 1
+  const long long ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
+  const T kxv = T(kx) * T(g.sx), kyv = T(q) * T(g.sy), kzv = T(r) * T(g.sz);
+  const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+  const T dt = T(a.dt);
+  const V* nh = static_cast<const V*>(a.a6);
+#pragma unroll
   for (int grp = 0; grp < NG; ++grp) {
     const bool mag = grp == 1;
+    const int c0 = 3 * grp;
+    V v0 = ldv(nh + (c0 + 0) * ccs + ci), v1 = ldv(nh + (c0 + 1) * ccs + ci), v2 = ldv(nh + (c0 + 2) * ccs + ci);
+    if (!mag) {
+      if (a.extra) {  // closure term (LES), compact layout
+        const V* ex0 = static_cast<const V*>(a.extra) + ci;
+        v0 = cadd(v0, ldv(ex0));
+        v1 = cadd(v1, ldv(ex0 + ccs));
+        v2 = cadd(v2, ldv(ex0 + 2 * ccs));
+      }
+      const V* fb = static_cast<const V*>(a.fbox);
+      if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
+        const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
+        const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
+        const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
+        v0 = cadd(v0, ldv(fb + fo));
+        v1 = cadd(v1, ldv(fb + fo + fcs2));
+        v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
+      }
+      if (k2 > T(0)) {
+        // Leray projection v - k (k.v)/|k|^2
+        const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
+        const T ik2 = T(1) / k2;
+        v0 = csub(v0, cscale(kd, kxv * ik2));
+        v1 = csub(v1, cscale(kd, kyv * ik2));
+        v2 = csub(v2, cscale(kd, kzv * ik2));
+      } else {
+        v0 = v1 = v2 = czero<V>();
+      }
+    } else {
+      // curl(u x B): i k x v
+      const V w0 = cmul_i(csub(cscale(v2, kyv), cscale(v1, kzv)));
+      const V w1 = cmul_i(csub(cscale(v0, kzv), cscale(v2, kxv)));
+      const V w2 = cmul_i(csub(cscale(v1, kxv), cscale(v0, kyv)));
+      v0 = w0;
+      v1 = w1;
+      v2 = w2;
+    }
+    const V kk[3] = {v0, v1, v2};
+    const V* pu = static_cast<const V*>(a.u_n.p) + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
+                  (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
+    V* po = static_cast<V*>(a.out_full) + c0 * fcs + orow * g.nh + kx;
+    if (a.mode == ZF_RHS) {
+      const T vk = T(mag ? a.eta : a.nu) * k2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) po[c * fcs] = csub(kk[c], cscale(ldv(pu + c * a.u_n.cs), vk));
+      continue;
+    }
+    // Lawson RK with E = exp(-damp |k|^2 dt/2) = ex(p) ey(q) ez(r)
     const T* ifx = static_cast<const T*>(mag ? a.jfx : a.ifx);
     const T* ify = static_cast<const T*>(mag ? a.jfy : a.ify);
     const T* ifz = static_cast<const T*>(mag ? a.jfz : a.ifz);
-    const T damp = T(mag ? a.eta : a.nu);
-    const V* in = static_cast<const V*>(a.b6) + 3 * grp * cs_in + (long long)(colin ? iy : 0) * g.kxp +
-                  (colin ? kx : 0);
-    V X[3][E];
+    const T Ef = __ldg(ifx + kx) * __ldg(ify + iy) * __ldg(ifz + iz);
+    const T E2 = Ef * Ef;
+    V* acc = static_cast<V*>(a.acc) + c0 * ccs + ci;
+    V* nxt = static_cast<V*>(a.nxt) + c0 * ccs + ci;
+    V u[3], ac[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const long long n = j0 + m * (N / E);
-        X[c][m] = colin ? ldv(in + c * cs_in + n * g.cy * g.kxp) : czero<V>();
-      }
-      line_fft<N, E, -1>(X[c], j0, tw, ex);
+      u[c] = ldv(pu + c * a.u_n.cs);
+      ac[c] = (a.mode == ZF_RK4_1 || a.mode == ZF_RK2_1) ? czero<V>() : acc[c * ccs];
     }
-    const T ey = (a.mode != ZF_RHS && bret) ? ify[iy] : T(0);
-    const T exx = (a.mode != ZF_RHS && kx <= g.Kx) ? ifx[kx] : T(0);
-    const int c0 = 3 * grp;  // state component of this group's first field
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int n = j0 + m * (N / E);
-      const int r = sidx(n, N);
-      const bool keep = bret && kept(g, kx, q, r);
-      V o[3] = {czero<V>(), czero<V>(), czero<V>()};
-      V v0 = czero<V>(), v1 = czero<V>(), v2 = czero<V>();
-      long long ci = 0;
-      if (keep) {
-        const int iz = rowof(r, g.cz);
-        ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
-        v0 = cscale(X[0][m], inv);
-        v1 = cscale(X[1][m], inv);
-        v2 = cscale(X[2][m], inv);
-        const T kzv = T(r) * sz;
-        const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-        if (!mag) {
-          if (a.extra) {  // closure term (LES), compact layout
-            const V* ex0 = static_cast<const V*>(a.extra) + ci;
-            v0 = cadd(v0, ldv(ex0));
-            v1 = cadd(v1, ldv(ex0 + ccs));
-            v2 = cadd(v2, ldv(ex0 + 2 * ccs));
-          }
-          if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
-            const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
-            const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
-            const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
-            v0 = cadd(v0, ldv(fb + fo));
-            v1 = cadd(v1, ldv(fb + fo + fcs2));
-            v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
-          }
-          if (k2 > T(0)) {
-            // Leray projection v - k (k.v)/|k|^2
-            const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
-            const T ik2 = T(1) / k2;
-            v0 = csub(v0, cscale(kd, kxv * ik2));
-            v1 = csub(v1, cscale(kd, kyv * ik2));
-            v2 = csub(v2, cscale(kd, kzv * ik2));
-          } else {
-            v0 = v1 = v2 = czero<V>();
-          }
-        } else {
-          // curl(u x B): i k x v
-          const V w0 = cmul_i(csub(cscale(v2, kyv), cscale(v1, kzv)));
-          const V w1 = cmul_i(csub(cscale(v0, kzv), cscale(v2, kxv)));
-          const V w2 = cmul_i(csub(cscale(v1, kxv), cscale(v0, kyv)));
-          v0 = w0;
-          v1 = w1;
-          v2 = w2;
-        }
-        const V* pu = un + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
-                      (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
-        if (a.mode == ZF_RHS) {
-          const T vk = damp * k2;
-          o[0] = csub(v0, cscale(ldv(pu), vk));
-          o[1] = csub(v1, cscale(ldv(pu + a.u_n.cs), vk));
-          o[2] = csub(v2, cscale(ldv(pu + 2 * a.u_n.cs), vk));
-        } else {
-          // Lawson RK with E = exp(-nu |k|^2 dt/2) = ex(p) ey(q) ez(r)
-          const T Ef = exx * ey * ifz[iz];
-          const T E2 = Ef * Ef;
-          V* acc = static_cast<V*>(a.acc) + c0 * ccs + ci;
-          V* nxt = static_cast<V*>(a.nxt) + c0 * ccs + ci;
-          const V kk[3] = {v0, v1, v2};
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const V u = ldv(pu + c * a.u_n.cs);
-            const V k = kk[c];
-            switch (a.mode) {
-              case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
-                acc[c * ccs] = cscale(k, E2);
-                nxt[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), Ef);
-                break;
-              case ZF_RK4_2: {  // acc += 2 E k2 ; next = E u + dt/2 k2
-                const V ac = acc[c * ccs];
-                acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
-                nxt[c * ccs] = cadd(cscale(u, Ef), cscale(k, T(0.5) * dt));
-                break;
-              }
-              case ZF_RK4_3: {  // acc += 2 E k3 ; next = E^2 u + dt E k3
-                const V ac = acc[c * ccs];
-                acc[c * ccs] = cadd(ac, cscale(k, T(2) * Ef));
-                nxt[c * ccs] = cadd(cscale(u, E2), cscale(k, dt * Ef));
-                break;
-              }
-              case ZF_RK4_4: {  // u+ = E^2 u + dt/6 (acc + k4)
-                const V ac = acc[c * ccs];
-                o[c] = cadd(cscale(u, E2), cscale(cadd(ac, k), dt / T(6)));
-                break;
-              }
-              case ZF_RK2_1:  // next = E^2 (u + dt k1) ; acc = E^2 (u + dt/2 k1)
-                nxt[c * ccs] = cscale(cadd(u, cscale(k, dt)), E2);
-                acc[c * ccs] = cscale(cadd(u, cscale(k, T(0.5) * dt)), E2);
-                break;
-              case ZF_RK2_2: {  // u+ = acc + dt/2 k2
-                const V ac = acc[c * ccs];
-                o[c] = cadd(ac, cscale(k, T(0.5) * dt));
-                break;
-              }
-              default: break;
-            }
-          }
-        }
-      }
-      if (full && bvalid && kx < g.nh) {
-        V* po = static_cast<V*>(a.out_full) + c0 * fcs + ((long long)n * g.ny + bidx) * g.nh + kx;
-        po[0] = o[0];
-        po[fcs] = o[1];
-        po[2 * fcs] = o[2];
+    for (int c = 0; c < 3; ++c) {
+      const V k = kk[c];
+      switch (a.mode) {
+        case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
+          acc[c * ccs] = cscale(k, E2);
+          nxt[c * ccs] = cscale(cadd(u[c], cscale(k, T(0.5) * dt)), Ef);
+          break;
+        case ZF_RK4_2:  // acc += 2 E k2 ; next = E u + dt/2 k2
+          acc[c * ccs] = cadd(ac[c], cscale(k, T(2) * Ef));
+          nxt[c * ccs] = cadd(cscale(u[c], Ef), cscale(k, T(0.5) * dt));
+          break;
+        case ZF_RK4_3:  // acc += 2 E k3 ; next = E^2 u + dt E k3
+          acc[c * ccs] = cadd(ac[c], cscale(k, T(2) * Ef));
+          nxt[c * ccs] = cadd(cscale(u[c], E2), cscale(k, dt * Ef));
+          break;
+        case ZF_RK4_4:  // u+ = E^2 u + dt/6 (acc + k4)
+          po[c * fcs] = cadd(cscale(u[c], E2), cscale(cadd(ac[c], k), dt / T(6)));
+          break;
+        case ZF_RK2_1:  // next = E^2 (u + dt k1) ; acc = E^2 (u + dt/2 k1)
+          nxt[c * ccs] = cscale(cadd(u[c], cscale(k, dt)), E2);
+          acc[c * ccs] = cscale(cadd(u[c], cscale(k, T(0.5) * dt)), E2);
+          break;
+        case ZF_RK2_2:  // u+ = acc + dt/2 k2
+          po[c * fcs] = cadd(ac[c], cscale(k, T(0.5) * dt));
+          break;
+        default:
+          break;
       }
     }
   }
@@ -711,12 +737,12 @@ cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
 template <typename T, int N>
 cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yinv<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 6 * a.ng);
-  k_yinv<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  k_yinv<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
 // Shared memory of the x pass for rpc rows: two input stages of 6 ng rows
@@ -724,7 +750,9 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
 template <typename T, int N>
 size_t xpass_smem(const Geo& g, int rpc, int ng) {
   using V = typename cplx<T>::type;
-  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N + (PS_XTWSMEM ? N : 0)) * sizeof(V);
+  constexpr int E = EOf<T, N>::v;
+  const size_t tt = (!XTwReg<T, N>::v && XTwTable<T, N>::v) ? (size_t)TwSlots<N, E>::total * (N / E) : 0;
+  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N + tt) * sizeof(V);
 }
 
 template <typename T, int N, int NG>
@@ -759,29 +787,33 @@ cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
 template <typename T, int N>
 cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 3 * a.ng);
-  k_yfwd<T, N><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
-  return cudaGetLastError();
-}
-template <typename T, int N, int NG>
-cudaError_t zfwd_ng(const PassArgs& a, cudaStream_t s) {
-  using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  const size_t smem = 2ull * NB * N * TX * sizeof(V);
-  cudaError_t e = prep(k_zfwd<T, N, NG>, smem);
-  if (e != cudaSuccess) return e;
-  const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
-  dim3 grid(full ? (a.g.nh + TX - 1) / TX : a.g.kxp / TX, full ? (a.g.ny + NB - 1) / NB : (a.g.cy + NB - 1) / NB);
-  k_zfwd<T, N, NG><<<grid, ColThreads<T, N>::v, smem, s>>>(a, full);
+  k_yfwd<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int N>
 cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
-  return a.ng == 2 ? zfwd_ng<T, N, 2>(a, s) : zfwd_ng<T, N, 1>(a, s);
+  using V = typename cplx<T>::type;
+  constexpr int TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
+  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  cudaError_t e = prep(k_zfwd<T, N>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB, 3 * a.ng);
+  k_zfwd<T, N><<<grid, ColThreads<T, N, 2>::v, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t update_launch(const PassArgs& a, cudaStream_t s) {
+  const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
+  const long long n = full ? (long long)a.g.nz * a.g.ny * a.g.nh : (long long)a.g.cz * a.g.cy * a.g.cx;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (a.ng == 2) k_update<T, 2><<<blocks, 256, 0, s>>>(a, full);
+  else k_update<T, 1><<<blocks, 256, 0, s>>>(a, full);
+  return cudaGetLastError();
 }
 
 #define PS_DISPATCH_N(n, CALL)                     \

@@ -325,6 +325,7 @@ ps_status run_rhs_passes(ps_plan* p, PassArgs& a) {
     a.extra = p->les.extra;
   }
   if ((s = launch(p, 4, [&] { return launch_zfwd<T>(a, p->stream); }, "z-forward pass")) != PS_OK) return s;
+  if ((s = launch(p, 6, [&] { return launch_update<T>(a, p->stream); }, "update")) != PS_OK) return s;
   return PS_OK;
 }
 
@@ -494,7 +495,8 @@ const char* ps_status_string(ps_status s) {
 const char* ps_last_error(void) { return g_last_error.c_str(); }
 
 const char* ps_kind_name(int kind) {
-  static const char* names[PS_NKINDS] = {"z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward_rk", "aux"};
+  static const char* names[PS_NKINDS] = {"z_inverse", "y_inverse", "x_fused", "y_forward",
+                                         "z_forward", "aux", "update"};
   return (kind >= 0 && kind < PS_NKINDS) ? names[kind] : "?";
 }
 

@@ -181,6 +181,7 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   if ((e = launch_xpass<T>(a, s)) != cudaSuccess) return cuda_bad(e, "x pass");
   if ((e = launch_yfwd<T>(a, s)) != cudaSuccess) return cuda_bad(e, "y-forward pass");
   if ((e = launch_zfwd<T>(a, s)) != cudaSuccess) return cuda_bad(e, "z-forward pass");
+  if ((e = launch_update<T>(a, s)) != cudaSuccess) return cuda_bad(e, "update");
   return PS_OK;
 }
 

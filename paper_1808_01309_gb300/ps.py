@@ -41,7 +41,7 @@ class Dealias(enum.IntEnum):
 PS_OK, PS_ERR_INVALID_ARG, PS_ERR_UNSUPPORTED, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_NONFINITE, PS_ERR_TIMEOUT = range(7)
 _STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
            5: "non-finite", 6: "timeout"}
-PS_NKINDS = 6
+PS_NKINDS = 7
 
 # Exported symbols and their signatures (kept in step with include/ps.h).
 SYMBOLS = (

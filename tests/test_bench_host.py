@@ -51,9 +51,10 @@ def test_algorithmic_bytes_model():
     K, cx, c2 = 170, 171, 341
     assert b["x_fused"] == 9 * 512 * 512 * cx * 8
     assert b["z_inverse"] == (3 * c2 * c2 * cx + 6 * 512 * c2 * cx) * 8
-    # one RK4 step moves about 52.7 GB at 512^3 FP32
+    # one RK4 step moves about 56.6 GB at 512^3 FP32 (the z-forward transform
+    # hands the retained nonlinear term to the update kernel through HBM)
     step = 4 * sum(v for k, v in b.items())
-    assert 50e9 < step < 56e9
+    assert 54e9 < step < 59e9
 
 
 def test_traffic_lookup_requires_matching_sources(tmp_path, monkeypatch):
@@ -85,6 +86,6 @@ def test_roofline_model_bytes_add_up_to_the_step_model():
     model, step = b.model_bytes(n, 8)
     assert step == 198 * S
     assert abs(4 * sum(model.values()) - step) < 1e-6 * step
-    assert sum(model[k] for k in model if k != "z_forward_rk") + 6 * S == 42 * S
+    assert sum(model[k] for k in model if k != "update") == 42 * S
     pruned = b.algorithmic_bytes(n, 8)
     assert all(pruned[k] < model[k] for k in model)

@@ -96,7 +96,7 @@ def test_graph_replayed_steps_equal_single_steps(ps):
     plan.rk_steps(b, dt, 3, t=3 * dt)  # replay of the same graph
     torch.cuda.synchronize()
     assert torch.equal(a, b)
-    assert ps.ps_plan_launch_count(plan.handle) - l0 >= 2 * 3 * 21
+    assert ps.ps_plan_launch_count(plan.handle) - l0 >= 2 * 3 * 25
     # a different step size re-captures
     plan.rk_step(a, 1e-3)
     plan.rk_steps(b, 1e-3, 1)
@@ -127,9 +127,9 @@ def test_timing_and_launch_counts(ps):
     t = ps.ps_plan_get_timing(plan.handle)
     ps.ps_plan_set_timing(plan.handle, False)
     launched = ps.ps_plan_launch_count(plan.handle) - l0
-    # per RK4 step: 4 x (5 passes) + energy reduction; dt unchanged -> no table launch
-    assert launched == 2 * 21
-    for kind in ("z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward_rk"):
+    # per RK4 step: 4 x (5 passes + update) + energy reduction; dt unchanged -> no table launch
+    assert launched == 2 * 25
+    for kind in ("z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward", "update"):
         ms, count = t[kind]
         assert count == 8 and ms > 0
     assert sum(c for _, c in t.values()) == launched
