@@ -444,4 +444,103 @@ struct RowExchange {
   __device__ __forceinline__ void flip() { par ^= 1; }
 };
 
+// Exchange for NL lines of one row transformed together (line_fft_rows): line
+// l of the row's region at buf + l * lstride, slots permuted as in RowExchange.
+// With NBUF = 1 one buffer serves every exchange (a second barrier after the
+// reads frees it); NBUF = 2 alternates two buffers bufsz apart.
+template <typename V, int NBUF = 1>
+struct LinesExchange {
+  V* buf;
+  int lstride;
+  int bufsz;
+  int par;
+  int bar_id = 0;   // > 0: named barrier of this row's nthr threads; < 0: the row is within a warp
+  int nthr = 0;
+  template <int NS, int R>
+  __device__ __forceinline__ void put(int l, int n, V v) {
+    buf[par * bufsz + l * lstride + RowExchange<V>::template pos<NS, R>(n)] = v;
+  }
+  template <int NS, int R>
+  __device__ __forceinline__ V get(int l, int n) const {
+    return buf[par * bufsz + l * lstride + RowExchange<V>::template pos<NS, R>(n)];
+  }
+  __device__ __forceinline__ void sync() {
+    if (bar_id > 0) asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+    else if (bar_id < 0) __syncwarp();
+    else __syncthreads();
+  }
+  __device__ __forceinline__ void flip() {
+    if constexpr (NBUF == 2) par ^= 1;
+    else sync();
+  }
+};
+
+// One Stockham stage (as in stage()) applied to NL independent lines held by
+// the same threads: the butterflies of all lines are issued together (the
+// stage twiddles are shared), then one exchange moves all lines.
+template <int N, int E, int R, int NS, int DIR, bool LAST, int NL, typename V, class TW, class X>
+__device__ __forceinline__ void stage_rows(V (&a)[NL][E], int j0, const TW& tw, X& ex) {
+  constexpr int NB = E / R;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = j0 + b * (N / E);
+    const int k = j % NS;
+    V w[R];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const V t = tw.template at<NS, R>(r, b, r * k * (N / (NS * R)));
+        w[r] = DIR > 0 ? cconj(t) : t;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      V x[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = a[l][b + r * NB];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
+      }
+      dft<R, DIR>(x);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[l][b + r * NB] = x[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) ex.template put<NS, R>(l, (j - k) * R + k + r * NS, x[r]);
+      }
+    }
+  }
+  if constexpr (!LAST) {
+    ex.sync();
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int m = 0; m < E; ++m) a[l][m] = ex.template get<NS, R>(l, j0 + m * (N / E));
+    ex.flip();
+  }
+}
+
+// NL line transforms of length N at once (see line_fft_tw).
+template <int N, int E, int DIR, int NL, typename V, class TW, class X>
+__device__ __forceinline__ void line_fft_rows(V (&a)[NL][E], int j0, const TW& tw, X& ex) {
+  using S = Sched<N, E>;
+  if constexpr (S::S == 1) {
+    stage_rows<N, E, S::R0, 1, DIR, true>(a, j0, tw, ex);
+  } else if constexpr (S::S == 2) {
+    stage_rows<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R1, S::R0, DIR, true>(a, j0, tw, ex);
+  } else if constexpr (S::S == 3) {
+    stage_rows<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R1, S::R0, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R2, S::R0 * S::R1, DIR, true>(a, j0, tw, ex);
+  } else {
+    stage_rows<N, E, S::R0, 1, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R1, S::R0, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R2, S::R0 * S::R1, DIR, false>(a, j0, tw, ex);
+    stage_rows<N, E, S::R3, S::R0 * S::R1 * S::R2, DIR, true>(a, j0, tw, ex);
+  }
+}
+
 }  // namespace ps

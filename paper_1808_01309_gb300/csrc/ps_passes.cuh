@@ -30,15 +30,10 @@ namespace ps {
 #ifndef PS_TX32
 #define PS_TX32 8
 #endif
-#ifndef PS_TXY32
-#define PS_TXY32 8
-#endif
-#ifndef PS_TXZF32
-#define PS_TXZF32 8
-#endif
-// K: 0 z-inverse, 1 y passes, 2 z-forward
+// (K names the pass: 0 z-inverse, 1 y passes, 2 z-forward; 128-byte segments
+// (16 FP32 columns) measured slower for the y and z-forward passes)
 template <typename T, int K = 0> struct TXOf {
-  static constexpr int v = sizeof(T) == 4 ? (K == 1 ? PS_TXY32 : K == 2 ? PS_TXZF32 : PS_TX32) : 4;
+  static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4;
 };
 // lines batched per CTA in the strided passes (about 256 threads per CTA)
 template <typename T, int N, int K = 0> struct NBOf {
@@ -60,6 +55,9 @@ template <typename T, int N> struct XTwTable {
   static constexpr int E = EOf<T, N>::v;
   static constexpr bool v = (size_t)TwSlots<N, E>::total * (N / E) * sizeof(typename cplx<T>::type) <= 8192;
 };
+
+// x pass: lines per row transformed together (exchange region of a row)
+constexpr int XLINES = 3;
 
 // x pass: twiddles in registers for the whole kernel when there are few
 #ifndef PS_XTWREG
@@ -298,21 +296,24 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs 
 
 // ---------------------------------------------------------------------------
 // xpass: per physical (z, y) row.  Persistent CTAs loop over groups of rpc
-// consecutive rows; the six input rows of the next group are brought into a
-// second shared-memory stage by TMA bulk copies while the current group is
-// transformed.  Thread j0 of a row's group of G threads holds the points
-// n = j0 + m N/E.
+// consecutive rows.  The input rows of a group are brought into shared memory
+// by TMA bulk copies; once every thread has gathered its points into registers
+// the copies of the next group are issued into the same stage, so they land
+// while the current group is transformed.  Thread j0 of a row's group of G
+// threads holds the points n = j0 + m N/E.  The packed lines of a row are
+// transformed together (line_fft_rows): the inverse lines three at a time, the
+// forward lines of the products together, one exchange for all of them.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int NG>
 __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ? MinB<T, N>::xpass : 1)
     k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E;
-  constexpr int LEN = N;
   constexpr int NF = 6 * NG;  // input fields: u, omega (, B, j)
+  constexpr int NFW = NG == 1 ? 2 : 3;  // forward packed lines
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[1];
   __shared__ int abort_flag;
   const Geo& g = a.g;
   const int kxp = g.kxp;
@@ -320,21 +321,19 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
   const int j0 = tid % G, rl = tid / G;
   const long long rows = (long long)g.nz * g.ny;
   const long long ngroups = (rows + rpc - 1) / rpc;
-  const int stage_elems = NF * rpc * kxp;
   V* stage = reinterpret_cast<V*>(smraw);
-  V* exbuf = stage + 2 * stage_elems;
-  RowExchange<V> ex{exbuf + rl * LEN, rpc * LEN, 0};
-#if PS_XROWBAR
-  // rows are independent between the stage barriers: sync only the row's threads
+  V* exbuf = stage + NF * rpc * kxp;
+  // exchange region of this row: XLINES lines of N slots, single buffer
+  LinesExchange<V, 1> ex{exbuf + rl * XLINES * N, N, 0, 0};
+  // rows are independent between the group barriers: sync only the row's threads
   if (G >= 32) {
     ex.bar_id = 1 + rl;
     ex.nthr = G;
   } else {
     ex.bar_id = -1;
   }
-#endif
-  // per-thread twiddle table (when it is small): thread j0 of every row reads
-  // its own column, conflict-free; larger tables stay in global memory
+  // stage twiddles: in registers when few, else a per-thread table in shared
+  // memory (thread j0 of every row reads its own column), else global memory
   constexpr bool TR = XTwReg<T, N>::v;
   constexpr bool TT = !TR && XTwTable<T, N>::v;
   using TwAcc = typename std::conditional<TR, RegTw<V, N, E>,
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
   if constexpr (TR) {
     tw.load(static_cast<const V*>(a.tw_x), j0);
   } else if constexpr (TT) {
-    V* twt = exbuf + 2 * rpc * LEN;
+    V* twt = exbuf + rpc * XLINES * N;
     if (rl == 0) fill_thread_tw<N, E>(twt, static_cast<const V*>(a.tw_x), j0);
     tw = TwAcc{twt, j0};
   } else {
@@ -353,45 +352,39 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
   V* C = static_cast<V*>(a.a6);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
     abort_flag = 0;
     mbar_fence_init();
   }
   __syncthreads();
-  // stage s <- the NF input fields of row group grp (rpc contiguous rows each)
-  auto issue = [&](long long grp, int s) {
+  // stage <- the NF input fields of row group grp (rpc contiguous rows each)
+  auto issue = [&](long long grp) {
     const long long r0 = grp * rpc;
     const long long nr = rows - r0 < rpc ? rows - r0 : rpc;
     const uint32_t bytes = (uint32_t)(nr * kxp * sizeof(V));
-    mbar_arrive_expect_tx(&bar[s], (uint32_t)NF * bytes);
+    mbar_arrive_expect_tx(&bar[0], (uint32_t)NF * bytes);
     for (int c = 0; c < NF; ++c)
-      bulk_g2s(stage + s * stage_elems + c * rpc * kxp, B + ((long long)c * rows + r0) * kxp, bytes, &bar[s]);
+      bulk_g2s(stage + c * rpc * kxp, B + ((long long)c * rows + r0) * kxp, bytes, &bar[0]);
   };
-  uint32_t ph0 = 0u, ph1 = 0u;  // completed-phase parity of each stage barrier
+  uint32_t ph = 0u;  // completed-phase parity of the stage barrier
   long long it = blockIdx.x;
-  int s = 0;
-  if (tid == 0 && it < ngroups) issue(it, 0);
+  if (tid == 0 && it < ngroups) issue(it);
   T umax2 = 0;
   while (it < ngroups) {
     const long long nxt = it + gridDim.x;
-    if (tid == 0 && nxt < ngroups) {
-      fence_proxy_async();
-      issue(nxt, s ^ 1);
-    }
-    const bool ok = mbar_wait(&bar[s], s ? ph1 : ph0);
-    if (s) ph1 ^= 1u; else ph0 ^= 1u;
-    if (!ok) abort_flag = 1;
+    const uint32_t cur = ph;
+    ph ^= 1u;
+    if (!mbar_wait(&bar[0], cur)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
       if (tid == 0) {
         atomicExch(a.err, PS_DEV_TIMEOUT_XPASS);
-        if (nxt < ngroups) mbar_wait(&bar[s ^ 1], s ? ph0 : ph1);  // let the prefetch land
+        mbar_wait(&bar[0], cur);  // bounded: let a late copy land before the CTA exits
       }
       break;
     }
     const long long row = it * rpc + rl;
     const bool rvalid = row < rows;
-    const V* st = stage + s * stage_elems + rl * kxp;
+    const V* st = stage + rl * kxp;
     // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c
     V U[3 * NG][E];
 #pragma unroll
@@ -417,10 +410,32 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
         }
         U[c][m] = v;
       }
-      line_fft_tw<N, E, +1>(U[c], j0, tw, ex);
+    }
+    // every thread has its points: the stage takes the next group's rows
+    __syncthreads();
+    if (tid == 0 && nxt < ngroups) {
+      fence_proxy_async();
+      issue(nxt);
+    }
+    if constexpr (NG == 1) {
+      line_fft_rows<N, E, +1>(U, j0, tw, ex);
+    } else {
+#pragma unroll
+      for (int h = 0; h < NG; ++h) {
+        V L[3][E];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int m = 0; m < E; ++m) L[c][m] = U[3 * h + c][m];
+        line_fft_rows<N, E, +1>(L, j0, tw, ex);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int m = 0; m < E; ++m) U[3 * h + c][m] = L[c][m];
+      }
     }
     // products at the thread's points (real part = field, imaginary = curl)
-    V F[NG == 1 ? 2 : 3][E];
+    V F[NFW][E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
@@ -443,23 +458,23 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
       }
     }
     if (!a.xdiag) {  // uniform across the grid
-      constexpr int NFW = NG == 1 ? 2 : 3;
-#pragma unroll
-      for (int w = 0; w < NFW; ++w) line_fft_tw<N, E, -1>(F[w], j0, tw, ex);
+      line_fft_rows<N, E, -1>(F, j0, tw, ex);
       const long long rrow = rvalid ? row : 0;
       const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
       // split each packed transform F = DFT(a) + i DFT(b) of two real fields
-      // with its mirrored entry F[N-k]; for HD the second line has b = 0
+      // with its mirrored entry F[N-k] (all split lines through one exchange);
+      // for HD the second line has b = 0
+      constexpr int NSP = NG == 1 ? 1 : NFW;  // lines that need the split
+#pragma unroll
+      for (int w = 0; w < NSP; ++w)
+#pragma unroll
+        for (int m = 0; m < E; ++m) ex.template put<0, 0>(w, j0 + m * (N / E), F[w][m]);
+      ex.sync();
 #pragma unroll
       for (int w = 0; w < NFW; ++w) {
-        const bool split = (NG == 2) || w == 0;
+        const bool split = w < NSP;
         V* ca = C + ((long long)(2 * w) * rows + rrow) * kxp;
         V* cb = C + ((long long)(2 * w + 1) * rows + rrow) * kxp;
-        if (split) {
-#pragma unroll
-          for (int m = 0; m < E; ++m) ex.put(j0 + m * (N / E), F[w][m]);
-          ex.sync();
-        }
 #pragma unroll
         for (int m = 0; m < E; ++m) {
           const int k = j0 + m * (N / E);
@@ -468,7 +483,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
             if (k <= g.Kx) {
               const V Fk = F[w][m];
               if (split) {
-                const V Fm = cconj(ex.get(k == 0 ? 0 : N - k));
+                const V Fm = cconj(ex.template get<0, 0>(w, k == 0 ? 0 : N - k));
                 va = cscale(cadd(Fk, Fm), T(0.5));
                 vb = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
               } else {
@@ -479,11 +494,9 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
             if (split) cb[k] = vb;
           }
         }
-        if (split) ex.flip();
       }
     }
-    __syncthreads();  // stage s and the exchange buffers are free again
-    s ^= 1;
+    __syncthreads();  // the exchange buffers are free again
     it = nxt;
   }
   if (a.umax2) {
@@ -745,14 +758,14 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
   k_yinv<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
-// Shared memory of the x pass for rpc rows: two input stages of 6 ng rows
-// each and the double-buffered exchange.
+// Shared memory of the x pass for rpc rows: one input stage of 6 ng rows, the
+// exchange region (XLINES lines per row) and, when used, the twiddle table.
 template <typename T, int N>
 size_t xpass_smem(const Geo& g, int rpc, int ng) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v;
   const size_t tt = (!XTwReg<T, N>::v && XTwTable<T, N>::v) ? (size_t)TwSlots<N, E>::total * (N / E) : 0;
-  return (2ull * 6 * ng * rpc * g.kxp + 2ull * rpc * N + tt) * sizeof(V);
+  return (6ull * ng * rpc * g.kxp + (size_t)XLINES * rpc * N + tt) * sizeof(V);
 }
 
 template <typename T, int N, int NG>
