@@ -30,8 +30,8 @@ namespace ps {
 #ifndef PS_TX32
 #define PS_TX32 8
 #endif
-// (K names the pass: 0 z-inverse, 1 y passes, 2 z-forward; 128-byte segments
-// (16 FP32 columns) measured slower for the y and z-forward passes)
+// (K names the pass: 0 z-inverse, 1 y passes, 2 z-forward.  Segments of 32 B
+// (4 columns) and 128 B (16 columns) measured slower in every strided pass.)
 template <typename T, int K = 0> struct TXOf {
   static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4;
 };
@@ -727,7 +727,9 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
 // ---------------------------------------------------------------------------
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the 48 KB default covers static and dynamic shared memory together: opt
+  // in well before the dynamic part alone reaches it
+  if (smem > 32 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }
 
