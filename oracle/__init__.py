@@ -16,14 +16,20 @@ computes (Rosenberg et al., arXiv:1808.01309, Sec. 2), in float64 numpy:
 * the pressure acting as a projection onto divergence-free fields,
 * 2/3-rule dealiasing, and
 * an explicit Runge-Kutta step (2nd or 4th order, Sec. 2) written with the
-  viscous integrating factor (Lawson form).
+  viscous integrating factor (Lawson form),
+* the MHD system (Eqs. uMHD, bMHD) and the Boussinesq system (Eqs. mom,
+  temp, divv) with the same transforms, projection and Lawson scheme.
 
 The readings taken where the paper is silent or garbled are listed in the
 module docstring of :mod:`oracle.spectral`.
 
 Pinning status: every function is pinned by ``tests/test_oracle_pins.py``
 (brute-force DFT, Parseval, closed-form flows, exact rational Taylor
-coefficients, conservation laws, alias-free brute-force convolution, RK order).
+coefficients, conservation laws, alias-free brute-force convolution, RK order),
+``tests/test_oracle_mhd_pins.py``, ``tests/test_oracle_boussinesq_pins.py``
+(exact rational tendency, brute-force scalar convolution, ideal energy
+conservation, internal-wave frequency and RK4 order, exact diffusion) and
+``tests/test_oracle_les_pins.py``.
 """
 
 from .spectral import (  # noqa: F401
@@ -44,4 +50,8 @@ from .spectral import (  # noqa: F401
     mhd_rhs,
     mhd_rk_step,
     mhd_diagnostics,
+    boussinesq_nonlinear,
+    boussinesq_rhs,
+    boussinesq_rk_step,
+    boussinesq_diagnostics,
 )

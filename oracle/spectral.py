@@ -41,6 +41,14 @@ Readings of the paper (each one is repeated where it is used):
      (exp(-eta |k|^2 dt/2) for the magnetic field).
   R9 (diagnostics, not in the paper): Hermitian weight w = 1 on the planes
      kx = 0 and kx = Nx/2, else 2; shells K = floor(|k| + 1/2).
+  R13 (Boussinesq, Eqs. mom, temp, divv; the advection forms are not stated):
+     velocity in rotational form as in R7 with the buoyancy -N theta z_hat
+     added before the projection; scalar advection in divergence form
+     u . grad theta = div(u theta) (equal for divergence-free u), i.e.
+     -i k . F[u theta]; the source N w of Eq. temp uses the vertical velocity
+     of the same state; theta is not forced; Lawson factors
+     exp(-nu |k|^2 dt/2) on u and exp(-kappa |k|^2 dt/2) on theta, the
+     buoyancy coupling is part of the explicit right-hand side.
 """
 
 from __future__ import annotations
@@ -68,6 +76,8 @@ class Config:
     dealias: int = CUBIC
     rk_order: int = 4
     eta: float = 0.0  # magnetic diffusivity (MHD)
+    n_bv: float = 0.0  # Brunt-Vaisala frequency (Boussinesq)
+    kappa: float = 0.0  # scalar diffusivity (Boussinesq)
 
     @property
     def nh(self) -> int:
@@ -297,6 +307,75 @@ def mhd_diagnostics(ub: np.ndarray, cfg: Config, cfl: float = 0.5) -> dict:
     d["magnetic_energy"] = float(np.sum(0.5 * w * np.sum(np.abs(b) ** 2, axis=0)))
     d["cross_helicity"] = float(np.sum(w * np.real(np.sum(np.conj(u) * b, axis=0))))
     d["magnetic_helicity"] = float(np.sum(w * np.real(np.sum(np.conj(a) * b, axis=0))))
+    return d
+
+
+# --------------------------------------------------------------------------
+# Boussinesq (Eqs. mom, temp, divv): state = 4 components (u_x, u_y, u_z, theta)
+# --------------------------------------------------------------------------
+
+def boussinesq_nonlinear(ut: np.ndarray, cfg: Config):
+    """Masked nonlinear terms of the Boussinesq system (reading R13):
+    N_u = D F[u x omega] (the gradient part of the advection is removed by the
+    projection) and N_theta = -D (i k . F[u theta]) = -D F[u . grad theta]."""
+    D = dealias_mask(cfg)
+    u_hat, th_hat = ut[:3] * D, ut[3] * D
+    u = inverse(u_hat, cfg)
+    om = inverse(curl_hat(u_hat, cfg), cfg)
+    th = inverse(th_hat, cfg)
+    n_u = forward(np.cross(u, om, axis=0)) * D
+    g = forward(u * th)  # F[u theta], three components
+    kx, ky, kz = wavenumbers(cfg)
+    n_th = -1j * (kx * g[0] + ky * g[1] + kz * g[2]) * D
+    return n_u, n_th
+
+
+def _bq_nonviscous(ut, cfg: Config, forcing, nonlinear_on=True):
+    """R = (D P(N_u + f - N theta z_hat), D (N_theta + N w)): the right-hand side
+    without the diffusion terms (Eqs. mom, temp with reading R13)."""
+    D = dealias_mask(cfg)
+    u_hat, th_hat = ut[:3] * D, ut[3] * D
+    v = _forcing_or_zero(forcing, cfg, u_hat)
+    v[2] = v[2] - cfg.n_bv * th_hat
+    r_th = cfg.n_bv * u_hat[2]
+    if nonlinear_on:
+        n_u, n_th = boussinesq_nonlinear(ut, cfg)
+        v = v + n_u
+        r_th = r_th + n_th
+    return np.concatenate([project(v, cfg) * D, (r_th * D)[None]])
+
+
+def boussinesq_rhs(ut: np.ndarray, cfg: Config, forcing=None, nonlinear_on: bool = True) -> np.ndarray:
+    """d/dt of (u_hat, theta_hat): D P(N_u + f - N theta z_hat) - nu |k|^2 D u_hat
+    and D (N_theta + N w_hat) - kappa |k|^2 D theta_hat (Eqs. mom, temp, divv)."""
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    D = dealias_mask(cfg)
+    lin = np.concatenate([cfg.nu * k2 * ut[:3] * D, (cfg.kappa * k2 * ut[3] * D)[None]])
+    return _bq_nonviscous(ut, cfg, forcing, nonlinear_on) - lin
+
+
+def boussinesq_rk_step(ut: np.ndarray, dt: float, cfg: Config, forcing=None,
+                       nonlinear_on: bool = True) -> np.ndarray:
+    """One IF-RK step of the Boussinesq system: the Lawson scheme of
+    _lawson_step with E = exp(-nu |k|^2 dt/2) on u and exp(-kappa |k|^2 dt/2)
+    on theta (reading R13)."""
+    kx, ky, kz = wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz + np.zeros(ut.shape[1:])
+    E = np.concatenate([np.broadcast_to(np.exp(-cfg.nu * k2 * dt / 2.0), (3,) + k2.shape),
+                        np.exp(-cfg.kappa * k2 * dt / 2.0)[None]])
+    u = ut * dealias_mask(cfg)
+    return _lawson_step(u, E, lambda v: _bq_nonviscous(v, cfg, forcing, nonlinear_on), dt, cfg.rk_order)
+
+
+def boussinesq_diagnostics(ut: np.ndarray, cfg: Config, cfl: float = 0.5) -> dict:
+    """HD diagnostics of u plus the potential energy 1/2 sum w |theta_hat|^2
+    (reading R9); energy + potential_energy is the quantity Eqs. mom and temp
+    conserve without diffusion, forcing and (by the truncation) aliasing."""
+    d = diagnostics(ut[:3], cfg, cfl)
+    th = ut[3] * dealias_mask(cfg)
+    w = hermitian_weight(cfg)
+    d["potential_energy"] = float(np.sum(0.5 * w * np.abs(th) ** 2))
     return d
 
 

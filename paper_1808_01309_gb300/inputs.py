@@ -153,6 +153,46 @@ def random_solenoidal_field(nx, ny, nz, seed=1, kmax=None, lx=2 * math.pi,
     return f
 
 
+def random_scalar_field(nx, ny, nz, seed=61, kmax=None, lx=2 * math.pi,
+                        ly=2 * math.pi, lz=2 * math.pi, variance=0.5, k_peak=4.0):
+    """Random real scalar (Boussinesq temperature) of shape (1, nz, ny, nx/2+1)
+    with shell spectrum proportional to K^4 exp(-2 (K/k_peak)^2) and
+    1/2 sum w |theta_hat|^2 = variance: a seeded complex normal per stored
+    mode of the cube (stream component 3), Hermitian kx = 0 plane, per-shell
+    rescaling as for the velocity."""
+    if kmax is None:
+        kmax = (cube_halfwidth(nx), cube_halfwidth(ny), cube_halfwidth(nz))
+    nh = nx // 2 + 1
+    p, q, r, iq, ir = _cube_indices(nx, ny, nz, kmax)
+    P, Q, R = np.meshgrid(p, q, r, indexing="ij")
+    P, Q, R = P.transpose(2, 1, 0), Q.transpose(2, 1, 0), R.transpose(2, 1, 0)
+    a = complex_normal(seed, P, Q, R, 3)
+    f = np.zeros((1, nz, ny, nh), dtype=np.complex128)
+    f[0][np.ix_(ir, iq, p)] = np.where((P == 0) & (Q == 0) & (R == 0), 0.0, a)
+    _hermitian_kx0(f)
+    Pf = np.arange(nh).reshape(1, 1, -1)
+    Qf = _signed(ny).reshape(1, -1, 1)
+    Rf = _signed(nz).reshape(-1, 1, 1)
+    kxf, kyf, kzf = _kvec(Pf, Qf, Rf, lx, ly, lz)
+    kmag = np.sqrt(kxf ** 2 + kyf ** 2 + kzf ** 2) + np.zeros((nz, ny, nh))
+    shell = np.floor(kmag + 0.5).astype(np.int64)
+    w = np.full(nh, 2.0)
+    w[0] = 1.0
+    if nx % 2 == 0:
+        w[-1] = 1.0
+    e_mode = 0.5 * w.reshape(1, 1, -1) * np.abs(f[0]) ** 2
+    ns = int(shell.max()) + 1
+    e_shell = np.bincount(shell.ravel(), weights=e_mode.ravel(), minlength=ns)
+    K = np.arange(ns, dtype=np.float64)
+    target = K ** 4 * np.exp(-2.0 * (K / k_peak) ** 2)
+    scale = np.where(e_shell > 0, np.sqrt(target / np.where(e_shell > 0, e_shell, 1.0)), 0.0)
+    f *= scale[shell][None]
+    e_tot = float(np.sum(0.5 * w.reshape(1, 1, -1) * np.abs(f[0]) ** 2))
+    if e_tot > 0:
+        f *= math.sqrt(variance / e_tot)
+    return f
+
+
 def forcing_field(nx, ny, nz, seed=2, kmin=2.0, kmax_shell=3.0, rms=0.25, kmax=None,
                   lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi):
     """Constant-in-time solenoidal forcing on kmin <= |k| <= kmax_shell: every
