@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--mhd-steps", type=int, default=5)
+    ap.add_argument("--boussinesq-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
@@ -373,12 +374,33 @@ def run_ours(args, world, rank, local):
         del ub, fd
         torch.cuda.empty_cache()
 
+    # ---- Boussinesq variant (u and theta: one more field each way) -----------
+    bq = None
+    if args.boussinesq_steps > 0:
+        from paper_1808_01309_gb300 import inputs
+        th = inputs.random_scalar_field(n, n, n, seed=61)
+        ut = torch.from_numpy(np.concatenate([u, th])).to(dev, torch.complex64)
+        del th
+        fd = torch.from_numpy(f).to(dev, torch.complex64)
+        plan = ps.Plan(n, prec=ps.Precision.FP32, eq=ps.Equations.BOUSSINESQ, nu=nu, kappa=nu, n_bv=1.0,
+                       rk_order=4, forcing=fd, stream=stream)
+        msb, _ = time_steps(plan, ut, dt, args.boussinesq_steps, 3, stream, world, ps)
+        msb = reduce_max(msb, world) / args.boussinesq_steps
+        bq = {"ms_per_step": round(msb, 3), "value": round(world * 4 * n ** 3 / (msb * 1e-3) / 1e9, 3),
+              "unit": UNIT, "steps": args.boussinesq_steps, "prec": "fp32",
+              "workload": f"{n}^3 Boussinesq, u seeded as above, theta with the same spectrum shape "
+                          "(seed 61, variance 0.5), N = 1, kappa = nu",
+              "vs_hd_step": round(msb / ms_step, 2)}
+        plan.close()
+        del ut, fd
+        torch.cuda.empty_cache()
+
     ens = None
     if not args.no_ensemble:
         ens = run_ensemble(args, dev, stream)
         torch.cuda.empty_cache()
 
-    out.update(mhd=mhd, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
+    out.update(mhd=mhd, bq=bq, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
                achieved=achieved, achieved_pruned=achieved_pruned, model=model, step_model=step_model,
                kernel_model_gbs=kernel_model_gbs,
                hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
@@ -525,6 +547,7 @@ def main():
         "e2e": res["e2e"],
         "fp64": res["fp64"],
         "mhd": res["mhd"],
+        "boussinesq": res["bq"],
         "ensemble": res["ens"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],

@@ -34,8 +34,8 @@
  * C order [component][kz 0..nz-1][ky 0..ny-1][kx 0..nx/2], kx fastest,
  * ky and kz in FFT order (0..n/2-1, -n/2..-1).  This is the layout of
  * torch.fft.rfftn / numpy.fft.rfftn of a real (nz, ny, nx) array per
- * component.  Components: 3 (u) for PS_HD, 6 (u, B) for PS_MHD.  Field
- * bytes: ncomp * nz * ny * (nx/2+1) * (8 or 16).
+ * component.  Components: 3 (u) for PS_HD, 6 (u, B) for PS_MHD, 4 (u, theta)
+ * for PS_BOUSSINESQ.  Field bytes: ncomp * nz * ny * (nx/2+1) * (8 or 16).
  *
  * Ownership: the caller owns the state, right-hand-side and forcing buffers.
  * The plan owns its scratch (intermediate fields, twiddles, stage registers).
@@ -70,7 +70,7 @@ typedef enum {
 } ps_status;
 
 typedef enum { PS_FP32 = 0, PS_FP64 = 1 } ps_precision;
-typedef enum { PS_HD = 0, PS_MHD = 1 } ps_equations;
+typedef enum { PS_HD = 0, PS_MHD = 1, PS_BOUSSINESQ = 2 } ps_equations;
 typedef enum { PS_DEALIAS_CUBIC = 0, PS_DEALIAS_SPHERICAL = 1, PS_DEALIAS_NONE = 2 } ps_dealias;
 
 typedef struct ps_plan ps_plan;
@@ -81,10 +81,18 @@ typedef struct ps_plan ps_plan;
  *   prec       : arithmetic and storage precision of all fields
  *   eq         : PS_HD, or PS_MHD (Eqs. uMHD, bMHD: the state then has six
  *                components u_x, u_y, u_z, B_x, B_y, B_z; the magnetic
- *                field advances with dB/dt = curl(u x B) - eta |k|^2 B)
+ *                field advances with dB/dt = curl(u x B) - eta |k|^2 B), or
+ *                PS_BOUSSINESQ (Eqs. mom, temp, divv: four components u_x,
+ *                u_y, u_z, theta; du/dt = P(F[u x omega] + f - n_bv theta z)
+ *                - nu |k|^2 u and dtheta/dt = -F[u . grad theta] + n_bv w
+ *                - kappa |k|^2 theta, grad theta taken in spectral space
+ *                before the backward transforms, the scalar integrated
+ *                with the factor exp(-kappa |k|^2 dt/2))
  *   dealias    : truncation rule
  *   rk_order   : 2 or 4
  *   nu         : kinematic viscosity >= 0;  eta: magnetic diffusivity >= 0 (MHD)
+ *   n_bv       : Brunt-Vaisala frequency (Boussinesq, finite, any sign)
+ *   kappa      : scalar diffusivity >= 0 (Boussinesq)
  *   forcing    : device pointer to a constant-in-time forcing of the
  *                velocity (three components, state layout and precision), or
  *                NULL.  Its retained modes are copied at plan creation; later
@@ -98,6 +106,7 @@ typedef struct {
   int rk_order;
   double nu, eta;
   const void* forcing;
+  double n_bv, kappa;
 } ps_config;
 
 /* Global diagnostics of the retained state, accumulated in FP64.
@@ -112,12 +121,14 @@ typedef struct {
  *   MHD only (0 for HD): magnetic_energy = 1/2 sum w |B_hat|^2,
  *   cross_helicity = sum w Re(u_hat* . B_hat), magnetic_helicity =
  *   sum w Re(A_hat* . B_hat) with A_hat = i k x B_hat/|k|^2 (Coulomb gauge);
- *   the velocity entries above describe u only. */
+ *   the velocity entries above describe u only.
+ *   Boussinesq only (0 otherwise): potential_energy = 1/2 sum w |theta_hat|^2. */
 typedef struct {
   double energy, enstrophy, helicity, max_div, max_u, cfl_dt, time;
   double* spectrum;
   int nshells;
   double magnetic_energy, cross_helicity, magnetic_helicity;
+  double potential_energy;
 } ps_diag;
 
 #define PS_NKINDS 7
@@ -184,7 +195,8 @@ enum { PS_HOST_AUTO = 0, PS_HOST_COPY = 1, PS_HOST_MAPPED = 2, PS_HOST_SMCOPY = 
 ps_status ps_rk_step_host(ps_plan* plan, void* uhat_host, double dt, double t, int nsteps);
 ps_status ps_plan_set_host_mode(ps_plan* plan, int mode);
 
-/* Energy (kinetic + magnetic for MHD) and max |u(x)| (FP64) of the state at
+/* Energy (kinetic + magnetic for MHD, + potential 1/2 theta^2 for Boussinesq)
+ * and max |u(x)| (FP64) of the state at
  * the start of the last ps_rk_step.  Synchronises the plan stream. */
 ps_status ps_step_stats(ps_plan* plan, double* energy, double* max_u);
 

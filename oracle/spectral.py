@@ -45,7 +45,9 @@ Readings of the paper (each one is repeated where it is used):
      velocity in rotational form as in R7 with the buoyancy -N theta z_hat
      added before the projection; scalar advection in divergence form
      u . grad theta = div(u theta) (equal for divergence-free u), i.e.
-     -i k . F[u theta]; the source N w of Eq. temp uses the vertical velocity
+     -i k . F[u theta] (the CUDA path forms u . grad theta from the spectral
+     gradient instead: the same Galerkin term, with its FP32 rounding relative
+     to the advection term rather than to u theta); the source N w of Eq. temp uses the vertical velocity
      of the same state; theta is not forced; Lawson factors
      exp(-nu |k|^2 dt/2) on u and exp(-kappa |k|^2 dt/2) on theta, the
      buoyancy coupling is part of the explicit right-hand side.

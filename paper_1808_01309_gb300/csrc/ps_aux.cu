@@ -102,17 +102,20 @@ cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, 
 }
 
 // Spectral diagnostics, one CTA per retained kz plane; row blk of `part`
-// holds [E, Omega, H, max|k.u|, E_B, H_c, H_m, 0, spectrum(0..nshells-1)] of
-// that plane (the magnetic entries only for mhd != 0: B = components 3..5).
+// holds [E, Omega, H, max|k.u|, E_B, H_c, H_m, E_P, spectrum(0..nshells-1)] of
+// that plane (the magnetic entries only for eq = 1 (MHD): B = components
+// 3..5; the potential energy 1/2 w |theta|^2 only for eq = 2 (Boussinesq):
+// theta = component 3).
 template <typename T>
-__global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nshells, int mhd) {
+__global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nshells, int eq) {
+  const int mhd = eq == 1;
   using V = typename cplx<T>::type;
   __shared__ double red[32];
   const int iz = blockIdx.x;
   const int r = iz <= g.Kz ? iz : iz - g.cz;
   const V* up = static_cast<const V*>(u.p);
   double* row = part + (long long)blockIdx.x * (DIAG_HEAD + nshells);
-  double e = 0, om = 0, h = 0, md = 0, eb = 0, hc = 0, hm = 0;
+  double e = 0, om = 0, h = 0, md = 0, eb = 0, hc = 0, hm = 0, ep = 0;
   const int per = g.cy * g.cx;
   for (int i = threadIdx.x; i < per; i += blockDim.x) {
     const int iy = i / g.cx, p = i % g.cx;
@@ -151,6 +154,10 @@ __global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nsh
         hm += w * re / k2;
       }
     }
+    if (eq == 2) {
+      const V t = pm[3 * u.cs];
+      ep += 0.5 * w * ((double)t.x * t.x + (double)t.y * t.y);
+    }
     const int sh = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
     if (sh < nshells) atomicAdd(row + DIAG_HEAD + sh, 0.5 * w * u2);
   }
@@ -161,6 +168,7 @@ __global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nsh
   const double teb = block_sum(eb, red);
   const double thc = block_sum(hc, red);
   const double thm = block_sum(hm, red);
+  const double tep = block_sum(ep, red);
   if (threadIdx.x == 0) {
     row[0] = te;
     row[1] = to;
@@ -169,13 +177,13 @@ __global__ void k_diag_spectral(const Geo g, const Spec u, double* part, int nsh
     row[4] = teb;
     row[5] = thc;
     row[6] = thm;
-    row[7] = 0.0;
+    row[7] = tep;
   }
 }
 
 template <typename T>
-cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int mhd, cudaStream_t s) {
-  k_diag_spectral<T><<<g.cz, 256, 0, s>>>(g, u, part, nshells, mhd);
+cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int eq, cudaStream_t s) {
+  k_diag_spectral<T><<<g.cz, 256, 0, s>>>(g, u, part, nshells, eq);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,8 @@ ps_status cu(cudaError_t e, const char* where) {
   } while (0)
 
 size_t state_bytes(const ps_config& c) {
-  return 3ull * (c.eq == PS_MHD ? 2 : 1) * c.nz * c.ny * (c.nx / 2 + 1) * (c.prec == PS_FP32 ? 8 : 16);
+  const size_t nc = c.eq == PS_MHD ? 6 : c.eq == PS_BOUSSINESQ ? 4 : 3;
+  return nc * c.nz * c.ny * (c.nx / 2 + 1) * (c.prec == PS_FP32 ? 8 : 16);
 }
 
 void drop_graph(ps_ensemble* e) {

@@ -55,8 +55,12 @@ struct PassArgs {
   const void* ifx;   // exp(-nu kx^2 dt/2) for p <= Kx
   const void* ify;   // ... per retained ky index
   const void* ifz;   // ... per retained kz index
-  double dt, nu, eta;
-  int ng;            // 3-component groups: 1 (HD: u) or 2 (MHD: u, B)
+  double dt, nu, eta;  // eta: diffusivity of the second field (MHD: eta, Boussinesq: kappa)
+  int ng;            // 3-component groups: 1 (HD: u; Boussinesq: u) or 2 (MHD: u, B)
+  int nsc;           // scalar components after the groups: 1 (Boussinesq: theta) or 0
+  int nfi;           // fields into the x pass: 6 ng + 3 nsc (u, omega, (B, j,) (grad theta))
+  int nfo;           // fields out of the x pass: 3 ng + nsc (u x omega (+ j x B), (u x B), (u . grad theta))
+  double n_bv;       // Boussinesq: Brunt-Vaisala frequency (the jf* tables hold kappa)
   const void* jfx;   // exp(-eta k^2 dt/2) tables of the magnetic group
   const void* jfy;
   const void* jfz;
@@ -87,10 +91,10 @@ template <typename T>
 cudaError_t launch_forcing_extent(const Geo& g, Spec f, int* ext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_forcing_gather(const Geo& g, Spec f, int Fx, int Fy, int Fz, void* box, cudaStream_t s);
-// Head of one diagnostics row: E, Omega, H, max|k.u|, E_B, H_c, H_m, spare.
+// Head of one diagnostics row: E, Omega, H, max|k.u|, E_B, H_c, H_m, E_P.
 constexpr int DIAG_HEAD = 8;
 template <typename T>
-cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int mhd, cudaStream_t s);
+cudaError_t launch_diag_spectral(const Geo& g, Spec u, double* part, int nshells, int eq, cudaStream_t s);
 cudaError_t launch_diag_final(const double* part, int nblk, int nshells, double* out, cudaStream_t s);
 
 // LES closure (ps_les.cu): -i k_j tau_hat_ij of the model stress of the state

@@ -134,7 +134,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // flight at once; the six transforms then read the tile from shared memory.
 // Thread (line, j0, bb) holds kz indices n = j0 + m N/E.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int NG>
+template <typename T, int N, int NG, int NSC>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
@@ -159,9 +159,13 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   const int cst = NB * g.cz * TX;                 // component stride in the tile
   const V* tb = tile + bb * g.cz * TX + line;     // this thread's column
   double esum = 0.0;
-  // one group of three components at a time: u (and then B for MHD)
+  // one group of three components at a time: u (and then B for MHD); then,
+  // for the Boussinesq system, the scalar theta (one component) whose
+  // gradient i k theta_hat is transformed (three fields)
 #pragma unroll 1
-  for (int grp = 0; grp < NG; ++grp) {
+  for (int grp = 0; grp < NG + NSC; ++grp) {
+  const bool sc = grp >= NG;
+  const int ncs = sc ? 1 : 3, nout = sc ? 3 : 6;
   const V* in = static_cast<const V*>(a.in.p) + 3 * grp * a.in.cs;
   // stage the tile: element (c, b, i, col) <- u_c(kx0 + col, q_b, r_i) at
   // tile[((c NB + b) cz + i) TX + col]; thread tid keeps column tid % TX and
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
         }
       }
       V* dst = tile + (tid / TX) * TX + col;
-      for (; c < 3; dst += RSTEP * TX) {
+      for (; c < ncs; dst += RSTEP * TX) {
         const int iyb = blockIdx.y * NB + b;
         if (iyb < g.cy) {
           const int qb = iyb <= g.Ky ? iyb : iyb - g.cy;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   for (int m = 0; m < E; ++m)
     if (bvalid && kept(g, kx, q, sidx(j0 + m * (N / E), N))) keepm |= 1u << m;
 #pragma unroll 1
-  for (int f = 0; f < 6; ++f) {
+  for (int f = 0; f < nout; ++f) {
     V x[E];
     T ssq = 0;
 #pragma unroll
@@ -220,7 +224,12 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
       V v = czero<V>();
       if ((keepm >> m) & 1u) {
         const V* pm = tb + rowof(r, g.cz) * TX;
-        if (f < 3) {
+        if (sc) {
+          // grad theta: i k_f theta_hat
+          const V t = pm[0];
+          if (f == 0) ssq += t.x * t.x + t.y * t.y;
+          v = cmul_i(cscale(t, f == 0 ? skx : f == 1 ? sky : T(r) * sz));
+        } else if (f < 3) {
           v = pm[f * cst];
           ssq += v.x * v.x + v.y * v.y;
         } else {
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   __syncthreads();  // the tile is restaged for the next group
   }
   if (a.e_part) {
-    // energy 1/2 sum w |u|^2 (+ |B|^2), w = 1 on the kx = 0 plane, else 2
+    // energy 1/2 sum w |u|^2 (+ |B|^2 or theta^2), w = 1 on the kx = 0 plane, else 2
     const double t = block_sum(esum * (kx == 0 ? 0.5 : 1.0), red);
     if (threadIdx.x == 0) a.e_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
@@ -303,14 +312,20 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs 
 // threads holds the points n = j0 + m N/E.  The packed lines of a row are
 // transformed together (line_fft_rows): the inverse lines three at a time, the
 // forward lines of the products together, one exchange for all of them.
+// NG = 2 (MHD): u + i omega and B + i j in, u x omega + j x B and u x B out.
+// NSC = 1 (Boussinesq): u + i omega and grad theta in, u x omega and
+// u . grad theta out.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int NG>
-__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ? MinB<T, N>::xpass : 1)
+template <typename T, int N, int NG, int NSC>
+__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v),
+                                  NG == 1 && NSC == 0 ? MinB<T, N>::xpass : 1)
     k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v, G = N / E;
-  constexpr int NF = 6 * NG;  // input fields: u, omega (, B, j)
-  constexpr int NFW = NG == 1 ? 2 : 3;  // forward packed lines
+  constexpr int NF = 6 * NG + 3 * NSC;  // input fields: u, omega (, B, j) (, grad theta)
+  constexpr int NLI = 3 * NG + 2 * NSC;  // inverse packed lines
+  constexpr bool HD = NG == 1 && NSC == 0;
+  constexpr int NFW = NG == 2 ? 3 : 2;  // forward packed lines
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ __align__(8) uint64_t bar[1];
@@ -385,13 +400,17 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
     const long long row = it * rpc + rl;
     const bool rvalid = row < rows;
     const V* st = stage + rl * kxp;
-    // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c
-    V U[3 * NG][E];
+    // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c; for
+    // the Boussinesq system d_x theta + i d_y theta and d_z theta + i 0
+    V U[NLI][E];
 #pragma unroll
-    for (int c = 0; c < 3 * NG; ++c) {
-      const int fr = (c < 3) ? c : 6 + (c - 3);  // real part field
+    for (int c = 0; c < NLI; ++c) {
+      const bool scl = NSC && c == 4;  // the unpaired line
+      // real and imaginary part fields
+      const int fr = c < 3 ? c : NSC ? (c == 3 ? 6 : 8) : 6 + (c - 3);
+      const int fi = c < 3 ? c + 3 : NSC ? (c == 3 ? 7 : 8) : 9 + (c - 3);
       const V* pu = st + fr * rpc * kxp;
-      const V* pw = st + (fr + 3) * rpc * kxp;
+      const V* pw = st + fi * rpc * kxp;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int n = j0 + m * (N / E);
@@ -406,7 +425,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
             X = cconj(X);
             W = cconj(W);
           }
-          v = mk<V>(X.x - W.y, X.y + W.x);
+          v = scl ? X : mk<V>(X.x - W.y, X.y + W.x);
         }
         U[c][m] = v;
       }
@@ -417,8 +436,28 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
       fence_proxy_async();
       issue(nxt);
     }
-    if constexpr (NG == 1) {
+    if constexpr (HD) {
       line_fft_rows<N, E, +1>(U, j0, tw, ex);
+    } else if constexpr (NSC == 1) {
+      V L[3][E], S[2][E];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) L[c][m] = U[c][m];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) S[c][m] = U[3 + c][m];
+      line_fft_rows<N, E, +1>(L, j0, tw, ex);
+      line_fft_rows<N, E, +1>(S, j0, tw, ex);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) U[c][m] = L[c][m];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) U[3 + c][m] = S[c][m];
     } else {
 #pragma unroll
       for (int h = 0; h < NG; ++h) {
@@ -442,9 +481,14 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
       const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
       umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
       T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
-      if constexpr (NG == 1) {
+      if constexpr (HD) {
         F[0][m] = mk<V>(nx, ny);
         F[1][m] = mk<V>(nz, T(0));
+      } else if constexpr (NSC == 1) {
+        // u . grad theta
+        const T adv = ux * U[3][m].x + uy * U[3][m].y + uz * U[4][m].x;
+        F[0][m] = mk<V>(nx, ny);
+        F[1][m] = mk<V>(nz, adv);
       } else {
         const T bx = U[3][m].x, by = U[4][m].x, bz = U[5][m].x;
         const T jx = U[3][m].y, jy = U[4][m].y, jz = U[5][m].y;
@@ -464,7 +508,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v), NG == 1 ?
       // split each packed transform F = DFT(a) + i DFT(b) of two real fields
       // with its mirrored entry F[N-k] (all split lines through one exchange);
       // for HD the second line has b = 0
-      constexpr int NSP = NG == 1 ? 1 : NFW;  // lines that need the split
+      constexpr int NSP = HD ? 1 : NFW;  // lines that need the split
 #pragma unroll
       for (int w = 0; w < NSP; ++w)
 #pragma unroll
@@ -579,17 +623,21 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs 
 
 // ---------------------------------------------------------------------------
 // update: per mode, from the compact transformed nonlinear term Nh (a6)
-//   velocity group: v = P(Nh + f + closure), P = I - k k^T/|k|^2, v(0) = 0
+//   velocity group: v = P(Nh + f + closure - n_bv theta z), P = I - k k^T/|k|^2,
+//                   v(0) = 0 (the buoyancy term only for the Boussinesq system)
 //   magnetic group: v = i k x Nh  (the curl of u x B)
-// then the selected output (ZfwdMode): the right-hand side v - damp |k|^2 u, or
-// a Lawson RK stage update of the compact stage buffers / the caller's state.
+//   scalar:         v = -Nh(u . grad theta) + n_bv w  (Boussinesq)
+// with theta and w of the stage input; then the selected output (ZfwdMode):
+// the right-hand side v - damp |k|^2 u, or a Lawson RK stage update of the
+// compact stage buffers / the caller's state.
 // full != 0: one thread per mode of the caller's layout (modes outside the
 // retained set are written as zero); otherwise one thread per retained mode.
 // Consecutive threads take consecutive kx: every access is a contiguous row.
 // ---------------------------------------------------------------------------
-template <typename T, int NG>
+template <typename T, int NG, int NSC>
 __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full) {
   using V = typename cplx<T>::type;
+  constexpr int NC = 3 * NG + NSC;  // state components
   const Geo& g = a.g;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int kx, q, r;
@@ -614,7 +662,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     if (full) {
       V* po = static_cast<V*>(a.out_full) + orow * g.nh + kx;
 #pragma unroll
-      for (int c = 0; c < 3 * NG; ++c) po[c * fcs] = czero<V>();
+      for (int c = 0; c < NC; ++c) po[c * fcs] = czero<V>();
     }
     return;
   }
@@ -625,72 +673,91 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
   const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
   const T dt = T(a.dt);
   const V* nh = static_cast<const V*>(a.a6);
+  V w_s = czero<V>(), th_s = czero<V>();  // Boussinesq: w and theta of the stage input
+  if constexpr (NSC == 1) {
+    const V* pi = static_cast<const V*>(a.in.p) + (long long)rowof(r, a.in.zwrap) * a.in.zs +
+                  (long long)rowof(q, a.in.ywrap) * a.in.ys + kx;
+    w_s = ldv(pi + 2 * a.in.cs);
+    th_s = ldv(pi + 3 * a.in.cs);
+  }
 #pragma unroll
-  for (int grp = 0; grp < NG; ++grp) {
-    const bool mag = grp == 1;
+  for (int grp = 0; grp < NG + NSC; ++grp) {
+    const bool scl = NSC == 1 && grp == NG;  // the scalar (one component)
+    const bool mag = NG == 2 && grp == 1;
     const int c0 = 3 * grp;
-    V v0 = ldv(nh + (c0 + 0) * ccs + ci), v1 = ldv(nh + (c0 + 1) * ccs + ci), v2 = ldv(nh + (c0 + 2) * ccs + ci);
-    if (!mag) {
-      if (a.extra) {  // closure term (LES), compact layout
-        const V* ex0 = static_cast<const V*>(a.extra) + ci;
-        v0 = cadd(v0, ldv(ex0));
-        v1 = cadd(v1, ldv(ex0 + ccs));
-        v2 = cadd(v2, ldv(ex0 + 2 * ccs));
-      }
-      const V* fb = static_cast<const V*>(a.fbox);
-      if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
-        const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
-        const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
-        const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
-        v0 = cadd(v0, ldv(fb + fo));
-        v1 = cadd(v1, ldv(fb + fo + fcs2));
-        v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
-      }
-      if (k2 > T(0)) {
-        // Leray projection v - k (k.v)/|k|^2
-        const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
-        const T ik2 = T(1) / k2;
-        v0 = csub(v0, cscale(kd, kxv * ik2));
-        v1 = csub(v1, cscale(kd, kyv * ik2));
-        v2 = csub(v2, cscale(kd, kzv * ik2));
-      } else {
-        v0 = v1 = v2 = czero<V>();
-      }
+    const int nc = scl ? 1 : 3;
+    V kk[3];
+    if (scl) {
+      kk[0] = csub(cscale(w_s, T(a.n_bv)), ldv(nh + 3 * ccs + ci));
+      kk[1] = kk[2] = czero<V>();
     } else {
-      // curl(u x B): i k x v
-      const V w0 = cmul_i(csub(cscale(v2, kyv), cscale(v1, kzv)));
-      const V w1 = cmul_i(csub(cscale(v0, kzv), cscale(v2, kxv)));
-      const V w2 = cmul_i(csub(cscale(v1, kxv), cscale(v0, kyv)));
-      v0 = w0;
-      v1 = w1;
-      v2 = w2;
+      V v0 = ldv(nh + (c0 + 0) * ccs + ci), v1 = ldv(nh + (c0 + 1) * ccs + ci), v2 = ldv(nh + (c0 + 2) * ccs + ci);
+      if (!mag) {
+        if (a.extra) {  // closure term (LES), compact layout
+          const V* ex0 = static_cast<const V*>(a.extra) + ci;
+          v0 = cadd(v0, ldv(ex0));
+          v1 = cadd(v1, ldv(ex0 + ccs));
+          v2 = cadd(v2, ldv(ex0 + 2 * ccs));
+        }
+        const V* fb = static_cast<const V*>(a.fbox);
+        if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
+          const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
+          const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
+          const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
+          v0 = cadd(v0, ldv(fb + fo));
+          v1 = cadd(v1, ldv(fb + fo + fcs2));
+          v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
+        }
+        if constexpr (NSC == 1) v2 = csub(v2, cscale(th_s, T(a.n_bv)));  // buoyancy -N theta z
+        if (k2 > T(0)) {
+          // Leray projection v - k (k.v)/|k|^2
+          const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
+          const T ik2 = T(1) / k2;
+          v0 = csub(v0, cscale(kd, kxv * ik2));
+          v1 = csub(v1, cscale(kd, kyv * ik2));
+          v2 = csub(v2, cscale(kd, kzv * ik2));
+        } else {
+          v0 = v1 = v2 = czero<V>();
+        }
+      } else {
+        // curl(u x B): i k x v
+        const V w0 = cmul_i(csub(cscale(v2, kyv), cscale(v1, kzv)));
+        const V w1 = cmul_i(csub(cscale(v0, kzv), cscale(v2, kxv)));
+        const V w2 = cmul_i(csub(cscale(v1, kxv), cscale(v0, kyv)));
+        v0 = w0;
+        v1 = w1;
+        v2 = w2;
+      }
+      kk[0] = v0;
+      kk[1] = v1;
+      kk[2] = v2;
     }
-    const V kk[3] = {v0, v1, v2};
     const V* pu = static_cast<const V*>(a.u_n.p) + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
                   (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
     V* po = static_cast<V*>(a.out_full) + c0 * fcs + orow * g.nh + kx;
+    const bool second = mag || scl;  // diffusivity and factor tables of the second field
     if (a.mode == ZF_RHS) {
-      const T vk = T(mag ? a.eta : a.nu) * k2;
+      const T vk = T(second ? a.eta : a.nu) * k2;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) po[c * fcs] = csub(kk[c], cscale(ldv(pu + c * a.u_n.cs), vk));
+      for (int c = 0; c < nc; ++c) po[c * fcs] = csub(kk[c], cscale(ldv(pu + c * a.u_n.cs), vk));
       continue;
     }
     // Lawson RK with E = exp(-damp |k|^2 dt/2) = ex(p) ey(q) ez(r)
-    const T* ifx = static_cast<const T*>(mag ? a.jfx : a.ifx);
-    const T* ify = static_cast<const T*>(mag ? a.jfy : a.ify);
-    const T* ifz = static_cast<const T*>(mag ? a.jfz : a.ifz);
+    const T* ifx = static_cast<const T*>(second ? a.jfx : a.ifx);
+    const T* ify = static_cast<const T*>(second ? a.jfy : a.ify);
+    const T* ifz = static_cast<const T*>(second ? a.jfz : a.ifz);
     const T Ef = __ldg(ifx + kx) * __ldg(ify + iy) * __ldg(ifz + iz);
     const T E2 = Ef * Ef;
     V* acc = static_cast<V*>(a.acc) + c0 * ccs + ci;
     V* nxt = static_cast<V*>(a.nxt) + c0 * ccs + ci;
     V u[3], ac[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < nc; ++c) {
       u[c] = ldv(pu + c * a.u_n.cs);
       ac[c] = (a.mode == ZF_RK4_1 || a.mode == ZF_RK2_1) ? czero<V>() : acc[c * ccs];
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < nc; ++c) {
       const V k = kk[c];
       switch (a.mode) {
         case ZF_RK4_1:  // acc = E^2 k1 ; next = E (u + dt/2 k1)
@@ -733,21 +800,22 @@ static cudaError_t prep(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename T, int N, int NG>
+template <typename T, int N, int NG, int NSC>
 cudaError_t zinv_ng(const PassArgs& a, cudaStream_t s, int* nb) {
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   const size_t smem = (1ull * NB * N * TX + 3ull * NB * a.g.cz * TX) * sizeof(V);
-  cudaError_t e = prep(k_zinv<T, N, NG>, smem);
+  cudaError_t e = prep(k_zinv<T, N, NG, NSC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB);
   if (nb) *nb = grid.x * grid.y;
-  k_zinv<T, N, NG><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  k_zinv<T, N, NG, NSC><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int N>
 cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
-  return a.ng == 2 ? zinv_ng<T, N, 2>(a, s, nb) : zinv_ng<T, N, 1>(a, s, nb);
+  if (a.ng == 2) return zinv_ng<T, N, 2, 0>(a, s, nb);
+  return a.nsc ? zinv_ng<T, N, 1, 1>(a, s, nb) : zinv_ng<T, N, 1, 0>(a, s, nb);
 }
 template <typename T, int N>
 cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
@@ -756,47 +824,49 @@ cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yinv<T, N>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 6 * a.ng);
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfi);
   k_yinv<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
 // Shared memory of the x pass for rpc rows: one input stage of 6 ng rows, the
 // exchange region (XLINES lines per row) and, when used, the twiddle table.
 template <typename T, int N>
-size_t xpass_smem(const Geo& g, int rpc, int ng) {
+size_t xpass_smem(const Geo& g, int rpc, int nf) {
   using V = typename cplx<T>::type;
   constexpr int E = EOf<T, N>::v;
   const size_t tt = (!XTwReg<T, N>::v && XTwTable<T, N>::v) ? (size_t)TwSlots<N, E>::total * (N / E) : 0;
-  return (6ull * ng * rpc * g.kxp + (size_t)XLINES * rpc * N + tt) * sizeof(V);
+  return ((size_t)nf * rpc * g.kxp + (size_t)XLINES * rpc * N + tt) * sizeof(V);
 }
 
-template <typename T, int N, int NG>
+template <typename T, int N, int NG, int NSC>
 cudaError_t xpass_ng(const PassArgs& a, cudaStream_t s) {
+  constexpr int NF = 6 * NG + 3 * NSC;
   constexpr int E = EOf<T, N>::v, G = N / E;
   // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
   int rpc = RPCOf<T, N>::v;
-  while (rpc > 1 && xpass_smem<T, N>(a.g, rpc, NG) > 113 * 1024) rpc /= 2;
+  while (rpc > 1 && xpass_smem<T, N>(a.g, rpc, NF) > 113 * 1024) rpc /= 2;
   if (a.xrpc > 0 && a.xrpc < rpc) rpc = a.xrpc;  // tuned (smaller) row groups
-  const size_t smem = xpass_smem<T, N>(a.g, rpc, NG);
-  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = xpass_smem<T, N>(a.g, rpc, NF);
+  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N, NG, NSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, N, NG>, rpc * G, smem)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, N, NG, NSC>, rpc * G, smem)) !=
       cudaSuccess)
     return e;
   const long long rows = (long long)a.g.nz * a.g.ny;
   const long long groups = (rows + rpc - 1) / rpc;
   long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > groups) grid = groups;
-  k_xpass<T, N, NG><<<(unsigned)grid, rpc * G, smem, s>>>(a, rpc);
+  k_xpass<T, N, NG, NSC><<<(unsigned)grid, rpc * G, smem, s>>>(a, rpc);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
-  return a.ng == 2 ? xpass_ng<T, N, 2>(a, s) : xpass_ng<T, N, 1>(a, s);
+  if (a.ng == 2) return xpass_ng<T, N, 2, 0>(a, s);
+  return a.nsc ? xpass_ng<T, N, 1, 1>(a, s) : xpass_ng<T, N, 1, 0>(a, s);
 }
 
 template <typename T, int N>
@@ -806,7 +876,7 @@ cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, 3 * a.ng);
+  dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfo);
   k_yfwd<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -817,7 +887,7 @@ cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_zfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB, 3 * a.ng);
+  dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB, a.nfo);
   k_zfwd<T, N><<<grid, ColThreads<T, N, 2>::v, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -826,8 +896,9 @@ cudaError_t update_launch(const PassArgs& a, cudaStream_t s) {
   const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
   const long long n = full ? (long long)a.g.nz * a.g.ny * a.g.nh : (long long)a.g.cz * a.g.cy * a.g.cx;
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  if (a.ng == 2) k_update<T, 2><<<blocks, 256, 0, s>>>(a, full);
-  else k_update<T, 1><<<blocks, 256, 0, s>>>(a, full);
+  if (a.ng == 2) k_update<T, 2, 0><<<blocks, 256, 0, s>>>(a, full);
+  else if (a.nsc) k_update<T, 1, 1><<<blocks, 256, 0, s>>>(a, full);
+  else k_update<T, 1, 0><<<blocks, 256, 0, s>>>(a, full);
   return cudaGetLastError();
 }
 

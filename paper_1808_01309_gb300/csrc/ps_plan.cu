@@ -51,9 +51,12 @@ ps_status validate(const ps_config* c) {
   if (!(std::isfinite(c->lx) && std::isfinite(c->ly) && std::isfinite(c->lz) && c->lx > 0 && c->ly > 0 && c->lz > 0))
     return fail(PS_ERR_INVALID_ARG, "box lengths must be finite and positive");
   if (c->prec != PS_FP32 && c->prec != PS_FP64) return fail(PS_ERR_INVALID_ARG, "unknown precision");
-  if (c->eq != PS_HD && c->eq != PS_MHD) return fail(PS_ERR_INVALID_ARG, "unknown equation set");
+  if (c->eq != PS_HD && c->eq != PS_MHD && c->eq != PS_BOUSSINESQ)
+    return fail(PS_ERR_INVALID_ARG, "unknown equation set");
   if (c->eq == PS_MHD && !(std::isfinite(c->eta) && c->eta >= 0))
     return fail(PS_ERR_INVALID_ARG, "eta must be finite and >= 0");
+  if (c->eq == PS_BOUSSINESQ && !(std::isfinite(c->kappa) && c->kappa >= 0 && std::isfinite(c->n_bv)))
+    return fail(PS_ERR_INVALID_ARG, "kappa must be finite and >= 0, n_bv finite");
   if (c->dealias != PS_DEALIAS_CUBIC && c->dealias != PS_DEALIAS_SPHERICAL && c->dealias != PS_DEALIAS_NONE)
     return fail(PS_ERR_INVALID_ARG, "unknown dealias rule");
   if (c->rk_order != 2 && c->rk_order != 4) return fail(PS_ERR_INVALID_ARG, "rk_order must be 2 or 4");
@@ -89,21 +92,33 @@ struct Sizes {
   size_t state;    // caller-layout field (elements)
 };
 
-// ng = number of 3-component groups (1: HD velocity; 2: MHD velocity and field)
-Sizes sizes(const Geo& g, ps_precision p, int ng) {
+// Field counts of an equation set: ng 3-component groups with a curl (HD: u;
+// MHD: u, B), nsc scalars (Boussinesq: theta), ncomp state components, nfi
+// fields into the x pass (u, omega, (B, j,) (grad theta)) and nfo out of it
+// (u x omega (+ j x B), (u x B), (u . grad theta)).
+struct Counts {
+  int ng, nsc, ncomp, nfi, nfo;
+};
+Counts counts_of(const ps_config* c) {
+  if (c->eq == PS_MHD) return {2, 0, 6, 12, 6};
+  if (c->eq == PS_BOUSSINESQ) return {1, 1, 4, 9, 4};
+  return {1, 0, 3, 6, 3};
+}
+
+Sizes sizes(const Geo& g, ps_precision p, const Counts& n) {
   Sizes s{};
   s.vb = p == PS_FP32 ? 8 : 16;
   const size_t kxp = g.kxp;
-  const size_t a1 = 6ull * ng * g.nz * g.cy * kxp, a2 = 3ull * ng * g.nz * g.ny * kxp;
-  const size_t b1 = 6ull * ng * g.nz * g.ny * kxp, b2 = 3ull * ng * g.nz * g.cy * kxp;
+  // a6: z-inverse out [nfi][nz][cy], x-pass out [nfo][nz][ny], z-forward out [nfo][cz][cy]
+  const size_t a1 = (size_t)n.nfi * g.nz * g.cy * kxp, a2 = (size_t)n.nfo * g.nz * g.ny * kxp;
+  // b6: y-inverse out [nfi][nz][ny], y-forward out [nfo][nz][cy]
+  const size_t b1 = (size_t)n.nfi * g.nz * g.ny * kxp, b2 = (size_t)n.nfo * g.nz * g.cy * kxp;
   s.a6 = a1 > a2 ? a1 : a2;
   s.b6 = b1 > b2 ? b1 : b2;
-  s.cmp = 3ull * ng * g.cz * g.cy * kxp;
-  s.state = 3ull * ng * g.nz * g.ny * g.nh;
+  s.cmp = (size_t)n.ncomp * g.cz * g.cy * kxp;
+  s.state = (size_t)n.ncomp * g.nz * g.ny * g.nh;
   return s;
 }
-
-int groups_of(const ps_config* c) { return c->eq == PS_MHD ? 2 : 1; }
 
 int nshells_of(const Geo& g) {
   const double kx = g.Kx * g.sx, ky = g.Ky * g.sy, kz = g.Kz * g.sz;
@@ -131,7 +146,8 @@ struct ps_plan {
   bool les_on = false;
   ps::LesScratch les{};
   void* les_mem[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  int ng = 1;    // 3-component groups: 1 HD, 2 MHD
+  int ng = 1;    // 3-component groups: 1 HD and Boussinesq, 2 MHD
+  Counts cn{1, 0, 3, 6, 3};
   Geo g{};
   Sizes sz{};
   void* a6 = nullptr;
@@ -278,7 +294,11 @@ PassArgs base_args(ps_plan* p) {
   a.jfy = static_cast<char*>(p->iftab) + half + tb * p->g.cx;
   a.jfz = static_cast<char*>(p->iftab) + half + tb * (p->g.cx + p->g.cy);
   a.ng = p->ng;
-  a.eta = p->cfg.eta;
+  a.nsc = p->cn.nsc;
+  a.nfi = p->cn.nfi;
+  a.nfo = p->cn.nfo;
+  a.n_bv = p->cfg.eq == PS_BOUSSINESQ ? p->cfg.n_bv : 0.0;
+  a.eta = p->cfg.eq == PS_BOUSSINESQ ? p->cfg.kappa : p->cfg.eta;
   a.nxt = p->nxt;
   a.acc = p->acc;
   a.err = p->err;
@@ -346,9 +366,10 @@ ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
     if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, p->cfg.nu, dt, p->iftab, p->stream); },
                     "integrating-factor tables")) != PS_OK)
       return s;
-    if (p->ng == 2) {
+    if (p->ng == 2 || p->cn.nsc) {
       void* jt = static_cast<char*>(p->iftab) + sizeof(T) * (p->g.cx + p->g.cy + p->g.cz);
-      if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, p->cfg.eta, dt, jt, p->stream); },
+      const double d2 = p->cfg.eq == PS_BOUSSINESQ ? p->cfg.kappa : p->cfg.eta;
+      if ((s = launch(p, 5, [&] { return launch_if_tables<T>(p->g, d2, dt, jt, p->stream); },
                       "integrating-factor tables")) != PS_OK)
         return s;
     }
@@ -377,7 +398,7 @@ ps_status do_diag(ps_plan* p, const void* uhat, double* host_out) {
   PS_CU(cudaMemsetAsync(p->dpart, 0, sizeof(double) * (size_t)p->g.cz * w, p->stream), "diag reset");
   PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "diag reset");
   const Spec u = caller_spec(p->g, uhat);
-  if ((s = launch(p, 5, [&] { return launch_diag_spectral<T>(p->g, u, p->dpart, p->nshells, p->ng == 2, p->stream); },
+  if ((s = launch(p, 5, [&] { return launch_diag_spectral<T>(p->g, u, p->dpart, p->nshells, (int)p->cfg.eq, p->stream); },
                   "spectral diagnostics")) != PS_OK)
     return s;
   if ((s = launch(p, 5, [&] { return launch_diag_final(p->dpart, p->g.cz, p->nshells, p->dout, p->stream); },
@@ -505,7 +526,7 @@ ps_status ps_plan_workspace_bytes(const ps_config* cfg, size_t* bytes) {
   if (s != PS_OK) return s;
   if (!bytes) return fail(PS_ERR_INVALID_ARG, "bytes is NULL");
   const Geo g = make_geo(cfg);
-  const Sizes z = sizes(g, cfg->prec, groups_of(cfg));
+  const Sizes z = sizes(g, cfg->prec, counts_of(cfg));
   const size_t tb = cfg->prec == PS_FP32 ? 4 : 8;
   *bytes = z.vb * (z.a6 + z.b6 + 2 * z.cmp + (size_t)(g.nx + g.ny + g.nz)) + 2 * tb * (g.cx + g.cy + g.cz) +
            sizeof(double) * (size_t)(g.cz * (g.kxp + DIAG_HEAD + nshells_of(g)) + 16);
@@ -522,8 +543,9 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   p->cfg = *cfg;
   p->stream = static_cast<cudaStream_t>(cuda_stream);
   p->g = make_geo(cfg);
-  p->ng = groups_of(cfg);
-  p->sz = sizes(p->g, cfg->prec, p->ng);
+  p->cn = counts_of(cfg);
+  p->ng = p->cn.ng;
+  p->sz = sizes(p->g, cfg->prec, p->cn);
   p->nshells = nshells_of(p->g);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
@@ -625,7 +647,7 @@ cudaError_t zero_outside_cube(ps_plan* p, char* host) {
   const ps::Geo& g = p->g;
   const size_t vb = p->sz.vb, row = (size_t)g.nh * vb, plane = (size_t)g.ny * row;
   const size_t fcs = (size_t)g.nz * plane;
-  const int nc = 3 * p->ng;
+  const int nc = p->cn.ncomp;
   cudaStream_t st = p->side;
   const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
   cudaError_t e = cudaSuccess;
@@ -769,7 +791,7 @@ ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int 
     PS_CU(cudaStreamWaitEvent(p->side, p->side_go, 0), "side event");
     PS_CU(zero_outside_cube(p, static_cast<char*>(uhat_host)), "zero fill of the masked modes");
     PS_CU(cudaEventRecord(p->side_done, p->side), "side event");
-    PS_CU(ps::launch_copy_cube(mapped, p->hstate, p->g, 3 * p->ng, p->sz.vb, nsm, p->stream), "state upload");
+    PS_CU(ps::launch_copy_cube(mapped, p->hstate, p->g, p->cn.ncomp, p->sz.vb, nsm, p->stream), "state upload");
     p->launches++;
   } else if (mapped) {
     PS_CU(ps::launch_stream_copy(mapped, p->hstate, bytes, nsm, p->stream), "state upload");
@@ -785,7 +807,7 @@ ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int 
     }
   }
   if (cube) {
-    PS_CU(ps::launch_copy_cube(p->hstate, mapped, p->g, 3 * p->ng, p->sz.vb, nsm, p->stream), "state download");
+    PS_CU(ps::launch_copy_cube(p->hstate, mapped, p->g, p->cn.ncomp, p->sz.vb, nsm, p->stream), "state download");
     p->launches++;
     PS_CU(cudaStreamWaitEvent(p->stream, p->side_done, 0), "side event");
   } else if (mapped) {
@@ -830,6 +852,7 @@ ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out)
   out->magnetic_energy = h[4];
   out->cross_helicity = h[5];
   out->magnetic_helicity = h[6];
+  out->potential_energy = h[7];
   const double dmin = std::fmin(p->cfg.lx / p->cfg.nx, std::fmin(p->cfg.ly / p->cfg.ny, p->cfg.lz / p->cfg.nz));
   out->cfl_dt = out->max_u > 0 ? cfl * dmin / out->max_u : INFINITY;
   out->time = p->time;
@@ -878,7 +901,7 @@ ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* nor
   for (int i = 0; i < 12; ++i)
     if (!std::isfinite(norm12[i]) || (i >= 5 && !(norm12[i] > 0)))
       return fail(PS_ERR_INVALID_ARG, "normalisation: finite values, positive std, s_tau and s_A required");
-  if (p->cfg.prec != PS_FP32 || p->ng != 1 || p->cfg.dealias == PS_DEALIAS_SPHERICAL)
+  if (p->cfg.prec != PS_FP32 || p->cfg.eq != PS_HD || p->cfg.dealias == PS_DEALIAS_SPHERICAL)
     return fail(PS_ERR_UNSUPPORTED, "the LES closure needs an FP32 HD plan with the cubic or no truncation");
   const auto les_n = [](int n) { return n >= 16 && n <= 512 && (n % 16 == 0) && ((n & (n - 1)) == 0 || n % 48 == 0); };
   if (!les_n(p->g.nx) || !les_n(p->g.ny) || !les_n(p->g.nz))

@@ -148,6 +148,9 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   a.tw_z = tw + g.nx + g.ny;
   a.nu = c->nu;
   a.ng = 1;  // velocity only (HD)
+  a.nsc = 0;
+  a.nfi = 6;
+  a.nfo = 3;
   a.err = reinterpret_cast<int*>(p + a_b + b_b + tw_b + box_b);
   a.Fx = a.Fy = a.Fz = -1;
   Spec in;
@@ -197,7 +200,7 @@ extern "C" ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, con
         cfg->ly > 0 && cfg->lz > 0))
     return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: box lengths must be finite and positive");
   if (cfg->prec != PS_FP32 && cfg->prec != PS_FP64) return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: precision");
-  if (cfg->eq != PS_HD) return bad(cfg->eq == PS_MHD ? PS_ERR_UNSUPPORTED : PS_ERR_INVALID_ARG,
+  if (cfg->eq != PS_HD) return bad(cfg->eq == PS_MHD || cfg->eq == PS_BOUSSINESQ ? PS_ERR_UNSUPPORTED : PS_ERR_INVALID_ARG,
                                    "ps_rhs_noalloc: only the HD equations are implemented");
   if (cfg->dealias != PS_DEALIAS_CUBIC && cfg->dealias != PS_DEALIAS_SPHERICAL && cfg->dealias != PS_DEALIAS_NONE)
     return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: unknown dealias rule");

@@ -30,6 +30,7 @@ class Precision(enum.IntEnum):
 class Equations(enum.IntEnum):
     HD = 0
     MHD = 1
+    BOUSSINESQ = 2
 
 
 class Dealias(enum.IntEnum):
@@ -69,6 +70,7 @@ class PsConfig(ctypes.Structure):
         ("rk_order", ctypes.c_int),
         ("nu", ctypes.c_double), ("eta", ctypes.c_double),
         ("forcing", ctypes.c_void_p),
+        ("n_bv", ctypes.c_double), ("kappa", ctypes.c_double),
     ]
 
 
@@ -80,6 +82,7 @@ class PsDiag(ctypes.Structure):
         ("spectrum", ctypes.POINTER(ctypes.c_double)), ("nshells", ctypes.c_int),
         ("magnetic_energy", ctypes.c_double), ("cross_helicity", ctypes.c_double),
         ("magnetic_helicity", ctypes.c_double),
+        ("potential_energy", ctypes.c_double),
     ]
 
 
@@ -158,14 +161,14 @@ def _check(status: int) -> None:
 
 def make_config(nx, ny=None, nz=None, *, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi,
                 prec=Precision.FP32, eq=Equations.HD, dealias=Dealias.CUBIC, rk_order=4,
-                nu=0.0, eta=0.0, forcing=None) -> PsConfig:
+                nu=0.0, eta=0.0, forcing=None, n_bv=0.0, kappa=0.0) -> PsConfig:
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     fptr = None
     if forcing is not None:
         fptr = forcing.data_ptr() if hasattr(forcing, "data_ptr") else int(forcing)
     return PsConfig(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz), int(prec), int(eq),
-                    int(dealias), int(rk_order), float(nu), float(eta), fptr)
+                    int(dealias), int(rk_order), float(nu), float(eta), fptr, float(n_bv), float(kappa))
 
 
 def _ptr(t) -> int:
@@ -239,6 +242,7 @@ def ps_diagnostics(plan, uhat, cfl: float = 0.5, nshells: int = 4096) -> dict:
     out = dict(energy=d.energy, enstrophy=d.enstrophy, helicity=d.helicity, max_div=d.max_div,
                max_u=d.max_u, cfl_dt=d.cfl_dt, time=d.time, magnetic_energy=d.magnetic_energy,
                cross_helicity=d.cross_helicity, magnetic_helicity=d.magnetic_helicity,
+               potential_energy=d.potential_energy,
                spectrum=[spec[i] for i in range(min(d.nshells, nshells))], status=st)
     if st not in (PS_OK, PS_ERR_NONFINITE):
         _check(st)
@@ -370,7 +374,8 @@ class Plan:
     @property
     def shape(self):
         c = self.cfg
-        return (6 if c.eq == Equations.MHD else 3, c.nz, c.ny, c.nx // 2 + 1)
+        nc = {Equations.MHD: 6, Equations.BOUSSINESQ: 4}.get(Equations(c.eq), 3)
+        return (nc, c.nz, c.ny, c.nx // 2 + 1)
 
     def _check_field(self, t):
         import torch

@@ -70,6 +70,24 @@ def test_mhd_rejects_negative_diffusivity(ps):
     assert e.value.status == ps.PS_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("bad", [dict(kappa=-1.0), dict(kappa=math.nan), dict(n_bv=math.inf), dict(eq=3)])
+def test_boussinesq_rejects_bad_parameters(ps, bad):
+    kw = dict(eq=ps.Equations.BOUSSINESQ, kappa=1e-3, n_bv=1.0)
+    kw.update(bad)
+    cfg = ps.make_config(32, **kw)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_plan_create(cfg)
+    assert e.value.status == ps.PS_ERR_INVALID_ARG
+
+
+def test_boussinesq_workspace_holds_the_scalar_fields(ps):
+    # 9 fields into the x pass instead of 6 (u, omega, grad theta), 4 out
+    # instead of 3, 4-component stage buffers
+    hd = ps.ps_plan_workspace_bytes(ps.make_config(128))
+    bq = ps.ps_plan_workspace_bytes(ps.make_config(128, eq=ps.Equations.BOUSSINESQ, kappa=1e-3, n_bv=1.0))
+    assert 1.35 < bq / hd < 1.55
+
+
 def test_mhd_workspace_is_about_twice_hd(ps):
     hd = ps.ps_plan_workspace_bytes(ps.make_config(128))
     mhd = ps.ps_plan_workspace_bytes(ps.make_config(128, eq=ps.Equations.MHD))
