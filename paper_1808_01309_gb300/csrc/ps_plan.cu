@@ -325,7 +325,8 @@ ps_status run_inverse_and_x(ps_plan* p, PassArgs& a) {
   return PS_OK;
 }
 
-// One evaluation of D P(N + f) followed by the selected z-forward epilogue.
+// One evaluation of D P(N + f) followed by the selected output of the update
+// kernel (right-hand side or RK stage update).
 template <typename T>
 ps_status run_rhs_passes(ps_plan* p, PassArgs& a) {
   ps_status s;
