@@ -359,6 +359,35 @@ ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int
  * two buffers.  Asynchronous. */
 ps_status ps_les_filter(int n_dns, const void* uhat_dns, int n_les, int kc, void* uhat_les, void* cuda_stream);
 
+/* ---- Checkpoint and resume -----------------------------------------------
+ * The paper returns the fields to the host to write restart files (Sec. 3)
+ * and describes no format; this is one.  A checkpoint file is a 136-byte
+ * little-endian header followed by the state exactly as in device memory
+ * (the ABI layout above, ncomp * nz * ny * (nx/2+1) complex values):
+ *   off   0: magic "PSCKPT "   off   8: uint32 version (1)
+ *   off  12: uint32 header bytes (136)
+ *   off  16: int32 nx, ny, nz, prec, eq, dealias, rk_order, ncomp
+ *   off  48: double lx, ly, lz, nu, eta, n_bv, kappa, t
+ *   off 112: int64 step          off 120: uint64 payload bytes
+ *   off 128: uint64 FNV-1a (64-bit) checksum of the payload
+ * The forcing is not part of a checkpoint (it is the caller's, constant).
+ *
+ * ps_checkpoint_save: writes the device state uhat of the plan (after the
+ *   work queued on the plan stream) with time t and step number `step` to
+ *   `path` (through path + ".part", renamed when complete).  Synchronises.
+ * ps_checkpoint_load: reads `path` into the device state uhat of a plan with
+ *   the same grid, box, precision and equations (else PS_ERR_INVALID_ARG);
+ *   the checksum is verified before uhat is touched (a corrupted or truncated
+ *   file returns PS_ERR_INVALID_ARG and leaves uhat unchanged); t and step
+ *   (optional) receive the saved values.  Synchronises.
+ * ps_checkpoint_info: reads and checks the header only, filling cfg (forcing
+ *   NULL), t and step (each optional); needs no GPU.
+ * Continuing from a loaded checkpoint with the same plan configuration gives
+ * the same states bit for bit as the uninterrupted run. */
+ps_status ps_checkpoint_save(ps_plan* plan, const void* uhat, double t, long long step, const char* path);
+ps_status ps_checkpoint_load(ps_plan* plan, void* uhat, double* t, long long* step, const char* path);
+ps_status ps_checkpoint_info(const char* path, ps_config* cfg, double* t, long long* step);
+
 /* Size of the static device array behind ps_rhs_noalloc: 32 MiB. */
 #define PS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

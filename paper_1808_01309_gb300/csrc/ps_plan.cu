@@ -497,6 +497,9 @@ cudaStream_t plan_stream(const ps_plan* p) { return p->stream; }
 void plan_set_xrpc(ps_plan* p, int rpc) { p->xrpc = rpc; }
 void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
 void plan_set_time(ps_plan* p, double t) { p->time = t; }
+// used by the checkpoint layer (ps_io.cu)
+ps_config plan_config(const ps_plan* p) { return p->cfg; }
+size_t plan_state_bytes(const ps_plan* p) { return p->sz.state * p->sz.vb; }
 }  // namespace ps
 
 extern "C" {

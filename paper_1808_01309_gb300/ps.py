@@ -53,7 +53,7 @@ SYMBOLS = (
     "ps_ensemble_rk_steps", "ps_ensemble_tune", "ps_mlp_forward", "ps_mlp_grad", "ps_mlp_adam",
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
     "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
-    "ps_plan_closure_grad_transfer",
+    "ps_plan_closure_grad_transfer", "ps_checkpoint_save", "ps_checkpoint_load", "ps_checkpoint_info",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -136,6 +136,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_closure_grad_transfer.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, P, P,
                                                   ctypes.c_int]
     lib.ps_rk_steps.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.ps_checkpoint_save.argtypes = [P, P, ctypes.c_double, ctypes.c_longlong, ctypes.c_char_p]
+    lib.ps_checkpoint_load.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.c_char_p]
+    lib.ps_checkpoint_info.argtypes = [ctypes.c_char_p, ctypes.POINTER(PsConfig), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
     lib.ps_mlp_backward.argtypes = [P, P, P, ctypes.c_longlong, P, P]
     lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
     lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
@@ -221,6 +226,22 @@ def ps_rk_steps(plan, uhat, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
     _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_checkpoint_save(plan, uhat, t: float, step: int, path: str) -> None:
+    _check(load().ps_checkpoint_save(plan, _ptr(uhat), float(t), int(step), os.fsencode(path)))
+
+
+def ps_checkpoint_load(plan, uhat, path: str) -> tuple[float, int]:
+    t, step = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().ps_checkpoint_load(plan, _ptr(uhat), ctypes.byref(t), ctypes.byref(step), os.fsencode(path)))
+    return t.value, step.value
+
+
+def ps_checkpoint_info(path: str) -> tuple[PsConfig, float, int]:
+    cfg, t, step = PsConfig(), ctypes.c_double(), ctypes.c_longlong()
+    _check(load().ps_checkpoint_info(os.fsencode(path), ctypes.byref(cfg), ctypes.byref(t), ctypes.byref(step)))
+    return cfg, t.value, step.value
 
 
 def ps_plan_set_host_mode(plan, mode: int) -> None:
