@@ -62,6 +62,7 @@ def parse_args():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--mhd-steps", type=int, default=5)
     ap.add_argument("--boussinesq-steps", type=int, default=5)
+    ap.add_argument("--fp32-error-steps", type=int, default=100)
     ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
@@ -218,10 +219,10 @@ def model_bytes(n: int, vb: int):
 
 
 def make_inputs(n: int):
-    from paper_1808_01309_gb300 import inputs
-    u = inputs.random_solenoidal_field(n, n, n, seed=1)
-    f = inputs.forcing_field(n, n, n, seed=2)
-    return u, f
+    """Initial state and forcing of the forced n^3 workload (workloads.forced)."""
+    from paper_1808_01309_gb300 import workloads
+    w = workloads.forced(n)
+    return w.initial_state(), w.forcing()
 
 
 def time_steps(plan, ud, dt, steps, warmup, stream, world, ps):
@@ -395,12 +396,17 @@ def run_ours(args, world, rank, local):
         del ut, fd
         torch.cuda.empty_cache()
 
+    # ---- FP32 error per step against FP64 at 256^3 (the 256^3 workload) ------
+    err = None
+    if args.fp32_error_steps > 0:
+        err = fp32_error_per_step(args.fp32_error_steps, dev, stream)
+
     ens = None
     if not args.no_ensemble:
         ens = run_ensemble(args, dev, stream)
         torch.cuda.empty_cache()
 
-    out.update(mhd=mhd, bq=bq, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
+    out.update(mhd=mhd, bq=bq, err=err, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
                achieved=achieved, achieved_pruned=achieved_pruned, model=model, step_model=step_model,
                kernel_model_gbs=kernel_model_gbs,
                hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
@@ -412,7 +418,47 @@ def run_ours(args, world, rank, local):
 CPU_N = 256  # the oracle's sample grid: one 256^3 RHS takes ~7 s, a 512^3 one ~1 min
 
 
-ENSEMBLE_SIZES = [64] * 16 + [96] * 16 + [128] * 16
+def _ensemble_sizes():
+    from paper_1808_01309_gb300 import workloads
+    return workloads.ENSEMBLE_SIZES
+
+
+ENSEMBLE_SIZES = _ensemble_sizes()
+
+
+def fp32_error_per_step(steps, dev, stream):
+    """The forced 256^3 workload stepped in FP32 and in FP64 side by side:
+    relative L2 distance of the FP32 state from the FP64 one after every step
+    and the relative energy difference at the end.  The FP64 CUDA path stands
+    in for the FP64 oracle (each of its right-hand sides is held to 1e-12 of
+    the oracle by the parity tests; 100 oracle RK4 steps at 256^3 would take
+    most of an hour)."""
+    import torch
+    from paper_1808_01309_gb300 import ps, workloads
+    w = workloads.forced(256, steps=steps)
+    u0, f = w.initial_state(), w.forcing()
+    plans, states = [], []
+    for prec, dt in ((ps.Precision.FP32, torch.complex64), (ps.Precision.FP64, torch.complex128)):
+        fd = torch.from_numpy(f).to(dev, dt)
+        plans.append(ps.Plan(256, prec=prec, nu=w.nu, rk_order=4, forcing=fd, stream=stream))
+        states.append(torch.from_numpy(u0).to(dev, dt))
+    errs = []
+    for i in range(steps):
+        for p, s in zip(plans, states):
+            p.rk_step(s, w.dt, t=i * w.dt)
+        d = states[0].to(torch.complex128) - states[1]
+        errs.append(float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(states[1])))
+    e32 = plans[0].diagnostics(states[0])["energy"]
+    e64 = plans[1].diagnostics(states[1])["energy"]
+    for p in plans:
+        p.close()
+    del states
+    torch.cuda.empty_cache()
+    return {"workload": "forced 256^3, nu = 2e-3, dt = 1e-3, IF-RK4", "steps": steps,
+            "rel_l2_after_step": {str(i + 1): float(f"{errs[i]:.3e}")
+                                  for i in sorted(set(range(0, steps, max(1, steps // 10))) | {steps - 1})},
+            "max_rel_l2": float(f"{max(errs):.3e}"), "energy_rel_diff": float(f"{abs(e32 - e64) / e64:.3e}"),
+            "reference": "FP64 CUDA path (per-RHS parity with the FP64 oracle 1e-12)"}
 
 
 def run_ensemble(args, dev, stream):
@@ -548,6 +594,7 @@ def main():
         "fp64": res["fp64"],
         "mhd": res["mhd"],
         "boussinesq": res["bq"],
+        "fp32_error_256": res["err"],
         "ensemble": res["ens"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],

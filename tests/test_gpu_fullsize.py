@@ -109,3 +109,14 @@ def test_fp32_energy_after_100_steps_256(ps):
     e64 = _energy_after(ps, 256, "fp64", 100)
     assert abs(e32 - e64) <= 1e-4 * e64
     assert math.isfinite(e32) and 0.3 < e32 < 0.7
+
+
+def test_fp32_state_error_per_step_256(ps):
+    """FP32 against the FP64 CUDA path on the forced 256^3 workload, every step
+    of 100: the relative L2 distance of the states stays small (its growth is
+    the FP32 rounding carried by the flow) and the energies agree to 1e-4."""
+    import bench
+    r = bench.fp32_error_per_step(100, torch.device("cuda"), torch.cuda.current_stream())
+    assert r["max_rel_l2"] < 1e-4
+    assert r["energy_rel_diff"] < 1e-4
+
