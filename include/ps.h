@@ -359,6 +359,21 @@ ps_status ps_les_training_sample(int n_dns, const void* uhat_dns, int n_les, int
  * two buffers.  Asynchronous. */
 ps_status ps_les_filter(int n_dns, const void* uhat_dns, int n_les, int kc, void* uhat_les, void* cuda_stream);
 
+/* ---- Plain 3D transforms ----------------------------------------------------
+ * The discrete Fourier sum of Eq. (fftsum) on an n^3 grid (2 pi box) for
+ * nfields real FP32 fields, with the line transforms the passes are built
+ * from but without pruning, masking or fusion (every mode is kept):
+ *   ps_fft_r2c: spec[f](k) = (1/n^3) sum_x phys[f](x) exp(-i k.x)
+ *   ps_fft_c2r: phys[f](x) = sum_k spec[f](k) exp(+i k.x) over the full
+ *               Hermitian spectrum (the unnormalised backward sum)
+ * spec: [nfields][n][n][n/2+1] complex64 in the state layout (device);
+ * phys: [nfields][n][n][n] float32, x fastest (device); the input is not
+ * modified.  n in {16, 32, 48, 64, 96, 128, 192, 256, 512}, 1 <= nfields
+ * <= 16.  Allocate and free their scratch (twiddles; for c2r a copy of the
+ * spectrum) and synchronise the stream. */
+ps_status ps_fft_r2c(int n, int nfields, const float* phys, void* spec, void* cuda_stream);
+ps_status ps_fft_c2r(int n, int nfields, const void* spec, float* phys, void* cuda_stream);
+
 /* ---- Checkpoint and resume -----------------------------------------------
  * The paper returns the fields to the host to write restart files (Sec. 3)
  * and describes no format; this is one.  A checkpoint file is a 136-byte

@@ -828,3 +828,61 @@ extern "C" ps_status ps_les_filter(int n_dns, const void* uhat_dns, int n_les, i
   }
   return PS_OK;
 }
+
+// Plain 3D transforms of FP32 fields (include/ps.h, ps_fft_c2r / ps_fft_r2c):
+// the line transforms of the passes without pruning, masking or fusion.
+namespace {
+
+ps_status fft_bad(ps_status s, const std::string& m) {
+  ps::set_last_error(m);
+  return s;
+}
+
+ps_status fft_run(int n, int nfields, const void* in, void* out, void* cuda_stream, bool backward) {
+  using namespace ps;
+  using namespace ps::les;
+  const char* name = backward ? "ps_fft_c2r" : "ps_fft_r2c";
+  const auto ok_n = [](int v) {
+    return v == 16 || v == 32 || v == 48 || v == 64 || v == 96 || v == 128 || v == 192 || v == 256 || v == 512;
+  };
+  if (!in || !out) return fft_bad(PS_ERR_INVALID_ARG, std::string(name) + ": NULL buffer");
+  if (!ok_n(n)) return fft_bad(PS_ERR_INVALID_ARG, std::string(name) + ": n must be 16, 32, 48, 64, 96, 128, 192, 256 or 512");
+  if (nfields < 1 || nfields > 16) return fft_bad(PS_ERR_INVALID_ARG, std::string(name) + ": nfields must be in 1..16");
+  const Geo g = cube_geo(n);
+  const long long M = (long long)g.nz * g.ny * g.nh, P = (long long)n * n * n;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  V* tw = nullptr;
+  V* spec = nullptr;
+  cudaError_t e = cudaMalloc(&tw, sizeof(V) * n);
+  if (e == cudaSuccess && backward) e = cudaMalloc(&spec, sizeof(V) * nfields * M);  // the z, y passes work in place
+  if (e != cudaSuccess) {
+    cudaFree(tw);
+    (void)cudaGetLastError();
+    return fft_bad(PS_ERR_OOM, std::string(name) + ": device allocation failed");
+  }
+  k_tw<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  e = cudaGetLastError();
+  if (backward) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(spec, in, sizeof(V) * nfields * M, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = spec2phys(g, nfields, spec, static_cast<float*>(out), tw, tw, tw, s);
+  } else {
+    if (e == cudaSuccess) e = phys2spec(g, nfields, static_cast<const float*>(in), static_cast<V*>(out), tw, tw, tw, s);
+  }
+  const cudaError_t es = cudaStreamSynchronize(s);  // the scratch is freed below
+  if (e == cudaSuccess) e = es;
+  cudaFree(tw);
+  cudaFree(spec);
+  (void)P;
+  if (e != cudaSuccess) return fft_bad(PS_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" ps_status ps_fft_c2r(int n, int nfields, const void* spec, float* phys, void* cuda_stream) {
+  return fft_run(n, nfields, spec, phys, cuda_stream, true);
+}
+
+extern "C" ps_status ps_fft_r2c(int n, int nfields, const float* phys, void* spec, void* cuda_stream) {
+  return fft_run(n, nfields, phys, spec, cuda_stream, false);
+}

@@ -54,6 +54,7 @@ SYMBOLS = (
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
     "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
     "ps_plan_closure_grad_transfer", "ps_checkpoint_save", "ps_checkpoint_load", "ps_checkpoint_info",
+    "ps_fft_r2c", "ps_fft_c2r",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -137,6 +138,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                   ctypes.c_int]
     lib.ps_rk_steps.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     lib.ps_checkpoint_save.argtypes = [P, P, ctypes.c_double, ctypes.c_longlong, ctypes.c_char_p]
+    lib.ps_fft_r2c.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.ps_fft_c2r.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
     lib.ps_checkpoint_load.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.c_char_p]
     lib.ps_checkpoint_info.argtypes = [ctypes.c_char_p, ctypes.POINTER(PsConfig), ctypes.POINTER(ctypes.c_double),
@@ -226,6 +229,14 @@ def ps_rk_steps(plan, uhat, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
     _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_fft_r2c(n: int, nfields: int, phys, spec, stream=None) -> None:
+    _check(load().ps_fft_r2c(int(n), int(nfields), _ptr(phys), _ptr(spec), _stream_handle(stream)))
+
+
+def ps_fft_c2r(n: int, nfields: int, spec, phys, stream=None) -> None:
+    _check(load().ps_fft_c2r(int(n), int(nfields), _ptr(spec), _ptr(phys), _stream_handle(stream)))
 
 
 def ps_checkpoint_save(plan, uhat, t: float, step: int, path: str) -> None:

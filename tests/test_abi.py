@@ -111,3 +111,12 @@ def test_workspace_bytes_scale_with_the_retained_cube(ps):
     # 512^3 FP32: two 6-field intermediates and two compact 3-field stage buffers
     b512 = ps.ps_plan_workspace_bytes(ps.make_config(512))
     assert 4.0e9 < b512 < 5.5e9
+
+
+@pytest.mark.parametrize("n,nf", [(8, 1), (1024, 1), (100, 1), (64, 0), (64, 17)])
+def test_plain_transforms_check_their_arguments(ps, n, nf):
+    lib = ps.load()
+    assert lib.ps_fft_r2c(n, nf, 1, 2, None) == ps.PS_ERR_INVALID_ARG
+    assert lib.ps_fft_c2r(n, nf, 1, 2, None) == ps.PS_ERR_INVALID_ARG
+    assert lib.ps_fft_r2c(64, 1, None, None, None) == ps.PS_ERR_INVALID_ARG
+
