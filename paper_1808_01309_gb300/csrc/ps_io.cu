@@ -152,8 +152,28 @@ extern "C" ps_status ps_checkpoint_info(const char* path, ps_config* cfg, double
   return PS_OK;
 }
 
+namespace {
+ps_status save_to(ps_plan* plan, const void* uhat, double t, long long step, const std::string& tmp);
+}
+
 extern "C" ps_status ps_checkpoint_save(ps_plan* plan, const void* uhat, double t, long long step, const char* path) {
   if (!plan || !uhat || !path) return bad(PS_ERR_INVALID_ARG, "checkpoint: NULL plan, state or path");
+  const std::string tmp = std::string(path) + ".part";
+  const ps_status s = save_to(plan, uhat, t, step, tmp);
+  if (s != PS_OK) {
+    std::remove(tmp.c_str());  // no partial file is left behind
+    return s;
+  }
+  if (std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return bad(PS_ERR_INVALID_ARG, std::string("checkpoint: cannot rename to ") + path);
+  }
+  return PS_OK;
+}
+
+namespace {
+// Header (checksum written once the payload is known) and payload into tmp.
+ps_status save_to(ps_plan* plan, const void* uhat, double t, long long step, const std::string& tmp) {
   const ps_config c = plan_config(plan);
   Header h{};
   h.nx = c.nx;
@@ -174,7 +194,6 @@ extern "C" ps_status ps_checkpoint_save(ps_plan* plan, const void* uhat, double 
   h.t = t;
   h.step = step;
   h.payload = plan_state_bytes(plan);
-  const std::string tmp = std::string(path) + ".part";
   std::FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return bad(PS_ERR_INVALID_ARG, std::string("checkpoint: cannot create ") + tmp);
   FileCloser fc{f};
@@ -197,14 +216,12 @@ extern "C" ps_status ps_checkpoint_save(ps_plan* plan, const void* uhat, double 
   encode(h, hb);
   if (std::fseek(f, 0, SEEK_SET) != 0 || std::fwrite(hb, 1, kHeader, f) != kHeader)
     return bad(PS_ERR_INVALID_ARG, "checkpoint: write failed");
-  if (std::fclose(f) != 0) {
-    fc.f = nullptr;
-    return bad(PS_ERR_INVALID_ARG, "checkpoint: close failed");
-  }
+  const int cl = std::fclose(f);
   fc.f = nullptr;
-  if (std::rename(tmp.c_str(), path) != 0) return bad(PS_ERR_INVALID_ARG, std::string("checkpoint: cannot rename to ") + path);
+  if (cl != 0) return bad(PS_ERR_INVALID_ARG, "checkpoint: close failed");
   return PS_OK;
 }
+}  // namespace
 
 extern "C" ps_status ps_checkpoint_load(ps_plan* plan, void* uhat, double* t, long long* step, const char* path) {
   if (!plan || !uhat || !path) return bad(PS_ERR_INVALID_ARG, "checkpoint: NULL plan, state or path");
