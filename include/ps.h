@@ -10,7 +10,9 @@
  * Galerkin ODEs for the coefficients advanced by an explicit Runge-Kutta
  * scheme of 2nd or 4th order, the nonlinear term formed in physical space
  * between a backward and a forward 3D transform, and the pressure acting as a
- * projection of that term onto divergence-free fields.
+ * projection of that term onto divergence-free fields.  The same machinery
+ * advances the MHD system (Eqs. uMHD, bMHD) and the Boussinesq system
+ * (Eqs. mom, temp, divv), selected by ps_config.eq.
  *
  * Conventions fixed by this library (readings of the paper):
  *   - Forward transform: u_hat(k) = (1/(Nx Ny Nz)) sum_x u(x) exp(-i k.x);

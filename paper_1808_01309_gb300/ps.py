@@ -394,8 +394,9 @@ def ps_mlp_grad_tb(params, X, A, T, count: int, s_A: float, s_tau: float, grad, 
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Plan:
-    """Owns one ps_plan; fields are torch tensors of shape (3, nz, ny, nx//2+1),
-    complex64 (FP32) or complex128 (FP64), contiguous, on the plan's device."""
+    """Owns one ps_plan; fields are torch tensors of shape (ncomp, nz, ny,
+    nx//2+1) with ncomp = 3 (HD), 6 (MHD) or 4 (Boussinesq), complex64 (FP32)
+    or complex128 (FP64), contiguous, on the plan's device."""
 
     def __init__(self, nx, ny=None, nz=None, *, stream=None, **kw):
         self.cfg = make_config(nx, ny, nz, **kw)
