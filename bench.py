@@ -112,7 +112,7 @@ def source_hash(files) -> str:
 def ncu_traffic(kind: str, n: int):
     """DRAM bytes per launch of `kind` at n^3 FP32 from the committed ncu
     summary, or None if absent or taken on different kernel sources."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic_rk4_512_fp32.md")
     if not os.path.exists(path):
         return None
     want = source_hash(KIND_FILES[kind])
