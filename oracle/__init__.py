@@ -9,7 +9,9 @@ It is a plain, slow, obviously-correct restatement of what the method
 computes (Rosenberg et al., arXiv:1808.01309, Sec. 2), in float64 numpy:
 
 * the discrete Fourier expansion of Eq. (fftsum) with the forward sum
-  normalised by 1/(Nx Ny Nz) and the backward sum unnormalised,
+  normalised by 1/(Nx Ny Nz) and the backward sum unnormalised, computed by a
+  plain recursive mixed-radix Cooley-Tukey transform (:mod:`oracle.fft`; no
+  FFT library),
 * the Galerkin ODEs for the Fourier coefficients (Sec. 2, after Eq. fftsum),
   with the nonlinear term formed pointwise in physical space (rotational
   form u x omega) and transformed back,
@@ -23,13 +25,18 @@ computes (Rosenberg et al., arXiv:1808.01309, Sec. 2), in float64 numpy:
 The readings taken where the paper is silent or garbled are listed in the
 module docstring of :mod:`oracle.spectral`.
 
-Pinning status: every function is pinned by ``tests/test_oracle_pins.py``
+Pinning status: every function is pinned by ``tests/test_oracle_fft_pins.py``
+(the transform against the direct O(N^2) sum at lengths 1-512 incl. primes,
+impulses, tones, shift theorem, round trip), ``tests/test_oracle_pins.py``
 (brute-force DFT, Parseval, closed-form flows, exact rational Taylor
 coefficients, conservation laws, alias-free brute-force convolution, RK order),
 ``tests/test_oracle_mhd_pins.py``, ``tests/test_oracle_boussinesq_pins.py``
 (exact rational tendency, brute-force scalar convolution, ideal energy
 conservation, internal-wave frequency and RK4 order, exact diffusion) and
-``tests/test_oracle_les_pins.py``.
+``tests/test_oracle_les_pins.py``; ``tests/test_oracle_planted.py`` plants
+25 plausible mistakes (transform, curl, product, projection, RK, mask,
+weights, box lengths, every LES basis tensor, the adjoint) and checks that
+each one fails a pin.
 """
 
 from .spectral import (  # noqa: F401

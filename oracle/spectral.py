@@ -7,8 +7,8 @@ imports this module.
 Array conventions (shared by the C-ABI, written independently there):
   * a vector field in spectral space is a complex array of shape
     (3, nz, ny, nx//2 + 1): component, kz, ky, kx with kx fastest; ky and kz in
-    FFT order (0..n/2-1, -n/2..-1).  This is the layout ``numpy.fft.rfftn``
-    gives for a real array of shape (nz, ny, nx).
+    FFT order (0..n/2-1, -n/2..-1): the half spectrum of a real array of
+    shape (nz, ny, nx) with the x axis halved.
   * a vector field in physical space is a real array of shape (3, nz, ny, nx)
     sampled at x_i = Lx i / nx (and likewise in y, z).
 
@@ -59,6 +59,8 @@ import dataclasses
 import math
 
 import numpy as np
+
+from . import fft as _fft
 
 CUBIC, SPHERICAL, NONE = 0, 1, 2
 
@@ -139,14 +141,15 @@ def hermitian_weight(cfg: Config) -> np.ndarray:
 def forward(u: np.ndarray) -> np.ndarray:
     """Forward transform of real data over the last three axes:
     u_hat(p,q,r) = (1/(Nx Ny Nz)) sum_ijk u_ijk exp(-2 pi i (p i/Nx + q j/Ny + r k/Nz)).
-    Eq. (fftsum) with readings R1, R2; the local FFT is a library routine."""
-    return np.fft.rfftn(u, axes=(-3, -2, -1), norm="forward")
+    Eq. (fftsum) with readings R1, R2, by the plain mixed-radix Cooley-Tukey
+    transform of oracle/fft.py."""
+    return _fft.rfft3(u)
 
 
 def inverse(uh: np.ndarray, cfg: Config) -> np.ndarray:
     """Backward transform, the unnormalised sum with the opposite sign
     (Sec. 2, text after Eq. fftsum; reading R2), to real data on the grid."""
-    return np.fft.irfftn(uh, s=(cfg.nz, cfg.ny, cfg.nx), axes=(-3, -2, -1), norm="forward")
+    return _fft.irfft3(uh, cfg.nz, cfg.ny, cfg.nx)
 
 
 def curl_hat(uh: np.ndarray, cfg: Config) -> np.ndarray:

@@ -57,6 +57,12 @@ def test_invariants_closed_forms():
     g = 0.9
     lam = _inv([[0, g, 0], [0, 0, 0], [0, 0, 0]])
     assert np.allclose(lam, [g * g / 2, -g * g / 2, 0, 0, -g ** 4 / 8], atol=1e-15)
+    # diagonal strain (a, b, c) with a rotation w about z: R^2 = diag(-w^2, -w^2, 0)
+    a, b, w = 0.8, -0.3, 1.1
+    c = -a - b
+    lam = _inv([[a, -w, 0], [w, b, 0], [0, 0, c]])
+    assert np.allclose(lam, [a * a + b * b + c * c, -2 * w * w, a ** 3 + b ** 3 + c ** 3,
+                             -w * w * (a + b), -w * w * (a * a + b * b)], atol=1e-15)
 
 
 def test_gradient_of_taylor_green_is_analytic():

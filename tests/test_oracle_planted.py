@@ -1,0 +1,321 @@
+"""Planted mistakes: each plausible error in the oracle must fail a pin.
+
+Every case below replaces one function of the oracle (oracle/fft.py,
+oracle/spectral.py, oracle/les.py) by a copy with one mistake planted (a
+flipped sign, a transposed index, a dropped term, a wrong coefficient) and
+runs the CPU pins of tests/test_oracle_*pins.py until one of them fails.  A
+case passes when some pin fails; a mistake that no pin notices fails the case.
+CPU only; nothing here touches the CUDA path."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fft as offt
+from oracle import les
+from oracle import spectral as sp
+
+from . import test_oracle_fft_pins as FP
+from . import test_oracle_les_pins as LP
+from . import test_oracle_pins as P
+
+
+def _patch(monkeypatch, name, fn, mods):
+    for m in mods:
+        if hasattr(m, name):
+            monkeypatch.setattr(m, name, fn)
+
+
+def some_pin_fails(pins):
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, FloatingPointError, ValueError, IndexError):
+            return pin
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the transform (oracle/fft.py) and the right-hand side (oracle/spectral.py)
+# ---------------------------------------------------------------------------
+
+HD_PINS = [
+    lambda: FP.test_matches_the_direct_sum(12, -1),
+    lambda: FP.test_matches_the_direct_sum(96, +1),
+    lambda: FP.test_real_transforms_match_the_direct_sum((8, 6, 10)),
+    lambda: P.test_forward_is_the_direct_sum((8, 8, 8)),
+    lambda: P.test_inverse_is_the_unnormalised_direct_sum((6, 10, 12)),
+    P.test_parseval_with_hermitian_weights,
+    lambda: P.test_two_thirds_halfwidth(96, 31),
+    P.test_curl_of_taylor_green_is_analytic,
+    lambda: P.test_rhs_of_crossed_shear_is_closed_form(4.0, 9.0, 2.5),
+    P.test_projected_rhs_is_divergence_free_with_zero_mean,
+    P.test_taylor_green_tendency_matches_exact_rational_advection,
+    lambda: P.test_rhs_equals_bruteforce_truncated_convolution((8, 12, 16)),
+    lambda: P.test_abc_flow_decays_exactly(4),
+    lambda: P.test_abc_flow_decays_exactly(2),
+    lambda: P.test_linear_forced_response(4),
+    lambda: P.test_linear_forced_response(2),
+    lambda: P.test_runge_kutta_order(4, 16.0),
+    lambda: P.test_runge_kutta_order(2, 4.0),
+    P.test_diagnostics_match_physical_space,
+]
+
+
+def _fft_first_output_transposed(x, sign):
+    """Output read with k2 fastest instead of k1 (index slip)."""
+    n, B = x.shape
+    if n == 1:
+        return np.array(x, dtype=np.complex128)
+    r = offt._radix(n)
+    if r == n:
+        return offt.dft_matrix(n, sign) @ x
+    m = n // r
+    y = offt.dft_matrix(r, sign) @ x.reshape(r, m * B)
+    y = y.reshape(r, m, B) * offt._twiddles(r, m, sign)
+    y = np.ascontiguousarray(y.transpose(1, 0, 2))
+    z = _fft_first_output_transposed(y.reshape(m, r * B), sign)
+    return np.ascontiguousarray(z.reshape(m, r, B).transpose(1, 0, 2)).reshape(n, B)
+
+
+def _twiddles_conjugated(r, m, sign):
+    k1 = np.arange(r).reshape(-1, 1)
+    n2 = np.arange(m).reshape(1, -1)
+    return offt._roots(k1 * n2, r * m, -sign).reshape(r, m, 1)
+
+
+def _irfft3_without_conj(uh, nz, ny, nx):
+    nh = nx // 2 + 1
+    out = np.empty(uh.shape[:-3] + (nz, ny, nx))
+    for idx in np.ndindex(*uh.shape[:-3]):
+        a = offt.fft_axis(offt.fft_axis(uh[idx], -3, +1), -2, +1)
+        full = np.empty((nz, ny, nx), dtype=np.complex128)
+        full[..., :nh] = a
+        full[..., nh:] = a[..., nx - nh:0:-1]  # the conjugate is missing
+        out[idx] = offt.fft_axis(full, -1, +1).real
+    return out
+
+
+_orig_rfft3 = offt.rfft3
+_orig_curl = sp.curl_hat
+_orig_project = sp.project
+_orig_wavenumbers = sp.wavenumbers
+_orig_rhs = sp.rhs
+
+
+def _nonlinear_omega_cross_u(uh, cfg):
+    D = sp.dealias_mask(cfg)
+    u_hat = uh * D
+    u = sp.inverse(u_hat, cfg)
+    om = sp.inverse(sp.curl_hat(u_hat, cfg), cfg)
+    return sp.forward(np.cross(om, u, axis=0)) * D  # operands swapped
+
+
+def _project_drops_z(vh, cfg):
+    out = _orig_project(vh, cfg)
+    kx, ky, kz = sp.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = np.where(k2 > 0, (kx * vh[0] + ky * vh[1] + kz * vh[2]) / np.where(k2 > 0, k2, 1), 0)
+    out[2] = out[2] + kz * s  # the k_z (k . v)/|k|^2 term is lost
+    return out
+
+
+def _lawson_rk4_weight_one(u, E, R, dt, order):
+    if order != 4:
+        return _orig_lawson(u, E, R, dt, order)
+    k1 = R(u)
+    k2 = R(E * (u + 0.5 * dt * k1))
+    k3 = R(E * u + 0.5 * dt * k2)
+    k4 = R(E * E * u + dt * E * k3)
+    return E * E * u + (dt / 6.0) * (E * E * k1 + E * (k2 + k3) + k4)  # weight 1 instead of 2
+
+
+def _lawson_rk2_full_first_stage(u, E, R, dt, order):
+    if order != 2:
+        return _orig_lawson(u, E, R, dt, order)
+    k1 = R(u)
+    k2 = R(E * E * (u + dt * k1))
+    return E * E * (u + dt * k1) + 0.5 * dt * k2  # dt instead of dt/2 on k1
+
+
+_orig_lawson = sp._lawson_step
+
+
+def _rk_step_full_step_factor(uh, dt, cfg, forcing=None, nonlinear_on=True):
+    kx, ky, kz = sp.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    E = np.exp(-cfg.nu * k2 * dt) + np.zeros_like(uh, dtype=np.float64)  # dt instead of dt/2
+    u = uh * sp.dealias_mask(cfg)
+    return sp._lawson_step(u, E, lambda v: sp._nonviscous(v, cfg, forcing, nonlinear_on), dt, cfg.rk_order)
+
+
+def _halfwidth_floor(n, dealias):
+    return n // 2 - 1 if dealias == sp.NONE else n // 3  # floor(n/3) aliases when 3 divides n
+
+
+def _weight_two_everywhere(cfg):
+    return np.full((1, 1, cfg.nh), 2.0)
+
+
+def _wavenumbers_swapped_boxes(cfg):
+    kx, ky, kz = _orig_wavenumbers(cfg)
+    return kx, ky * (cfg.ly / cfg.lx), kz  # ky scaled with Lx
+
+
+def _rhs_viscous_sign(uh, cfg, forcing=None, nonlinear_on=True):
+    kx, ky, kz = sp.wavenumbers(cfg)
+    k2 = kx * kx + ky * ky + kz * kz
+    return sp._nonviscous(uh, cfg, forcing, nonlinear_on) + cfg.nu * k2 * (uh * sp.dealias_mask(cfg))
+
+
+HD_MISTAKES = {
+    "twiddle sign": ("_twiddles", _twiddles_conjugated, [offt]),
+    "output index order": ("fft_first", _fft_first_output_transposed, [offt]),
+    "hermitian fill without conjugate": ("irfft3", _irfft3_without_conj, [offt]),
+    "forward normalisation dropped": ("rfft3", lambda u: _orig_rfft3(u) * np.prod(np.shape(u)[-3:]), [offt]),
+    "curl sign": ("curl_hat", lambda uh, cfg: -_orig_curl(uh, cfg), [sp, oracle]),
+    "cross product order": ("nonlinear", _nonlinear_omega_cross_u, [sp, oracle]),
+    "projection term dropped": ("project", _project_drops_z, [sp, oracle]),
+    "rk4 stage weight": ("_lawson_step", _lawson_rk4_weight_one, [sp]),
+    "rk2 first-stage coefficient": ("_lawson_step", _lawson_rk2_full_first_stage, [sp]),
+    "integrating factor over a full step": ("rk_step", _rk_step_full_step_factor, [sp, oracle]),
+    "mask half-width floor(N/3)": ("retained_halfwidth", _halfwidth_floor, [sp, oracle]),
+    "hermitian weight": ("hermitian_weight", _weight_two_everywhere, [sp, oracle]),
+    "box lengths swapped": ("wavenumbers", _wavenumbers_swapped_boxes, [sp, oracle]),
+    "viscous term sign": ("rhs", _rhs_viscous_sign, [sp, oracle]),
+}
+
+
+@pytest.mark.parametrize("name", list(HD_MISTAKES))
+def test_planted_hd_mistake_fails_a_pin(name, monkeypatch):
+    fn_name, fn, mods = HD_MISTAKES[name]
+    _patch(monkeypatch, fn_name, fn, mods)
+    assert some_pin_fails(HD_PINS) is not None, f"no pin notices: {name}"
+
+
+# ---------------------------------------------------------------------------
+# the LES closure (oracle/les.py): every basis tensor, the invariants, the
+# network gradient and the adjoint of the force loss
+# ---------------------------------------------------------------------------
+
+LES_PINS = [
+    LP.test_invariants_closed_forms,
+    LP.test_tensor_basis_closed_forms,
+    LP.test_tensor_basis_gradient_model_identity_and_equivariance,
+    LP.test_gelu_derivative_matches_finite_differences,
+    LP.test_mlp_gradients_match_central_differences,
+    LP.test_force_loss_is_the_grid_mean_of_the_residual,
+    LP.test_force_loss_gradients_match_central_differences,
+]
+
+
+def _basis_with_mistake(which):
+    """tensor_basis with tensor `which` (0-based) built by a mistaken formula."""
+
+    def tb(A, s_A=1.0):
+        At = np.swapaxes(A, 0, 1)
+        S = 0.5 * (A + At) / s_A
+        R = 0.5 * (A - At) / s_A
+
+        def mm(X, Y):
+            return np.einsum("ik...,kj...->ij...", X, Y)
+
+        def tr(X):
+            return np.einsum("ii...->...", X)
+
+        eye = np.eye(3).reshape((3, 3) + (1,) * (A.ndim - 2))
+        S2, R2 = mm(S, S), mm(R, R)
+        T = [S, mm(S, R) - mm(R, S), S2 - tr(S2) * eye / 3.0, R2 - tr(R2) * eye / 3.0,
+             mm(R, S2) - mm(S2, R), mm(R2, S) + mm(S, R2) - 2.0 * tr(mm(S, R2)) * eye / 3.0]
+        wrong = [0.5 * (A - At) / s_A,                          # R in place of S
+                 mm(R, S) - mm(S, R),                           # commutator sign
+                 S2,                                            # trace not removed
+                 R2 - tr(R2) * eye,                             # 1 instead of 1/3
+                 mm(S2, R) - mm(R, S2),                         # order swapped
+                 mm(R2, S) + mm(S, R2) - tr(mm(S, R2)) * eye / 3.0]  # 1/3 instead of 2/3
+        T[which] = wrong[which]
+        return np.stack([np.stack([t[i, j] for (i, j) in les.SYM]) for t in T])
+
+    return tb
+
+
+def _invariants_with_mistake(A):
+    At = np.swapaxes(A, 0, 1)
+    S, R = 0.5 * (A + At), 0.5 * (A - At)
+
+    def mm(X, Y):
+        return np.einsum("ik...,kj...->ij...", X, Y)
+
+    def tr(X):
+        return np.einsum("ii...->...", X)
+
+    S2, R2 = mm(S, S), mm(R, R)
+    return np.stack([tr(S2), tr(R2), tr(mm(S2, S)), tr(mm(S2, R)), tr(mm(S2, R2))])  # tr(S^2 R) for tr(S R^2)
+
+
+def _gelu_grad_without_chain(x):
+    t = np.tanh(les.C_GELU * (x + 0.044715 * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * les.C_GELU  # the 1 + 3 a x^2 factor is lost
+
+
+def _force_loss_with_mistake(kind):
+    """force_loss_and_grads with one mistake planted in its adjoint."""
+
+    def f(uh, cfg, p, norm, f_hat, rnd=None):
+        D = sp.dealias_mask(cfg)
+        A = les.gradient(uh, cfg)
+        lam = les.invariants(A)
+        X = (lam.reshape(5, -1).T - norm["mean"]) / norm["std"]
+        y, cache = les.mlp_forward(p, X, rnd)
+        Tb = les.tensor_basis(A, norm["s_A"]).reshape(6, 6, -1)
+        tau = norm["s_tau"] * np.einsum("nmp,pn->mp", Tb, y).reshape((6,) + lam.shape[1:])
+        th = sp.forward(tau)
+        k = sp.wavenumbers(cfg)
+        full = {}
+        for m, (i, j) in enumerate(les.SYM):
+            full[(i, j)] = th[m]
+            full[(j, i)] = th[m]
+        div = np.stack([sum(1j * k[j] * full[(i, j)] for j in range(3)) for i in range(3)])
+        r_hat = sp.project(-div * D, cfg) * D - np.asarray(f_hat) * D
+        w = sp.hermitian_weight(cfg)
+        L = float(np.sum(w * np.abs(r_hat) ** 2))
+        G = np.stack([np.stack([sp.inverse((1j * k[j] * r_hat[i])[None], cfg)[0] for j in range(3)])
+                      for i in range(3)])
+        scale = (1.0 if kind == "scale" else 2.0) / (cfg.nx * cfg.ny * cfg.nz)
+        if kind == "symmetric part":
+            dtau = np.stack([scale * G[i, j] for (i, j) in les.SYM])
+        elif kind == "sign":
+            dtau = np.stack([-scale * (G[i, j] + G[j, i]) if i != j else -scale * G[i, i] for (i, j) in les.SYM])
+        else:
+            dtau = np.stack([scale * (G[i, j] + G[j, i]) if i != j else scale * G[i, i] for (i, j) in les.SYM])
+        dy = norm["s_tau"] * np.einsum("nmp,mp->pn", Tb, dtau.reshape(6, -1))
+        return L, les._backward(p, cache, dy, rnd)
+
+    return f
+
+
+LES_MISTAKES = {f"basis tensor T{n + 1}": ("tensor_basis", _basis_with_mistake(n)) for n in range(6)}
+LES_MISTAKES.update({
+    "invariant tr(S R^2)": ("invariants", _invariants_with_mistake),
+    "gelu derivative": ("gelu_grad", _gelu_grad_without_chain),
+    "adjoint scale": ("force_loss_and_grads", _force_loss_with_mistake("scale")),
+    "adjoint symmetric part": ("force_loss_and_grads", _force_loss_with_mistake("symmetric part")),
+    "adjoint sign": ("force_loss_and_grads", _force_loss_with_mistake("sign")),
+})
+
+
+@pytest.mark.parametrize("name", list(LES_MISTAKES))
+def test_planted_les_mistake_fails_a_pin(name, monkeypatch):
+    fn_name, fn = LES_MISTAKES[name]
+    monkeypatch.setattr(les, fn_name, fn)
+    assert some_pin_fails(LES_PINS) is not None, f"no pin notices: {name}"
+
+
+def test_unmodified_oracle_passes_every_listed_pin():
+    """Control: with nothing planted, none of the pins used above fails."""
+    assert some_pin_fails(HD_PINS) is None
+    assert some_pin_fails(LES_PINS) is None
+    assert math.isfinite(float(np.sum(oracle.hermitian_weight(sp.Config(8, 8, 8)))))
