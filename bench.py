@@ -14,6 +14,12 @@ RK step.  The FP64 path and the FP32/FP64 speed ratio are reported alongside.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The headline steps run with per-kernel timing off; a separate pass with the
+plan's per-kernel events gives the kernel split and the roofline of the
+dominant kernel.  The FP64 oracle (oracle/) is timed as the CPU baseline in
+child processes (one BLAS thread, and all cores) and, in the background while
+the GPU legs run, gives the per-output FP32 error table at 256^3.
+
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (the single-field solve is not sharded); value sums the ranks' points.
 """
@@ -21,6 +27,7 @@ Multi-GPU (torchrun): every rank runs an independent replica of the workload
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import math
@@ -29,6 +36,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -47,6 +55,9 @@ KIND_FILES = {
     "z_forward": _COMMON + ["k_zfwd_f32.cu"],
     "update": _COMMON + ["k_zfwd_f32.cu"],
 }
+CPU_N = 256       # grid of the oracle's CPU-baseline sample (one RHS: ~15-20 s)
+REF_N = 128       # grid of the reference arm's per-step sample (one RHS: ~2 s)
+ORACLE_ERR_N = 256  # grid of the per-output FP32 error table against the oracle
 
 
 def parse_args():
@@ -58,12 +69,14 @@ def parse_args():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-table", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--mhd-steps", type=int, default=5)
     ap.add_argument("--boussinesq-steps", type=int, default=5)
     ap.add_argument("--fp32-error-steps", type=int, default=100)
     ap.add_argument("--ensemble-steps", type=int, default=50)
+    ap.add_argument("--oracle-job", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -110,17 +123,20 @@ def source_hash(files) -> str:
 
 
 def ncu_traffic(kind: str, n: int):
-    """DRAM bytes per launch of `kind` at n^3 FP32 from the committed ncu
-    summary, or None if absent or taken on different kernel sources."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic_rk4_512_fp32.md")
-    if not os.path.exists(path):
+    """DRAM bytes per launch of `kind` at n^3 FP32 from a committed ncu summary
+    under profiles/ (a line "traffic <kind> n=<n> fp32 src=<hash>
+    bytes_per_launch=<B>"), or None if absent or taken on other kernel
+    sources."""
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    if not paths:
         return None
     want = source_hash(KIND_FILES[kind])
     pat = re.compile(r"^traffic\s+(\S+)\s+n=(\d+)\s+fp32\s+src=(\w+)\s+bytes_per_launch=([0-9.eE+]+)")
-    for line in open(path):
-        m = pat.match(line.strip())
-        if m and m.group(1) == kind and int(m.group(2)) == n and m.group(3) == want:
-            return float(m.group(4))
+    for path in paths:
+        for line in open(path):
+            m = pat.match(line.strip())
+            if m and m.group(1) == kind and int(m.group(2)) == n and m.group(3) == want:
+                return float(m.group(4))
     return None
 
 
@@ -180,13 +196,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------
+# Roofline models
+# ---------------------------------------------------------------------------
+
+def retained(n: int):
+    """K = ceil(n/3) - 1 (cubic 2/3 rule), cx = K + 1, c2 = 2K + 1, modes = c2^2 cx."""
+    K = (n + 2) // 3 - 1
+    cx, c2 = K + 1, 2 * K + 1
+    return K, cx, c2, c2 * c2 * cx
+
+
 def algorithmic_bytes(n: int, vb: int):
     """Compulsory HBM bytes per launch of each kernel kind for one RHS stage of
     an IF-RK4 step on an n^3 grid with the cubic 2/3 rule (vb bytes per complex
-    value).  Retained counts: cx = K+1, cy = cz = 2K+1, K = ceil(n/3) - 1."""
-    K = (n + 2) // 3 - 1
-    cx, c2 = K + 1, 2 * K + 1
-    modes = c2 * c2 * cx
+    value): every pass reads its input and writes its output once, for the
+    retained modes and lines only."""
+    K, cx, c2, modes = retained(n)
     b = {
         "z_inverse": (3 * modes + 6 * n * c2 * cx) * vb,
         "y_inverse": (6 * n * c2 * cx + 6 * n * n * cx) * vb,
@@ -207,16 +233,87 @@ def algorithmic_bytes(n: int, vb: int):
     return b
 
 
-def model_bytes(n: int, vb: int):
-    """Bytes per launch of each kernel kind in the roofline model of the fused
-    three-passes-per-direction schedule (no pruning): with S = n^2 (n/2+1) vb
-    one complex field, an HD RHS reads 3+6+6+3+3 S and writes 6+6+3+3+3 S
-    (42 S), an IF-RK4 step moves 4 x 42 S + 30 S = 198 S (the RK stage
-    updates, carried by the per-mode update kernel, 30 S / 4 per launch)."""
+def dense_model_bytes(n: int, vb: int):
+    """Bytes per launch in the roofline model of an unpruned fused
+    three-passes-per-direction schedule: with S = n^2 (n/2+1) vb one complex
+    field, an HD RHS reads 3+6+6+3+3 S and writes 6+6+3+3+3 S (42 S), an
+    IF-RK4 step moves 4 x 42 S + 30 S = 198 S.  Reported for context only: the
+    pruned design never moves the masked part of these bytes."""
     S = n * n * (n // 2 + 1) * vb
     return {"z_inverse": 9 * S, "y_inverse": 12 * S, "x_fused": 9 * S, "y_forward": 6 * S,
             "z_forward": 6 * S, "update": 30 * S / 4}, 198 * S
 
+
+# Radix schedules of the line transforms (the Sched table of csrc/ps_fft.cuh):
+# (points per thread E, line length N) -> stage radices.
+SCHED = {
+    (8, 8): [8], (16, 16): [16], (8, 16): [8, 2], (8, 32): [8, 4], (8, 64): [8, 8], (16, 128): [16, 8],
+    (8, 128): [8, 8, 2], (16, 256): [16, 16], (8, 256): [8, 8, 4], (8, 512): [8, 8, 8],
+    (16, 1024): [16, 8, 8], (8, 1024): [8, 8, 8, 2], (12, 48): [6, 4, 2], (12, 96): [6, 4, 4],
+    (12, 192): [6, 4, 4, 2],
+}
+
+
+def points_per_thread(fp64: bool, n: int) -> int:
+    if n % 3 == 0:
+        return 12
+    return 16 if (not fp64 and n in (16, 128, 256, 1024)) else 8
+
+
+def dft_flops(r: int) -> int:
+    """Real flops of the in-register DFT of radix r: the radix-2 network for
+    powers of two (4 per butterfly, plus 6 for a general twiddle, 4 for one on
+    the diagonal, 0 for +-i), 16 for the 3-point DFT, two of those plus two
+    twiddles and six adds for r = 6."""
+    if r == 3:
+        return 16
+    if r == 6:
+        return 2 * 16 + 2 * 6 + 6 * 2
+    total, length = 0, 2
+    while length <= r:
+        for _ in range(r // length):
+            for j in range(length // 2):
+                s = (16 // length) * j
+                total += 4 + (0 if s in (0, 4) else 4 if s in (2, 6) else 6)
+        length *= 2
+    return total
+
+
+def line_flops(n: int, fp64: bool) -> int:
+    """Real flops of one length-n line transform of the kernels' schedule:
+    the stage DFTs and, after the first stage, (r - 1) complex twiddle
+    multiplications (6 flops) per butterfly."""
+    radices = SCHED[(points_per_thread(fp64, n), n)]
+    f = 0
+    for s, r in enumerate(radices):
+        f += (n // r) * (dft_flops(r) + (6 * (r - 1) if s > 0 else 0))
+    return f
+
+
+def flops_per_rhs(n: int, fp64: bool):
+    """Algorithmic flops of each pass of one HD right-hand side on the
+    retained lines (cubic 2/3 rule), and their total: line transforms from
+    the schedule plus the pointwise work (curl 18 and energy 12 flops per
+    retained mode, packing 6 and the product and max|u| 14 per grid point,
+    the split 16 per retained output mode of the x pass, 1/N^3 2 per mode
+    and the projection and stage update about 60 per mode)."""
+    K, cx, c2, modes = retained(n)
+    L = line_flops(n, fp64)
+    rows = n * n
+    f = {
+        "z_inverse": 6 * c2 * cx * L + 30 * modes,
+        "y_inverse": 6 * n * cx * L,
+        "x_fused": rows * 5 * L + rows * n * 20 + rows * cx * 16,
+        "y_forward": 3 * n * cx * L,
+        "z_forward": 3 * c2 * cx * L + 6 * modes,
+        "update": 60 * modes,
+    }
+    return f, sum(f.values())
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
 
 def make_inputs(n: int):
     """Initial state and forcing of the forced n^3 workload (workloads.forced)."""
@@ -226,6 +323,9 @@ def make_inputs(n: int):
 
 
 def time_steps(plan, ud, dt, steps, warmup, stream, world, ps):
+    """Device time (ms, CUDA events on the plan stream) of `steps` RK4 steps
+    after `warmup` untimed ones, bracketed by a barrier and a synchronisation
+    on both sides; returns (ms, kernel launches in the timed region)."""
     import torch
     for i in range(warmup):
         plan.rk_step(ud, dt, t=i * dt)
@@ -246,6 +346,25 @@ def time_steps(plan, ud, dt, steps, warmup, stream, world, ps):
     return ms, ps.ps_plan_launch_count(plan.handle) - l0
 
 
+def start_oracle_job(job: dict, threads):
+    """Runs `python bench.py --oracle-job <json>` in a child process (numpy
+    only, no GPU) with the BLAS pool set to `threads` (None = all cores)."""
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+    env.pop("WORLD_SIZE", None)
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-job", json.dumps(job)],
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+
+
+def finish_oracle_job(proc, timeout=1800):
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError(f"oracle job failed ({proc.returncode}): {err[-2000:]}")
+    return json.loads(out.strip().splitlines()[-1])
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -254,6 +373,13 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     from paper_1808_01309_gb300 import ps
 
+    # the oracle's 256^3 reference for the FP32 error table runs on the host
+    # cores while the GPU legs run (it is not timed)
+    ref_job, ref_dir = None, None
+    if rank == 0 and world == 1 and not args.no_oracle_table:
+        ref_dir = tempfile.mkdtemp(prefix="ps_oracle_")
+        ref_job = start_oracle_job({"kind": "reference_table", "n": ORACLE_ERR_N, "dir": ref_dir}, None)
+
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n, nu, dt = args.n, 2e-3, 1e-3
@@ -261,7 +387,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     out = {}
 
-    # ---- FP32 (headline) -------------------------------------------------
+    # ---- FP32 (headline): per-kernel timing off ----------------------------
     ud = torch.from_numpy(u).to(dev, torch.complex64)
     fd = torch.from_numpy(f).to(dev, torch.complex64)
     plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=fd, stream=stream)
@@ -269,30 +395,36 @@ def run_ours(args, world, rank, local):
     for i in range(args.warmup):
         plan.rk_step(ud, dt)
     torch.cuda.synchronize()
-    ps.ps_plan_set_timing(plan.handle, True)
     with ClockSampler(local) as clk:
         ms, launches = time_steps(plan, ud, dt, args.steps, 0, stream, world, ps)
-    kt = ps.ps_plan_get_timing(plan.handle)
-    ps.ps_plan_set_timing(plan.handle, False)
     ms_max = reduce_max(ms, world)
     ms_step = ms_max / args.steps
     e_step, umax_step = plan.step_stats()
 
-    # ---- per-kernel roofline of the dominant kernel -------------------------
+    # ---- per-kernel split: a separate pass with the plan's events -----------
+    ksplit = max(4, args.steps // 2)
+    ps.ps_plan_set_timing(plan.handle, True)
+    ms_split, _ = time_steps(plan, ud, dt, ksplit, 0, stream, world, ps)
+    kt = ps.ps_plan_get_timing(plan.handle)
+    ps.ps_plan_set_timing(plan.handle, False)
+    plan.close()
+
     hbm, peak_src = measured_peaks()
     alg = algorithmic_bytes(n, 8)
-    model, step_model = model_bytes(n, 8)
+    dense, step_dense = dense_model_bytes(n, 8)
     kinds = {k: v for k, v in kt.items() if k in alg and v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     avg_ms = kinds[dom][0] / kinds[dom][1]
-    achieved = model[dom] / (avg_ms * 1e-3) / 1e9
-    achieved_pruned = alg[dom] / (avg_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom, n)
+    kernel_ms = {k: round(v[0] / v[1], 4) for k, v in kinds.items()}
     kernel_share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
     kernel_gbs = {k: round(alg[k] / (v[0] / v[1] * 1e-3) / 1e9, 1) for k, v in kinds.items()}
-    kernel_model_gbs = {k: round(model[k] / (v[0] / v[1] * 1e-3) / 1e9, 1) for k, v in kinds.items()}
-    step_bytes = sum(alg[k] * kinds[k][1] for k in kinds) / args.steps
-    plan.close()
+    kernel_frac = {k: round(kernel_gbs[k] / hbm, 3) for k in kernel_gbs}
+    step_bytes = sum(alg[k] * kinds[k][1] for k in kinds) / ksplit
+    roof = {"dom": dom, "avg_ms": avg_ms, "achieved": alg[dom] / (avg_ms * 1e-3) / 1e9, "alg": alg[dom],
+            "dense": dense[dom], "dense_achieved": dense[dom] / (avg_ms * 1e-3) / 1e9, "step_dense": step_dense,
+            "kernel_ms": kernel_ms, "kernel_share": kernel_share, "kernel_gbs": kernel_gbs,
+            "kernel_frac": kernel_frac, "step_bytes": step_bytes, "split_ms_per_step": ms_split / ksplit,
+            "split_steps": ksplit, "traffic": ncu_traffic(dom, n), "hbm": hbm, "peak_src": peak_src}
 
     # ---- end to end: host buffers through the C ABI -------------------------
     e2e = None
@@ -317,8 +449,8 @@ def run_ours(args, world, rank, local):
         mapped_ms = host_steps(ps.HOST_MAPPED)
         e2e_ms = host_steps(ps.HOST_AUTO)
         nbytes = host.numel() * host.element_size()
-        K = -(-n // 3) - 1
-        retained = 3 * (K + 1) * (2 * K + 1) ** 2 * host.element_size()
+        _, cx, c2, _ = retained(n)
+        ret_bytes = 3 * cx * c2 * c2 * host.element_size()
 
         def gpts(ms):
             return round(world * 4 * n ** 3 / (ms * 1e-3) / 1e9, 3)
@@ -326,7 +458,7 @@ def run_ours(args, world, rank, local):
         e2e = {"value": gpts(e2e_ms), "unit": UNIT, "ms_per_step": round(e2e_ms, 3),
                # default mode: the retained modes cross the host link each way;
                # copy engines write the masked modes' zeros during the step
-               "h2d_bytes_per_step": retained, "d2h_bytes_per_step": nbytes, "steps": ksteps,
+               "h2d_bytes_per_step": ret_bytes, "d2h_bytes_per_step": nbytes, "steps": ksteps,
                "api": "ps_rk_step_host (pinned host state, 1 step per call; default mode: retained modes "
                       "gathered/scattered by kernels through the device mapping, masked modes zeroed by copy "
                       "engines during the step)",
@@ -334,13 +466,13 @@ def run_ours(args, world, rank, local):
                                             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                # in place: the passes read the retained modes 5 times and write the state once
                "in_place": {"ms_per_step": round(mapped_ms, 3), "value": gpts(mapped_ms),
-                            "h2d_bytes_per_step": 5 * retained, "d2h_bytes_per_step": nbytes}}
+                            "h2d_bytes_per_step": 5 * ret_bytes, "d2h_bytes_per_step": nbytes}}
         plan.close()
         del host
     del ud, fd
     torch.cuda.empty_cache()
 
-    # ---- FP64 ------------------------------------------------------------------
+    # ---- FP64: bound by the FP64 pipe (flops against the probed FMA rate) ----
     fp64 = None
     if args.fp64_steps > 0:
         ud = torch.from_numpy(u).to(dev, torch.complex128)
@@ -348,12 +480,37 @@ def run_ours(args, world, rank, local):
         plan = ps.Plan(n, prec=ps.Precision.FP64, nu=nu, rk_order=4, forcing=fd, stream=stream)
         ms64, _ = time_steps(plan, ud, dt, args.fp64_steps, 3, stream, world, ps)
         ms64 = reduce_max(ms64, world) / args.fp64_steps
-        fp64 = {"ms_per_step": round(ms64, 3), "value": round(world * 4 * n ** 3 / (ms64 * 1e-3) / 1e9, 3),
-                "unit": UNIT, "steps": args.fp64_steps, "fp32_speedup": round(ms64 / ms_step, 2),
-                "bound": "fp64 alu (GB300 FP64 ~1.06 TFLOP/s measured by an FMA probe)"}
+        ps.ps_plan_set_timing(plan.handle, True)
+        time_steps(plan, ud, dt, 1, 0, stream, world, ps)
+        kt64 = ps.ps_plan_get_timing(plan.handle)
+        ps.ps_plan_set_timing(plan.handle, False)
         plan.close()
         del ud, fd
         torch.cuda.empty_cache()
+        peak64 = ps.ps_probe_fma_tflops(ps.Precision.FP64, stream)
+        peak32 = ps.ps_probe_fma_tflops(ps.Precision.FP32, stream)
+        fl, fl_rhs = flops_per_rhs(n, True)
+        flops_step = 4 * fl_rhs
+        achieved = flops_step / (ms64 * 1e-3) / 1e12
+        alg64 = algorithmic_bytes(n, 16)
+        bytes64 = sum(alg64[k] * kt64[k][1] for k in alg64 if k in kt64)
+        per_kernel = {}
+        for k in fl:
+            if k in kt64 and kt64[k][1] > 0:
+                t = kt64[k][0] / kt64[k][1] * 1e-3
+                per_kernel[k] = {"ms": round(t * 1e3, 3), "tflops": round(fl[k] / t / 1e12, 3),
+                                 "frac_fp64": round(fl[k] / t / 1e12 / peak64, 3),
+                                 "frac_hbm": round(alg64[k] / t / 1e9 / hbm, 3)}
+        fp64 = {"ms_per_step": round(ms64, 3), "value": round(world * 4 * n ** 3 / (ms64 * 1e-3) / 1e9, 3),
+                "unit": UNIT, "steps": args.fp64_steps, "fp32_speedup": round(ms64 / ms_step, 2),
+                "roofline": {"bound": "alu", "flops_per_step": flops_step, "achieved": round(achieved, 3),
+                             "peak": round(peak64, 3), "unit": "TFLOP/s", "frac": round(achieved / peak64, 3),
+                             "peak_source": "measured live: ps_probe_fma_tflops(FP64), FMA chains, CUDA events",
+                             "flop_model": "line transforms of the kernels' radix schedules on the retained "
+                                           "lines + pointwise work (bench.flops_per_rhs)",
+                             "hbm_frac": round(bytes64 / (ms64 * 1e-3) / 1e9 / hbm, 3),
+                             "per_kernel": per_kernel},
+                "fp32_fma_peak_tflops": round(peak32, 2)}
 
     # ---- MHD variant (u and B, twice the transforms per RHS) -----------------
     mhd = None
@@ -401,21 +558,25 @@ def run_ours(args, world, rank, local):
     if args.fp32_error_steps > 0:
         err = fp32_error_per_step(args.fp32_error_steps, dev, stream)
 
+    # ---- FP32 outputs at 256^3 for the table against the oracle ---------------
+    gpu_table = fp32_outputs(ORACLE_ERR_N, dev, stream) if ref_job is not None else None
+
     ens = None
     if not args.no_ensemble:
         ens = run_ensemble(args, dev, stream)
         torch.cuda.empty_cache()
 
-    out.update(mhd=mhd, bq=bq, err=err, ens=ens, ms_step=ms_step, launches=launches, clocks=clk.summary(), dom=dom, avg_ms=avg_ms,
-               achieved=achieved, achieved_pruned=achieved_pruned, model=model, step_model=step_model,
-               kernel_model_gbs=kernel_model_gbs,
-               hbm=hbm, peak_src=peak_src, traffic=traffic, kernel_share=kernel_share,
-               kernel_gbs=kernel_gbs, step_bytes=step_bytes, e2e=e2e, fp64=fp64, energy=e_step,
-               max_u=umax_step, alg=alg)
-    return out, u, f
+    table = None
+    if ref_job is not None:
+        finish_oracle_job(ref_job)
+        table = fp32_error_table(gpu_table, ref_dir)
+        for name in os.listdir(ref_dir):
+            os.remove(os.path.join(ref_dir, name))
+        os.rmdir(ref_dir)
 
-
-CPU_N = 256  # the oracle's sample grid: one 256^3 RHS takes ~7 s, a 512^3 one ~1 min
+    out.update(mhd=mhd, bq=bq, err=err, ens=ens, table=table, ms_step=ms_step, launches=launches,
+               clocks=clk.summary(), roof=roof, e2e=e2e, fp64=fp64, energy=e_step, max_u=umax_step)
+    return out
 
 
 def _ensemble_sizes():
@@ -430,9 +591,9 @@ def fp32_error_per_step(steps, dev, stream):
     """The forced 256^3 workload stepped in FP32 and in FP64 side by side:
     relative L2 distance of the FP32 state from the FP64 one after every step
     and the relative energy difference at the end.  The FP64 CUDA path stands
-    in for the FP64 oracle (each of its right-hand sides is held to 1e-12 of
-    the oracle by the parity tests; 100 oracle RK4 steps at 256^3 would take
-    most of an hour)."""
+    in for the FP64 oracle over the 100 steps (each of its right-hand sides
+    is held to 1e-12 of the oracle by the parity tests); the first step is
+    compared with the oracle itself by the error table."""
     import torch
     from paper_1808_01309_gb300 import ps, workloads
     w = workloads.forced(256, steps=steps)
@@ -459,6 +620,66 @@ def fp32_error_per_step(steps, dev, stream):
                                   for i in sorted(set(range(0, steps, max(1, steps // 10))) | {steps - 1})},
             "max_rel_l2": float(f"{max(errs):.3e}"), "energy_rel_diff": float(f"{abs(e32 - e64) / e64:.3e}"),
             "reference": "FP64 CUDA path (per-RHS parity with the FP64 oracle 1e-12)"}
+
+
+def fp32_outputs(n, dev, stream):
+    """FP32 CUDA outputs of the forced n^3 workload from its initial state:
+    the right-hand side, the state after one IF-RK4 step and the diagnostics
+    of both states (numpy, on the host)."""
+    import numpy as np
+    import torch
+    from paper_1808_01309_gb300 import ps, workloads
+    w = workloads.forced(n)
+    u0, f = w.initial_state(), w.forcing()
+    fd = torch.from_numpy(f).to(dev, torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=w.nu, rk_order=4, forcing=fd, stream=stream)
+    ud = torch.from_numpy(u0).to(dev, torch.complex64)
+    rhs = plan.rhs(ud).cpu().numpy().astype(np.complex128)
+    d0 = plan.diagnostics(ud)
+    plan.rk_step(ud, w.dt)
+    u1 = ud.cpu().numpy().astype(np.complex128)
+    d1 = plan.diagnostics(ud)
+    plan.close()
+    del ud, fd
+    torch.cuda.empty_cache()
+    return {"rhs": rhs, "u1": u1, "d0": d0, "d1": d1}
+
+
+def _diag_errors(g, r):
+    """Relative error of each diagnostic of the CUDA path (g) against the
+    oracle's (r); helicity relative to its Schwarz bound 2 sqrt(E Omega)."""
+    out = {}
+    for k in ("energy", "enstrophy", "max_u", "cfl_dt"):
+        out[k] = float(f"{abs(g[k] - r[k]) / abs(r[k]):.3e}")
+    out["helicity"] = float(f"{abs(g['helicity'] - r['helicity']) / (2 * math.sqrt(r['energy'] * r['enstrophy'])):.3e}")
+    spec_r = r["spectrum"]
+    spec_g = g["spectrum"][:len(spec_r)]
+    rel = [abs(a - b) / b for a, b in zip(spec_g, spec_r) if b > 1e-12 * max(spec_r)]
+    out["spectrum_max_rel"] = float(f"{max(rel):.3e}")
+    out["max_div_gpu"] = float(f"{g['max_div']:.3e}")
+    return out
+
+
+def fp32_error_table(g, ref_dir):
+    """Per-output error of the FP32 CUDA path against the FP64 oracle on the
+    forced 256^3 workload (right-hand side, state after one RK4 step,
+    diagnostics of the initial and the stepped state)."""
+    import numpy as np
+    ref = np.load(os.path.join(ref_dir, "table.npz"))
+    with open(os.path.join(ref_dir, "diag.json")) as fh:
+        rd = json.load(fh)
+
+    def field(a, b):
+        d = a - b
+        return {"rel_l2": float(f"{np.linalg.norm(d) / np.linalg.norm(b):.3e}"),
+                "max_mode_rel": float(f"{np.max(np.abs(d)) / np.max(np.abs(b)):.3e}")}
+
+    return {"workload": f"forced {ORACLE_ERR_N}^3 (seeded field + forcing, nu = 2e-3, dt = 1e-3), FP32 CUDA path "
+                        "against the FP64 oracle",
+            "rhs": field(g["rhs"], ref["rhs"]), "state_after_rk4_step": field(g["u1"], ref["u1"]),
+            "diagnostics_initial": _diag_errors(g["d0"], rd["d0"]),
+            "diagnostics_after_step": _diag_errors(g["d1"], rd["d1"]),
+            "tolerances": {"rhs_rel_l2": 2e-6, "energy_after_100_steps": 1e-4}}
 
 
 def run_ensemble(args, dev, stream):
@@ -500,22 +721,104 @@ def run_ensemble(args, dev, stream):
     return out
 
 
-def oracle_rhs_sample(u, f, n):
-    """Times one FP64 oracle right-hand side on the full n^3 field."""
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (child processes; numpy only)
+# ---------------------------------------------------------------------------
+
+def oracle_job(job: dict) -> dict:
+    """Work of one oracle child process (see start_oracle_job):
+      rhs_time        : times one oracle RHS of the forced n^3 workload
+      reference_table : the oracle's RHS, one IF-RK4 step and the diagnostics
+                        of both states of the forced n^3 workload, written to
+                        job["dir"] for the FP32 error table."""
+    import numpy as np
+
     import oracle
-    cfg = oracle.Config(n, n, n, nu=2e-3, rk_order=4)
-    t0 = time.perf_counter()
-    oracle.rhs(u, cfg, forcing=f)
-    return time.perf_counter() - t0
+    from paper_1808_01309_gb300 import workloads
+    n = int(job["n"])
+    w = workloads.forced(n)
+    u, f = w.initial_state(), w.forcing()
+    cfg = oracle.Config(n, n, n, nu=w.nu, rk_order=4)
+    if job["kind"] == "rhs_time":
+        t0 = time.perf_counter()
+        oracle.rhs(u, cfg, forcing=f)
+        return {"seconds": time.perf_counter() - t0, "n": n}
+    if job["kind"] == "reference_table":
+        rhs = oracle.rhs(u, cfg, forcing=f)
+        u1 = oracle.rk_step(u, w.dt, cfg, forcing=f)
+        d0, d1 = oracle.diagnostics(u, cfg), oracle.diagnostics(u1, cfg)
+        np.savez(os.path.join(job["dir"], "table.npz"), rhs=rhs, u1=u1)
+        js = {k: {kk: (vv.tolist() if hasattr(vv, "tolist") else vv) for kk, vv in d.items()}
+              for k, d in (("d0", d0), ("d1", d1))}
+        with open(os.path.join(job["dir"], "diag.json"), "w") as fh:
+            json.dump(js, fh)
+        return {"ok": True}
+    raise ValueError(f"unknown oracle job {job['kind']!r}")
 
 
-def cpu_sample_desc(n_cpu, n, secs):
-    return (f"one FP64 oracle RHS of the same recipe (seeded field + forcing, nu=2e-3) on a {n_cpu}^3 grid "
-            f"instead of {n}^3 ({secs:.1f} s; numpy FFT, single thread), throughput per grid point")
+def cpu_cores() -> int:
+    return os.cpu_count() or 1
+
+
+def cpu_baseline_rows(n: int):
+    """One oracle RHS of the forced n^3 workload timed in a child process with
+    one BLAS thread and with all cores; Gpoints/s per grid point."""
+    rows = {}
+    for name, threads in (("single_core", 1), ("all_cores", None)):
+        r = finish_oracle_job(start_oracle_job({"kind": "rhs_time", "n": n}, threads))
+        rows[name] = {"value": round(n ** 3 / r["seconds"] / 1e9, 6), "unit": UNIT, "seconds": round(r["seconds"], 2),
+                      "cores": 1 if threads == 1 else cpu_cores()}
+    return rows
+
+
+def cpu_sample_desc(n_cpu, n, secs, cores):
+    return (f"one FP64 oracle RHS of the same recipe (seeded field + forcing, nu = 2e-3) on a {n_cpu}^3 grid "
+            f"instead of {n}^3 ({secs:.1f} s; numpy, the oracle's own mixed-radix FFT, BLAS pool of {cores} "
+            f"thread{'s' if cores > 1 else ''}; elementwise steps single-threaded), throughput per grid point")
+
+
+def config_of(n: int, world: int) -> dict:
+    return {"workload": f"{n}^3 forced HD: seeded E(K)~K^4 exp(-2(K/4)^2) field (E=0.5), forcing on "
+                        f"2<=|k|<=3, nu=2e-3, dt=1e-3, IF-RK4, cubic 2/3 dealias, FP32 bulk + FP64 "
+                        f"reductions; step = one RK4 step = 4 RHS", "n": n, "rk_order": 4,
+            "l2": f"inputs larger than L2 (state {3 * n * n * (n // 2 + 1) * 8 / 1e9:.2f} GB, 129 MB L2), no flush",
+            "parallelism": f"replicas x{world}"}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (all of them): each
+    step is one FP64 oracle RHS of the same recipe at REF_N^3, a bounded
+    sample of the workload, so that the whole run ends within minutes."""
+    import oracle
+    nc = min(args.n, REF_N)
+    u, f = make_inputs(nc)
+    cfg = oracle.Config(nc, nc, nc, nu=2e-3, rk_order=4)
+    for _ in range(args.warmup):
+        oracle.rhs(u, cfg, forcing=f)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.rhs(u, cfg, forcing=f)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = nc ** 3 / t / 1e9
+    desc = ("each step: " + cpu_sample_desc(nc, args.n, t, cpu_cores())
+            + "; ms_per_step is the time of that sample, the work each timed step did")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args.n, args.gpus),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse_args()
+    if args.oracle_job is not None:
+        print(json.dumps(oracle_job(json.loads(args.oracle_job))), flush=True)
+        return
     world, rank, local = dist_env()
     if world > 1:
         import torch
@@ -527,73 +830,56 @@ def main():
 
     if args.impl == "reference":
         # the oracle, timed as it stands on this host (rank 0 only)
-        if rank != 0:
-            return
-        nc = min(n, CPU_N)
-        u, f = make_inputs(nc)
-        for _ in range(min(args.warmup, 1)):
-            oracle_rhs_sample(u, f, nc)
-        times = [oracle_rhs_sample(u, f, nc) for _ in range(args.steps)]
-        t = statistics.median(times)
-        value = nc ** 3 / t / 1e9
-        line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(4 * t * 1e3, 1),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": f"{n}^3 forced HD, IF-RK4, nu=2e-3, dt=1e-3 (FP64 numpy oracle)",
-                           "n": n},
-                "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": "each step: " + cpu_sample_desc(nc, n, t)
-                                           + "; ms_per_step = 4 RHS at that size"},
-                "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        if rank == 0:
+            run_reference(args)
         return
 
-    res, u, f = run_ours(args, world, rank, local)
+    res = run_ours(args, world, rank, local)
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         nc = min(n, CPU_N)
-        uc, fc = (u, f) if nc == n else make_inputs(nc)
-        t = min(oracle_rhs_sample(uc, fc, nc) for _ in range(2))
-        cpu = {"value": round(nc ** 3 / t / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "best of two: " + cpu_sample_desc(nc, n, t)}
+        rows = cpu_baseline_rows(nc)
+        a = rows["all_cores"]
+        cpu = {"value": a["value"], "unit": UNIT, "cores": a["cores"], "kind": "oracle",
+               "sample": cpu_sample_desc(nc, n, a["seconds"], a["cores"]),
+               "single_core": {"value": rows["single_core"]["value"], "cores": 1,
+                               "seconds": rows["single_core"]["seconds"]}}
     ms = res["ms_step"]
     value = world * 4 * n ** 3 / (ms * 1e-3) / 1e9
-    frac = res["achieved"] / res["hbm"]
+    r = res["roof"]
+    hbm = r["hbm"]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{n}^3 forced HD: seeded E(K)~K^4 exp(-2(K/4)^2) field (E=0.5), forcing on "
-                               f"2<=|k|<=3, nu=2e-3, dt=1e-3, IF-RK4, cubic 2/3 dealias, FP32 bulk + FP64 "
-                               f"reductions; step = one RK4 step = 4 RHS", "n": n, "rk_order": 4,
-                   "l2": f"inputs larger than L2 (state {3 * n * n * (n // 2 + 1) * 8 / 1e9:.2f} GB, "
-                         f"129 MB L2), no flush",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": res["dom"], "achieved": round(res["achieved"], 1),
-                     "peak": res["hbm"], "unit": "GB/s", "frac": round(frac, 4),
-                     "peak_source": f"{res['peak_src']} (MEASURED_PEAKS.json hbm_gbs)" if res["peak_src"] == "measured"
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(n, world),
+        "roofline": {"bound": "hbm", "kernel": r["dom"], "achieved": round(r["achieved"], 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(r["achieved"] / hbm, 4),
+                     "traffic": r["traffic"],
+                     "algorithmic_bytes": r["alg"],
+                     "bytes_model": "compulsory bytes of the pruned passes: each pass reads its input and writes "
+                                    "its output once, retained modes and lines only (bench.algorithmic_bytes)",
+                     "peak_source": f"{r['peak_src']} (MEASURED_PEAKS.json hbm_gbs)" if r["peak_src"] == "measured"
                      else "fallback 6800 GB/s",
-                     "traffic": res["traffic"],
-                     # model bytes of the unpruned fused schedule (42 S per RHS, 198 S per RK4 step)
-                     "algorithmic_bytes": res["model"][res["dom"]],
-                     "avg_launch_ms": round(res["avg_ms"], 4),
-                     "kernel_share": res["kernel_share"], "kernel_model_gbs": res["kernel_model_gbs"],
-                     "step_model_bytes": res["step_model"],
-                     "step_frac": round(res["step_model"] / (ms * 1e-3) / 1e9 / res["hbm"], 4),
-                     # the same against the compulsory bytes of this pruned design (retained modes only)
-                     "pruned": {"algorithmic_bytes": res["alg"][res["dom"]],
-                                "achieved": round(res["achieved_pruned"], 1),
-                                "frac": round(res["achieved_pruned"] / res["hbm"], 4),
-                                "kernel_alg_gbs": res["kernel_gbs"], "step_alg_bytes": res["step_bytes"],
-                                "step_frac": round(res["step_bytes"] / (ms * 1e-3) / 1e9 / res["hbm"], 4)}},
+                     "avg_launch_ms": round(r["avg_ms"], 4),
+                     "kernel_ms": r["kernel_ms"], "kernel_share": r["kernel_share"],
+                     "kernel_alg_gbs": r["kernel_gbs"], "kernel_frac": r["kernel_frac"],
+                     "step_alg_bytes": r["step_bytes"],
+                     "step_frac": round(r["step_bytes"] / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "split_pass": {"steps": r["split_steps"], "ms_per_step": round(r["split_ms_per_step"], 3),
+                                    "note": "per-kernel times from a separate pass with the plan's per-kernel "
+                                            "events; the headline steps run without them"},
+                     # the unpruned 42 S / 198 S model, for context only
+                     "dense_model": {"algorithmic_bytes": r["dense"], "achieved": round(r["dense_achieved"], 1),
+                                     "frac": round(r["dense_achieved"] / hbm, 4), "step_bytes": r["step_dense"],
+                                     "step_frac": round(r["step_dense"] / (ms * 1e-3) / 1e9 / hbm, 4)}},
         "cpu_baseline": cpu,
         "e2e": res["e2e"],
         "fp64": res["fp64"],
         "mhd": res["mhd"],
         "boussinesq": res["bq"],
+        "fp32_vs_oracle_256": res["table"],
         "fp32_error_256": res["err"],
         "ensemble": res["ens"],
         "clocks": res["clocks"],

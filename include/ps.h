@@ -216,6 +216,18 @@ ps_status ps_plan_get_timing(ps_plan* plan, ps_timing* out);
 /* Number of kernels this plan has launched since creation. */
 ps_status ps_plan_launch_count(ps_plan* plan, long long* launches);
 
+/* Test hook for the failure path of the bounded device waits (the paper has
+ * no counterpart).  With polls > 0, every CTA of the x pass of the plan's
+ * following right-hand sides waits for a copy that is never issued and gives
+ * up after `polls` polls of its barrier (instead of the default 2^26): the
+ * pass records PS_ERR_TIMEOUT in the plan's device error word, the update
+ * kernel writes NaN into every retained output of that right-hand side, and
+ * the next synchronising call (ps_step_stats, ps_diagnostics, ps_rk_step_host,
+ * ...) returns PS_ERR_TIMEOUT once and clears the word.  No fault, trap or
+ * hang is involved and the context stays usable.  polls = 0 (the default)
+ * turns the hook off; polls outside [0, 2^20] returns PS_ERR_INVALID_ARG. */
+ps_status ps_plan_set_wait_test(ps_plan* plan, int polls);
+
 /* Name of a kernel kind of ps_timing (0..PS_NKINDS-1), or "?". */
 const char* ps_kind_name(int kind);
 
@@ -381,7 +393,7 @@ ps_status ps_fft_c2r(int n, int nfields, const void* spec, float* phys, void* cu
  * and describes no format; this is one.  A checkpoint file is a 136-byte
  * little-endian header followed by the state exactly as in device memory
  * (the ABI layout above, ncomp * nz * ny * (nx/2+1) complex values):
- *   off   0: magic "PSCKPT "   off   8: uint32 version (1)
+ *   off   0: magic "PSCKPT" then the bytes 0x00 0x01   off   8: uint32 version (1)
  *   off  12: uint32 header bytes (136)
  *   off  16: int32 nx, ny, nz, prec, eq, dealias, rk_order, ncomp
  *   off  48: double lx, ly, lz, nu, eta, n_bv, kappa, t
@@ -413,20 +425,36 @@ ps_status ps_checkpoint_info(const char* path, ps_config* cfg, double* t, long l
  * device to its own pool allocator, a plugin or callback that must keep the
  * memory footprint fixed, or code that cannot accept the synchronisation
  * cudaMalloc/cudaFree may cause.  The paper has no counterpart of this call.
- *   cfg         : as for ps_plan_create (the forcing pointer, if any, is read
- *                 during the call)
+ *   cfg         : as for ps_plan_create; the forcing buffer, if any, is read
+ *                 by the kernels queued on cuda_stream, so it must stay valid
+ *                 and unchanged until that work has completed, like uhat
  *   cuda_stream : cudaStream_t the kernels run on (NULL = legacy default)
  *   uhat, rhs_out, t : as for ps_rhs (device buffers, must not overlap)
  * Scratch: one file-scope __device__ array of PS_NOALLOC_SCRATCH_BYTES that
  * every GPU loading this library holds until exit (enough for a 64^3 grid in
  * FP32 or FP64, with forcing).  A grid needing more returns
  * PS_ERR_INVALID_ARG, with the sizes in ps_last_error(), before any launch.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and each overwrites it, nothing in
- * it needs to start at zero, and calls whose kernels overlap on the GPU race
- * on it: serialise them (one stream, or events).  Asynchronous. */
+ * Every call looks up the array's device address with the device current
+ * (the first call on a device may also load the library's device code, so
+ * make it before any stream capture).  All calls share the one array and
+ * each overwrites it; the one word in it that must start at zero (the error
+ * word of the x pass's bounded waits) is cleared by every call; calls whose
+ * kernels overlap on the GPU race on it: serialise them (one stream, or
+ * events).  Asynchronous: a bounded device wait that gives up cannot be
+ * reported as a status here (there is no later synchronising call), so it
+ * turns every retained mode of rhs_out into NaN instead. */
 ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, const void* uhat, void* rhs_out, double t);
+
+/* ---- Measurement ------------------------------------------------------------
+ * Fused multiply-add rate of the current device in TFLOP/s (2 flops per FMA)
+ * for prec (PS_FP32 or PS_FP64): eight independent FMA chains per thread, 8
+ * CTAs of 256 threads per SM, best of five timed launches after one warm-up,
+ * CUDA events on cuda_stream (NULL = legacy default).  The denominator of the
+ * arithmetic roofline of the FP64 passes, which the GPU's FP64 rate bounds
+ * rather than HBM (the paper has no counterpart).  Synchronises the stream;
+ * allocates nothing and changes no device setting.  *tflops receives the
+ * rate; PS_ERR_INVALID_ARG for a NULL pointer or an unknown precision. */
+ps_status ps_probe_fma_tflops(ps_precision prec, void* cuda_stream, double* tflops);
 
 const char* ps_status_string(ps_status s);
 const char* ps_last_error(void);

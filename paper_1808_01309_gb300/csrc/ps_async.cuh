@@ -2,8 +2,10 @@
 //   - 1D bulk copies by the tensor-memory-access (TMA) unit completing on an
 //     mbarrier (cp.async.bulk ... mbarrier::complete_tx::bytes),
 //   - per-thread 8-byte cp.async for strided tiles (8-byte aligned rows).
-// Every wait is bounded: after PS_WAIT_LIMIT polls it gives up and the caller
-// records an error instead of hanging the GPU.
+// Every wait is bounded: after a limit of polls (PS_WAIT_LIMIT unless the
+// caller passes another) it gives up and the caller records an error instead
+// of hanging the GPU.  A CTA that gave up still waits, up to PS_DRAIN_LIMIT
+// polls, for a copy it has in flight before it exits.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,6 +14,9 @@ namespace ps {
 
 #ifndef PS_WAIT_LIMIT
 #define PS_WAIT_LIMIT (1u << 26)
+#endif
+#ifndef PS_DRAIN_LIMIT
+#define PS_DRAIN_LIMIT (1u << 27)
 #endif
 
 // Error codes written to the plan's device error word.
@@ -36,10 +41,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Polls the barrier until the phase with the given parity has completed.
-// Returns false if it gave up after PS_WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Returns false if it gave up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = PS_WAIT_LIMIT) {
   const uint32_t a = smem_addr(bar);
-  for (uint32_t i = 0; i < PS_WAIT_LIMIT; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

@@ -69,6 +69,8 @@ struct PassArgs {
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
   int xrpc;          // x pass rows per CTA (0 = largest that keeps two CTAs per SM)
   int* err;          // device error word (bounded waits that gave up), never null
+  unsigned wait_polls;  // x pass: polls before a wait gives up (0 = PS_WAIT_LIMIT)
+  int wait_test;     // x pass: test hook, the first copy of every CTA is never issued
   const void* extra; // compact closure term added to the velocity group before projection, or null
 };
 

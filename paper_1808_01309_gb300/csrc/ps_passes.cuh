@@ -382,18 +382,26 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v),
   };
   uint32_t ph = 0u;  // completed-phase parity of the stage barrier
   long long it = blockIdx.x;
-  if (tid == 0 && it < ngroups) issue(it);
+  const uint32_t polls = a.wait_polls ? a.wait_polls : PS_WAIT_LIMIT;
+  // thread 0: a copy into the stage is in flight (the test hook never issues
+  // the first one, so that the wait below runs out)
+  bool inflight = false;
+  if (tid == 0 && it < ngroups && !a.wait_test) {
+    issue(it);
+    inflight = true;
+  }
   T umax2 = 0;
   while (it < ngroups) {
     const long long nxt = it + gridDim.x;
     const uint32_t cur = ph;
     ph ^= 1u;
-    if (!mbar_wait(&bar[0], cur)) abort_flag = 1;
+    if (!mbar_wait(&bar[0], cur, polls)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
       if (tid == 0) {
         atomicExch(a.err, PS_DEV_TIMEOUT_XPASS);
-        mbar_wait(&bar[0], cur);  // bounded: let a late copy land before the CTA exits
+        // bounded: let a copy still in flight land before the CTA exits
+        if (inflight) mbar_wait(&bar[0], cur, PS_DRAIN_LIMIT);
       }
       break;
     }
@@ -432,9 +440,12 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v),
     }
     // every thread has its points: the stage takes the next group's rows
     __syncthreads();
-    if (tid == 0 && nxt < ngroups) {
-      fence_proxy_async();
-      issue(nxt);
+    if (tid == 0) {
+      inflight = nxt < ngroups;
+      if (inflight) {
+        fence_proxy_async();
+        issue(nxt);
+      }
     }
     if constexpr (HD) {
       line_fft_rows<N, E, +1>(U, j0, tw, ex);
@@ -666,6 +677,9 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     }
     return;
   }
+  // a bounded wait of this right-hand side gave up: its nonlinear term is
+  // incomplete, so every retained output becomes NaN instead of a wrong value
+  const bool failed = *a.err != 0;
   const int iy = rowof(q, g.cy), iz = rowof(r, g.cz);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
   const long long ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
@@ -731,6 +745,10 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
       kk[0] = v0;
       kk[1] = v1;
       kk[2] = v2;
+    }
+    if (failed) {
+      const T qnan = T(NAN);
+      kk[0] = kk[1] = kk[2] = mk<V>(qnan, qnan);
     }
     const V* pu = static_cast<const V*>(a.u_n.p) + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
                   (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;

@@ -142,6 +142,7 @@ struct ps_plan {
   cudaStream_t stream = nullptr;
   int device = 0;
   int xrpc = 0;  // x-pass rows per CTA override (0 = automatic)
+  unsigned wait_test_polls = 0;  // ps_plan_set_wait_test: 0 = off
   // learned LES closure (ps_plan_set_closure)
   bool les_on = false;
   ps::LesScratch les{};
@@ -303,6 +304,8 @@ PassArgs base_args(ps_plan* p) {
   a.acc = p->acc;
   a.err = p->err;
   a.xrpc = p->xrpc;
+  a.wait_test = p->wait_test_polls ? 1 : 0;
+  a.wait_polls = p->wait_test_polls;
   return a;
 }
 
@@ -311,7 +314,12 @@ ps_status check_device_error(ps_plan* p) {
   int e = 0;
   PS_CU(cudaMemcpyAsync(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream), "error word");
   PS_CU(cudaStreamSynchronize(p->stream), "error word");
-  if (e != 0) return fail(PS_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy never completed)");
+  if (e != 0) {
+    // reported once: the word is cleared so that the plan's next calls start clean
+    PS_CU(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream), "error word");
+    PS_CU(cudaStreamSynchronize(p->stream), "error word");
+    return fail(PS_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy never completed)");
+  }
   return PS_OK;
 }
 
@@ -880,6 +888,13 @@ ps_status ps_plan_set_timing(ps_plan* p, int enable) {
     p->n_acc[k] = 0;
   }
   p->timing = enable != 0;
+  return PS_OK;
+}
+
+ps_status ps_plan_set_wait_test(ps_plan* p, int polls) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  if (polls < 0 || polls > (1 << 20)) return fail(PS_ERR_INVALID_ARG, "polls must be in [0, 2^20]");
+  p->wait_test_polls = (unsigned)polls;
   return PS_OK;
 }
 

@@ -10,7 +10,6 @@
 // paper has no counterpart of this entry point.
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "ps.h"
@@ -28,26 +27,16 @@ namespace {
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
 // Device address of g_noalloc_scratch on the current device.  In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// symbol is only a host-side stand-in, so the address is looked up with the
+// device current.  The lookup is repeated on every call (it is cheap), so an
+// address never outlives the context it belongs to (after cudaDeviceReset the
+// next call finds the array of the new context).
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -123,7 +112,7 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   const size_t b_b = up256((b1 > b2 ? b1 : b2) * vb);
   const size_t tw_b = up256((size_t)(g.nx + g.ny + g.nz) * vb);
   const size_t box_b = c->forcing ? up256(3ull * g.cz * g.cy * g.cx * vb) : 0;
-  const size_t err_b = 256;  // error word of bounded device waits (written, never read here)
+  const size_t err_b = 256;  // error word of the x pass's bounded waits, cleared by every call
   const size_t need = a_b + b_b + tw_b + box_b + err_b;
   if (need > (size_t)PS_NOALLOC_SCRATCH_BYTES) {
     char msg[256];
@@ -165,6 +154,9 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   a.out_full = out;
   a.mode = ZF_RHS;
 
+  // the previous call's error word: a wait that gave up then must not turn
+  // this call's output into NaN (the update kernel reads the word)
+  if ((e = cudaMemsetAsync(a.err, 0, sizeof(int), s)) != cudaSuccess) return cuda_bad(e, "error word");
   const int ntw = g.nx + g.ny + g.nz;
   k_twiddles<V><<<(ntw + 255) / 256, 256, 0, s>>>(tw, g.nx, g.ny, g.nz);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_bad(e, "twiddles");

@@ -54,7 +54,7 @@ SYMBOLS = (
     "ps_plan_set_closure", "ps_les_training_sample", "ps_mlp_grad_tb",
     "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
     "ps_plan_closure_grad_transfer", "ps_checkpoint_save", "ps_checkpoint_load", "ps_checkpoint_info",
-    "ps_fft_r2c", "ps_fft_c2r",
+    "ps_fft_r2c", "ps_fft_c2r", "ps_probe_fma_tflops", "ps_plan_set_wait_test",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -148,6 +148,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_plan_closure_grad.argtypes = [P, P, P, P, P, P, ctypes.c_int]
     lib.ps_les_filter.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
     lib.ps_mlp_grad_tb.argtypes = [P, P, P, P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, P, P, P]
+    lib.ps_probe_fma_tflops.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
+    lib.ps_plan_set_wait_test.argtypes = [P, ctypes.c_int]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -229,6 +231,19 @@ def ps_rk_steps(plan, uhat, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
     _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_plan_set_wait_test(plan, polls: int) -> None:
+    """Test hook: the x pass waits for a copy that never comes and gives up
+    after `polls` polls (0 turns the hook off)."""
+    _check(load().ps_plan_set_wait_test(plan, int(polls)))
+
+
+def ps_probe_fma_tflops(prec: int, stream=None) -> float:
+    """Measured FMA rate of the device in TFLOP/s (FP32 or FP64)."""
+    out = ctypes.c_double()
+    _check(load().ps_probe_fma_tflops(int(prec), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def ps_fft_r2c(n: int, nfields: int, phys, spec, stream=None) -> None:

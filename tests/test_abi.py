@@ -120,3 +120,12 @@ def test_plain_transforms_check_their_arguments(ps, n, nf):
     assert lib.ps_fft_c2r(n, nf, 1, 2, None) == ps.PS_ERR_INVALID_ARG
     assert lib.ps_fft_r2c(64, 1, None, None, None) == ps.PS_ERR_INVALID_ARG
 
+
+
+def test_test_hook_and_probe_reject_bad_arguments_on_the_host(ps):
+    lib = ps.load()
+    assert lib.ps_plan_set_wait_test(None, 10) == ps.PS_ERR_INVALID_ARG
+    assert lib.ps_probe_fma_tflops(1, None, None) == ps.PS_ERR_INVALID_ARG
+    import ctypes
+    out = ctypes.c_double()
+    assert lib.ps_probe_fma_tflops(7, None, ctypes.byref(out)) == ps.PS_ERR_INVALID_ARG

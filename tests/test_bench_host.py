@@ -83,9 +83,45 @@ def test_roofline_model_bytes_add_up_to_the_step_model():
     spec.loader.exec_module(b)
     n = 512
     S = n * n * (n // 2 + 1) * 8
-    model, step = b.model_bytes(n, 8)
+    model, step = b.dense_model_bytes(n, 8)
     assert step == 198 * S
     assert abs(4 * sum(model.values()) - step) < 1e-6 * step
     assert sum(model[k] for k in model if k != "update") == 42 * S
     pruned = b.algorithmic_bytes(n, 8)
     assert all(pruned[k] < model[k] for k in model)
+
+
+def test_flop_model_of_the_line_transforms():
+    """The in-register DFT counts follow the radix-2 network (R/2 log2 R
+    butterflies of 4 flops plus the non-trivial twiddles), and a 512-point
+    line of the radix-8 schedule costs 3 stages of 64 radix-8 DFTs plus two
+    stages of 7 twiddle multiplications per butterfly."""
+    assert bench.dft_flops(2) == 4
+    assert bench.dft_flops(4) == 16
+    assert bench.dft_flops(8) == 12 * 4 + 2 * 4
+    assert bench.line_flops(512, True) == 3 * 64 * 56 + 2 * 64 * 7 * 6
+    f, total = bench.flops_per_rhs(512, True)
+    assert total == sum(f.values()) and 4.5e10 < total < 5.0e10
+    # every kernel schedule in the table has radices multiplying to the length
+    import math as m
+    for (e, n), radices in bench.SCHED.items():
+        assert m.prod(radices) == n and radices[0] <= e
+
+
+def test_oracle_child_job_times_one_rhs():
+    r = bench.finish_oracle_job(bench.start_oracle_job({"kind": "rhs_time", "n": 16}, 1), timeout=300)
+    assert r["n"] == 16 and r["seconds"] > 0
+
+
+def test_reference_arm_reports_our_config():
+    """The reference arm runs the oracle as it stands on a bounded sample and
+    reports it under the same config as the GPU arm."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--n", "32"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"] == bench.config_of(32, 1)
+    assert line["cpu_baseline"]["cores"] >= 1 and line["value"] > 0
+    assert abs(line["steps"] * line["ms_per_step"] - 1e3 * 32 ** 3 / line["value"] / 1e9) < 1.0

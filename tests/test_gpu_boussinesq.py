@@ -10,6 +10,8 @@ import pytest
 import oracle
 from paper_1808_01309_gb300 import inputs
 
+from .parity import assert_parity
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +56,7 @@ def test_boussinesq_rhs_matches_oracle(ps, prec, shape):
                    **kw, **box)
     assert plan.shape == (4, nz, ny, nx // 2 + 1)
     got = plan.rhs(torch.from_numpy(st).to("cuda", dt)).cpu().numpy().astype(np.complex128)
-    assert relerr(got, ref) < TOL[prec]
+    assert_parity(got, ref, TOL[prec], "boussinesq rhs")
     assert relerr(got[3], ref[3]) < TOL[prec]  # the scalar alone
     assert np.all(got[:, ~oracle.dealias_mask(cfg)] == 0)
     plan.close()
@@ -77,7 +79,7 @@ def test_boussinesq_rk_steps_match_oracle(ps, prec, order):
     d = torch.from_numpy(st).to("cuda", dtype)
     for i in range(3):
         plan.rk_step(d, dt, t=i * dt)
-    assert relerr(d.cpu().numpy().astype(np.complex128), ref) < TOL[prec]
+    assert_parity(d.cpu().numpy().astype(np.complex128), ref, TOL[prec], "boussinesq step")
     plan.close()
 
 
@@ -139,7 +141,7 @@ def test_boussinesq_rhs_256_fp32_matches_oracle(ps):
     plan = ps.Plan(n, prec=ps.Precision.FP32, eq=ps.Equations.BOUSSINESQ, rk_order=4,
                    forcing=torch.from_numpy(f).to("cuda", torch.complex64), **kw)
     got = plan.rhs(torch.from_numpy(st).to("cuda", torch.complex64)).cpu().numpy().astype(np.complex128)
-    assert relerr(got, ref) < 2e-6
+    assert_parity(got, ref, 2e-6, "boussinesq rhs 256")
     plan.close()
 
 

@@ -9,6 +9,8 @@
 * 100 IF-RK4 steps in FP32: total energy within 1e-4 of the FP64 oracle
   (64^3, oracle run in full) and of the FP64 CUDA path (256^3, whose every
   RHS is itself held to 1e-12 of the oracle by test_gpu_parity).
+* The 256^3 workload in FP32 against the oracle itself for its right-hand
+  side and its first two RK4 steps, mode by mode.
 """
 
 import math
@@ -20,6 +22,7 @@ import oracle
 from paper_1808_01309_gb300 import inputs
 
 from . import exact_fourier as xf
+from .parity import assert_parity
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,7 +53,7 @@ def test_bench_workload_rhs_512_matches_oracle(ps):
     del ud, fd, out
     torch.cuda.empty_cache()
     ref = oracle.rhs(u, oracle.Config(n, n, n, nu=nu), forcing=f)
-    assert relerr(got.astype(np.complex128), ref) < 2e-6
+    assert_parity(got.astype(np.complex128), ref, 2e-6, "512^3 rhs")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -120,3 +123,35 @@ def test_fp32_state_error_per_step_256(ps):
     assert r["max_rel_l2"] < 1e-4
     assert r["energy_rel_diff"] < 1e-4
 
+
+
+def test_fp32_rk4_steps_256_match_oracle(ps):
+    """The forced 256^3 workload in FP32 against the FP64 oracle itself, mode
+    by mode: the right-hand side and the states after the first two IF-RK4
+    steps (relative L2 and per-mode bound 2e-6), and the diagnostics of the
+    stepped state."""
+    n, nu, dt = 256, 2e-3, 1e-3
+    u = inputs.random_solenoidal_field(n, n, n, seed=1)
+    f = inputs.forcing_field(n, n, n, seed=2)
+    cfg = oracle.Config(n, n, n, nu=nu, rk_order=4)
+    ud = torch.from_numpy(u).to("cuda", torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, rk_order=4,
+                   forcing=torch.from_numpy(f).to("cuda", torch.complex64))
+    got_rhs = plan.rhs(ud).cpu().numpy().astype(np.complex128)
+    got = []
+    for i in range(2):
+        plan.rk_step(ud, dt, t=i * dt)
+        got.append(ud.cpu().numpy().astype(np.complex128))
+    d_gpu = plan.diagnostics(ud)
+    plan.close()
+    del ud
+    torch.cuda.empty_cache()
+    assert_parity(got_rhs, oracle.rhs(u, cfg, forcing=f), 2e-6, "256^3 rhs")
+    ref = u
+    for i in range(2):
+        ref = oracle.rk_step(ref, dt, cfg, forcing=f)
+        assert_parity(got[i], ref, 2e-6, f"256^3 state after step {i + 1}")
+    d = oracle.diagnostics(ref, cfg)
+    for key in ("energy", "enstrophy", "max_u", "cfl_dt"):
+        assert abs(d_gpu[key] - d[key]) <= 2e-6 * abs(d[key]), key
+    assert abs(d_gpu["helicity"] - d["helicity"]) <= 2e-6 * 2 * math.sqrt(d["energy"] * d["enstrophy"])

@@ -11,6 +11,8 @@ import pytest
 import oracle
 from paper_1808_01309_gb300 import inputs
 
+from .parity import assert_parity
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +87,7 @@ def test_rhs_matches_oracle(ps, prec, case):
     before = ud.clone()
     out = plan.rhs(ud)
     got = to_np(out)
-    assert relerr(got, ref) < TOL[prec]
+    assert_parity(got, ref, TOL[prec], "rhs")
     # masked modes are exactly zero, the input is untouched
     mask = oracle.dealias_mask(cfg)
     assert np.all(got[:, ~mask] == 0)
@@ -111,7 +113,7 @@ def test_rk_step_matches_oracle(ps, prec, order, n3):
     for i in range(3):
         plan.rk_step(ud, dt, t=i * dt)
     got = to_np(ud)
-    assert relerr(got, ref) < TOL[prec]
+    assert_parity(got, ref, TOL[prec], "rk step")
     # stats of the state at the start of the last step
     prev = u
     for i in range(2):
@@ -161,7 +163,7 @@ def test_taylor_green_config(ps):
     for i in range(10):
         plan.rk_step(ud, dt, t=i * dt)
     got = to_np(ud)
-    assert relerr(got, ref) < 1e-12
+    assert_parity(got, ref, 1e-12, "taylor-green steps")
     d = plan.diagnostics(ud)
     assert abs(d["energy"] - oracle.diagnostics(ref, cfg)["energy"]) < 1e-14
     plan.close()
