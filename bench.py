@@ -77,6 +77,10 @@ def parse_args():
     ap.add_argument("--fp32-error-steps", type=int, default=100)
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--oracle-job", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--kernel-case", default=None,
+                    help="small profiling case 'nx,ny,nz[,fp64]': run --reps right-hand sides of the seeded "
+                         "random field on that grid and exit (for ncu captures of one kernel)")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -814,10 +818,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def kernel_case(spec: str, reps: int) -> None:
+    """Right-hand sides of the seeded random field (with forcing) on a small
+    grid, one after the other on the default stream: the launch sequence of
+    the bench's passes at a size that an ncu capture of one kernel handles
+    quickly (e.g. 512,512,128 for the x and y passes with 512-point lines,
+    256,128,512 for the z passes)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_01309_gb300 import inputs, ps
+    parts = spec.split(",")
+    nx, ny, nz = (int(v) for v in parts[:3])
+    fp64 = len(parts) > 3 and parts[3] == "fp64"
+    P, dt = (ps.Precision.FP64, torch.complex128) if fp64 else (ps.Precision.FP32, torch.complex64)
+    u = torch.from_numpy(inputs.random_solenoidal_field(nx, ny, nz, seed=1)).to("cuda", dt)
+    f = torch.from_numpy(inputs.forcing_field(nx, ny, nz, seed=2)).to("cuda", dt)
+    plan = ps.Plan(nx, ny, nz, prec=P, nu=2e-3, rk_order=4, forcing=f)
+    out = torch.empty_like(u)
+    for _ in range(reps):
+        plan.rhs(u, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": spec, "reps": reps, "rhs_norm": float(torch.linalg.vector_norm(out))}))
+    plan.close()
+
+
 def main():
     args = parse_args()
     if args.oracle_job is not None:
         print(json.dumps(oracle_job(json.loads(args.oracle_job))), flush=True)
+        return
+    if args.kernel_case is not None:
+        kernel_case(args.kernel_case, args.reps)
         return
     world, rank, local = dist_env()
     if world > 1:
