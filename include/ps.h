@@ -38,6 +38,9 @@
  * torch.fft.rfftn / numpy.fft.rfftn of a real (nz, ny, nx) array per
  * component.  Components: 3 (u) for PS_HD, 6 (u, B) for PS_MHD, 4 (u, theta)
  * for PS_BOUSSINESQ.  Field bytes: ncomp * nz * ny * (nx/2+1) * (8 or 16).
+ * Every device field must start on a multiple of its element size (8 bytes
+ * in FP32, 16 in FP64; cudaMalloc and torch allocations are); a misaligned
+ * pointer returns PS_ERR_INVALID_ARG before any launch.
  *
  * Ownership: the caller owns the state, right-hand-side and forcing buffers.
  * The plan owns its scratch (intermediate fields, twiddles, stage registers).

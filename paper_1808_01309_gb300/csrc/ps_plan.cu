@@ -5,6 +5,7 @@
 #include <cmath>
 #include <new>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -60,6 +61,8 @@ ps_status validate(const ps_config* c) {
   if (c->dealias != PS_DEALIAS_CUBIC && c->dealias != PS_DEALIAS_SPHERICAL && c->dealias != PS_DEALIAS_NONE)
     return fail(PS_ERR_INVALID_ARG, "unknown dealias rule");
   if (c->rk_order != 2 && c->rk_order != 4) return fail(PS_ERR_INVALID_ARG, "rk_order must be 2 or 4");
+  if (c->forcing && reinterpret_cast<uintptr_t>(c->forcing) % (c->prec == PS_FP32 ? 8 : 16))
+    return fail(PS_ERR_INVALID_ARG, "the forcing buffer must be aligned to the complex element size");
   if (!(std::isfinite(c->nu) && c->nu >= 0)) return fail(PS_ERR_INVALID_ARG, "nu must be finite and >= 0");
   return PS_OK;
 }
@@ -428,6 +431,10 @@ ps_status do_diag(ps_plan* p, const void* uhat, double* host_out) {
   return PS_OK;
 }
 
+// Device fields must start on a multiple of their complex element size (the
+// passes copy whole elements, 16 bytes at a time in FP64).
+bool misaligned(const void* ptr, size_t vb) { return (reinterpret_cast<uintptr_t>(ptr) % vb) != 0; }
+
 bool ranges_overlap(const void* a, const void* b, size_t n) {
   const char* x = static_cast<const char*>(a);
   const char* y = static_cast<const char*>(b);
@@ -624,6 +631,8 @@ ps_status ps_plan_destroy(ps_plan* p) {
 ps_status ps_rhs(ps_plan* p, const void* uhat, void* rhs_out, double t) {
   (void)t;
   if (!p || !uhat || !rhs_out) return fail(PS_ERR_INVALID_ARG, "NULL plan or buffer");
+  if (misaligned(uhat, p->sz.vb) || misaligned(rhs_out, p->sz.vb))
+    return fail(PS_ERR_INVALID_ARG, "uhat and rhs_out must be aligned to the complex element size");
   if (ranges_overlap(uhat, rhs_out, p->sz.state * p->sz.vb))
     return fail(PS_ERR_INVALID_ARG, "rhs_out overlaps uhat");
   DeviceGuard dg(p->device);
@@ -632,6 +641,7 @@ ps_status ps_rhs(ps_plan* p, const void* uhat, void* rhs_out, double t) {
 
 ps_status ps_rk_step(ps_plan* p, void* uhat, double dt, double t) {
   if (!p || !uhat) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
+  if (misaligned(uhat, p->sz.vb)) return fail(PS_ERR_INVALID_ARG, "uhat must be aligned to the complex element size");
   if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
   DeviceGuard dg(p->device);
   ps_status s = p->cfg.prec == PS_FP32 ? do_rk_step<float>(p, uhat, dt) : do_rk_step<double>(p, uhat, dt);
@@ -706,6 +716,7 @@ cudaError_t zero_outside_cube(ps_plan* p, char* host) {
 
 ps_status ps_rk_steps(ps_plan* p, void* uhat, double dt, double t, int nsteps) {
   if (!p || !uhat) return fail(PS_ERR_INVALID_ARG, "NULL plan or state");
+  if (misaligned(uhat, p->sz.vb)) return fail(PS_ERR_INVALID_ARG, "uhat must be aligned to the complex element size");
   if (nsteps < 0) return fail(PS_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!std::isfinite(dt) || !std::isfinite(t)) return fail(PS_ERR_INVALID_ARG, "dt and t must be finite");
   if (nsteps == 0) return PS_OK;
@@ -849,6 +860,7 @@ ps_status ps_step_stats(ps_plan* p, double* energy, double* max_u) {
 
 ps_status ps_diagnostics(ps_plan* p, const void* uhat, double cfl, ps_diag* out) {
   if (!p || !uhat || !out) return fail(PS_ERR_INVALID_ARG, "NULL plan, state or output");
+  if (misaligned(uhat, p->sz.vb)) return fail(PS_ERR_INVALID_ARG, "uhat must be aligned to the complex element size");
   if (!std::isfinite(cfl)) return fail(PS_ERR_INVALID_ARG, "cfl must be finite");
   if (out->spectrum && out->nshells < 0) return fail(PS_ERR_INVALID_ARG, "negative spectrum capacity");
   DeviceGuard dg(p->device);

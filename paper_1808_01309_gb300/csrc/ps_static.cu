@@ -9,6 +9,7 @@
 // file-scope device array below, whose size is fixed at build time.  The
 // paper has no counterpart of this entry point.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <string>
 
@@ -198,6 +199,10 @@ extern "C" ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, con
     return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: unknown dealias rule");
   if (!(std::isfinite(cfg->nu) && cfg->nu >= 0)) return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: nu");
   const size_t bytes = 3ull * cfg->nz * cfg->ny * (cfg->nx / 2 + 1) * (cfg->prec == PS_FP32 ? 8 : 16);
+  const size_t vb = cfg->prec == PS_FP32 ? 8 : 16;
+  if (reinterpret_cast<uintptr_t>(uhat) % vb || reinterpret_cast<uintptr_t>(rhs_out) % vb ||
+      (cfg->forcing && reinterpret_cast<uintptr_t>(cfg->forcing) % vb))
+    return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: buffers must be aligned to the complex element size");
   const char* x = static_cast<const char*>(uhat);
   const char* y = static_cast<const char*>(rhs_out);
   if (x < y + bytes && y < x + bytes) return bad(PS_ERR_INVALID_ARG, "ps_rhs_noalloc: rhs_out overlaps uhat");

@@ -129,3 +129,12 @@ def test_test_hook_and_probe_reject_bad_arguments_on_the_host(ps):
     import ctypes
     out = ctypes.c_double()
     assert lib.ps_probe_fma_tflops(7, None, ctypes.byref(out)) == ps.PS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec,addr", [(0, 0x1004), (1, 0x1008)])
+def test_misaligned_forcing_is_rejected_before_any_cuda_call(ps, prec, addr):
+    cfg = ps.make_config(32, prec=ps.Precision(prec), forcing=addr)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_plan_create(cfg)
+    assert e.value.status == ps.PS_ERR_INVALID_ARG
+    assert "aligned" in str(e.value)

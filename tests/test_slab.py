@@ -1,0 +1,92 @@
+"""Slab decomposition of the right-hand side (paper_1808_01309_gb300/slab.py),
+on CPU: the partition, and the right-hand side assembled from P ranks' kx
+slabs against the oracle's right-hand side of the whole field, with the two
+all-to-all exchanges done by a loopback in one process and by
+torch.distributed over gloo between 2 and 3 CPU processes.  The local passes
+come from a test backend built on the oracle's transforms
+(tests/slab_cpu_backend.py); the CUDA backend runs the same exchanges in
+tests/test_gpu_slab.py."""
+
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_01309_gb300 import inputs, slab
+
+from .parity import assert_parity
+
+torch = pytest.importorskip("torch")
+
+
+def test_split_covers_every_item_once_with_sizes_within_one():
+    for n in (1, 5, 20, 171, 512):
+        for parts in (1, 2, 3, 4, 7):
+            spans = [slab.split(n, parts, i) for i in range(parts)]
+            assert spans[0][0] == 0 and spans[-1][1] == n
+            assert all(spans[i][1] == spans[i + 1][0] for i in range(parts - 1))
+            sizes = [hi - lo for lo, hi in spans]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        slab.split(10, 0, 0)
+
+
+def _case():
+    nx, ny, nz = 24, 12, 20
+    cfg = oracle.Config(nx, ny, nz, lx=2 * math.pi, ly=3.0, lz=5.0, nu=3e-3)
+    u = inputs.random_solenoidal_field(nx, ny, nz, seed=7, ly=3.0, lz=5.0)
+    f = inputs.forcing_field(nx, ny, nz, seed=2, ly=3.0, lz=5.0)
+    return cfg, u, f
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 4])
+def test_loopback_slabs_match_the_oracle(P):
+    from .slab_cpu_backend import CpuBackend, assemble, local_columns
+    cfg, u, f = _case()
+    cx = slab.retained_columns(cfg.nx)
+    lays = [slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, cx, P, r) for r in range(P)]
+    backends = [CpuBackend(cfg, lay, local_columns(f, lay)) for lay in lays]
+    parts = slab.rhs_loopback(backends, lays, [local_columns(u, lay) for lay in lays])
+    got = assemble([p.numpy() for p in parts], lays, cfg.nx // 2 + 1)
+    assert_parity(got, oracle.rhs(u, cfg, forcing=f), 1e-13, f"loopback P={P}")
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from tests.slab_cpu_backend import CpuBackend, local_columns
+        cfg, u, f = _case()
+        lay = slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, slab.retained_columns(cfg.nx), world, rank)
+        comm = slab.TorchDistributed()
+        out = slab.rhs_local(CpuBackend(cfg, lay, local_columns(f, lay)), lay, local_columns(u, lay), comm)
+        q.put((rank, out.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_match_the_oracle(world):
+    import multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    cfg, u, f = _case()
+    lays = [slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, slab.retained_columns(cfg.nx), world, r) for r in range(world)]
+    from .slab_cpu_backend import assemble
+    full = assemble([got[r] for r in range(world)], lays, cfg.nx // 2 + 1)
+    assert_parity(full, oracle.rhs(u, cfg, forcing=f), 1e-13, f"gloo world={world}")
+    assert np.all(full[..., slab.retained_columns(cfg.nx):] == 0)
