@@ -76,6 +76,7 @@ def parse_args():
     ap.add_argument("--boussinesq-steps", type=int, default=5)
     ap.add_argument("--fp32-error-steps", type=int, default=100)
     ap.add_argument("--ensemble-steps", type=int, default=50)
+    ap.add_argument("--les-steps", type=int, default=200)
     ap.add_argument("--oracle-job", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None,
                     help="small profiling case 'nx,ny,nz[,fp64]': run --reps right-hand sides of the seeded "
@@ -570,6 +571,8 @@ def run_ours(args, world, rank, local):
         ens = run_ensemble(args, dev, stream)
         torch.cuda.empty_cache()
 
+    les = run_les_cost(args, dev, stream, ms_step) if args.les_steps > 0 else None
+
     table = None
     if ref_job is not None:
         finish_oracle_job(ref_job)
@@ -578,7 +581,7 @@ def run_ours(args, world, rank, local):
             os.remove(os.path.join(ref_dir, name))
         os.rmdir(ref_dir)
 
-    out.update(mhd=mhd, bq=bq, err=err, ens=ens, table=table, ms_step=ms_step, launches=launches,
+    out.update(mhd=mhd, bq=bq, err=err, ens=ens, table=table, les=les, ms_step=ms_step, launches=launches,
                clocks=clk.summary(), roof=roof, e2e=e2e, fp64=fp64, energy=e_step, max_u=umax_step)
     return out
 
@@ -722,6 +725,42 @@ def run_ensemble(args, dev, stream):
                      "gpoints_s": round(points / (ms * 1e-3) / 1e9, 3), "first_call_s": round(first, 3)}
     out["graph_speedup"] = round(out["sequential"]["ms"] / out["graph"]["ms"], 3)
     ps.ps_ensemble_destroy(ens)
+    return out
+
+
+def run_les_cost(args, dev, stream, ms_dns):
+    """Cost of the learned LES closure against the DNS it replaces: the 64^3
+    FP32 LES step with the closure attached (MLP 5-64-64-6 on the BF16
+    tensor cores inside every RK4 stage, graph-replayed through
+    ps_rk_steps, dt = 5e-3) against the headline 512^3 DNS step (dt =
+    1e-3), per unit of simulated time.  The network weights here are the
+    initial ones (the cost does not depend on them); the accuracy of the
+    trained closure comes from the LES workflow (paper_1808_01309_gb300.les)."""
+    import torch
+    from paper_1808_01309_gb300 import inputs, les, ps
+    n, dt_les, dt_dns, K = 64, 5e-3, 1e-3, args.les_steps
+    f = torch.from_numpy(inputs.forcing_field(n, n, n, seed=2)).to(dev, torch.complex64)
+    u = torch.from_numpy(inputs.random_solenoidal_field(n, n, n, seed=1)).to(dev, torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=2e-3, rk_order=4, forcing=f, stream=stream)
+    out = {"workload": f"{n}^3 FP32 LES, IF-RK4, dt = {dt_les}, kc = 21, forcing as the DNS; steps "
+                       f"graph-replayed (ps_rk_steps)", "steps": K}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for name, params in (("no_closure", None), ("closure", torch.from_numpy(les.init_params(1)).to(dev))):
+        if params is not None:
+            plan.set_closure(params, {"mean": [0.0] * 5, "std": [1.0] * 5, "s_tau": 1e-6, "s_A": 1.0})
+        plan.rk_steps(u, dt_les, K)  # capture and warm-up
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plan.rk_steps(u, dt_les, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"ms_les_{name}"] = round(e0.elapsed_time(e1) / K, 4)
+    plan.close()
+    ms_les = out["ms_les_closure"]
+    out.update({"ms_les": ms_les, "ms_dns": round(ms_dns, 3), "dt_les": dt_les, "dt_dns": dt_dns,
+                "dns": "512^3 FP32 headline step", "cost_ratio": round((ms_dns / dt_dns) / (ms_les / dt_les), 1),
+                "target": ">= 10x lower cost per simulated time"})
     return out
 
 
@@ -915,6 +954,7 @@ def main():
         "fp32_vs_oracle_256": res["table"],
         "fp32_error_256": res["err"],
         "ensemble": res["ens"],
+        "les": res["les"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "stats": {"energy_at_last_step_start": res["energy"], "max_u": res["max_u"]},

@@ -448,6 +448,52 @@ ps_status ps_checkpoint_info(const char* path, ps_config* cfg, double* t, long l
  * turns every retained mode of rhs_out into NaN instead. */
 ps_status ps_rhs_noalloc(const ps_config* cfg, void* cuda_stream, const void* uhat, void* rhs_out, double t);
 
+/* ---- Slab decomposition over several ranks ---------------------------------
+ * The paper distributes each 3D transform as slabs and exchanges the data
+ * once per transform with an all-to-all between the passes along the local
+ * axes and the pass along the distributed axis (Sec. 2, slab decomposition;
+ * Sec. 3.3, transpose and exchange).  A ps_slab runs the passes of one HD
+ * right-hand side for one rank: its retained kx columns [kx_lo, kx_hi) of all
+ * (ky, kz) in spectral space and its z planes [z_lo, z_hi) of all (y, x) in
+ * physical space.  The caller moves the data between the three calls (two
+ * all-to-alls: 6 fields after ps_slab_inverse, 3 after ps_slab_xpass), e.g.
+ * with NCCL; paper_1808_01309_gb300/slab.py does this bookkeeping.
+ *
+ * Local layouts (interleaved complex as above; kxp and cxp from
+ * ps_slab_info: ncx = kx_hi - kx_lo local columns, kxp = ncx rounded up to a
+ * multiple of 16, cxp = (Kx + 1) rounded up likewise, rows = (z_hi - z_lo) ny):
+ *   uhat_local, rhs_local, forcing : [3][nz][ny][ncx], FFT order in ky, kz
+ *   out6 (ps_slab_inverse)         : [6][nz][ny][kxp]  u, omega after the
+ *                                    backward z and y transforms
+ *   xin  (ps_slab_xpass)           : [6][rows][cxp]    the same fields, full x
+ *                                    rows of the local planes (kx < Kx + 1
+ *                                    used, the rest ignored)
+ *   xout (ps_slab_xpass)           : [3][rows][cxp]    forward x transform of
+ *                                    u x omega, kx < Kx + 1 (the rest zero)
+ *   yin  (ps_slab_forward)         : [3][nz][ny][kxp]  xout of every rank's
+ *                                    planes for the local columns
+ * rhs_local receives the right-hand side of ps_rhs restricted to the local
+ * columns (zero at masked modes).  Every buffer is the caller's device
+ * memory, 16-byte aligned (else PS_ERR_INVALID_ARG); the slab owns its
+ * scratch.  Calls are asynchronous on the slab's stream; ps_slab_check
+ * synchronises it and returns PS_ERR_TIMEOUT once if a bounded wait of the
+ * x pass gave up.  cfg->forcing, if set, is the local forcing
+ * [3][nz][ny][ncx], read (into the slab's copy) during ps_slab_create.
+ * PS_ERR_UNSUPPORTED for other equation sets; PS_ERR_INVALID_ARG for ranges
+ * outside 0 <= kx_lo < kx_hi <= Kx + 1, 0 <= z_lo < z_hi <= nz. */
+typedef struct ps_slab ps_slab;
+typedef struct {
+  int ncx, kxp, cxp, rows;
+} ps_slab_info;
+ps_status ps_slab_create(const ps_config* cfg, int kx_lo, int kx_hi, int z_lo, int z_hi, void* cuda_stream,
+                         ps_slab** out);
+ps_status ps_slab_destroy(ps_slab* slab);
+ps_status ps_slab_info_get(const ps_slab* slab, ps_slab_info* out);
+ps_status ps_slab_inverse(ps_slab* slab, const void* uhat_local, void* out6);
+ps_status ps_slab_xpass(ps_slab* slab, const void* xin, void* xout);
+ps_status ps_slab_forward(ps_slab* slab, const void* yin, const void* uhat_local, void* rhs_local);
+ps_status ps_slab_check(ps_slab* slab);
+
 /* ---- Measurement ------------------------------------------------------------
  * Fused multiply-add rate of the current device in TFLOP/s (2 flops per FMA)
  * for prec (PS_FP32 or PS_FP64): eight independent FMA chains per thread, 8

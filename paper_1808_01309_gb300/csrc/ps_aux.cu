@@ -87,7 +87,7 @@ __global__ void k_forcing_gather(const Geo g, const Spec f, int Fx, int Fy, int 
   const int c = i / per, rem = i % per;
   const int p = rem % nxb, q = (rem / nxb) % nyb - Fy, r = rem / (nxb * nyb) - Fz;
   V v = czero<V>();
-  if (kept(g, p, q, r)) {
+  if (p < ncols(g) && kept(g, g.kx0 + p, q, r)) {  // p: local column of a kx slab
     const V* fp = static_cast<const V*>(f.p);
     v = fp[c * f.cs + (long long)rowof(r, f.zwrap) * f.zs + (long long)rowof(q, f.ywrap) * f.ys + p];
   }

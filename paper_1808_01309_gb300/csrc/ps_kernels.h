@@ -16,7 +16,13 @@ struct Geo {
   int kxp;          // padded kx extent of the compact buffers (multiple of 16)
   int sphere;       // spherical truncation on top of the cube
   double sx, sy, sz;  // 2 pi / L per axis
+  // kx slab of a decomposed problem (zero for a whole problem): local column
+  // c is the global kx0 + c; ncx local retained columns (0: cx); caller rows
+  // of rowlen entries (0: nh)
+  int kx0, ncx, rowlen;
 };
+__host__ __device__ inline int ncols(const Geo& g) { return g.ncx ? g.ncx : g.cx; }
+__host__ __device__ inline int rowlen(const Geo& g) { return g.rowlen ? g.rowlen : g.nh; }
 
 // A spectral vector field in HBM: element (c, r, q, p) at
 // p + ys*row_y(q) + zs*row_z(r) + cs*c, with row(s) = s >= 0 ? s : s + wrap.

@@ -148,12 +148,13 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
   const int iy = blockIdx.y * NB + bb;
   const bool bvalid = iy < g.cy;
-  const int kx = blockIdx.x * TX + line;
+  const int kx = blockIdx.x * TX + line;  // local column
+  const int kxg = g.kx0 + kx;              // its global kx
   const int q = iy <= g.Ky ? iy : iy - g.cy;
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
   const V* tw = static_cast<const V*>(a.tw_z);
   V* out = static_cast<V*>(a.a6);
-  const T skx = T(kx) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
+  const T skx = T(kxg) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
   const long long fstride = (long long)g.nz * g.cy * g.kxp;
   const long long zstride = (long long)g.cy * g.kxp;
   const int cst = NB * g.cz * TX;                 // component stride in the tile
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
     constexpr int RSTEP = NTH / TX;
     const int col = tid % TX;
     const int kxc = blockIdx.x * TX + col;
-    if (kxc <= g.Kx) {
+    if (kxc < ncols(g)) {
       int i = tid / TX, b = 0, c = 0;
       while (i >= g.cz) {
         i -= g.cz;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   unsigned keepm = 0;  // bit m: mode (kx, q, r(n)) of element m is retained
 #pragma unroll
   for (int m = 0; m < E; ++m)
-    if (bvalid && kept(g, kx, q, sidx(j0 + m * (N / E), N))) keepm |= 1u << m;
+    if (bvalid && kx < ncols(g) && kept(g, kxg, q, sidx(j0 + m * (N / E), N))) keepm |= 1u << m;
 #pragma unroll 1
   for (int f = 0; f < nout; ++f) {
     V x[E];
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   }
   if (a.e_part) {
     // energy 1/2 sum w |u|^2 (+ |B|^2 or theta^2), w = 1 on the kx = 0 plane, else 2
-    const double t = block_sum(esum * (kx == 0 ? 0.5 : 1.0), red);
+    const double t = block_sum(esum * (kxg == 0 ? 0.5 : 1.0), red);
     if (threadIdx.x == 0) a.e_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
 }
@@ -627,7 +628,8 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs 
     for (int m = 0; m < E; ++m) {
       const int r = sidx(j0 + m * (N / E), N);
       if (r <= g.Kz && r >= -g.Kz)
-        out[(long long)rowof(r, g.cz) * g.cy * g.kxp] = kept(g, kx, q, r) ? cscale(x[m], inv) : czero<V>();
+        out[(long long)rowof(r, g.cz) * g.cy * g.kxp] =
+            kx < ncols(g) && kept(g, g.kx0 + kx, q, r) ? cscale(x[m], inv) : czero<V>();
     }
   }
 }
@@ -645,33 +647,36 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs 
 // retained set are written as zero); otherwise one thread per retained mode.
 // Consecutive threads take consecutive kx: every access is a contiguous row.
 // ---------------------------------------------------------------------------
-template <typename T, int NG, int NSC>
+template <typename T, int NG, int NSC, bool SLAB = false>
 __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full) {
   using V = typename cplx<T>::type;
   constexpr int NC = 3 * NG + NSC;  // state components
   const Geo& g = a.g;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int kx, q, r;
+  // a whole problem (not a kx slab) has rows of nh entries and cx columns
+  const int rl = SLAB ? rowlen(g) : g.nh, nc = SLAB ? ncols(g) : g.cx;
+  int kx, q, r;  // kx: local column (array index); kxg = g.kx0 + kx its global kx
   long long orow = 0;  // row of the caller layout (z * ny + y)
   if (full) {
-    if (idx >= (long long)g.nz * g.ny * g.nh) return;
-    kx = (int)(idx % g.nh);
-    orow = idx / g.nh;
+    if (idx >= (long long)g.nz * g.ny * rl) return;
+    kx = (int)(idx % rl);
+    orow = idx / rl;
     q = sidx((int)(orow % g.ny), g.ny);
     r = sidx((int)(orow / g.ny), g.nz);
   } else {
-    if (idx >= (long long)g.cz * g.cy * g.cx) return;
-    kx = (int)(idx % g.cx);
-    const long long crow = idx / g.cx;
+    if (idx >= (long long)g.cz * g.cy * nc) return;
+    kx = (int)(idx % nc);
+    const long long crow = idx / nc;
     const int iy = (int)(crow % g.cy), iz = (int)(crow / g.cy);
     q = iy <= g.Ky ? iy : iy - g.cy;
     r = iz <= g.Kz ? iz : iz - g.cz;
   }
-  const long long fcs = (long long)g.nz * g.ny * g.nh;  // caller layout component stride
-  const bool keep = kept(g, kx, q, r);
+  const int kxg = SLAB ? g.kx0 + kx : kx;
+  const long long fcs = (long long)g.nz * g.ny * rl;  // caller layout component stride
+  const bool keep = (!SLAB || kx < nc) && kept(g, kxg, q, r);
   if (!keep) {
     if (full) {
-      V* po = static_cast<V*>(a.out_full) + orow * g.nh + kx;
+      V* po = static_cast<V*>(a.out_full) + orow * rl + kx;
 #pragma unroll
       for (int c = 0; c < NC; ++c) po[c * fcs] = czero<V>();
     }
@@ -683,7 +688,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
   const int iy = rowof(q, g.cy), iz = rowof(r, g.cz);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
   const long long ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
-  const T kxv = T(kx) * T(g.sx), kyv = T(q) * T(g.sy), kzv = T(r) * T(g.sz);
+  const T kxv = T(kxg) * T(g.sx), kyv = T(q) * T(g.sy), kzv = T(r) * T(g.sz);
   const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
   const T dt = T(a.dt);
   const V* nh = static_cast<const V*>(a.a6);
@@ -752,7 +757,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     }
     const V* pu = static_cast<const V*>(a.u_n.p) + c0 * a.u_n.cs + (long long)rowof(r, a.u_n.zwrap) * a.u_n.zs +
                   (long long)rowof(q, a.u_n.ywrap) * a.u_n.ys + kx;
-    V* po = static_cast<V*>(a.out_full) + c0 * fcs + orow * g.nh + kx;
+    V* po = static_cast<V*>(a.out_full) + c0 * fcs + orow * rl + kx;
     const bool second = mag || scl;  // diffusivity and factor tables of the second field
     if (a.mode == ZF_RHS) {
       const T vk = T(second ? a.eta : a.nu) * k2;
@@ -764,7 +769,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     const T* ifx = static_cast<const T*>(second ? a.jfx : a.ifx);
     const T* ify = static_cast<const T*>(second ? a.jfy : a.ify);
     const T* ifz = static_cast<const T*>(second ? a.jfz : a.ifz);
-    const T Ef = __ldg(ifx + kx) * __ldg(ify + iy) * __ldg(ifz + iz);
+    const T Ef = __ldg(ifx + kxg) * __ldg(ify + iy) * __ldg(ifz + iz);
     const T E2 = Ef * Ef;
     V* acc = static_cast<V*>(a.acc) + c0 * ccs + ci;
     V* nxt = static_cast<V*>(a.nxt) + c0 * ccs + ci;
@@ -912,9 +917,11 @@ cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
 template <typename T>
 cudaError_t update_launch(const PassArgs& a, cudaStream_t s) {
   const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
-  const long long n = full ? (long long)a.g.nz * a.g.ny * a.g.nh : (long long)a.g.cz * a.g.cy * a.g.cx;
+  const long long n = full ? (long long)a.g.nz * a.g.ny * rowlen(a.g) : (long long)a.g.cz * a.g.cy * ncols(a.g);
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  if (a.ng == 2) k_update<T, 2, 0><<<blocks, 256, 0, s>>>(a, full);
+  const bool slab = a.g.kx0 != 0 || a.g.ncx != 0 || a.g.rowlen != 0;
+  if (slab) k_update<T, 1, 0, true><<<blocks, 256, 0, s>>>(a, full);  // slabs: HD only
+  else if (a.ng == 2) k_update<T, 2, 0><<<blocks, 256, 0, s>>>(a, full);
   else if (a.nsc) k_update<T, 1, 1><<<blocks, 256, 0, s>>>(a, full);
   else k_update<T, 1, 0><<<blocks, 256, 0, s>>>(a, full);
   return cudaGetLastError();

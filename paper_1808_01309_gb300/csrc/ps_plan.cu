@@ -1024,3 +1024,221 @@ ps_status ps_plan_launch_count(ps_plan* p, long long* launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Slab decomposition (include/ps.h, ps_slab_*): the passes of one right-hand
+// side on a rank's kx columns and z planes; the exchanges between them are
+// the caller's (paper Sec. 2 and Sec. 3.3: one all-to-all per 3D transform).
+// ---------------------------------------------------------------------------
+struct ps_slab {
+  ps_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int kx_lo = 0, kx_hi = 0, z_lo = 0, z_hi = 0;
+  Geo gl{};  // the local kx columns (all z, y)
+  Geo gx{};  // the x rows of the local z planes (all kx)
+  size_t vb = 8;
+  void* a6 = nullptr;  // z-backward output [6][nz][cy][kxp]; z-forward output [3][cz][cy][kxp]
+  void* b6 = nullptr;  // y-forward output [3][nz][cy][kxp]
+  void* tw = nullptr;  // [nx | ny | nz] twiddles
+  void* fbox = nullptr;
+  int* err = nullptr;
+};
+
+namespace {
+
+void slab_release(ps_slab* s) {
+  void* bufs[] = {s->a6, s->b6, s->tw, s->fbox, s->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+}
+
+PassArgs slab_args(const ps_slab* s, const Geo& g) {
+  PassArgs a{};
+  a.g = g;
+  a.tw_x = s->tw;
+  a.tw_y = static_cast<char*>(s->tw) + s->vb * g.nx;
+  a.tw_z = static_cast<char*>(s->tw) + s->vb * (g.nx + g.ny);
+  a.nu = s->cfg.nu;
+  a.ng = 1;
+  a.nsc = 0;
+  a.nfi = 6;
+  a.nfo = 3;
+  a.err = s->err;
+  a.fbox = s->fbox;
+  a.Fx = s->fbox ? g.ncx - 1 : -1;
+  a.Fy = s->fbox ? g.Ky : -1;
+  a.Fz = s->fbox ? g.Kz : -1;
+  return a;
+}
+
+Spec local_spec(const Geo& g, const void* ptr) {
+  Spec sp;
+  sp.p = ptr;
+  sp.ys = g.rowlen;
+  sp.zs = (long long)g.ny * g.rowlen;
+  sp.cs = (long long)g.nz * g.ny * g.rowlen;
+  sp.zwrap = g.nz;
+  sp.ywrap = g.ny;
+  return sp;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+ps_status ps_slab_create(const ps_config* cfg, int kx_lo, int kx_hi, int z_lo, int z_hi, void* cuda_stream,
+                         ps_slab** out) {
+  if (!out) return fail(PS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ps_status st = validate(cfg);
+  if (st != PS_OK) return st;
+  if (cfg->eq != PS_HD) return fail(PS_ERR_UNSUPPORTED, "slab decomposition: HD equations only");
+  const Geo g = make_geo(cfg);
+  if (!(0 <= kx_lo && kx_lo < kx_hi && kx_hi <= g.cx))
+    return fail(PS_ERR_INVALID_ARG, "kx range must satisfy 0 <= kx_lo < kx_hi <= Kx + 1");
+  if (!(0 <= z_lo && z_lo < z_hi && z_hi <= g.nz))
+    return fail(PS_ERR_INVALID_ARG, "z range must satisfy 0 <= z_lo < z_hi <= nz");
+  ps_slab* s = new (std::nothrow) ps_slab();
+  if (!s) return fail(PS_ERR_OOM, "host allocation failed");
+  s->cfg = *cfg;
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&s->device);
+  s->kx_lo = kx_lo;
+  s->kx_hi = kx_hi;
+  s->z_lo = z_lo;
+  s->z_hi = z_hi;
+  s->vb = cfg->prec == PS_FP32 ? 8 : 16;
+  s->gl = g;
+  s->gl.kx0 = kx_lo;
+  s->gl.ncx = kx_hi - kx_lo;
+  s->gl.rowlen = kx_hi - kx_lo;
+  s->gl.kxp = (s->gl.ncx + 15) / 16 * 16;
+  s->gx = g;
+  s->gx.nz = z_hi - z_lo;  // the x pass sees only the rows of the local planes
+  const size_t kxp = s->gl.kxp;
+  auto bail = [&](ps_status r) {
+    slab_release(s);
+    delete s;
+    return r;
+  };
+  cudaError_t e;
+  const size_t a6 = std::max(6ull * g.nz * g.cy * kxp, 3ull * g.cz * g.cy * kxp);
+  if ((e = cudaMalloc(&s->a6, a6 * s->vb)) != cudaSuccess) return bail(cuda_fail(e, "slab scratch"));
+  if ((e = cudaMalloc(&s->b6, 3ull * g.nz * g.cy * kxp * s->vb)) != cudaSuccess)
+    return bail(cuda_fail(e, "slab scratch"));
+  if ((e = cudaMalloc(&s->tw, (size_t)(g.nx + g.ny + g.nz) * s->vb)) != cudaSuccess)
+    return bail(cuda_fail(e, "slab twiddles"));
+  if ((e = cudaMalloc(&s->err, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "slab error word"));
+  if ((e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream)) != cudaSuccess)
+    return bail(cuda_fail(e, "slab error word"));
+  if (cfg->prec == PS_FP32) {
+    std::vector<float2> h;
+    fill_twiddles(h, g.nx);
+    fill_twiddles(h, g.ny);
+    fill_twiddles(h, g.nz);
+    e = cudaMemcpy(s->tw, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<double2> h;
+    fill_twiddles(h, g.nx);
+    fill_twiddles(h, g.ny);
+    fill_twiddles(h, g.nz);
+    e = cudaMemcpy(s->tw, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return bail(cuda_fail(e, "slab twiddle upload"));
+  if (cfg->forcing) {
+    // the whole local retained block as the forcing box
+    const size_t n = 3ull * s->gl.ncx * g.cy * g.cz;
+    if ((e = cudaMalloc(&s->fbox, n * s->vb)) != cudaSuccess) return bail(cuda_fail(e, "slab forcing box"));
+    const Spec f = local_spec(s->gl, cfg->forcing);
+    e = cfg->prec == PS_FP32 ? launch_forcing_gather<float>(s->gl, f, s->gl.ncx - 1, g.Ky, g.Kz, s->fbox, s->stream)
+                             : launch_forcing_gather<double>(s->gl, f, s->gl.ncx - 1, g.Ky, g.Kz, s->fbox, s->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "slab forcing gather"));
+  }
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(cuda_fail(e, "slab create sync"));
+  *out = s;
+  return PS_OK;
+}
+
+ps_status ps_slab_destroy(ps_slab* s) {
+  if (!s) return PS_OK;
+  DeviceGuard dg(s->device);
+  cudaStreamSynchronize(s->stream);
+  slab_release(s);
+  delete s;
+  return PS_OK;
+}
+
+ps_status ps_slab_info_get(const ps_slab* s, ps_slab_info* out) {
+  if (!s || !out) return fail(PS_ERR_INVALID_ARG, "NULL slab or output");
+  out->ncx = s->gl.ncx;
+  out->kxp = s->gl.kxp;
+  out->cxp = s->gx.kxp;
+  out->rows = s->gx.nz * s->gx.ny;
+  return PS_OK;
+}
+
+ps_status ps_slab_inverse(ps_slab* s, const void* uhat_local, void* out6) {
+  if (!s || !uhat_local || !out6) return fail(PS_ERR_INVALID_ARG, "NULL slab or buffer");
+  if (!aligned16(uhat_local) || !aligned16(out6)) return fail(PS_ERR_INVALID_ARG, "slab buffers must be 16-byte aligned");
+  DeviceGuard dg(s->device);
+  PassArgs a = slab_args(s, s->gl);
+  a.in = local_spec(s->gl, uhat_local);
+  a.a6 = s->a6;
+  a.b6 = out6;
+  const bool f32 = s->cfg.prec == PS_FP32;
+  PS_CU(f32 ? launch_zinv<float>(a, s->stream, nullptr) : launch_zinv<double>(a, s->stream, nullptr), "slab z-inverse");
+  PS_CU(f32 ? launch_yinv<float>(a, s->stream) : launch_yinv<double>(a, s->stream), "slab y-inverse");
+  return PS_OK;
+}
+
+ps_status ps_slab_xpass(ps_slab* s, const void* xin, void* xout) {
+  if (!s || !xin || !xout) return fail(PS_ERR_INVALID_ARG, "NULL slab or buffer");
+  if (!aligned16(xin) || !aligned16(xout)) return fail(PS_ERR_INVALID_ARG, "slab buffers must be 16-byte aligned");
+  DeviceGuard dg(s->device);
+  PassArgs a = slab_args(s, s->gx);
+  a.b6 = const_cast<void*>(xin);
+  a.a6 = xout;
+  PS_CU(s->cfg.prec == PS_FP32 ? launch_xpass<float>(a, s->stream) : launch_xpass<double>(a, s->stream), "slab x pass");
+  return PS_OK;
+}
+
+ps_status ps_slab_forward(ps_slab* s, const void* yin, const void* uhat_local, void* rhs_local) {
+  if (!s || !yin || !uhat_local || !rhs_local) return fail(PS_ERR_INVALID_ARG, "NULL slab or buffer");
+  if (!aligned16(yin) || !aligned16(uhat_local) || !aligned16(rhs_local))
+    return fail(PS_ERR_INVALID_ARG, "slab buffers must be 16-byte aligned");
+  const size_t bytes = 3ull * s->gl.nz * s->gl.ny * s->gl.rowlen * s->vb;
+  if (ranges_overlap(uhat_local, rhs_local, bytes)) return fail(PS_ERR_INVALID_ARG, "rhs_local overlaps uhat_local");
+  DeviceGuard dg(s->device);
+  const bool f32 = s->cfg.prec == PS_FP32;
+  PassArgs a = slab_args(s, s->gl);
+  a.a6 = const_cast<void*>(yin);
+  a.b6 = s->b6;
+  PS_CU(f32 ? launch_yfwd<float>(a, s->stream) : launch_yfwd<double>(a, s->stream), "slab y-forward");
+  a.a6 = s->a6;
+  PS_CU(f32 ? launch_zfwd<float>(a, s->stream) : launch_zfwd<double>(a, s->stream), "slab z-forward");
+  a.in = local_spec(s->gl, uhat_local);
+  a.u_n = a.in;
+  a.out_full = rhs_local;
+  a.mode = ZF_RHS;
+  PS_CU(f32 ? launch_update<float>(a, s->stream) : launch_update<double>(a, s->stream), "slab update");
+  return PS_OK;
+}
+
+ps_status ps_slab_check(ps_slab* s) {
+  if (!s) return fail(PS_ERR_INVALID_ARG, "NULL slab");
+  DeviceGuard dg(s->device);
+  int e = 0;
+  PS_CU(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "slab error word");
+  PS_CU(cudaStreamSynchronize(s->stream), "slab sync");
+  if (e != 0) {
+    PS_CU(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream), "slab error word");
+    PS_CU(cudaStreamSynchronize(s->stream), "slab sync");
+    return fail(PS_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy never completed)");
+  }
+  return PS_OK;
+}
+
+}  // extern "C"

@@ -55,6 +55,8 @@ SYMBOLS = (
     "ps_les_filter", "ps_mlp_backward", "ps_plan_closure_grad", "ps_plan_set_host_mode", "ps_rk_steps",
     "ps_plan_closure_grad_transfer", "ps_checkpoint_save", "ps_checkpoint_load", "ps_checkpoint_info",
     "ps_fft_r2c", "ps_fft_c2r", "ps_probe_fma_tflops", "ps_plan_set_wait_test",
+    "ps_slab_create", "ps_slab_destroy", "ps_slab_info_get", "ps_slab_inverse", "ps_slab_xpass",
+    "ps_slab_forward", "ps_slab_check",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
 MLP_NPARAM = 4934
@@ -90,6 +92,10 @@ class PsDiag(ctypes.Structure):
 class PsEnsTuning(ctypes.Structure):
     _fields_ = [("branches", ctypes.c_int), ("nsizes", ctypes.c_int), ("n", ctypes.c_int * 8),
                 ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double)]
+
+
+class PsSlabInfo(ctypes.Structure):
+    _fields_ = [("ncx", ctypes.c_int), ("kxp", ctypes.c_int), ("cxp", ctypes.c_int), ("rows", ctypes.c_int)]
 
 
 class PsTiming(ctypes.Structure):
@@ -150,6 +156,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_mlp_grad_tb.argtypes = [P, P, P, P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, P, P, P]
     lib.ps_probe_fma_tflops.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
     lib.ps_plan_set_wait_test.argtypes = [P, ctypes.c_int]
+    lib.ps_slab_create.argtypes = [ctypes.POINTER(PsConfig), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   P, ctypes.POINTER(P)]
+    lib.ps_slab_destroy.argtypes = [P]
+    lib.ps_slab_info_get.argtypes = [P, ctypes.POINTER(PsSlabInfo)]
+    lib.ps_slab_inverse.argtypes = [P, P, P]
+    lib.ps_slab_xpass.argtypes = [P, P, P]
+    lib.ps_slab_forward.argtypes = [P, P, P, P]
+    lib.ps_slab_check.argtypes = [P]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name in ("ps_kind_name", "ps_status_string", "ps_last_error"):
@@ -231,6 +245,39 @@ def ps_rk_steps(plan, uhat, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
 
 def ps_rk_step_host(plan, uhat_host, dt: float, t: float = 0.0, nsteps: int = 1) -> None:
     _check(load().ps_rk_step_host(plan, _ptr(uhat_host), float(dt), float(t), int(nsteps)))
+
+
+def ps_slab_create(cfg: PsConfig, kx_lo: int, kx_hi: int, z_lo: int, z_hi: int, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().ps_slab_create(ctypes.byref(cfg), int(kx_lo), int(kx_hi), int(z_lo), int(z_hi),
+                                 _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def ps_slab_destroy(slab) -> None:
+    _check(load().ps_slab_destroy(slab))
+
+
+def ps_slab_info_get(slab) -> PsSlabInfo:
+    info = PsSlabInfo()
+    _check(load().ps_slab_info_get(slab, ctypes.byref(info)))
+    return info
+
+
+def ps_slab_inverse(slab, uhat_local, out6) -> None:
+    _check(load().ps_slab_inverse(slab, _ptr(uhat_local), _ptr(out6)))
+
+
+def ps_slab_xpass(slab, xin, xout) -> None:
+    _check(load().ps_slab_xpass(slab, _ptr(xin), _ptr(xout)))
+
+
+def ps_slab_forward(slab, yin, uhat_local, rhs_local) -> None:
+    _check(load().ps_slab_forward(slab, _ptr(yin), _ptr(uhat_local), _ptr(rhs_local)))
+
+
+def ps_slab_check(slab) -> None:
+    _check(load().ps_slab_check(slab))
 
 
 def ps_plan_set_wait_test(plan, polls: int) -> None:

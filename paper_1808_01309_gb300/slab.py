@@ -173,3 +173,54 @@ def rhs_loopback(backends, lays, uhats):
     sends = [pack_b(lays[s], xo[s]) for s in range(P)]
     yin = [unpack_b(lays[r], [sends[s][r] for s in range(P)]) for r in range(P)]
     return [backends[r].forward_yz(yin[r], uhats[r]) for r in range(P)]
+
+
+class CudaSlab:
+    """The CUDA backend of one rank: the ps_slab_* calls of the C ABI on
+    device tensors (this class only allocates buffers, pads rows to the
+    kernels' widths and passes pointers)."""
+
+    def __init__(self, lay: SlabLayout, **plan_kwargs):
+        import torch
+
+        from . import ps
+        self.ps = ps
+        self.lay = lay
+        self.forcing = plan_kwargs.get("forcing")
+        cfg = ps.make_config(lay.nx, lay.ny, lay.nz, **plan_kwargs)
+        self.dtype = torch.complex64 if cfg.prec == ps.Precision.FP32 else torch.complex128
+        lo, hi = lay.kx_range()
+        zlo, zhi = lay.z_range()
+        self.handle = ps.ps_slab_create(cfg, lo, hi, zlo, zhi)
+        self.info = ps.ps_slab_info_get(self.handle)
+
+    def inverse_yz(self, uhat_local):
+        import torch
+        lay, i = self.lay, self.info
+        out6 = torch.empty((6, lay.nz, lay.ny, i.kxp), dtype=self.dtype, device=uhat_local.device)
+        self.ps.ps_slab_inverse(self.handle, uhat_local, out6)
+        return out6[..., : i.ncx]
+
+    def x_pass(self, xin):
+        import torch
+        i = self.info
+        xp = torch.zeros((6, i.rows, i.cxp), dtype=self.dtype, device=xin.device)
+        xp[..., : xin.shape[2]] = xin
+        xo = torch.empty((3, i.rows, i.cxp), dtype=self.dtype, device=xin.device)
+        self.ps.ps_slab_xpass(self.handle, xp, xo)
+        return xo[..., : xin.shape[2]]
+
+    def forward_yz(self, yin, uhat_local):
+        import torch
+        lay, i = self.lay, self.info
+        yp = torch.zeros((3, lay.nz, lay.ny, i.kxp), dtype=self.dtype, device=yin.device)
+        yp[..., : i.ncx] = yin
+        out = torch.empty_like(uhat_local)
+        self.ps.ps_slab_forward(self.handle, yp, uhat_local, out)
+        self.ps.ps_slab_check(self.handle)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.ps.ps_slab_destroy(self.handle)
+            self.handle = None
