@@ -858,26 +858,59 @@ def run_reference(args):
 
 
 def kernel_case(spec: str, reps: int) -> None:
-    """Right-hand sides of the seeded random field (with forcing) on a small
-    grid, one after the other on the default stream: the launch sequence of
-    the bench's passes at a size that an ncu capture of one kernel handles
-    quickly (e.g. 512,512,128 for the x and y passes with 512-point lines,
-    256,128,512 for the z passes)."""
+    """Small cases for ncu captures of one kernel family, run one after the
+    other on the default stream.  spec = "nx,ny,nz[,fp64][,mhd|boussinesq]"
+    runs `reps` right-hand sides of the seeded random field with forcing on
+    that grid (e.g. 512,512,128 for the x and y passes with 512-point lines,
+    256,128,512 for the z passes); "les" runs `reps` 64^3 RK4 steps with the
+    learned closure attached; "mlp" runs `reps` MLP forward evaluations of
+    64^3 samples."""
+    import numpy as np
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1808_01309_gb300 import inputs, ps
+    from paper_1808_01309_gb300 import inputs, les, ps
     parts = spec.split(",")
+    if parts[0] == "mlp":
+        P = 64 ** 3
+        params = torch.from_numpy(les.init_params(1)).to("cuda")
+        X = torch.randn((P, 5), device="cuda")
+        Y = torch.empty((P, 6), device="cuda")
+        for _ in range(reps):
+            ps.ps_mlp_forward(params, X, Y, P)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": spec, "reps": reps, "y_norm": float(Y.norm())}))
+        return
+    if parts[0] == "les":
+        n = 64
+        f = torch.from_numpy(inputs.forcing_field(n, n, n, seed=2)).to("cuda", torch.complex64)
+        u = torch.from_numpy(inputs.random_solenoidal_field(n, n, n, seed=1)).to("cuda", torch.complex64)
+        plan = ps.Plan(n, prec=ps.Precision.FP32, nu=2e-3, rk_order=4, forcing=f)
+        plan.set_closure(torch.from_numpy(les.init_params(1)).to("cuda"),
+                         {"mean": [0.0] * 5, "std": [1.0] * 5, "s_tau": 1e-6, "s_A": 1.0})
+        for _ in range(reps):
+            plan.rk_step(u, 5e-3)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": spec, "reps": reps, "u_norm": float(torch.linalg.vector_norm(u))}))
+        plan.close()
+        return
     nx, ny, nz = (int(v) for v in parts[:3])
-    fp64 = len(parts) > 3 and parts[3] == "fp64"
+    fp64 = "fp64" in parts[3:]
+    eq = ps.Equations.MHD if "mhd" in parts[3:] else ps.Equations.BOUSSINESQ if "boussinesq" in parts[3:] \
+        else ps.Equations.HD
     P, dt = (ps.Precision.FP64, torch.complex128) if fp64 else (ps.Precision.FP32, torch.complex64)
-    u = torch.from_numpy(inputs.random_solenoidal_field(nx, ny, nz, seed=1)).to("cuda", dt)
+    u = inputs.random_solenoidal_field(nx, ny, nz, seed=1)
+    if eq == ps.Equations.MHD:
+        u = np.concatenate([u, inputs.random_solenoidal_field(nx, ny, nz, seed=51)])
+    elif eq == ps.Equations.BOUSSINESQ:
+        u = np.concatenate([u, inputs.random_scalar_field(nx, ny, nz, seed=61)])
+    ud = torch.from_numpy(u).to("cuda", dt)
     f = torch.from_numpy(inputs.forcing_field(nx, ny, nz, seed=2)).to("cuda", dt)
-    plan = ps.Plan(nx, ny, nz, prec=P, nu=2e-3, rk_order=4, forcing=f)
-    out = torch.empty_like(u)
+    plan = ps.Plan(nx, ny, nz, prec=P, eq=eq, nu=2e-3, eta=2e-3, kappa=2e-3, n_bv=1.0, rk_order=4, forcing=f)
+    out = torch.empty_like(ud)
     for _ in range(reps):
-        plan.rhs(u, out=out)
+        plan.rhs(ud, out=out)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_case": spec, "reps": reps, "rhs_norm": float(torch.linalg.vector_norm(out))}))
     plan.close()

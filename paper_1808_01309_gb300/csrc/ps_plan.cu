@@ -483,6 +483,16 @@ ps_status setup_forcing(ps_plan* p) {
   return PS_OK;
 }
 
+// Forget the graph ps_rk_steps captured: the launch sequence or its
+// arguments change with the closure, the wait test hook and the x-pass rows.
+void drop_cached_graph(ps_plan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  p->g_n = 0;
+}
+
 void release(ps_plan* p) {
   void* bufs[] = {p->a6, p->b6, p->nxt, p->acc, p->tw, p->iftab, p->fbox, p->e_part, p->stats,
                   p->umax2, p->ext, p->err, p->dpart, p->dout, p->hstate, p->les_mem[0], p->les_mem[1],
@@ -509,7 +519,10 @@ void release(ps_plan* p) {
 namespace ps {
 void plan_set_stream(ps_plan* p, cudaStream_t s) { p->stream = s; }
 cudaStream_t plan_stream(const ps_plan* p) { return p->stream; }
-void plan_set_xrpc(ps_plan* p, int rpc) { p->xrpc = rpc; }
+void plan_set_xrpc(ps_plan* p, int rpc) {
+  if (p->xrpc != rpc) drop_cached_graph(p);
+  p->xrpc = rpc;
+}
 void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
 void plan_set_time(ps_plan* p, double t) { p->time = t; }
 // used by the checkpoint layer (ps_io.cu)
@@ -906,6 +919,7 @@ ps_status ps_plan_set_timing(ps_plan* p, int enable) {
 ps_status ps_plan_set_wait_test(ps_plan* p, int polls) {
   if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
   if (polls < 0 || polls > (1 << 20)) return fail(PS_ERR_INVALID_ARG, "polls must be in [0, 2^20]");
+  if (p->wait_test_polls != (unsigned)polls) drop_cached_graph(p);
   p->wait_test_polls = (unsigned)polls;
   return PS_OK;
 }
@@ -925,6 +939,7 @@ ps_status ps_plan_get_timing(ps_plan* p, ps_timing* out) {
 ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* norm12) {
   if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
   if (!params) {
+    if (p->les_on) drop_cached_graph(p);
     p->les_on = false;
     return PS_OK;
   }
@@ -965,6 +980,7 @@ ps_status ps_plan_set_closure(ps_plan* p, const float* params, const double* nor
   p->les.X = static_cast<float*>(p->les_mem[4]);
   p->les.Y = static_cast<float*>(p->les_mem[5]);
   p->les.extra = static_cast<float2*>(p->les_mem[6]);
+  if (!p->les_on) drop_cached_graph(p);  // the closure launches join the step
   p->les_on = true;
   return PS_OK;
 }

@@ -148,6 +148,36 @@ def test_les_rk_steps_match_oracle(ps, order):
     plan.close()
 
 
+def test_step_graph_follows_the_closure(ps):
+    """ps_rk_steps caches its captured graph per (state, dt, steps): attaching
+    or detaching the closure must rebuild it, so that the replayed steps are
+    the plain launches with the closure as it is now."""
+    n, nu, dt = 32, 1e-2, 5e-3
+    u = 2.0 * inputs.random_solenoidal_field(n, n, n, seed=12)
+    cfg = oracle.Config(n, n, n, nu=nu)
+    v, _ = fp32_params(4)
+    norm = norm_of(u, cfg, 0.1)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu)
+    u0 = to_dev(u)
+    x = u0.clone()
+    plan.rk_steps(x, dt, 3)                       # graph without the closure
+    plain = x.clone()
+    plan.set_closure(torch.from_numpy(v).cuda(), norm)
+    x.copy_(u0)
+    plan.rk_steps(x, dt, 3)                       # same state, dt, steps: a new graph
+    y = u0.clone()
+    for i in range(3):
+        plan.rk_step(y, dt, t=i * dt)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y) and not torch.equal(x, plain)
+    plan.set_closure(None)
+    x.copy_(u0)
+    plan.rk_steps(x, dt, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(x, plain)
+    plan.close()
+
+
 def test_constant_strain_network_is_an_eddy_viscosity(ps):
     """W3 = 0, b3 = (c, 0, ..): tau = s_tau c S/s_A, so the closure adds
     (s_tau c/(2 s_A)) |k|^2 u_hat to the right-hand side."""
