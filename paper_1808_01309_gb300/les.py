@@ -209,11 +209,13 @@ def _timed_steps(plan, u, dt: float, nsteps: int, t0: float) -> float:
 
 def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_spin=8.0, t_train=2.0,
                n_snap=8, t_eval=5.0, n_eval=10, iters=2000, lr=2e-3, fit="both", force_iters=1000,
-               force_lr=1e-3, drain_only=False, seed=1, verbose=True) -> dict:
+               force_lr=1e-3, drain_only=False, seed=1, verbose=True, points_per_snap=0) -> dict:
     """Runs the workflow of the module docstring; fit = "stress" (tensor-basis
     stress loss), "force" (stress fit refined on the force loss), "transfer"
     (stress fit refined on the shell energy-transfer loss) or "both" (all
-    three models evaluated)."""
+    three models evaluated).  points_per_snap > 0 keeps that many LES grid
+    points of every snapshot for the stress fit (the same seeded subset each
+    time; 0 keeps all n_les^3)."""
     torch = _torch()
     dev = "cuda"
     say = print if verbose else (lambda *a, **k: None)
@@ -222,7 +224,7 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     u = torch.from_numpy(inputs.random_solenoidal_field(n_dns, n_dns, n_dns, seed=seed)).to(dev, torch.complex64)
     dns = ps.Plan(n_dns, prec=ps.Precision.FP32, nu=nu, rk_order=4, forcing=f_dns)
     t = 0.0
-    out = dict(n_dns=n_dns, n_les=n_les, kc=kc, nu=nu, dt_dns=dt_dns, dt_les=dt_les, t_spin=t_spin,
+    out = dict(n_dns=n_dns, n_les=n_les, kc=kc, nu=nu, dt_dns=dt_dns, dt_les=dt_les, t_spin=t_spin, points_per_snap=points_per_snap,
                t_train=t_train, n_snap=n_snap, t_eval=t_eval, n_eval=n_eval, iters=iters, lr=lr)
     # 1. spin-up (energy recorded every half time unit)
     n_spin = int(round(t_spin / dt_dns))
@@ -248,8 +250,14 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
     norm = calibrate(Xr, A, T)
     del Xr
     Xs, As, Ts, snaps = [], [], [], []
+    keep = None
+    if 0 < points_per_snap < n_les ** 3:
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        keep = torch.randperm(n_les ** 3, generator=g)[:points_per_snap].to(dev)
     for k in range(n_snap):
         X, A, T = training_pairs(u, n_dns, n_les, kc, norm)
+        if keep is not None:
+            X, A, T = X[keep], A[keep], T[keep]
         Xs.append(X)
         As.append(A)
         Ts.append(T)
@@ -402,12 +410,14 @@ def main(argv=None):
     ap.add_argument("--force-iters", type=int, default=1000)
     ap.add_argument("--force-lr", type=float, default=1e-3)
     ap.add_argument("--drain-only", action="store_true", help="transfer fit: target min(T_exact, 0) per shell")
+    ap.add_argument("--points-per-snap", type=int, default=0,
+                    help="stress fit: LES grid points kept per snapshot (0 = all)")
     ap.add_argument("--out", default=None, help="write the result as JSON here")
     a = ap.parse_args(argv)
     r = experiment(n_dns=a.n_dns, n_les=a.n_les, kc=a.kc, nu=a.nu, dt_dns=a.dt_dns, dt_les=a.dt_les,
                    t_spin=a.t_spin, t_train=a.t_train, n_snap=a.n_snap, t_eval=a.t_eval, n_eval=a.n_eval,
                    iters=a.iters, lr=a.lr, fit=a.fit, force_iters=a.force_iters, force_lr=a.force_lr,
-                   drain_only=a.drain_only)
+                   drain_only=a.drain_only, points_per_snap=a.points_per_snap)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(r, fh, indent=1)
