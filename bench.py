@@ -254,7 +254,7 @@ def dense_model_bytes(n: int, vb: int):
 SCHED = {
     (8, 8): [8], (16, 16): [16], (8, 16): [8, 2], (8, 32): [8, 4], (8, 64): [8, 8], (16, 128): [16, 8],
     (8, 128): [8, 8, 2], (16, 256): [16, 16], (8, 256): [8, 8, 4], (8, 512): [8, 8, 8],
-    (16, 1024): [16, 8, 8], (8, 1024): [8, 8, 8, 2], (12, 48): [6, 4, 2], (12, 96): [6, 4, 4],
+    (16, 1024): [16, 8, 8], (8, 1024): [8, 8, 8, 2], (32, 512): [32, 16], (12, 48): [6, 4, 2], (12, 96): [6, 4, 4],
     (12, 192): [6, 4, 4, 2],
 }
 
@@ -278,8 +278,8 @@ def dft_flops(r: int) -> int:
     while length <= r:
         for _ in range(r // length):
             for j in range(length // 2):
-                s = (16 // length) * j
-                total += 4 + (0 if s in (0, 4) else 4 if s in (2, 6) else 6)
+                s = (32 // length) * j  # twiddle exp(2 pi i s/32)
+                total += 4 + (0 if s in (0, 8) else 4 if s in (4, 12) else 6)
         length *= 2
     return total
 
@@ -452,6 +452,7 @@ def run_ours(args, world, rank, local):
 
         copy_ms = host_steps(ps.HOST_COPY)
         mapped_ms = host_steps(ps.HOST_MAPPED)
+        ce_ms = host_steps(ps.HOST_CUBE_CE)
         e2e_ms = host_steps(ps.HOST_AUTO)
         nbytes = host.numel() * host.element_size()
         _, cx, c2, _ = retained(n)
@@ -462,11 +463,13 @@ def run_ours(args, world, rank, local):
 
         e2e = {"value": gpts(e2e_ms), "unit": UNIT, "ms_per_step": round(e2e_ms, 3),
                # default mode: the retained modes cross the host link each way;
-               # copy engines write the masked modes' zeros during the step
-               "h2d_bytes_per_step": ret_bytes, "d2h_bytes_per_step": nbytes, "steps": ksteps,
+               # host threads write the masked modes' zeros during the step
+               "h2d_bytes_per_step": ret_bytes, "d2h_bytes_per_step": ret_bytes, "steps": ksteps,
                "api": "ps_rk_step_host (pinned host state, 1 step per call; default mode: retained modes "
-                      "gathered/scattered by kernels through the device mapping, masked modes zeroed by copy "
-                      "engines during the step)",
+                      "gathered/scattered by kernels through the device mapping, masked modes zeroed by host "
+                      "threads during the step)",
+               "cube_copy_engine_zeros": {"ms_per_step": round(ce_ms, 3), "value": gpts(ce_ms),
+                                          "h2d_bytes_per_step": ret_bytes, "d2h_bytes_per_step": nbytes},
                "copy_engines_whole_state": {"ms_per_step": round(copy_ms, 3), "value": gpts(copy_ms),
                                             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                # in place: the passes read the retained modes 5 times and write the state once

@@ -184,9 +184,11 @@ ps_status ps_rk_steps(ps_plan* plan, void* uhat, double dt, double t, int nsteps
  *                    cudaHostRegister) only the retained cube of modes crosses
  *                    the host link, gathered and scattered by kernels through
  *                    the buffer's device mapping (NVLink-C2C on Grace
- *                    systems), while copy engines write the zeros of the
- *                    masked modes into the host buffer during the steps;
- *                    pageable memory takes PS_HOST_COPY;
+ *                    systems), while host threads of the calling process write
+ *                    the zeros of the masked modes into the host buffer during
+ *                    the steps; pageable memory takes PS_HOST_COPY;
+ *   PS_HOST_CUBE_CE: as PS_HOST_AUTO with the zeros written by copy engines
+ *                    (3D copies from a device buffer of zeros over the link);
  *   PS_HOST_COPY   : cudaMemcpyAsync of the whole state to a plan-owned device
  *                    buffer (allocated on the first call) and back;
  *   PS_HOST_SMCOPY : the whole state copied by a streaming kernel through the
@@ -196,7 +198,7 @@ ps_status ps_rk_steps(ps_plan* plan, void* uhat, double dt, double t, int nsteps
  *                    modes, the last stage writes it).
  * SMCOPY and MAPPED fail with PS_ERR_UNSUPPORTED on pageable memory.  The
  * modes outside the retained set are zero on return in every mode. */
-enum { PS_HOST_AUTO = 0, PS_HOST_COPY = 1, PS_HOST_MAPPED = 2, PS_HOST_SMCOPY = 3 };
+enum { PS_HOST_AUTO = 0, PS_HOST_COPY = 1, PS_HOST_MAPPED = 2, PS_HOST_SMCOPY = 3, PS_HOST_CUBE_CE = 4 };
 ps_status ps_rk_step_host(ps_plan* plan, void* uhat_host, double dt, double t, int nsteps);
 ps_status ps_plan_set_host_mode(ps_plan* plan, int mode);
 

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ps.h"
@@ -664,7 +665,7 @@ ps_status ps_rk_step(ps_plan* p, void* uhat, double dt, double t) {
 
 ps_status ps_plan_set_host_mode(ps_plan* p, int mode) {
   if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
-  if (mode < PS_HOST_AUTO || mode > PS_HOST_SMCOPY)
+  if (mode < PS_HOST_AUTO || mode > PS_HOST_CUBE_CE)
     return fail(PS_ERR_INVALID_ARG, "unknown host mode");
   p->host_mode = mode;
   return PS_OK;
@@ -723,6 +724,47 @@ cudaError_t zero_outside_cube(ps_plan* p, char* host) {
     }
   }
   return e;
+}
+
+// The same zeros written by host threads: every (component, kz) plane of the
+// host state is one task; a masked plane is cleared whole, a retained plane
+// in its masked rows (one contiguous block) and in the tails kx > Kx of its
+// retained rows.  Nothing crosses the host link.
+void zero_outside_cube_host(const ps_plan* p, char* host) {
+  const ps::Geo& g = p->g;
+  const size_t vb = p->sz.vb, row = (size_t)g.nh * vb, plane = (size_t)g.ny * row;
+  const int nc = p->cn.ncomp;
+  const long long nplanes = (long long)nc * g.nz;
+  auto work = [&](long long first, long long last) {
+    for (long long i = first; i < last; ++i) {
+      const int c = (int)(i / g.nz), z = (int)(i % g.nz);
+      char* base = host + (size_t)c * g.nz * plane + (size_t)z * plane;
+      const int r = z < (g.nz + 1) / 2 ? z : z - g.nz;
+      if (r > g.Kz || r < -g.Kz) {
+        std::memset(base, 0, plane);
+        continue;
+      }
+      const int yr0 = g.Ky + 1, nyr = g.ny - 2 * g.Ky - 1;
+      if (nyr > 0) std::memset(base + (size_t)yr0 * row, 0, (size_t)nyr * row);
+      const size_t tail = (size_t)(g.nh - g.cx) * vb;
+      if (tail == 0) continue;
+      for (int y = 0; y < g.ny; ++y) {
+        const int q = y < (g.ny + 1) / 2 ? y : y - g.ny;
+        if (q > g.Ky || q < -g.Ky) continue;
+        std::memset(base + (size_t)y * row + (size_t)g.cx * vb, 0, tail);
+      }
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = nt < 1 ? 1 : nt > 16 ? 16 : nt;
+  std::vector<std::thread> pool;
+  const long long per = (nplanes + nt - 1) / nt;
+  for (unsigned t = 1; t < nt; ++t) {
+    const long long a = t * per, b = std::min<long long>(nplanes, a + per);
+    if (a < b) pool.emplace_back(work, a, b);
+  }
+  work(0, std::min<long long>(nplanes, per));
+  for (auto& th : pool) th.join();
 }
 
 }  // namespace
@@ -812,8 +854,14 @@ ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int 
   if (!p->hstate) PS_CU(cudaMalloc(&p->hstate, bytes), "host-path state");
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
-  const bool cube = mapped && p->host_mode == PS_HOST_AUTO;
-  if (cube) {
+  const bool cube = mapped && (p->host_mode == PS_HOST_AUTO || p->host_mode == PS_HOST_CUBE_CE);
+  const bool host_zero = cube && p->host_mode == PS_HOST_AUTO;
+  if (host_zero) {
+    // only the retained modes cross the host link; host threads write the
+    // zeros of the masked modes while the GPU runs the steps
+    PS_CU(ps::launch_copy_cube(mapped, p->hstate, p->g, p->cn.ncomp, p->sz.vb, nsm, p->stream), "state upload");
+    p->launches++;
+  } else if (cube) {
     // only the retained modes cross the host link; the masked modes of the
     // host state are zeroed by copy engines while the steps run
     if (!p->side) {
@@ -838,20 +886,24 @@ ps_status ps_rk_step_host(ps_plan* p, void* uhat_host, double dt, double t, int 
   for (int i = 0; i < nsteps; ++i) {
     ps_status s = ps_rk_step(p, p->hstate, dt, t + i * dt);
     if (s != PS_OK) {
-      if (cube) cudaStreamSynchronize(p->side);
+      if (cube && !host_zero) cudaStreamSynchronize(p->side);
+      if (host_zero) cudaStreamSynchronize(p->stream);
       return s;
     }
   }
   if (cube) {
     PS_CU(ps::launch_copy_cube(p->hstate, mapped, p->g, p->cn.ncomp, p->sz.vb, nsm, p->stream), "state download");
     p->launches++;
-    PS_CU(cudaStreamWaitEvent(p->stream, p->side_done, 0), "side event");
+    if (!host_zero) PS_CU(cudaStreamWaitEvent(p->stream, p->side_done, 0), "side event");
   } else if (mapped) {
     PS_CU(ps::launch_stream_copy(p->hstate, mapped, bytes, nsm, p->stream), "state download");
     p->launches++;
   } else {
     PS_CU(cudaMemcpyAsync(uhat_host, p->hstate, bytes, cudaMemcpyDeviceToHost, p->stream), "state download");
   }
+  // the host threads' zeros touch only masked modes, the kernels only
+  // retained ones: both run while the steps are queued on the GPU
+  if (host_zero) zero_outside_cube_host(p, static_cast<char*>(uhat_host));
   PS_CU(cudaStreamSynchronize(p->stream), "host-path sync");
   return check_device_error(p);
 }

@@ -58,7 +58,7 @@ SYMBOLS = (
     "ps_slab_create", "ps_slab_destroy", "ps_slab_info_get", "ps_slab_inverse", "ps_slab_xpass",
     "ps_slab_forward", "ps_slab_check",
 )
-HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY = 0, 1, 2, 3
+HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY, HOST_CUBE_CE = 0, 1, 2, 3, 4
 MLP_NPARAM = 4934
 ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
 ENS_MAX_SIZES = 8

@@ -37,7 +37,7 @@ def test_host_buffer_steps_equal_device_steps(ps):
     plan.close()
 
 
-@pytest.mark.parametrize("mode", ["auto", "copy", "mapped", "smcopy"])
+@pytest.mark.parametrize("mode", ["auto", "copy", "mapped", "smcopy", "cube_ce"])
 def test_host_state_modes_match_device_steps(ps, mode):
     """Host-buffer stepping copies the state or lets the kernels access the
     page-locked buffer in place; both give the device result bit for bit."""
@@ -52,7 +52,8 @@ def test_host_state_modes_match_device_steps(ps, mode):
     mask = oracle.dealias_mask(oracle.Config(n, n, n))
     assert np.all(dev.cpu().numpy()[:, ~mask] == 0)
     ps.ps_plan_set_host_mode(plan.handle, {"auto": ps.HOST_AUTO, "copy": ps.HOST_COPY,
-                                           "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY}[mode])
+                                           "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY,
+                                           "cube_ce": ps.HOST_CUBE_CE}[mode])
     host = torch.from_numpy(u.astype(np.complex64)).pin_memory()
     for i in range(2):
         ps.ps_rk_step_host(plan.handle, host, dt, i * dt, 1)
@@ -66,7 +67,8 @@ def test_host_state_modes_match_device_steps(ps, mode):
     dm = torch.from_numpy(ub).cuda()
     pm.rk_step(dm, dt)
     ps.ps_plan_set_host_mode(pm.handle, {"auto": ps.HOST_AUTO, "copy": ps.HOST_COPY,
-                                         "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY}[mode])
+                                         "mapped": ps.HOST_MAPPED, "smcopy": ps.HOST_SMCOPY,
+                                           "cube_ce": ps.HOST_CUBE_CE}[mode])
     hm = torch.from_numpy(ub).pin_memory()
     ps.ps_rk_step_host(pm.handle, hm, dt, 0.0, 1)
     assert torch.equal(hm, dm.cpu())
@@ -76,7 +78,7 @@ def test_host_state_modes_match_device_steps(ps, mode):
         with pytest.raises(ps.PsError):
             ps.ps_rk_step_host(plan.handle, pageable, dt, 0.0, 1)
     with pytest.raises(ps.PsError):
-        ps.ps_plan_set_host_mode(plan.handle, 7)
+        ps.ps_plan_set_host_mode(plan.handle, 9)
     plan.close()
 
 
