@@ -254,7 +254,7 @@ def dense_model_bytes(n: int, vb: int):
 SCHED = {
     (8, 8): [8], (16, 16): [16], (8, 16): [8, 2], (8, 32): [8, 4], (8, 64): [8, 8], (16, 128): [16, 8],
     (8, 128): [8, 8, 2], (16, 256): [16, 16], (8, 256): [8, 8, 4], (8, 512): [8, 8, 8],
-    (16, 1024): [16, 8, 8], (8, 1024): [8, 8, 8, 2], (32, 512): [32, 16], (12, 48): [6, 4, 2], (12, 96): [6, 4, 4],
+    (16, 1024): [16, 8, 8], (8, 1024): [8, 8, 8, 2], (12, 48): [6, 4, 2], (12, 96): [6, 4, 4],
     (12, 192): [6, 4, 4, 2],
 }
 

@@ -16,11 +16,22 @@ struct Geo {
   int kxp;          // padded kx extent of the compact buffers (multiple of 16)
   int sphere;       // spherical truncation on top of the cube
   double sx, sy, sz;  // 2 pi / L per axis
+  float sxf, syf, szf;  // the same in FP32 (set_scales), for FP32 kernels
   // kx slab of a decomposed problem (zero for a whole problem): local column
   // c is the global kx0 + c; ncx local retained columns (0: cx); caller rows
   // of rowlen entries (0: nh)
   int kx0, ncx, rowlen;
 };
+// Sets the wavenumber scales 2 pi / L (and their FP32 copies) of g.
+inline void set_scales(Geo& g, double lx, double ly, double lz) {
+  const double two_pi = 6.283185307179586476925286766559;
+  g.sx = two_pi / lx;
+  g.sy = two_pi / ly;
+  g.sz = two_pi / lz;
+  g.sxf = (float)g.sx;
+  g.syf = (float)g.sy;
+  g.szf = (float)g.sz;
+}
 __host__ __device__ inline int ncols(const Geo& g) { return g.ncx ? g.ncx : g.cx; }
 __host__ __device__ inline int rowlen(const Geo& g) { return g.rowlen ? g.rowlen : g.nh; }
 
@@ -78,7 +89,28 @@ struct PassArgs {
   unsigned wait_polls;  // x pass: polls before a wait gives up (0 = PS_WAIT_LIMIT)
   int wait_test;     // x pass: test hook, the first copy of every CTA is never issued
   const void* extra; // compact closure term added to the velocity group before projection, or null
+  // Constants in the working precision, set by prepare_args() on the host so
+  // that FP32 kernels convert or divide no double on the GPU's slow FP64 pipe
+  float dtf, nuf, etaf, nbvf, inv_n3f;
+  double inv_n3;     // 1/(nx ny nz)
 };
+
+// Fills the derived constants of a (every launcher calls it on its copy).
+inline void prepare_args(PassArgs& a) {
+  a.dtf = (float)a.dt;
+  a.nuf = (float)a.nu;
+  a.etaf = (float)a.eta;
+  a.nbvf = (float)a.n_bv;
+  a.inv_n3 = 1.0 / ((double)a.g.nx * a.g.ny * a.g.nz);
+  a.inv_n3f = (float)a.inv_n3;
+}
+
+// The FP64 value in an FP64 kernel, its FP32 copy in an FP32 kernel.
+template <typename T>
+__host__ __device__ inline T pick(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 
 // Launchers (one per pass and precision); return the launch error.
 template <typename T> cudaError_t launch_zinv(const PassArgs& a, cudaStream_t s, int* nblocks_out);

@@ -250,7 +250,7 @@ __global__ void k_grad(const Geo g, const Spec u, V* out) {
     uu[1] = pm[u.cs];
     uu[2] = pm[2 * u.cs];
   }
-  const float k[3] = {float(p * g.sx), float(q * g.sy), float(r * g.sz)};
+  const float k[3] = {float(p) * g.sxf, float(q) * g.syf, float(r) * g.szf};
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -341,7 +341,7 @@ __global__ void k_div(const Geo g, const V* __restrict__ th, V* __restrict__ ext
   }
   const long long fs = (long long)g.nz * g.ny * g.nh;
   const long long fi = ((long long)rowof(r, g.nz) * g.ny + rowof(q, g.ny)) * g.nh + p;
-  const float k[3] = {float(p * g.sx), float(q * g.sy), float(r * g.sz)};
+  const float k[3] = {float(p) * g.sxf, float(q) * g.syf, float(r) * g.szf};
   // symmetric components in the order 11, 22, 33, 12, 13, 23
   const int idx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
 #pragma unroll
@@ -369,7 +369,7 @@ __global__ void k_force_residual(const Geo g, const V* __restrict__ extra, const
       const long long cs = (long long)g.cz * g.cy * g.kxp;
       const long long ci = ((long long)rowof(r, g.cz) * g.cy + rowof(q, g.cy)) * g.kxp + p;
       V v[3] = {extra[ci], extra[ci + cs], extra[ci + 2 * cs]};
-      const float kx = float(p * g.sx), ky = float(q * g.sy), kz = float(r * g.sz);
+      const float kx = float(p) * g.sxf, ky = float(q) * g.syf, kz = float(r) * g.szf;
       const float k2 = kx * kx + ky * ky + kz * kz;
       if (k2 > 0.f) {
         const V kd = cadd(cadd(cscale(v[0], kx), cscale(v[1], ky)), cscale(v[2], kz));
@@ -663,7 +663,8 @@ Geo cube_geo(int n) {
   g.cx = g.Kx + 1;
   g.cy = g.cz = 2 * g.Kx + 1;
   g.kxp = (g.cx + 15) / 16 * 16;
-  g.sx = g.sy = g.sz = 1.0;  // 2 pi box
+  set_scales(g, 6.283185307179586476925286766559, 6.283185307179586476925286766559,
+             6.283185307179586476925286766559);  // 2 pi box
   return g;
 }
 

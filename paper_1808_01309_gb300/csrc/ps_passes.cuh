@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
   const V* tw = static_cast<const V*>(a.tw_z);
   V* out = static_cast<V*>(a.a6);
-  const T skx = T(kxg) * T(g.sx), sky = T(q) * T(g.sy), sz = T(g.sz);
+  const T skx = T(kxg) * pick<T>(g.sx, g.sxf), sky = T(q) * pick<T>(g.sy, g.syf), sz = pick<T>(g.sz, g.szf);
   const long long fstride = (long long)g.nz * g.cy * g.kxp;
   const long long zstride = (long long)g.cy * g.kxp;
   const int cst = NB * g.cz * TX;                 // component stride in the tile
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
       }
       x[m] = v;
     }
-    if (f < 3) esum += (double)ssq;
+    if (a.e_part && f < 3) esum += (double)ssq;
     line_fft<N, E, +1>(x, j0, tw, ex);
     if (bvalid) {
 #pragma unroll
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs 
     x[m] = bvalid ? ldv(in + (long long)(j0 + m * (N / E)) * g.cy * g.kxp) : czero<V>();
   line_fft<N, E, -1>(x, j0, static_cast<const V*>(a.tw_z), ex);
   if (bvalid) {
-    const T inv = T(1.0 / ((double)g.nx * g.ny * g.nz));
+    const T inv = pick<T>(a.inv_n3, a.inv_n3f);
     V* out = static_cast<V*>(a.a6) + (long long)f * g.cz * g.cy * g.kxp + (long long)iy * g.kxp + kx;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -688,9 +688,9 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
   const int iy = rowof(q, g.cy), iz = rowof(r, g.cz);
   const long long ccs = (long long)g.cz * g.cy * g.kxp;  // compact component stride
   const long long ci = ((long long)iz * g.cy + iy) * g.kxp + kx;
-  const T kxv = T(kxg) * T(g.sx), kyv = T(q) * T(g.sy), kzv = T(r) * T(g.sz);
+  const T kxv = T(kxg) * pick<T>(g.sx, g.sxf), kyv = T(q) * pick<T>(g.sy, g.syf), kzv = T(r) * pick<T>(g.sz, g.szf);
   const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-  const T dt = T(a.dt);
+  const T dt = pick<T>(a.dt, a.dtf);
   const V* nh = static_cast<const V*>(a.a6);
   V w_s = czero<V>(), th_s = czero<V>();  // Boussinesq: w and theta of the stage input
   if constexpr (NSC == 1) {
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     const int nc = scl ? 1 : 3;
     V kk[3];
     if (scl) {
-      kk[0] = csub(cscale(w_s, T(a.n_bv)), ldv(nh + 3 * ccs + ci));
+      kk[0] = csub(cscale(w_s, pick<T>(a.n_bv, a.nbvf)), ldv(nh + 3 * ccs + ci));
       kk[1] = kk[2] = czero<V>();
     } else {
       V v0 = ldv(nh + (c0 + 0) * ccs + ci), v1 = ldv(nh + (c0 + 1) * ccs + ci), v2 = ldv(nh + (c0 + 2) * ccs + ci);
@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
           v1 = cadd(v1, ldv(fb + fo + fcs2));
           v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
         }
-        if constexpr (NSC == 1) v2 = csub(v2, cscale(th_s, T(a.n_bv)));  // buoyancy -N theta z
+        if constexpr (NSC == 1) v2 = csub(v2, cscale(th_s, pick<T>(a.n_bv, a.nbvf)));  // buoyancy -N theta z
         if (k2 > T(0)) {
           // Leray projection v - k (k.v)/|k|^2
           const V kd = cadd(cadd(cscale(v0, kxv), cscale(v1, kyv)), cscale(v2, kzv));
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     V* po = static_cast<V*>(a.out_full) + c0 * fcs + orow * rl + kx;
     const bool second = mag || scl;  // diffusivity and factor tables of the second field
     if (a.mode == ZF_RHS) {
-      const T vk = T(second ? a.eta : a.nu) * k2;
+      const T vk = (second ? pick<T>(a.eta, a.etaf) : pick<T>(a.nu, a.nuf)) * k2;
 #pragma unroll
       for (int c = 0; c < nc; ++c) po[c * fcs] = csub(kk[c], cscale(ldv(pu + c * a.u_n.cs), vk));
       continue;
@@ -824,7 +824,9 @@ static cudaError_t prep(K kernel, size_t smem) {
 }
 
 template <typename T, int N, int NG, int NSC>
-cudaError_t zinv_ng(const PassArgs& a, cudaStream_t s, int* nb) {
+cudaError_t zinv_ng(const PassArgs& a0, cudaStream_t s, int* nb) {
+  PassArgs a = a0;
+  prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   const size_t smem = (1ull * NB * N * TX + 3ull * NB * a.g.cz * TX) * sizeof(V);
@@ -841,7 +843,9 @@ cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
   return a.nsc ? zinv_ng<T, N, 1, 1>(a, s, nb) : zinv_ng<T, N, 1, 0>(a, s, nb);
 }
 template <typename T, int N>
-cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
+cudaError_t yinv_n(const PassArgs& a0, cudaStream_t s) {
+  PassArgs a = a0;
+  prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
@@ -862,7 +866,9 @@ size_t xpass_smem(const Geo& g, int rpc, int nf) {
 }
 
 template <typename T, int N, int NG, int NSC>
-cudaError_t xpass_ng(const PassArgs& a, cudaStream_t s) {
+cudaError_t xpass_ng(const PassArgs& a0, cudaStream_t s) {
+  PassArgs a = a0;
+  prepare_args(a);
   constexpr int NF = 6 * NG + 3 * NSC;
   constexpr int E = EOf<T, N>::v, G = N / E;
   // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
@@ -893,7 +899,9 @@ cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
 }
 
 template <typename T, int N>
-cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
+cudaError_t yfwd_n(const PassArgs& a0, cudaStream_t s) {
+  PassArgs a = a0;
+  prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
@@ -904,7 +912,9 @@ cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 template <typename T, int N>
-cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
+cudaError_t zfwd_n(const PassArgs& a0, cudaStream_t s) {
+  PassArgs a = a0;
+  prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
   const size_t smem = 2ull * NB * N * TX * sizeof(V);
@@ -915,7 +925,9 @@ cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t update_launch(const PassArgs& a, cudaStream_t s) {
+cudaError_t update_launch(const PassArgs& a0, cudaStream_t s) {
+  PassArgs a = a0;
+  prepare_args(a);
   const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
   const long long n = full ? (long long)a.g.nz * a.g.ny * rowlen(a.g) : (long long)a.g.cz * a.g.cy * ncols(a.g);
   const unsigned blocks = (unsigned)((n + 255) / 256);

@@ -82,10 +82,7 @@ Geo make_geo(const ps_config* c) {
   g.cz = 2 * g.Kz + 1;
   g.kxp = (g.cx + 15) / 16 * 16;
   g.sphere = c->dealias == PS_DEALIAS_SPHERICAL ? 1 : 0;
-  const double two_pi = 6.283185307179586476925286766559;
-  g.sx = two_pi / c->lx;
-  g.sy = two_pi / c->ly;
-  g.sz = two_pi / c->lz;
+  set_scales(g, c->lx, c->ly, c->lz);
   return g;
 }
 

@@ -101,10 +101,7 @@ ps_status run(const ps_config* c, cudaStream_t s, const void* uhat, void* out) {
   g.cz = 2 * g.Kz + 1;
   g.kxp = (g.cx + 15) / 16 * 16;
   g.sphere = c->dealias == PS_DEALIAS_SPHERICAL ? 1 : 0;
-  const double two_pi = 6.283185307179586476925286766559;
-  g.sx = two_pi / c->lx;
-  g.sy = two_pi / c->ly;
-  g.sz = two_pi / c->lz;
+  set_scales(g, c->lx, c->ly, c->lz);
 
   const size_t vb = sizeof(V), kxp = g.kxp;
   const size_t a1 = 6ull * g.nz * g.cy * kxp, a2 = 3ull * g.nz * g.ny * kxp;
