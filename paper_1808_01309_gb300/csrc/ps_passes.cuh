@@ -652,22 +652,25 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
   using V = typename cplx<T>::type;
   constexpr int NC = 3 * NG + NSC;  // state components
   const Geo& g = a.g;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // 32-bit mode index (the launcher checks that the modes fit): 64-bit
+  // integer division runs on the FP64 pipe, which is slow on this GPU
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   // a whole problem (not a kx slab) has rows of nh entries and cx columns
-  const int rl = SLAB ? rowlen(g) : g.nh, nc = SLAB ? ncols(g) : g.cx;
+  const unsigned rl = SLAB ? rowlen(g) : g.nh, nc = SLAB ? ncols(g) : g.cx;
   int kx, q, r;  // kx: local column (array index); kxg = g.kx0 + kx its global kx
   long long orow = 0;  // row of the caller layout (z * ny + y)
   if (full) {
-    if (idx >= (long long)g.nz * g.ny * rl) return;
+    if (idx >= (unsigned)g.nz * (unsigned)g.ny * rl) return;
     kx = (int)(idx % rl);
-    orow = idx / rl;
-    q = sidx((int)(orow % g.ny), g.ny);
-    r = sidx((int)(orow / g.ny), g.nz);
+    const unsigned orow32 = idx / rl;
+    orow = orow32;
+    q = sidx((int)(orow32 % (unsigned)g.ny), g.ny);
+    r = sidx((int)(orow32 / (unsigned)g.ny), g.nz);
   } else {
-    if (idx >= (long long)g.cz * g.cy * nc) return;
+    if (idx >= (unsigned)g.cz * (unsigned)g.cy * nc) return;
     kx = (int)(idx % nc);
-    const long long crow = idx / nc;
-    const int iy = (int)(crow % g.cy), iz = (int)(crow / g.cy);
+    const unsigned crow = idx / nc;
+    const int iy = (int)(crow % (unsigned)g.cy), iz = (int)(crow / (unsigned)g.cy);
     q = iy <= g.Ky ? iy : iy - g.cy;
     r = iz <= g.Kz ? iz : iz - g.cz;
   }
@@ -930,6 +933,7 @@ cudaError_t update_launch(const PassArgs& a0, cudaStream_t s) {
   prepare_args(a);
   const int full = (a.mode == ZF_RHS || a.mode == ZF_RK4_4 || a.mode == ZF_RK2_2) ? 1 : 0;
   const long long n = full ? (long long)a.g.nz * a.g.ny * rowlen(a.g) : (long long)a.g.cz * a.g.cy * ncols(a.g);
+  if (n >= (1LL << 32) - 256) return cudaErrorInvalidValue;  // the kernel indexes modes in 32 bits
   const unsigned blocks = (unsigned)((n + 255) / 256);
   const bool slab = a.g.kx0 != 0 || a.g.ncx != 0 || a.g.rowlen != 0;
   if (slab) k_update<T, 1, 0, true><<<blocks, 256, 0, s>>>(a, full);  // slabs: HD only
