@@ -35,24 +35,32 @@ namespace ps {
 template <typename T, int K = 0> struct TXOf {
   static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4;
 };
+// Points per thread of pass K (0 z-inverse, 1 y passes, 2 z-forward, 3 x
+// pass).  At 1024 points FP32 the x pass takes 8 points per thread (four
+// stages, 128 threads per row: 13.0 ms per 1024^3 launch against 13.6 ms
+// with 16) and the strided passes 16 (three stages, 64 threads per line),
+// each the faster for its pass.
+template <typename T, int N, int K> struct EPass {
+  static constexpr int v = sizeof(T) == 4 && N == 1024 && K == 3 ? 8 : EOf<T, N>::v;
+};
 // lines batched per CTA in the strided passes (about 256 threads per CTA)
 template <typename T, int N, int K = 0> struct NBOf {
-  static constexpr int G = N / EOf<T, N>::v;
+  static constexpr int G = N / EPass<T, N, K>::v;
   static constexpr int q = 256 / (TXOf<T, K>::v * G);
   static constexpr int v = q < 1 ? 1 : q;
 };
 template <typename T, int N, int K = 0> struct ColThreads {
-  static constexpr int v = TXOf<T, K>::v * (N / EOf<T, N>::v) * NBOf<T, N, K>::v;
+  static constexpr int v = TXOf<T, K>::v * (N / EPass<T, N, K>::v) * NBOf<T, N, K>::v;
 };
 // rows per CTA in the x pass
 template <typename T, int N> struct RPCOf {
-  static constexpr int G = N / EOf<T, N>::v;
+  static constexpr int G = N / EPass<T, N, 3>::v;
   static constexpr int v = G >= 256 ? 1 : 256 / G;
 };
 
 // x pass: per-thread twiddle table in shared memory when it takes at most 8 KB
 template <typename T, int N> struct XTwTable {
-  static constexpr int E = EOf<T, N>::v;
+  static constexpr int E = EPass<T, N, 3>::v;
   static constexpr bool v = (size_t)TwSlots<N, E>::total * (N / E) * sizeof(typename cplx<T>::type) <= 8192;
 };
 
@@ -64,7 +72,7 @@ constexpr int XLINES = 3;
 #define PS_XTWREG 14
 #endif
 template <typename T, int N> struct XTwReg {
-  static constexpr int E = EOf<T, N>::v;
+  static constexpr int E = EPass<T, N, 3>::v;
   static constexpr bool v = sizeof(T) == 4 && E == 8 && TwSlots<N, E>::total <= PS_XTWREG;
 };
 
@@ -79,7 +87,8 @@ template <typename T, int N> struct XTwReg {
 #define PS_MINB_XPASS 2
 #endif
 template <typename T, int N> struct MinB {
-  static constexpr int zinv = PS_MINB_ZINV, xpass = PS_MINB_XPASS;
+  // (1024-point z lines: the input tile and exchange hold one CTA per SM)
+  static constexpr int zinv = N == 1024 ? 1 : PS_MINB_ZINV, xpass = PS_MINB_XPASS;
 };
 
 __device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -137,7 +146,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 template <typename T, int N, int NG, int NSC>
 __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  constexpr int E = EPass<T, N, 0>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   constexpr int NTH = ColThreads<T, N>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
 template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -318,11 +327,11 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs 
 // u . grad theta out.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int NG, int NSC>
-__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v),
+__global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
                                   NG == 1 && NSC == 0 ? MinB<T, N>::xpass : 1)
     k_xpass(const PassArgs a, const int rpc) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E;
+  constexpr int E = EPass<T, N, 3>::v, G = N / E;
   constexpr int NF = 6 * NG + 3 * NSC;  // input fields: u, omega (, B, j) (, grad theta)
   constexpr int NLI = 3 * NG + 2 * NSC;  // inverse packed lines
   constexpr bool HD = NG == 1 && NSC == 0;
@@ -567,7 +576,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EOf<T, N>::v),
 template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -602,7 +611,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs 
 template <typename T, int N>
 __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
+  constexpr int E = EPass<T, N, 2>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -863,7 +872,7 @@ cudaError_t yinv_n(const PassArgs& a0, cudaStream_t s) {
 template <typename T, int N>
 size_t xpass_smem(const Geo& g, int rpc, int nf) {
   using V = typename cplx<T>::type;
-  constexpr int E = EOf<T, N>::v;
+  constexpr int E = EPass<T, N, 3>::v;
   const size_t tt = (!XTwReg<T, N>::v && XTwTable<T, N>::v) ? (size_t)TwSlots<N, E>::total * (N / E) : 0;
   return ((size_t)nf * rpc * g.kxp + (size_t)XLINES * rpc * N + tt) * sizeof(V);
 }
@@ -873,7 +882,7 @@ cudaError_t xpass_ng(const PassArgs& a0, cudaStream_t s) {
   PassArgs a = a0;
   prepare_args(a);
   constexpr int NF = 6 * NG + 3 * NSC;
-  constexpr int E = EOf<T, N>::v, G = N / E;
+  constexpr int E = EPass<T, N, 3>::v, G = N / E;
   // rows per CTA: as many as the launch bound allows while two CTAs fit an SM
   int rpc = RPCOf<T, N>::v;
   while (rpc > 1 && xpass_smem<T, N>(a.g, rpc, NF) > 113 * 1024) rpc /= 2;
