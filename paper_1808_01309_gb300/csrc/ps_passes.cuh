@@ -86,9 +86,26 @@ template <typename T, int N> struct XTwReg {
 #ifndef PS_MINB_XPASS
 #define PS_MINB_XPASS 2
 #endif
+#ifndef PS_MINB_Y1024
+#define PS_MINB_Y1024 2
+#endif
+#ifndef PS_MINB_ZF1024
+#define PS_MINB_ZF1024 2
+#endif
+// Exchange buffers of the y passes and the z-forward pass: two (one barrier
+// per exchange), or one (two barriers) at 1024 points FP32, where two
+// buffers of 1024-point lines (128 KB) would hold the SM to one CTA.
+#ifndef PS_COLBUF1024
+#define PS_COLBUF1024 1
+#endif
+template <typename T, int N> struct ColBuf {
+  static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : 2;
+};
 template <typename T, int N> struct MinB {
   // (1024-point z lines: the input tile and exchange hold one CTA per SM)
   static constexpr int zinv = N == 1024 ? 1 : PS_MINB_ZINV, xpass = PS_MINB_XPASS;
+  static constexpr int ypass = sizeof(T) == 4 && N == 1024 ? PS_MINB_Y1024 : 1;
+  static constexpr int zfwd = sizeof(T) == 4 && N == 1024 ? PS_MINB_ZF1024 : 1;
 };
 
 __device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -282,7 +299,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
 // yinv: backward transform along y of 6 fields.  CTA = TX columns x NB z planes.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yinv(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yinv(const PassArgs 
   const bool bvalid = iz < g.nz;
   const int kx = blockIdx.x * TX + line;
   const int f = blockIdx.z;
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
   V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
   V x[E];
@@ -574,7 +591,7 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
 // yfwd: forward transform along y of 3 fields, keep |ky| <= Ky.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -586,7 +603,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs 
   const bool bvalid = iz < g.nz;
   const int kx = blockIdx.x * TX + line;
   const int f = blockIdx.z;
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
   V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
   V x[E];
@@ -609,7 +626,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v) k_yfwd(const PassArgs 
 // retained).  The projection, forcing and stage update follow in k_update.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs a) {
+__global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 2>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -622,7 +639,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v) k_zfwd(const PassArgs 
   const int kx = blockIdx.x * TX + line;
   const int q = iy <= g.Ky ? iy : iy - g.cy;
   const int f = blockIdx.z;
-  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
+  ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const long long cs_in = (long long)g.nz * g.cy * g.kxp;
   const V* in = static_cast<const V*>(a.b6) + f * cs_in + (long long)(bvalid ? iy : 0) * g.kxp + kx;
   V x[E];
@@ -860,7 +877,7 @@ cudaError_t yinv_n(const PassArgs& a0, cudaStream_t s) {
   prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
-  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yinv<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfi);
@@ -916,7 +933,7 @@ cudaError_t yfwd_n(const PassArgs& a0, cudaStream_t s) {
   prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
-  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_yfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfo);
@@ -929,7 +946,7 @@ cudaError_t zfwd_n(const PassArgs& a0, cudaStream_t s) {
   prepare_args(a);
   using V = typename cplx<T>::type;
   constexpr int TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
-  const size_t smem = 2ull * NB * N * TX * sizeof(V);
+  const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
   cudaError_t e = prep(k_zfwd<T, N>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB, a.nfo);
