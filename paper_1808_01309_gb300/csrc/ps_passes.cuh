@@ -95,17 +95,26 @@ template <typename T, int N> struct XTwReg {
 // Exchange buffers of the y passes and the z-forward pass: two (one barrier
 // per exchange), or one (two barriers) at 1024 points FP32, where two
 // buffers of 1024-point lines (128 KB) would hold the SM to one CTA.
+#ifndef PS_COLBUF512
+#define PS_COLBUF512 2
+#endif
+#ifndef PS_MINB_Y512
+#define PS_MINB_Y512 0
+#endif
+#ifndef PS_MINB_ZF512
+#define PS_MINB_ZF512 0
+#endif
 #ifndef PS_COLBUF1024
 #define PS_COLBUF1024 1
 #endif
 template <typename T, int N> struct ColBuf {
-  static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : 2;
+  static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : sizeof(T) == 4 && N == 512 ? PS_COLBUF512 : 2;
 };
 template <typename T, int N> struct MinB {
   // (1024-point z lines: the input tile and exchange hold one CTA per SM)
   static constexpr int zinv = N == 1024 ? 1 : PS_MINB_ZINV, xpass = PS_MINB_XPASS;
-  static constexpr int ypass = sizeof(T) == 4 && N == 1024 ? PS_MINB_Y1024 : 1;
-  static constexpr int zfwd = sizeof(T) == 4 && N == 1024 ? PS_MINB_ZF1024 : 1;
+  static constexpr int ypass = sizeof(T) == 4 && N == 1024 ? PS_MINB_Y1024 : sizeof(T) == 4 && N == 512 ? PS_MINB_Y512 : 0;
+  static constexpr int zfwd = sizeof(T) == 4 && N == 1024 ? PS_MINB_ZF1024 : sizeof(T) == 4 && N == 512 ? PS_MINB_ZF512 : 0;
 };
 
 __device__ __forceinline__ int sidx(int n, int N) { return n < N / 2 ? n : n - N; }
