@@ -92,23 +92,30 @@ template <typename T, int N> struct XTwReg {
 #ifndef PS_MINB_ZF1024
 #define PS_MINB_ZF1024 2
 #endif
-// Exchange buffers of the y passes and the z-forward pass: two (one barrier
-// per exchange), or one (two barriers) at 1024 points FP32, where two
-// buffers of 1024-point lines (128 KB) would hold the SM to one CTA.
+// Exchange buffers of the y passes and the z-forward pass: one (two barriers
+// per exchange) for FP32 lines of 64 points and more, two (one barrier) else.
+// The single buffer lets more CTAs share an SM: four of 512 threads at 512
+// points (32 registers; 2 % faster than three CTAs with two buffers), two at
+// 1024 points (64 registers; two buffers of 128 KB held the SM to one CTA:
+// 1.3-1.4x slower), register-limited counts below (256^3 step 5 % faster).
 #ifndef PS_COLBUF512
-#define PS_COLBUF512 2
+#define PS_COLBUF512 1
 #endif
 #ifndef PS_MINB_Y512
-#define PS_MINB_Y512 0
+#define PS_MINB_Y512 4
 #endif
 #ifndef PS_MINB_ZF512
-#define PS_MINB_ZF512 0
+#define PS_MINB_ZF512 4
+#endif
+#ifndef PS_COLBUF_SMALL
+#define PS_COLBUF_SMALL 1
 #endif
 #ifndef PS_COLBUF1024
 #define PS_COLBUF1024 1
 #endif
 template <typename T, int N> struct ColBuf {
-  static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : sizeof(T) == 4 && N == 512 ? PS_COLBUF512 : 2;
+  static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : sizeof(T) == 4 && N == 512 ? PS_COLBUF512
+                           : sizeof(T) == 4 && N >= 64 ? PS_COLBUF_SMALL : 2;
 };
 template <typename T, int N> struct MinB {
   // (1024-point z lines: the input tile and exchange hold one CTA per SM)
