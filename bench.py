@@ -695,7 +695,10 @@ def fp32_error_table(g, ref_dir):
 def run_ensemble(args, dev, stream):
     """48 independent unforced solves (16 each at 64^3, 96^3, 128^3), seeds
     1000+i, nu_i = 1e-3 + 4e-3 U(seed 2000+i), FP32, IF-RK4, dt = 1e-3:
-    member-by-member launches vs one CUDA graph of all steps (autotuned)."""
+    member-by-member launches vs one CUDA graph of the members' launch chains
+    vs one persistent kernel over a (member, pass, tile) work queue (both
+    graphs autotuned); the persistent states are checked bit for bit against
+    the graph's."""
     import torch
     from paper_1808_01309_gb300 import inputs, ps
     cfgs, host = [], []
@@ -712,7 +715,8 @@ def run_ensemble(args, dev, stream):
            "tuning": tuning, "tune_s": round(tune_s, 2)}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    for mode, name in ((ps.ENS_SEQUENTIAL, "sequential"), (ps.ENS_GRAPH, "graph")):
+    finals = {}
+    for mode, name in ((ps.ENS_SEQUENTIAL, "sequential"), (ps.ENS_GRAPH, "graph"), (ps.ENS_PERSISTENT, "persistent")):
         states = [h.clone() for h in host]
         # warm-up (for the graph: captures and instantiates the K-step graph)
         t1 = time.perf_counter()
@@ -724,9 +728,15 @@ def run_ensemble(args, dev, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        ps.ps_ensemble_check(ens)
         out[name] = {"ms": round(ms, 3), "ms_per_step": round(ms / K, 4),
                      "gpoints_s": round(points / (ms * 1e-3) / 1e9, 3), "first_call_s": round(first, 3)}
+        finals[name] = states
     out["graph_speedup"] = round(out["sequential"]["ms"] / out["graph"]["ms"], 3)
+    out["persistent_speedup"] = round(out["sequential"]["ms"] / out["persistent"]["ms"], 3)
+    out["persistent_vs_graph"] = round(out["graph"]["ms"] / out["persistent"]["ms"], 3)
+    out["persistent_equals_graph"] = all(bool(torch.equal(a, b)) for a, b in zip(finals["persistent"], finals["graph"]))
+    out["default_mode"] = tuning["best_mode"]
     ps.ps_ensemble_destroy(ens)
     return out
 

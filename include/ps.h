@@ -249,20 +249,39 @@ typedef struct ps_ensemble ps_ensemble;
  * the ensemble stream.  PS_ENS_GRAPH: all nsteps steps of all members as one
  * CUDA graph launch; each member's launch chain is a branch, branches run
  * concurrently (number of branches chosen by ps_ensemble_tune, default
- * min(members, 16)).  The graph is captured on the first call with a given
- * (states, dt, t, nsteps) and replayed by later identical calls. */
-typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1 } ps_ens_mode;
+ * min(members, 16)).  PS_ENS_PERSISTENT: all nsteps steps of all members in
+ * ONE persistent kernel launch whose CTAs take (member, pass, tile) work items
+ * from a device queue; a member's pass starts once the member's previous pass
+ * is complete (device counters), so the passes of different members overlap.
+ * The launch is captured in a CUDA graph with the reset of its counters.  It
+ * needs members of one precision, the hydrodynamic system without a closure
+ * and axis lengths in {32, 48, 64, 96, 128} (PS_ERR_UNSUPPORTED otherwise);
+ * its bounded waits report through ps_ensemble_check.  PS_ENS_AUTO: the mode
+ * ps_ensemble_tune found faster (PS_ENS_GRAPH before tuning).  Graphs are
+ * captured on the first call with given (states, dt, nsteps) and replayed by
+ * later identical calls (t does not enter the right-hand side). */
+typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1, PS_ENS_PERSISTENT = 2, PS_ENS_AUTO = 3 } ps_ens_mode;
 
 /* Result of ps_ensemble_tune: concurrent branches, and per distinct grid
  * (first nsizes entries, n = nx of the grid) the x-pass rows per CTA chosen
  * (0 = the automatic maximum); step_ms = graph time of one step of all
- * members with the chosen shapes. */
+ * members with the chosen shapes.  The persistent launch's choices:
+ * resident CTAs per SM (0 = as many as fit), member order (0 = as created,
+ * 1 = largest grid first) and tiles per work item of the z-inverse,
+ * y-inverse, x, y-forward, z-forward and update passes (in that order);
+ * persistent_step_ms is its time of one step (-1: not supported by these
+ * members).  best_mode is what PS_ENS_AUTO now runs. */
 typedef struct {
   int branches;
   int nsizes;
   int n[PS_ENS_MAX_SIZES];
   int xrpc[PS_ENS_MAX_SIZES];
   double step_ms;
+  double persistent_step_ms;
+  int persistent_ctas_per_sm;
+  int persistent_order;
+  int persistent_tiles_per_item[6];
+  int best_mode;
 } ps_ens_tuning;
 
 /* Create count (1..PS_ENS_MAX_MEMBERS) member plans from cfgs[i] (each as for
@@ -281,6 +300,17 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
  * branches, keeps the fastest and reports them.  Allocates temporary copies
  * of the states.  Synchronises the ensemble stream. */
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
+
+/* Synchronises the ensemble stream and reports whether a bounded wait of a
+ * persistent launch gave up since the last check (PS_ERR_TIMEOUT; the member
+ * states are then invalid: the stage updates write NaN once the error word is
+ * set).  Clears the report. */
+ps_status ps_ensemble_check(ps_ensemble* e);
+
+/* Test hook of the persistent launch's failure path: with polls > 0 one pass
+ * instance waits for one tile more than its predecessor has, and every wait
+ * gives up after `polls` polls; 0 restores normal operation. */
+ps_status ps_ensemble_set_wait_test(ps_ensemble* e, unsigned polls);
 
 /* ---- Learned LES closure: pointwise MLP on the BF16 tensor cores --------
  * A multilayer perceptron 5 -> 64 -> 64 -> 6 with GELU (tanh form) maps the

@@ -1,16 +1,22 @@
 // Ensemble of independent solves of uneven sizes (include/ps.h,
-// ps_ensemble_*): one plan per member, stepped either member after member on
-// one stream, or as a single CUDA graph in which the members' launch chains
-// are independent branches that the GPU runs concurrently.  A small autotuner
-// picks the number of concurrent branches and, per grid size, the x-pass row
-// group (rows per CTA) by timing the candidates.
+// ps_ensemble_*): one plan per member, stepped member after member on one
+// stream, as a single CUDA graph in which the members' launch chains are
+// independent branches that the GPU runs concurrently, or as one persistent
+// kernel launch over a device work queue of (member, pass, tile) items
+// (ps_persist.cuh), itself captured in a CUDA graph.  An autotuner times the
+// graph's branch count and x-pass row groups, and the persistent launch's
+// tiles per work item, CTAs per SM and member order, and picks the faster
+// mode for PS_ENS_AUTO.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "ps.h"
 #include "ps_kernels.h"
+#include "ps_persist.cuh"
 
 namespace ps {
 void set_last_error(const std::string& msg);
@@ -33,6 +39,29 @@ struct ps_ensemble {
   std::vector<void*> key_states;
   double key_dt = NAN, key_t = NAN;
   int key_steps = -1, key_branches = -1;
+  // persistent launch: work list, counters and its captured graph
+  EnsPass* d_passes = nullptr;
+  PassArgs* d_args = nullptr;
+  unsigned* d_done = nullptr;
+  unsigned long long* d_head = nullptr;
+  int* d_err = nullptr;
+  size_t cap_passes = 0, cap_args = 0;
+  int npass = 0;
+  long long tickets = 0;
+  size_t smem = 0;
+  int grid = 0;
+  cudaGraph_t pgraph = nullptr;
+  cudaGraphExec_t pexec = nullptr;
+  std::vector<void*> pkey_states;
+  double pkey_dt = NAN;
+  int pkey_steps = -1;
+  // persistent tuning knobs: tiles per ticket per pass kind, CTAs per SM
+  // (0 = as many as fit), member order (0 = as created, 1 = largest first)
+  int per[7] = {1, 2, 1, 2, 1, 8, 1};
+  int ctas_per_sm = 0;
+  int order = 0;
+  unsigned wait_test = 0;  // > 0: test hook (one dependency never completes; polls limit)
+  ps_ens_mode auto_mode = PS_ENS_GRAPH;
 };
 
 namespace {
@@ -131,6 +160,192 @@ ps_status run_graph(ps_ensemble* e, void* const* u, double dt, double t, int nst
   return PS_OK;
 }
 
+void drop_pgraph(ps_ensemble* e) {
+  if (e->pexec) cudaGraphExecDestroy(e->pexec);
+  if (e->pgraph) cudaGraphDestroy(e->pgraph);
+  e->pexec = nullptr;
+  e->pgraph = nullptr;
+  e->pkey_steps = -1;
+}
+
+// Why the members cannot share one persistent launch ("" if they can).
+std::string persist_unsupported(const ps_ensemble* e) {
+  auto ok_n = [](int n) { return n == 32 || n == 48 || n == 64 || n == 96 || n == 128; };
+  for (size_t i = 0; i < e->plans.size(); ++i) {
+    const PlanView v = plan_view(e->plans[i]);
+    if (v.prec != plan_view(e->plans[0]).prec) return "members of both precisions";
+    if (v.eq != PS_HD) return "only the hydrodynamic system";
+    if (v.closure) return "a member has a learned closure attached";
+    if (!ok_n(v.g.nx) || !ok_n(v.g.ny) || !ok_n(v.g.nz)) return "axis lengths outside {32, 48, 64, 96, 128}";
+  }
+  return "";
+}
+
+// Builds the work list of nsteps steps of every member on the states u and
+// uploads it with the stage arguments.
+ps_status persist_build(ps_ensemble* e, void* const* u, double dt, int nsteps) {
+  const std::string why = persist_unsupported(e);
+  if (!why.empty()) return bad(PS_ERR_UNSUPPORTED, "ensemble: persistent mode: " + why);
+  const size_t m = e->plans.size();
+  const bool f32 = plan_view(e->plans[0]).prec == PS_FP32;
+  std::vector<PassArgs> args;
+  std::vector<int> base(m), nst(m);
+  for (size_t i = 0; i < m; ++i) {
+    const PlanView v = plan_view(e->plans[i]);
+    nst[i] = v.rk_stages;
+    base[i] = (int)args.size();
+    for (int st = 0; st < nst[i]; ++st) args.push_back(plan_stage_args(e->plans[i], u[i], dt, st, false));
+    args.push_back(plan_stage_args(e->plans[i], u[i], dt, 0, true));  // stage 0 with the step statistics
+  }
+  if (!e->d_err) ENS_CU(cudaMalloc(&e->d_err, sizeof(int)), "error word");
+  for (auto& a : args) a.err = e->d_err;
+  std::vector<int> ord(m);
+  std::iota(ord.begin(), ord.end(), 0);
+  if (e->order == 1)
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const Geo ga = plan_view(e->plans[a]).g, gb = plan_view(e->plans[b]).g;
+      return (long long)ga.nx * ga.ny * ga.nz > (long long)gb.nx * gb.ny * gb.nz;
+    });
+  std::vector<EnsPass> passes;
+  std::vector<int> last(m, -1);
+  size_t smem = 0;
+  long long tick = 0;
+  int max_st = *std::max_element(nst.begin(), nst.end());
+  const int kinds[] = {EK_ZINV, EK_SUM, EK_YINV, EK_XPASS, EK_YFWD, EK_ZFWD, EK_UPDATE};
+  for (int s = 0; s < nsteps; ++s)
+    for (int st = 0; st < max_st; ++st)
+      for (int kind : kinds)
+        for (int i : ord) {
+          if (st >= nst[i]) continue;
+          const bool stats = s == nsteps - 1 && st == 0;
+          if (kind == EK_SUM && !stats) continue;
+          const PlanView v = plan_view(e->plans[i]);
+          const Geo& g = v.g;
+          EnsPass P{};
+          P.args = base[i] + (stats ? nst[i] : st);
+          P.kind = kind;
+          P.dep = last[i];
+          P.need = last[i] >= 0 ? passes[last[i]].ntiles : 0;
+          P.per = e->per[kind] > 0 ? e->per[kind] : 1;
+          EnsShape sh;
+          if (kind == EK_UPDATE) {
+            P.full = (st == nst[i] - 1) ? 1 : 0;
+            const long long n = P.full ? (long long)g.nz * g.ny * g.nh : (long long)g.cz * g.cy * g.cx;
+            sh.ntiles = (int)((n + ENS_UPDATE_MODES - 1) / ENS_UPDATE_MODES);
+          } else if (kind == EK_SUM) {
+            sh.ntiles = 1;
+            sh.gx = v.n_epart;
+            P.sum_out = v.stats;
+            P.per = 1;
+          } else {
+            const int n = kind == EK_XPASS ? g.nx : (kind == EK_YINV || kind == EK_YFWD) ? g.ny : g.nz;
+            const int nf = kind == EK_YINV ? 6 : 3;
+            sh = f32 ? ens_shape<float>(kind, n, g, nf) : ens_shape<double>(kind, n, g, nf);
+            P.n = n;
+          }
+          if (sh.ntiles <= 0) return bad(PS_ERR_UNSUPPORTED, "ensemble: persistent mode: no tiles for a pass");
+          P.ntiles = sh.ntiles;
+          P.gx = sh.gx;
+          P.gy = sh.gy;
+          P.tick0 = tick;
+          tick += (P.ntiles + P.per - 1) / P.per;
+          smem = std::max(smem, sh.smem);
+          if (kind != EK_SUM) last[i] = (int)passes.size();
+          passes.push_back(P);
+        }
+  if (e->wait_test) {
+    // test hook: the first pass that waits for another waits for one tile too many
+    for (auto& P : passes)
+      if (P.dep >= 0) {
+        P.need += 1;
+        break;
+      }
+  }
+  if (passes.size() > e->cap_passes) {
+    if (e->d_passes) cudaFree(e->d_passes);
+    if (e->d_done) cudaFree(e->d_done);
+    e->d_passes = nullptr;
+    e->d_done = nullptr;
+    ENS_CU(cudaMalloc(&e->d_passes, passes.size() * sizeof(EnsPass)), "work list");
+    ENS_CU(cudaMalloc(&e->d_done, passes.size() * sizeof(unsigned)), "work counters");
+    e->cap_passes = passes.size();
+  }
+  if (args.size() > e->cap_args) {
+    if (e->d_args) cudaFree(e->d_args);
+    e->d_args = nullptr;
+    ENS_CU(cudaMalloc(&e->d_args, args.size() * sizeof(PassArgs)), "stage arguments");
+    e->cap_args = args.size();
+  }
+  if (!e->d_head) ENS_CU(cudaMalloc(&e->d_head, sizeof(unsigned long long)), "ticket counter");
+  ENS_CU(cudaMemcpy(e->d_passes, passes.data(), passes.size() * sizeof(EnsPass), cudaMemcpyHostToDevice), "work list");
+  ENS_CU(cudaMemcpy(e->d_args, args.data(), args.size() * sizeof(PassArgs), cudaMemcpyHostToDevice), "stage arguments");
+  e->npass = (int)passes.size();
+  e->tickets = tick;
+  e->smem = smem;
+  int dev = 0, nsm = 0, per_sm = 0;
+  ENS_CU(cudaGetDevice(&dev), "device");
+  ENS_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  ENS_CU(f32 ? ens_blocks_per_sm_f32(smem, &per_sm) : ens_blocks_per_sm_f64(smem, &per_sm), "occupancy");
+  if (per_sm < 1) return bad(PS_ERR_UNSUPPORTED, "ensemble: persistent kernel does not fit an SM");
+  if (e->ctas_per_sm > 0) per_sm = std::min(per_sm, e->ctas_per_sm);
+  e->grid = nsm * per_sm;
+  return PS_OK;
+}
+
+// Captures, on the capture stream: the members' integrating-factor tables,
+// the reset of the step-statistics maximum, of the work counters and of the
+// error word, then the persistent launch.
+ps_status persist_capture(ps_ensemble* e, void* const* u, double dt, int nsteps) {
+  drop_pgraph(e);
+  ps_status st = persist_build(e, u, dt, nsteps);
+  if (st != PS_OK) return st;
+  const bool f32 = plan_view(e->plans[0]).prec == PS_FP32;
+  ENS_CU(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t ce = cudaSuccess;
+  for (size_t i = 0; i < e->plans.size() && st == PS_OK; ++i) {
+    plan_set_stream(e->plans[i], e->cap);
+    st = (ps_status)plan_if_tables(e->plans[i], dt);
+    if (st == PS_OK) {
+      ce = cudaMemsetAsync(plan_view(e->plans[i]).umax2, 0, sizeof(unsigned long long), e->cap);
+      if (ce != cudaSuccess) st = cu(ce, "reset max|u|");
+    }
+  }
+  if (st == PS_OK) {
+    ce = cudaMemsetAsync(e->d_done, 0, (size_t)e->npass * sizeof(unsigned), e->cap);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->d_head, 0, sizeof(unsigned long long), e->cap);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->d_err, 0, sizeof(int), e->cap);
+    EnsLaunch L{e->d_passes, e->npass, e->d_args, e->d_done, e->d_head, e->tickets, e->d_err,
+                e->wait_test ? e->wait_test : (1u << 24)};
+    if (ce == cudaSuccess) ce = f32 ? ens_launch_f32(L, e->grid, e->smem, e->cap) : ens_launch_f64(L, e->grid, e->smem, e->cap);
+    if (ce != cudaSuccess) st = cu(ce, "persistent launch");
+  }
+  cudaGraph_t g = nullptr;
+  ce = cudaStreamEndCapture(e->cap, &g);
+  if (st != PS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  ENS_CU(ce, "end capture");
+  e->pgraph = g;
+  ENS_CU(cudaGraphInstantiate(&e->pexec, g, 0), "instantiate");
+  e->pkey_states.assign(u, u + e->plans.size());
+  e->pkey_dt = dt;
+  e->pkey_steps = nsteps;
+  return PS_OK;
+}
+
+ps_status run_persistent(ps_ensemble* e, void* const* u, double dt, double t, int nsteps) {
+  const bool same = e->pexec && e->pkey_steps == nsteps && e->pkey_dt == dt &&
+                    std::equal(e->pkey_states.begin(), e->pkey_states.end(), u);
+  if (!same) {
+    ps_status st = persist_capture(e, u, dt, nsteps);
+    if (st != PS_OK) return st;
+  }
+  ENS_CU(cudaGraphLaunch(e->pexec, e->main), "graph launch");
+  for (ps_plan* p : e->plans) plan_set_time(p, t + nsteps * dt);
+  return PS_OK;
+}
+
 // Average milliseconds of `reps` calls of f on the main stream.
 template <class F>
 ps_status time_ms(ps_ensemble* e, int reps, F&& f, double* ms) {
@@ -193,6 +408,9 @@ ps_status ps_ensemble_destroy(ps_ensemble* e) {
   if (!e) return PS_OK;
   cudaStreamSynchronize(e->main);
   drop_graph(e);
+  drop_pgraph(e);
+  for (void* d : {(void*)e->d_passes, (void*)e->d_args, (void*)e->d_done, (void*)e->d_head, (void*)e->d_err})
+    if (d) cudaFree(d);
   for (auto p : e->plans) ps_plan_destroy(p);
   for (auto s : e->branch)
     if (s) cudaStreamDestroy(s);
@@ -212,9 +430,31 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
   for (size_t i = 0; i < e->plans.size(); ++i)
     if (!uhats[i]) return bad(PS_ERR_INVALID_ARG, "ensemble: NULL member state");
   if (nsteps == 0) return PS_OK;
+  if (mode == PS_ENS_AUTO) mode = e->auto_mode;
   if (mode == PS_ENS_SEQUENTIAL) return run_sequential(e, uhats, dt, t, nsteps);
   if (mode == PS_ENS_GRAPH) return run_graph(e, uhats, dt, t, nsteps);
+  if (mode == PS_ENS_PERSISTENT) return run_persistent(e, uhats, dt, t, nsteps);
   return bad(PS_ERR_INVALID_ARG, "ensemble: unknown mode");
+}
+
+ps_status ps_ensemble_check(ps_ensemble* e) {
+  if (!e) return bad(PS_ERR_INVALID_ARG, "ensemble: NULL ensemble");
+  ENS_CU(cudaStreamSynchronize(e->main), "sync");
+  if (!e->d_err) return PS_OK;
+  int w = 0;
+  ENS_CU(cudaMemcpy(&w, e->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+  if (w != 0) {
+    ENS_CU(cudaMemset(e->d_err, 0, sizeof(int)), "error word");
+    return bad(PS_ERR_TIMEOUT, "ensemble: a bounded wait of the persistent launch gave up");
+  }
+  return PS_OK;
+}
+
+ps_status ps_ensemble_set_wait_test(ps_ensemble* e, unsigned polls) {
+  if (!e) return bad(PS_ERR_INVALID_ARG, "ensemble: NULL ensemble");
+  if (e->wait_test != polls) drop_pgraph(e);
+  e->wait_test = polls;
+  return PS_OK;
 }
 
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out) {
@@ -287,6 +527,52 @@ ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, 
     out->step_ms = best;
   }
   drop_graph(e);
+  // 3. persistent launch: CTAs per SM, member order and tiles per work item
+  //    per pass kind, one knob at a time (coordinate descent), each candidate
+  //    timed on one step of all members
+  out->persistent_step_ms = -1.0;
+  out->best_mode = PS_ENS_GRAPH;
+  e->auto_mode = PS_ENS_GRAPH;
+  if (st == PS_OK && persist_unsupported(e).empty()) {
+    auto timed = [&](double* ms) {
+      drop_pgraph(e);
+      return time_ms(e, 3, [&] { return run_persistent(e, work.data(), dt, 0.0, 1); }, ms);
+    };
+    double best = 1e30;
+    st = timed(&best);
+    auto knob = [&](int* k, std::initializer_list<int> cand) {
+      const int keep = *k;
+      int best_v = keep;
+      for (int v : cand) {
+        if (v == keep || st != PS_OK) continue;
+        *k = v;
+        double ms = 0;
+        st = timed(&ms);
+        if (st == PS_OK && ms < best * 0.98) {
+          best = ms;
+          best_v = v;
+        }
+      }
+      *k = best_v;
+    };
+    knob(&e->ctas_per_sm, {0, 1});
+    knob(&e->order, {0, 1});
+    knob(&e->per[EK_ZINV], {1, 2, 4});
+    knob(&e->per[EK_YINV], {1, 2, 4, 8});
+    knob(&e->per[EK_XPASS], {1, 2, 4});
+    knob(&e->per[EK_YFWD], {1, 2, 4, 8});
+    knob(&e->per[EK_ZFWD], {1, 2, 4});
+    knob(&e->per[EK_UPDATE], {4, 8, 16, 32});
+    drop_pgraph(e);
+    if (st == PS_OK) {
+      out->persistent_step_ms = best;
+      out->persistent_ctas_per_sm = e->ctas_per_sm;
+      out->persistent_order = e->order;
+      for (int k = 0; k < 6; ++k) out->persistent_tiles_per_item[k] = e->per[k];
+      if (best < out->step_ms) e->auto_mode = PS_ENS_PERSISTENT;
+      out->best_mode = e->auto_mode;
+    }
+  }
   cudaStreamSynchronize(e->main);
   for (void* w : work)
     if (w) cudaFree(w);

@@ -170,5 +170,21 @@ void plan_set_xrpc(struct ::ps_plan* p, int rpc);
 // (a captured graph must contain that launch).
 void plan_invalidate_tables(struct ::ps_plan* p);
 void plan_set_time(struct ::ps_plan* p, double t);
+// What the persistent ensemble launch (ps_persist.cu) needs of a member plan.
+struct PlanView {
+  Geo g;
+  int prec, eq, rk_stages;
+  bool closure;                 // a learned closure is attached
+  double* e_part;               // energy partials of the z-inverse pass
+  int n_epart;
+  double* stats;                // [energy] of the step statistics
+  unsigned long long* umax2;    // max |u|^2 bits of the step statistics
+};
+PlanView plan_view(const struct ::ps_plan* p);
+// Arguments of RK stage st of one step on the caller's state uhat, exactly as
+// ps_rk_step passes them to its kernels (derived constants prepared).
+PassArgs plan_stage_args(struct ::ps_plan* p, void* uhat, double dt, int st, bool stats);
+// Launches the integrating-factor tables for dt on the plan stream.
+int plan_if_tables(struct ::ps_plan* p, double dt);  // a ps_status value
 
 }  // namespace ps

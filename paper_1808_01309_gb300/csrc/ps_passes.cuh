@@ -139,7 +139,16 @@ __device__ __forceinline__ bool kept(const Geo& g, int p, int q, int r) {
   return in_cube(g, p, q, r) && (!g.sphere || in_sphere(g, p, q, r));
 }
 
-template <typename V> __device__ __forceinline__ V ldv(const V* p) { return __ldg(p); }
+// Loads of pass data.  COH = false: the read-only (non-coherent) path, for
+// kernels that never read what they or a concurrent CTA wrote.  COH = true:
+// ordinary (coherent) global loads, for data that other CTAs of the same
+// launch wrote before a release/acquire handshake (the persistent ensemble
+// kernel, whose passes run inside one launch: a CTA acquires the completion
+// of the previous pass before it reads that pass's output).
+template <bool COH = false, typename V> __device__ __forceinline__ V ldv(const V* p) {
+  if constexpr (COH) return *p;
+  else return __ldg(p);
+}
 
 // Sum of a per-thread double over the CTA; returns the total in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -176,8 +185,27 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // flight at once; the six transforms then read the tile from shared memory.
 // Thread (line, j0, bb) holds kz indices n = j0 + m N/E.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int NG, int NSC>
-__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
+// Tile coordinates of a pass: the launch's block index (one kernel per pass),
+// or an explicit tile of a persistent launch.  Read where the kernels read
+// blockIdx, so that the per-pass kernels compile as before.
+struct LaunchTile {
+  __device__ __forceinline__ int x() const { return blockIdx.x; }
+  __device__ __forceinline__ int y() const { return blockIdx.y; }
+  __device__ __forceinline__ int z() const { return blockIdx.z; }
+  __device__ __forceinline__ int gx() const { return gridDim.x; }
+};
+struct WorkTile {
+  int bx, by, bz, ngx;
+  __device__ __forceinline__ int x() const { return bx; }
+  __device__ __forceinline__ int y() const { return by; }
+  __device__ __forceinline__ int z() const { return bz; }
+  __device__ __forceinline__ int gx() const { return ngx; }
+};
+
+// One CTA tile (x, y) of the pass; gx = tiles along x (energy partial index
+// y gx + x).  COH: coherent loads (see ldv).
+template <typename T, int N, int NG, int NSC, bool COH, class TL>
+__device__ __forceinline__ void zinv_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 0>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
   constexpr int NTH = ColThreads<T, N>::v;
@@ -188,9 +216,9 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   V* tile = xbuf + NB * N * TX;              // input: [3][NB][cz][TX]
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
-  const int iy = blockIdx.y * NB + bb;
+  const int iy = tl.y() * NB + bb;
   const bool bvalid = iy < g.cy;
-  const int kx = blockIdx.x * TX + line;  // local column
+  const int kx = tl.x() * TX + line;  // local column
   const int kxg = g.kx0 + kx;              // its global kx
   const int q = iy <= g.Ky ? iy : iy - g.cy;
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, 1> ex{xbuf + bb * N * TX, 0, TX, line, 0};
@@ -217,7 +245,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
     static_assert(NTH % TX == 0, "whole rows per pass");
     constexpr int RSTEP = NTH / TX;
     const int col = tid % TX;
-    const int kxc = blockIdx.x * TX + col;
+    const int kxc = tl.x() * TX + col;
     if (kxc < ncols(g)) {
       int i = tid / TX, b = 0, c = 0;
       while (i >= g.cz) {
@@ -229,7 +257,7 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
       }
       V* dst = tile + (tid / TX) * TX + col;
       for (; c < ncs; dst += RSTEP * TX) {
-        const int iyb = blockIdx.y * NB + b;
+        const int iyb = tl.y() * NB + b;
         if (iyb < g.cy) {
           const int qb = iyb <= g.Ky ? iyb : iyb - g.cy;
           const int r = i <= g.Kz ? i : i - g.cz;
@@ -307,15 +335,20 @@ __global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(
   if (a.e_part) {
     // energy 1/2 sum w |u|^2 (+ |B|^2 or theta^2), w = 1 on the kx = 0 plane, else 2
     const double t = block_sum(esum * (kxg == 0 ? 0.5 : 1.0), red);
-    if (threadIdx.x == 0) a.e_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) a.e_part[tl.y() * tl.gx() + tl.x()] = t;
   }
+}
+
+template <typename T, int N, int NG, int NSC>
+__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
+  zinv_tile<T, N, NG, NSC, false>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
 // yinv: backward transform along y of 6 fields.  CTA = TX columns x NB z planes.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yinv(const PassArgs a) {
+template <typename T, int N, bool COH, class TL>
+__device__ __forceinline__ void yinv_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -323,10 +356,10 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
   const Geo& g = a.g;
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
-  const int iz = blockIdx.y * NB + bb;
+  const int iz = tl.y() * NB + bb;
   const bool bvalid = iz < g.nz;
-  const int kx = blockIdx.x * TX + line;
-  const int f = blockIdx.z;
+  const int kx = tl.x() * TX + line;
+  const int f = tl.z();
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
   V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
@@ -336,7 +369,7 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
     const int n = j0 + m * (N / E);
     const int q = sidx(n, N);
     V v = czero<V>();
-    if (bvalid && q <= g.Ky && q >= -g.Ky) v = ldv(in + (long long)rowof(q, g.cy) * g.kxp);
+    if (bvalid && q <= g.Ky && q >= -g.Ky) v = ldv<COH>(in + (long long)rowof(q, g.cy) * g.kxp);
     x[m] = v;
   }
   line_fft<N, E, +1>(x, j0, static_cast<const V*>(a.tw_y), ex);
@@ -344,6 +377,11 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
 #pragma unroll
     for (int m = 0; m < E; ++m) out[(long long)(j0 + m * (N / E)) * g.kxp] = x[m];
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yinv(const PassArgs a) {
+  yinv_tile<T, N, false>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
@@ -359,6 +397,170 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
 // NSC = 1 (Boussinesq): u + i omega and grad theta in, u x omega and
 // u . grad theta out.
 // ---------------------------------------------------------------------------
+// The work of the x pass on one row: gather the packed inverse lines (field f
+// of the row at st + f fst, retained kx only), transform them, form the
+// products, transform forward, split and store the retained kx of the output
+// row.  `gathered` runs once every thread holds its points (the TMA kernel
+// refills its stage there).  COH: st is global memory written earlier in the
+// same launch (coherent loads).
+template <typename T, int N, int NG, int NSC, bool COH, class TW, class AfterGather>
+__device__ __forceinline__ void xpass_row(const PassArgs& a, const long long row, const bool rvalid, const int j0,
+                                          const typename cplx<T>::type* st, const long long fst, const TW& tw,
+                                          LinesExchange<typename cplx<T>::type, 1>& ex, T& umax2,
+                                          AfterGather&& gathered) {
+  using V = typename cplx<T>::type;
+  constexpr int E = EPass<T, N, 3>::v;
+  constexpr int NLI = 3 * NG + 2 * NSC;  // inverse packed lines
+  constexpr bool HD = NG == 1 && NSC == 0;
+  constexpr int NFW = NG == 2 ? 3 : 2;  // forward packed lines
+  const Geo& g = a.g;
+  const int kxp = g.kxp;
+  const long long rows = (long long)g.nz * g.ny;
+  V* C = static_cast<V*>(a.a6);
+  // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c; for
+  // the Boussinesq system d_x theta + i d_y theta and d_z theta + i 0
+  V U[NLI][E];
+#pragma unroll
+  for (int c = 0; c < NLI; ++c) {
+    const bool scl = NSC && c == 4;  // the unpaired line
+    // real and imaginary part fields
+    const int fr = c < 3 ? c : NSC ? (c == 3 ? 6 : 8) : 6 + (c - 3);
+    const int fi = c < 3 ? c + 3 : NSC ? (c == 3 ? 7 : 8) : 9 + (c - 3);
+    const V* pu = st + fr * fst;
+    const V* pw = st + fi * fst;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = j0 + m * (N / E);
+      // full spectrum C[n] = a_hat[n] + i b_hat[n]; for n > N/2 the entries
+      // are conj(a_hat[N-n]) + i conj(b_hat[N-n]) (real a and b)
+      const bool hi = n > N / 2;
+      const int p = hi ? N - n : n;
+      V v = czero<V>();
+      if (rvalid && p <= g.Kx) {
+        V X, W;
+        if constexpr (COH) {
+          X = ldv<true>(pu + p);
+          W = ldv<true>(pw + p);
+        } else {
+          X = pu[p];
+          W = pw[p];
+        }
+        if (hi) {
+          X = cconj(X);
+          W = cconj(W);
+        }
+        v = scl ? X : mk<V>(X.x - W.y, X.y + W.x);
+      }
+      U[c][m] = v;
+    }
+  }
+  gathered();
+  if constexpr (HD) {
+    line_fft_rows<N, E, +1>(U, j0, tw, ex);
+  } else if constexpr (NSC == 1) {
+    V L[3][E], S[2][E];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) L[c][m] = U[c][m];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) S[c][m] = U[3 + c][m];
+    line_fft_rows<N, E, +1>(L, j0, tw, ex);
+    line_fft_rows<N, E, +1>(S, j0, tw, ex);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) U[c][m] = L[c][m];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) U[3 + c][m] = S[c][m];
+  } else {
+#pragma unroll
+    for (int h = 0; h < NG; ++h) {
+      V L[3][E];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) L[c][m] = U[3 * h + c][m];
+      line_fft_rows<N, E, +1>(L, j0, tw, ex);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) U[3 * h + c][m] = L[c][m];
+    }
+  }
+  // products at the thread's points (real part = field, imaginary = curl)
+  V F[NFW][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
+    const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
+    umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
+    T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+    if constexpr (HD) {
+      F[0][m] = mk<V>(nx, ny);
+      F[1][m] = mk<V>(nz, T(0));
+    } else if constexpr (NSC == 1) {
+      // u . grad theta
+      const T adv = ux * U[3][m].x + uy * U[3][m].y + uz * U[4][m].x;
+      F[0][m] = mk<V>(nx, ny);
+      F[1][m] = mk<V>(nz, adv);
+    } else {
+      const T bx = U[3][m].x, by = U[4][m].x, bz = U[5][m].x;
+      const T jx = U[3][m].y, jy = U[4][m].y, jz = U[5][m].y;
+      nx += jy * bz - jz * by;  // + j x B
+      ny += jz * bx - jx * bz;
+      nz += jx * by - jy * bx;
+      const T ex_ = uy * bz - uz * by, ey_ = uz * bx - ux * bz, ez_ = ux * by - uy * bx;  // u x B
+      F[0][m] = mk<V>(nx, ny);
+      F[1][m] = mk<V>(nz, ex_);
+      F[2][m] = mk<V>(ey_, ez_);
+    }
+  }
+  if (!a.xdiag) {  // uniform across the grid
+    line_fft_rows<N, E, -1>(F, j0, tw, ex);
+    const long long rrow = rvalid ? row : 0;
+    const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
+    // split each packed transform F = DFT(a) + i DFT(b) of two real fields
+    // with its mirrored entry F[N-k] (all split lines through one exchange);
+    // for HD the second line has b = 0
+    constexpr int NSP = HD ? 1 : NFW;  // lines that need the split
+#pragma unroll
+    for (int w = 0; w < NSP; ++w)
+#pragma unroll
+      for (int m = 0; m < E; ++m) ex.template put<0, 0>(w, j0 + m * (N / E), F[w][m]);
+    ex.sync();
+#pragma unroll
+    for (int w = 0; w < NFW; ++w) {
+      const bool split = w < NSP;
+      V* ca = C + ((long long)(2 * w) * rows + rrow) * kxp;
+      V* cb = C + ((long long)(2 * w + 1) * rows + rrow) * kxp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = j0 + m * (N / E);
+        if (rvalid && k < kend) {
+          V va = czero<V>(), vb = czero<V>();
+          if (k <= g.Kx) {
+            const V Fk = F[w][m];
+            if (split) {
+              const V Fm = cconj(ex.template get<0, 0>(w, k == 0 ? 0 : N - k));
+              va = cscale(cadd(Fk, Fm), T(0.5));
+              vb = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
+            } else {
+              va = Fk;
+            }
+          }
+          ca[k] = va;
+          if (split) cb[k] = vb;
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int N, int NG, int NSC>
 __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
                                   NG == 1 && NSC == 0 ? MinB<T, N>::xpass : 1)
@@ -366,9 +568,6 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 3>::v, G = N / E;
   constexpr int NF = 6 * NG + 3 * NSC;  // input fields: u, omega (, B, j) (, grad theta)
-  constexpr int NLI = 3 * NG + 2 * NSC;  // inverse packed lines
-  constexpr bool HD = NG == 1 && NSC == 0;
-  constexpr int NFW = NG == 2 ? 3 : 2;  // forward packed lines
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ __align__(8) uint64_t bar[1];
@@ -407,7 +606,6 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
     tw = TwAcc{static_cast<const V*>(a.tw_x)};
   }
   const V* B = static_cast<const V*>(a.b6);
-  V* C = static_cast<V*>(a.a6);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     abort_flag = 0;
@@ -449,151 +647,18 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
       break;
     }
     const long long row = it * rpc + rl;
-    const bool rvalid = row < rows;
-    const V* st = stage + rl * kxp;
-    // packed lines: u_c + i omega_c (c < 3) and, for MHD, B_c + i j_c; for
-    // the Boussinesq system d_x theta + i d_y theta and d_z theta + i 0
-    V U[NLI][E];
-#pragma unroll
-    for (int c = 0; c < NLI; ++c) {
-      const bool scl = NSC && c == 4;  // the unpaired line
-      // real and imaginary part fields
-      const int fr = c < 3 ? c : NSC ? (c == 3 ? 6 : 8) : 6 + (c - 3);
-      const int fi = c < 3 ? c + 3 : NSC ? (c == 3 ? 7 : 8) : 9 + (c - 3);
-      const V* pu = st + fr * rpc * kxp;
-      const V* pw = st + fi * rpc * kxp;
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int n = j0 + m * (N / E);
-        // full spectrum C[n] = a_hat[n] + i b_hat[n]; for n > N/2 the entries
-        // are conj(a_hat[N-n]) + i conj(b_hat[N-n]) (real a and b)
-        const bool hi = n > N / 2;
-        const int p = hi ? N - n : n;
-        V v = czero<V>();
-        if (rvalid && p <= g.Kx) {
-          V X = pu[p], W = pw[p];
-          if (hi) {
-            X = cconj(X);
-            W = cconj(W);
-          }
-          v = scl ? X : mk<V>(X.x - W.y, X.y + W.x);
-        }
-        U[c][m] = v;
-      }
-    }
-    // every thread has its points: the stage takes the next group's rows
-    __syncthreads();
-    if (tid == 0) {
-      inflight = nxt < ngroups;
-      if (inflight) {
-        fence_proxy_async();
-        issue(nxt);
-      }
-    }
-    if constexpr (HD) {
-      line_fft_rows<N, E, +1>(U, j0, tw, ex);
-    } else if constexpr (NSC == 1) {
-      V L[3][E], S[2][E];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < E; ++m) L[c][m] = U[c][m];
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int m = 0; m < E; ++m) S[c][m] = U[3 + c][m];
-      line_fft_rows<N, E, +1>(L, j0, tw, ex);
-      line_fft_rows<N, E, +1>(S, j0, tw, ex);
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < E; ++m) U[c][m] = L[c][m];
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int m = 0; m < E; ++m) U[3 + c][m] = S[c][m];
-    } else {
-#pragma unroll
-      for (int h = 0; h < NG; ++h) {
-        V L[3][E];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int m = 0; m < E; ++m) L[c][m] = U[3 * h + c][m];
-        line_fft_rows<N, E, +1>(L, j0, tw, ex);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int m = 0; m < E; ++m) U[3 * h + c][m] = L[c][m];
-      }
-    }
-    // products at the thread's points (real part = field, imaginary = curl)
-    V F[NFW][E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const T ux = U[0][m].x, uy = U[1][m].x, uz = U[2][m].x;
-      const T wx = U[0][m].y, wy = U[1][m].y, wz = U[2][m].y;
-      umax2 = fmax(umax2, ux * ux + uy * uy + uz * uz);
-      T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
-      if constexpr (HD) {
-        F[0][m] = mk<V>(nx, ny);
-        F[1][m] = mk<V>(nz, T(0));
-      } else if constexpr (NSC == 1) {
-        // u . grad theta
-        const T adv = ux * U[3][m].x + uy * U[3][m].y + uz * U[4][m].x;
-        F[0][m] = mk<V>(nx, ny);
-        F[1][m] = mk<V>(nz, adv);
-      } else {
-        const T bx = U[3][m].x, by = U[4][m].x, bz = U[5][m].x;
-        const T jx = U[3][m].y, jy = U[4][m].y, jz = U[5][m].y;
-        nx += jy * bz - jz * by;  // + j x B
-        ny += jz * bx - jx * bz;
-        nz += jx * by - jy * bx;
-        const T ex_ = uy * bz - uz * by, ey_ = uz * bx - ux * bz, ez_ = ux * by - uy * bx;  // u x B
-        F[0][m] = mk<V>(nx, ny);
-        F[1][m] = mk<V>(nz, ex_);
-        F[2][m] = mk<V>(ey_, ez_);
-      }
-    }
-    if (!a.xdiag) {  // uniform across the grid
-      line_fft_rows<N, E, -1>(F, j0, tw, ex);
-      const long long rrow = rvalid ? row : 0;
-      const int kend = kxp < N / 2 + 1 ? kxp : N / 2 + 1;
-      // split each packed transform F = DFT(a) + i DFT(b) of two real fields
-      // with its mirrored entry F[N-k] (all split lines through one exchange);
-      // for HD the second line has b = 0
-      constexpr int NSP = HD ? 1 : NFW;  // lines that need the split
-#pragma unroll
-      for (int w = 0; w < NSP; ++w)
-#pragma unroll
-        for (int m = 0; m < E; ++m) ex.template put<0, 0>(w, j0 + m * (N / E), F[w][m]);
-      ex.sync();
-#pragma unroll
-      for (int w = 0; w < NFW; ++w) {
-        const bool split = w < NSP;
-        V* ca = C + ((long long)(2 * w) * rows + rrow) * kxp;
-        V* cb = C + ((long long)(2 * w + 1) * rows + rrow) * kxp;
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const int k = j0 + m * (N / E);
-          if (rvalid && k < kend) {
-            V va = czero<V>(), vb = czero<V>();
-            if (k <= g.Kx) {
-              const V Fk = F[w][m];
-              if (split) {
-                const V Fm = cconj(ex.template get<0, 0>(w, k == 0 ? 0 : N - k));
-                va = cscale(cadd(Fk, Fm), T(0.5));
-                vb = cscale(cmul_mi(csub(Fk, Fm)), T(0.5));
-              } else {
-                va = Fk;
-              }
-            }
-            ca[k] = va;
-            if (split) cb[k] = vb;
-          }
-        }
-      }
-    }
+    xpass_row<T, N, NG, NSC, false>(a, row, row < rows, j0, stage + rl * kxp, (long long)rpc * kxp, tw, ex, umax2,
+                                   [&] {
+                                     // every thread has its points: the stage takes the next group's rows
+                                     __syncthreads();
+                                     if (tid == 0) {
+                                       inflight = nxt < ngroups;
+                                       if (inflight) {
+                                         fence_proxy_async();
+                                         issue(nxt);
+                                       }
+                                     }
+                                   });
     __syncthreads();  // the exchange buffers are free again
     it = nxt;
   }
@@ -606,8 +671,8 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
 // ---------------------------------------------------------------------------
 // yfwd: forward transform along y of 3 fields, keep |ky| <= Ky.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yfwd(const PassArgs a) {
+template <typename T, int N, bool COH, class TL>
+__device__ __forceinline__ void yfwd_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -615,16 +680,16 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
   const Geo& g = a.g;
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
-  const int iz = blockIdx.y * NB + bb;
+  const int iz = tl.y() * NB + bb;
   const bool bvalid = iz < g.nz;
-  const int kx = blockIdx.x * TX + line;
-  const int f = blockIdx.z;
+  const int kx = tl.x() * TX + line;
+  const int f = tl.z();
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const V* in = static_cast<const V*>(a.a6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.ny * g.kxp + kx;
   V* out = static_cast<V*>(a.b6) + ((long long)f * g.nz + (bvalid ? iz : 0)) * g.cy * g.kxp + kx;
   V x[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) x[m] = bvalid ? ldv(in + (long long)(j0 + m * (N / E)) * g.kxp) : czero<V>();
+  for (int m = 0; m < E; ++m) x[m] = bvalid ? ldv<COH>(in + (long long)(j0 + m * (N / E)) * g.kxp) : czero<V>();
   line_fft<N, E, -1>(x, j0, static_cast<const V*>(a.tw_y), ex);
   if (bvalid) {
 #pragma unroll
@@ -635,14 +700,19 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
   }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yfwd(const PassArgs a) {
+  yfwd_tile<T, N, false>(a, LaunchTile{});
+}
+
 // ---------------------------------------------------------------------------
 // zfwd: forward transform along z of one field per CTA (blockIdx.z), keep the
 // retained kz rows and scale by 1/(Nx Ny Nz).  Writes the compact transformed
 // nonlinear term [3 ng][cz][cy][kxp] into a6 (zero where the mode is not
 // retained).  The projection, forcing and stage update follow in k_update.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a) {
+template <typename T, int N, bool COH, class TL>
+__device__ __forceinline__ void zfwd_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
   constexpr int E = EPass<T, N, 2>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -650,18 +720,18 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zf
   const Geo& g = a.g;
   const int tid = threadIdx.x;
   const int line = tid % TX, rest = tid / TX, j0 = rest % G, bb = rest / G;
-  const int iy = blockIdx.y * NB + bb;
+  const int iy = tl.y() * NB + bb;
   const bool bvalid = iy < g.cy;
-  const int kx = blockIdx.x * TX + line;
+  const int kx = tl.x() * TX + line;
   const int q = iy <= g.Ky ? iy : iy - g.cy;
-  const int f = blockIdx.z;
+  const int f = tl.z();
   ColumnExchange<V, ilog2<Sched<N, E>::R0>::v, ColBuf<T, N>::v> ex{sm + bb * N * TX, NB * N * TX, TX, line, 0};
   const long long cs_in = (long long)g.nz * g.cy * g.kxp;
   const V* in = static_cast<const V*>(a.b6) + f * cs_in + (long long)(bvalid ? iy : 0) * g.kxp + kx;
   V x[E];
 #pragma unroll
   for (int m = 0; m < E; ++m)
-    x[m] = bvalid ? ldv(in + (long long)(j0 + m * (N / E)) * g.cy * g.kxp) : czero<V>();
+    x[m] = bvalid ? ldv<COH>(in + (long long)(j0 + m * (N / E)) * g.cy * g.kxp) : czero<V>();
   line_fft<N, E, -1>(x, j0, static_cast<const V*>(a.tw_z), ex);
   if (bvalid) {
     const T inv = pick<T>(a.inv_n3, a.inv_n3f);
@@ -674,6 +744,11 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zf
             kx < ncols(g) && kept(g, g.kx0 + kx, q, r) ? cscale(x[m], inv) : czero<V>();
     }
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a) {
+  zfwd_tile<T, N, false>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
@@ -689,14 +764,11 @@ __global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zf
 // retained set are written as zero); otherwise one thread per retained mode.
 // Consecutive threads take consecutive kx: every access is a contiguous row.
 // ---------------------------------------------------------------------------
-template <typename T, int NG, int NSC, bool SLAB = false>
-__global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full) {
+template <typename T, int NG, int NSC, bool SLAB, bool COH>
+__device__ __forceinline__ void update_mode(const PassArgs& a, const int full, const unsigned idx) {
   using V = typename cplx<T>::type;
   constexpr int NC = 3 * NG + NSC;  // state components
   const Geo& g = a.g;
-  // 32-bit mode index (the launcher checks that the modes fit): 64-bit
-  // integer division runs on the FP64 pipe, which is slow on this GPU
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   // a whole problem (not a kx slab) has rows of nh entries and cx columns
   const unsigned rl = SLAB ? rowlen(g) : g.nh, nc = SLAB ? ncols(g) : g.cx;
   int kx, q, r;  // kx: local column (array index); kxg = g.kx0 + kx its global kx
@@ -741,8 +813,8 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
   if constexpr (NSC == 1) {
     const V* pi = static_cast<const V*>(a.in.p) + (long long)rowof(r, a.in.zwrap) * a.in.zs +
                   (long long)rowof(q, a.in.ywrap) * a.in.ys + kx;
-    w_s = ldv(pi + 2 * a.in.cs);
-    th_s = ldv(pi + 3 * a.in.cs);
+    w_s = ldv<COH>(pi + 2 * a.in.cs);
+    th_s = ldv<COH>(pi + 3 * a.in.cs);
   }
 #pragma unroll
   for (int grp = 0; grp < NG + NSC; ++grp) {
@@ -752,25 +824,25 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     const int nc = scl ? 1 : 3;
     V kk[3];
     if (scl) {
-      kk[0] = csub(cscale(w_s, pick<T>(a.n_bv, a.nbvf)), ldv(nh + 3 * ccs + ci));
+      kk[0] = csub(cscale(w_s, pick<T>(a.n_bv, a.nbvf)), ldv<COH>(nh + 3 * ccs + ci));
       kk[1] = kk[2] = czero<V>();
     } else {
-      V v0 = ldv(nh + (c0 + 0) * ccs + ci), v1 = ldv(nh + (c0 + 1) * ccs + ci), v2 = ldv(nh + (c0 + 2) * ccs + ci);
+      V v0 = ldv<COH>(nh + (c0 + 0) * ccs + ci), v1 = ldv<COH>(nh + (c0 + 1) * ccs + ci), v2 = ldv<COH>(nh + (c0 + 2) * ccs + ci);
       if (!mag) {
         if (a.extra) {  // closure term (LES), compact layout
           const V* ex0 = static_cast<const V*>(a.extra) + ci;
-          v0 = cadd(v0, ldv(ex0));
-          v1 = cadd(v1, ldv(ex0 + ccs));
-          v2 = cadd(v2, ldv(ex0 + 2 * ccs));
+          v0 = cadd(v0, ldv<COH>(ex0));
+          v1 = cadd(v1, ldv<COH>(ex0 + ccs));
+          v2 = cadd(v2, ldv<COH>(ex0 + 2 * ccs));
         }
         const V* fb = static_cast<const V*>(a.fbox);
         if (fb && kx <= a.Fx && q <= a.Fy && q >= -a.Fy && r <= a.Fz && r >= -a.Fz) {
           const long long fzs = (long long)(2 * a.Fy + 1) * (a.Fx + 1);
           const long long fcs2 = (long long)(2 * a.Fz + 1) * fzs;
           const long long fo = (long long)(r + a.Fz) * fzs + (long long)(q + a.Fy) * (a.Fx + 1) + kx;
-          v0 = cadd(v0, ldv(fb + fo));
-          v1 = cadd(v1, ldv(fb + fo + fcs2));
-          v2 = cadd(v2, ldv(fb + fo + 2 * fcs2));
+          v0 = cadd(v0, ldv<COH>(fb + fo));
+          v1 = cadd(v1, ldv<COH>(fb + fo + fcs2));
+          v2 = cadd(v2, ldv<COH>(fb + fo + 2 * fcs2));
         }
         if constexpr (NSC == 1) v2 = csub(v2, cscale(th_s, pick<T>(a.n_bv, a.nbvf)));  // buoyancy -N theta z
         if (k2 > T(0)) {
@@ -807,7 +879,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     if (a.mode == ZF_RHS) {
       const T vk = (second ? pick<T>(a.eta, a.etaf) : pick<T>(a.nu, a.nuf)) * k2;
 #pragma unroll
-      for (int c = 0; c < nc; ++c) po[c * fcs] = csub(kk[c], cscale(ldv(pu + c * a.u_n.cs), vk));
+      for (int c = 0; c < nc; ++c) po[c * fcs] = csub(kk[c], cscale(ldv<COH>(pu + c * a.u_n.cs), vk));
       continue;
     }
     // Lawson RK with E = exp(-damp |k|^2 dt/2) = ex(p) ey(q) ez(r)
@@ -821,7 +893,7 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
     V u[3], ac[3];
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
-      u[c] = ldv(pu + c * a.u_n.cs);
+      u[c] = ldv<COH>(pu + c * a.u_n.cs);
       ac[c] = (a.mode == ZF_RK4_1 || a.mode == ZF_RK2_1) ? czero<V>() : acc[c * ccs];
     }
 #pragma unroll
@@ -855,6 +927,13 @@ __global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full
       }
     }
   }
+}
+
+// 32-bit mode index (the launcher checks that the modes fit): 64-bit integer
+// division runs on the FP64 pipe, which is slow on this GPU
+template <typename T, int NG, int NSC, bool SLAB = false>
+__global__ void __launch_bounds__(256) k_update(const PassArgs a, const int full) {
+  update_mode<T, NG, NSC, SLAB, false>(a, full, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------

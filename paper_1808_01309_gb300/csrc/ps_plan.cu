@@ -369,6 +369,22 @@ ps_status do_rhs(ps_plan* p, const void* uhat, void* out) {
   return run_rhs_passes<T>(p, a);
 }
 
+// Arguments of RK stage st of one step on the caller's state uhat: stage 0
+// reads the state, later stages the compact stage input; with stats stage 0
+// also writes the energy partials and max |u|^2 of the step statistics.
+PassArgs stage_args(ps_plan* p, void* uhat, double dt, int st, bool stats) {
+  const int nst = p->cfg.rk_order == 4 ? 4 : 2;
+  PassArgs a = base_args(p);
+  a.in = st == 0 ? caller_spec(p->g, uhat) : compact_spec(p->g, p->nxt);
+  a.u_n = caller_spec(p->g, uhat);
+  a.out_full = uhat;
+  a.dt = dt;
+  a.e_part = st == 0 && stats ? p->e_part : nullptr;
+  a.umax2 = st == 0 && stats ? p->umax2 : nullptr;
+  a.mode = nst == 4 ? ZF_RK4_1 + st : ZF_RK2_1 + st;
+  return a;
+}
+
 template <typename T>
 ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
   ps_status s;
@@ -388,14 +404,7 @@ ps_status do_rk_step(ps_plan* p, void* uhat, double dt) {
   PS_CU(cudaMemsetAsync(p->umax2, 0, sizeof(unsigned long long), p->stream), "reset max|u|");
   const int nst = p->cfg.rk_order == 4 ? 4 : 2;
   for (int st = 0; st < nst; ++st) {
-    PassArgs a = base_args(p);
-    a.in = st == 0 ? caller_spec(p->g, uhat) : compact_spec(p->g, p->nxt);
-    a.u_n = caller_spec(p->g, uhat);
-    a.out_full = uhat;
-    a.dt = dt;
-    a.e_part = st == 0 ? p->e_part : nullptr;
-    a.umax2 = st == 0 ? p->umax2 : nullptr;
-    a.mode = nst == 4 ? ZF_RK4_1 + st : ZF_RK2_1 + st;
+    PassArgs a = stage_args(p, uhat, dt, st, true);
     if ((s = run_rhs_passes<T>(p, a)) != PS_OK) return s;
   }
   return PS_OK;
@@ -523,6 +532,43 @@ void plan_set_xrpc(ps_plan* p, int rpc) {
 }
 void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
 void plan_set_time(ps_plan* p, double t) { p->time = t; }
+PlanView plan_view(const ps_plan* p) {
+  PlanView v{};
+  v.g = p->g;
+  v.prec = (int)p->cfg.prec;
+  v.eq = (int)p->cfg.eq;
+  v.rk_stages = p->cfg.rk_order == 4 ? 4 : 2;
+  v.closure = p->les_on;
+  v.e_part = p->e_part;
+  v.n_epart = p->n_epart;
+  v.stats = p->stats;
+  v.umax2 = p->umax2;
+  return v;
+}
+PassArgs plan_stage_args(ps_plan* p, void* uhat, double dt, int st, bool stats) {
+  PassArgs a = stage_args(p, uhat, dt, st, stats);
+  prepare_args(a);
+  return a;
+}
+int plan_if_tables(ps_plan* p, double dt) {
+  const bool f32 = p->cfg.prec == PS_FP32;
+  const size_t tb = f32 ? 4 : 8;
+  ps_status s = launch(p, 5, [&] {
+    return f32 ? launch_if_tables<float>(p->g, p->cfg.nu, dt, p->iftab, p->stream)
+               : launch_if_tables<double>(p->g, p->cfg.nu, dt, p->iftab, p->stream);
+  }, "integrating-factor tables");
+  if (s != PS_OK) return s;
+  if (p->ng == 2 || p->cn.nsc) {
+    void* jt = static_cast<char*>(p->iftab) + tb * (p->g.cx + p->g.cy + p->g.cz);
+    const double d2 = p->cfg.eq == PS_BOUSSINESQ ? p->cfg.kappa : p->cfg.eta;
+    s = launch(p, 5, [&] {
+      return f32 ? launch_if_tables<float>(p->g, d2, dt, jt, p->stream) : launch_if_tables<double>(p->g, d2, dt, jt, p->stream);
+    }, "integrating-factor tables");
+    if (s != PS_OK) return s;
+  }
+  p->if_dt = dt;
+  return PS_OK;
+}
 // used by the checkpoint layer (ps_io.cu)
 ps_config plan_config(const ps_plan* p) { return p->cfg; }
 size_t plan_state_bytes(const ps_plan* p) { return p->sz.state * p->sz.vb; }

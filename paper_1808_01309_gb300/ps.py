@@ -56,11 +56,12 @@ SYMBOLS = (
     "ps_plan_closure_grad_transfer", "ps_checkpoint_save", "ps_checkpoint_load", "ps_checkpoint_info",
     "ps_fft_r2c", "ps_fft_c2r", "ps_probe_fma_tflops", "ps_plan_set_wait_test",
     "ps_slab_create", "ps_slab_destroy", "ps_slab_info_get", "ps_slab_inverse", "ps_slab_xpass",
-    "ps_slab_forward", "ps_slab_check",
+    "ps_slab_forward", "ps_slab_check", "ps_ensemble_check", "ps_ensemble_set_wait_test",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY, HOST_CUBE_CE = 0, 1, 2, 3, 4
 MLP_NPARAM = 4934
-ENS_SEQUENTIAL, ENS_GRAPH = 0, 1
+ENS_SEQUENTIAL, ENS_GRAPH, ENS_PERSISTENT, ENS_AUTO = 0, 1, 2, 3
+ENS_PASSES = ("z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward", "update")
 ENS_MAX_SIZES = 8
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -91,7 +92,9 @@ class PsDiag(ctypes.Structure):
 
 class PsEnsTuning(ctypes.Structure):
     _fields_ = [("branches", ctypes.c_int), ("nsizes", ctypes.c_int), ("n", ctypes.c_int * 8),
-                ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double)]
+                ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double), ("persistent_step_ms", ctypes.c_double),
+                ("persistent_ctas_per_sm", ctypes.c_int), ("persistent_order", ctypes.c_int),
+                ("persistent_tiles_per_item", ctypes.c_int * 6), ("best_mode", ctypes.c_int)]
 
 
 class PsSlabInfo(ctypes.Structure):
@@ -132,6 +135,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ps_ensemble_rk_steps.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int]
     lib.ps_ensemble_tune.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(PsEnsTuning)]
+    lib.ps_ensemble_check.argtypes = [P]
+    lib.ps_ensemble_set_wait_test.argtypes = [P, ctypes.c_uint]
     lib.ps_mlp_forward.argtypes = [P, P, P, ctypes.c_longlong, P]
     lib.ps_mlp_grad.argtypes = [P, P, P, ctypes.c_longlong, P, P, P]
     lib.ps_mlp_adam.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -383,7 +388,20 @@ def ps_ensemble_tune(ens, states, dt: float) -> dict:
     t = PsEnsTuning()
     _check(load().ps_ensemble_tune(ens, _ptr_array(states), float(dt), ctypes.byref(t)))
     return {"branches": t.branches, "step_ms": t.step_ms,
-            "xrpc": {int(t.n[i]): int(t.xrpc[i]) for i in range(t.nsizes)}}
+            "xrpc": {int(t.n[i]): int(t.xrpc[i]) for i in range(t.nsizes)},
+            "persistent_step_ms": t.persistent_step_ms,
+            "persistent_ctas_per_sm": t.persistent_ctas_per_sm, "persistent_order": t.persistent_order,
+            "persistent_tiles_per_item": {ENS_PASSES[k]: int(t.persistent_tiles_per_item[k]) for k in range(6)},
+            "best_mode": {ENS_GRAPH: "graph", ENS_PERSISTENT: "persistent"}.get(t.best_mode, str(t.best_mode))}
+
+
+def ps_ensemble_check(ens) -> None:
+    """Raises PsError (PS_ERR_TIMEOUT) if a bounded wait of a persistent launch gave up."""
+    _check(load().ps_ensemble_check(ens))
+
+
+def ps_ensemble_set_wait_test(ens, polls: int) -> None:
+    _check(load().ps_ensemble_set_wait_test(ens, int(polls)))
 
 
 def ps_mlp_forward(params, X, Y, count: int, stream=None) -> None:

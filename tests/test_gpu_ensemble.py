@@ -112,3 +112,119 @@ def test_radix3_lengths_rhs_matches_oracle(ps, prec, shape):
     tol = 1e-12 if prec == "fp64" else 2e-6
     assert_parity(got, ref, tol, "ensemble member")
     plan.close()
+
+
+# ---- persistent launch: one kernel over a device queue of (member, pass, tile)
+
+def test_persistent_matches_graph_bitwise_and_replays(ps):
+    cfgs, s_per, _ = _members(ps)
+    s_graph = [s.clone() for s in s_per]
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, s_per, 2e-3, 0.0, 3, ps.ENS_PERSISTENT)
+    ps.ps_ensemble_rk_steps(ens, s_graph, 2e-3, 0.0, 3, ps.ENS_GRAPH)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    for a, b in zip(s_per, s_graph):
+        assert torch.equal(a, b)
+    # the captured persistent graph replays the next steps of the same trajectory
+    ps.ps_ensemble_rk_steps(ens, s_per, 2e-3, 0.0, 3, ps.ENS_PERSISTENT)
+    ps.ps_ensemble_rk_steps(ens, s_graph, 2e-3, 0.0, 3, ps.ENS_GRAPH)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    for a, b in zip(s_per, s_graph):
+        assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+@pytest.mark.parametrize("member", [0, 6])
+def test_persistent_member_matches_oracle_fp64(ps, member):
+    cfgs, states, host = _members(ps, "fp64")
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_PERSISTENT)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    n = SIZES[member]
+    ref = host[member]
+    cfg = oracle.Config(n, n, n, nu=cfgs[member].nu, rk_order=4)
+    for _ in range(2):
+        ref = oracle.rk_step(ref, 2e-3, cfg)
+    assert_parity(states[member].cpu().numpy(), ref, 1e-12, "persistent ensemble member")
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_persistent_fp32_rk2_forced_anisotropic_matches_oracle(ps):
+    shapes = [(64, 32, 48), (32, 96, 64), (128, 64, 32)]
+    cfgs, states, refs, keep = [], [], [], []
+    for i, (nx, ny, nz) in enumerate(shapes):
+        u = inputs.random_solenoidal_field(nx, ny, nz, seed=70 + i, kmax=(nx, ny, nz))
+        f = inputs.forcing_field(nx, ny, nz, seed=2)
+        fd = torch.from_numpy(f).to("cuda", torch.complex64)
+        cfgs.append(ps.make_config(nx, ny, nz, prec=ps.Precision.FP32, nu=3e-3, rk_order=2, forcing=fd))
+        states.append(torch.from_numpy(u).to("cuda", torch.complex64))
+        cfg = oracle.Config(nx, ny, nz, nu=3e-3, rk_order=2)
+        ref = u
+        for _ in range(2):
+            ref = oracle.rk_step(ref, 2e-3, cfg, forcing=f)
+        refs.append(ref)
+        keep.append(fd)
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_PERSISTENT)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    for s, ref in zip(states, refs):
+        assert_parity(s.cpu().numpy().astype(np.complex128), ref, 2e-6, "persistent ensemble member")
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_persistent_bounded_wait_reports_timeout_then_recovers(ps):
+    cfgs, states, _ = _members(ps)
+    start = [s.clone() for s in states]
+    ref = [s.clone() for s in states]
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_set_wait_test(ens, 1 << 12)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 1, ps.ENS_PERSISTENT)
+    with pytest.raises(ps.PsError) as ei:
+        ps.ps_ensemble_check(ens)
+    assert ei.value.status == ps.PS_ERR_TIMEOUT
+    ps.ps_ensemble_check(ens)  # reported once
+    ps.ps_ensemble_set_wait_test(ens, 0)
+    for s, s0 in zip(states, start):
+        s.copy_(s0)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 1, ps.ENS_PERSISTENT)
+    ps.ps_ensemble_rk_steps(ens, ref, 2e-3, 0.0, 1, ps.ENS_SEQUENTIAL)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    for a, b in zip(states, ref):
+        assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_persistent_rejects_unsupported_members(ps):
+    cfgs = [ps.make_config(32, prec=ps.Precision.FP32, nu=1e-3),
+            ps.make_config(256, 32, 32, prec=ps.Precision.FP32, nu=1e-3)]
+    states = [torch.zeros(3, 32, 32, 17, dtype=torch.complex64, device="cuda"),
+              torch.zeros(3, 32, 32, 129, dtype=torch.complex64, device="cuda")]
+    ens = ps.ps_ensemble_create(cfgs)
+    with pytest.raises(ps.PsError) as ei:
+        ps.ps_ensemble_rk_steps(ens, states, 1e-3, 0.0, 1, ps.ENS_PERSISTENT)
+    assert ei.value.status == ps.PS_ERR_UNSUPPORTED
+    ps.ps_ensemble_rk_steps(ens, states, 1e-3, 0.0, 1, ps.ENS_GRAPH)  # the other modes still run
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_tuner_times_persistent_knobs_and_auto_mode_runs_the_faster(ps):
+    cfgs, states, _ = _members(ps)
+    ens = ps.ps_ensemble_create(cfgs)
+    tuning = ps.ps_ensemble_tune(ens, states, 2e-3)
+    assert tuning["persistent_step_ms"] > 0
+    assert tuning["best_mode"] in ("graph", "persistent")
+    assert tuning["persistent_ctas_per_sm"] in (0, 1) and tuning["persistent_order"] in (0, 1)
+    assert all(v >= 1 for v in tuning["persistent_tiles_per_item"].values())
+    ref = [s.clone() for s in states]
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_AUTO)
+    ps.ps_ensemble_rk_steps(ens, ref, 2e-3, 0.0, 2, ps.ENS_SEQUENTIAL)
+    ps.ps_ensemble_check(ens)
+    torch.cuda.synchronize()
+    for a, b in zip(states, ref):
+        assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
