@@ -267,7 +267,9 @@ typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1, PS_ENS_PERSISTENT = 2, P
  * (0 = the automatic maximum); step_ms = graph time of one step of all
  * members with the chosen shapes.  The persistent launch's choices:
  * resident CTAs per SM (0 = as many as fit), member order (0 = as created,
- * 1 = largest grid first) and tiles per work item of the z-inverse,
+ * 1 = largest grid first, 2 = largest first and staggered: member k starts
+ * k mod 6 passes late, so that different passes run side by side) and
+ * tiles per work item of the z-inverse,
  * y-inverse, x, y-forward, z-forward and update passes (in that order);
  * persistent_step_ms is its time of one step (-1: not supported by these
  * members).  best_mode is what PS_ENS_AUTO now runs. */
