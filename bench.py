@@ -697,8 +697,8 @@ def run_ensemble(args, dev, stream):
     1000+i, nu_i = 1e-3 + 4e-3 U(seed 2000+i), FP32, IF-RK4, dt = 1e-3:
     member-by-member launches vs one CUDA graph of the members' launch chains
     vs one persistent kernel over a (member, pass, tile) work queue (both
-    graphs autotuned); the persistent states are checked bit for bit against
-    the graph's."""
+    graphs autotuned); the largest relative difference of the final states of
+    the two is reported."""
     import torch
     from paper_1808_01309_gb300 import inputs, ps
     cfgs, host = [], []
@@ -735,7 +735,10 @@ def run_ensemble(args, dev, stream):
     out["graph_speedup"] = round(out["sequential"]["ms"] / out["graph"]["ms"], 3)
     out["persistent_speedup"] = round(out["sequential"]["ms"] / out["persistent"]["ms"], 3)
     out["persistent_vs_graph"] = round(out["graph"]["ms"] / out["persistent"]["ms"], 3)
-    out["persistent_equals_graph"] = all(bool(torch.equal(a, b)) for a, b in zip(finals["persistent"], finals["graph"]))
+    # the graph runs the tuned tile shapes, the persistent launch the default
+    # ones: equal to rounding (bitwise with equal shapes, see the GPU tests)
+    out["persistent_vs_graph_max_rel"] = float(max(
+        ((a - b).abs().max() / b.abs().max()).item() for a, b in zip(finals["persistent"], finals["graph"])))
     out["default_mode"] = tuning["best_mode"]
     ps.ps_ensemble_destroy(ens)
     return out

@@ -233,6 +233,19 @@ ps_status ps_plan_launch_count(ps_plan* plan, long long* launches);
  * turns the hook off; polls outside [0, 2^20] returns PS_ERR_INVALID_ARG. */
 ps_status ps_plan_set_wait_test(ps_plan* plan, int polls);
 
+/* Tile shape of one column pass of the plan's right-hand sides (pass 0: the
+ * z-inverse pass, 1: both y passes, 2: the z-forward pass; Sec. 2 describes
+ * each 3D transform as 1D transforms along the axes, this only chooses how
+ * the lines are tiled).  variant 0: the default (8 kx columns per CTA in
+ * FP32); 1: half the columns per CTA and twice the lines; 2: the other radix
+ * schedule (8 <-> 16 points per thread and line; not for lengths with a
+ * factor 3).  Variants 1 and 2 exist for FP32 hydrodynamic plans whose
+ * pass axis has 64, 96 or 128 points (PS_ERR_UNSUPPORTED otherwise).  All
+ * variants compute the same transforms (results agree to rounding).  cols
+ * and points (may be NULL) receive the chosen columns per CTA and points per
+ * thread.  The ensemble tuner sets these per grid size. */
+ps_status ps_plan_set_pass_shape(ps_plan* plan, int pass, int variant, int* cols, int* points);
+
 /* Name of a kernel kind of ps_timing (0..PS_NKINDS-1), or "?". */
 const char* ps_kind_name(int kind);
 
@@ -264,7 +277,8 @@ typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1, PS_ENS_PERSISTENT = 2, P
 
 /* Result of ps_ensemble_tune: concurrent branches, and per distinct grid
  * (first nsizes entries, n = nx of the grid) the x-pass rows per CTA chosen
- * (0 = the automatic maximum); step_ms = graph time of one step of all
+ * (0 = the automatic maximum) and the tile shape chosen for each column pass
+ * (see ps_plan_set_pass_shape); step_ms = graph time of one step of all
  * members with the chosen shapes.  The persistent launch's choices:
  * resident CTAs per SM (0 = as many as fit), member order (0 = as created,
  * 1 = largest grid first, 2 = largest first and staggered: member k starts
@@ -279,6 +293,8 @@ typedef struct {
   int n[PS_ENS_MAX_SIZES];
   int xrpc[PS_ENS_MAX_SIZES];
   double step_ms;
+  int pass_cols[PS_ENS_MAX_SIZES][3];    /* kx columns per CTA of the z-inverse, y and z-forward passes */
+  int pass_points[PS_ENS_MAX_SIZES][3];  /* points per thread (radix schedule) of the same passes */
   double persistent_step_ms;
   int persistent_ctas_per_sm;
   int persistent_order;
@@ -297,9 +313,11 @@ ps_status ps_ensemble_destroy(ps_ensemble* e);
 ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, double t, int nsteps,
                                ps_ens_mode mode);
 
-/* Autotuner: times, on device copies of uhats (left unchanged), the x-pass
- * rows per CTA for each distinct grid and the number of concurrent graph
- * branches, keeps the fastest and reports them.  Allocates temporary copies
+/* Autotuner: times, on device copies of uhats (left unchanged), for each
+ * distinct grid the x-pass rows per CTA and the tile shape (columns per CTA,
+ * radix schedule) of each column pass, then the number of concurrent graph
+ * branches and the persistent launch's knobs; keeps the fastest and reports
+ * them.  Allocates temporary copies
  * of the states.  Synchronises the ensemble stream. */
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
 

@@ -518,13 +518,40 @@ ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, 
         best_r = r;
       }
     }
+    plan_set_xrpc(e->plans[i], best_r);
+    // tile shape of the column passes (columns per CTA, radix schedule), one
+    // pass at a time on top of the choices so far
+    int best_var[3] = {0, 0, 0};
+    for (int k = 0; k < 3 && st == PS_OK; ++k)
+      for (int var = 1; var <= 2 && st == PS_OK; ++var) {
+        if (!plan_set_shape(e->plans[i], k, var)) continue;
+        double ms = 0;
+        st = time_ms(e, 3, [&] { return ps_rk_step(e->plans[i], work[i], dt, 0.0); }, &ms);
+        if (st == PS_OK && ms < best * 0.98) {
+          best = ms;
+          best_var[k] = var;
+        }
+        plan_set_shape(e->plans[i], k, best_var[k]);
+      }
     for (size_t j = i; j < m; ++j) {
       const ps_config& d = e->cfgs[j];
-      if (d.nx == c.nx && d.ny == c.ny && d.nz == c.nz && d.prec == c.prec) plan_set_xrpc(e->plans[j], best_r);
+      if (d.nx == c.nx && d.ny == c.ny && d.nz == c.nz && d.prec == c.prec) {
+        plan_set_xrpc(e->plans[j], best_r);
+        for (int k = 0; k < 3; ++k) plan_set_shape(e->plans[j], k, best_var[k]);
+      }
     }
     if (out->nsizes < PS_ENS_MAX_SIZES) {
-      out->n[out->nsizes] = c.nx;
-      out->xrpc[out->nsizes] = best_r;
+      const int z = out->nsizes;
+      out->n[z] = c.nx;
+      out->xrpc[z] = best_r;
+      for (int k = 0; k < 3; ++k) {
+        const int len = k == 1 ? c.ny : c.nz;
+        int cols = 0, pts = 0;
+        if (c.prec == PS_FP32) pass_shape<float>(k, len, best_var[k], &cols, &pts);
+        else pass_shape<double>(k, len, best_var[k], &cols, &pts);
+        out->pass_cols[z][k] = cols;
+        out->pass_points[z][k] = pts;
+      }
       out->nsizes++;
     }
   }

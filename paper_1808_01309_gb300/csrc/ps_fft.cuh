@@ -191,6 +191,7 @@ template <> struct Sched<16, 16> { static constexpr int S = 1, R0 = 16, R1 = 1, 
 template <> struct Sched<16, 8> { static constexpr int S = 2, R0 = 8, R1 = 2, R2 = 1, R3 = 1; };
 template <> struct Sched<32, 8> { static constexpr int S = 2, R0 = 8, R1 = 4, R2 = 1, R3 = 1; };
 template <> struct Sched<64, 8> { static constexpr int S = 2, R0 = 8, R1 = 8, R2 = 1, R3 = 1; };
+template <> struct Sched<64, 16> { static constexpr int S = 2, R0 = 16, R1 = 4, R2 = 1, R3 = 1; };
 template <> struct Sched<128, 16> { static constexpr int S = 2, R0 = 16, R1 = 8, R2 = 1, R3 = 1; };
 template <> struct Sched<128, 8> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 2, R3 = 1; };
 template <> struct Sched<256, 16> { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, R3 = 1; };

@@ -85,6 +85,7 @@ struct PassArgs {
   int Fx, Fy, Fz;
   int xdiag;         // x pass: only the max |u| reduction (no product, no output)
   int xrpc;          // x pass rows per CTA (0 = largest that keeps two CTAs per SM)
+  int shape[3];      // shape variant of the z-inverse, y and z-forward passes (ColShape; 0 = default)
   int* err;          // device error word (bounded waits that gave up), never null
   unsigned wait_polls;  // x pass: polls before a wait gives up (0 = PS_WAIT_LIMIT)
   int wait_test;     // x pass: test hook, the first copy of every CTA is never issued
@@ -121,7 +122,12 @@ template <typename T> cudaError_t launch_zfwd(const PassArgs& a, cudaStream_t s)
 // projection, forcing, closure and the ZfwdMode output from the z-forward pass's a6
 template <typename T> cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
 // number of CTAs (energy partials) the z-inverse pass uses for this geometry
-template <typename T> int zinv_blocks(const Geo& g);
+// in shape variant var (-1: the largest over the variants)
+template <typename T> int zinv_blocks(const Geo& g, int var = 0);
+// Columns per CTA and points per thread of column pass k (0 z-inverse, 1 y
+// passes, 2 z-forward) on lines of n points in shape variant var; false if
+// the length has no such variant.
+template <typename T> bool pass_shape(int k, int n, int var, int* cols, int* points);
 
 // Auxiliary kernels (ps_aux.cu)
 template <typename T>
@@ -169,6 +175,9 @@ void plan_set_xrpc(struct ::ps_plan* p, int rpc);
 // Forget the cached integrating-factor tables so the next step recomputes them
 // (a captured graph must contain that launch).
 void plan_invalidate_tables(struct ::ps_plan* p);
+// Shape variant (ColShape) of column pass k of p; false if it has none such.
+bool plan_set_shape(struct ::ps_plan* p, int k, int var);
+int plan_shape(const struct ::ps_plan* p, int k);
 void plan_set_time(struct ::ps_plan* p, double t);
 // What the persistent ensemble launch (ps_persist.cu) needs of a member plan.
 struct PlanView {

@@ -52,6 +52,29 @@ template <typename T, int N, int K = 0> struct NBOf {
 template <typename T, int N, int K = 0> struct ColThreads {
   static constexpr int v = TXOf<T, K>::v * (N / EPass<T, N, K>::v) * NBOf<T, N, K>::v;
 };
+// Shape of column pass K (0 z-inverse, 1 y passes, 2 z-forward) on lines of
+// N points: kx columns per CTA (TX), points per thread (E), threads per line
+// (G), lines of the other index per CTA (NB, about 256 threads per CTA).
+// VAR 0 is the default above; VAR 1 halves the columns per CTA (twice the
+// lines); VAR 2 takes the other radix schedule, 8 <-> 16 points per thread
+// (lengths with a factor 3 keep theirs).  Plans of the grids that the
+// ensemble tuner shapes (HasShapes) carry the variant per pass.
+template <typename T, int N> struct AltE {
+  static constexpr int e0 = EOf<T, N>::v;
+  static constexpr int v = (N % 3 == 0) ? e0 : e0 == 16 ? 8 : 16;
+};
+template <typename T, int N, int K, int VAR = 0> struct ColShape {
+  static constexpr int TX = VAR == 1 ? TXOf<T, K>::v / 2 : TXOf<T, K>::v;
+  static constexpr int E = VAR == 2 ? AltE<T, N>::v : EPass<T, N, K>::v;
+  static constexpr int G = N / E;
+  static constexpr int q = 256 / (TX * G);
+  static constexpr int NB = q < 1 ? 1 : q;
+  static constexpr int NTH = TX * G * NB;
+};
+template <typename T, int N> struct HasShapes {
+  static constexpr bool v = sizeof(T) == 4 && (N == 64 || N == 96 || N == 128);
+};
+
 // rows per CTA in the x pass
 template <typename T, int N> struct RPCOf {
   static constexpr int G = N / EPass<T, N, 3>::v;
@@ -204,11 +227,12 @@ struct WorkTile {
 
 // One CTA tile (x, y) of the pass; gx = tiles along x (energy partial index
 // y gx + x).  COH: coherent loads (see ldv).
-template <typename T, int N, int NG, int NSC, bool COH, class TL>
+template <typename T, int N, int NG, int NSC, bool COH, int VAR, class TL>
 __device__ __forceinline__ void zinv_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 0>::v, G = N / E, TX = TXOf<T>::v, NB = NBOf<T, N>::v;
-  constexpr int NTH = ColThreads<T, N>::v;
+  using SH = ColShape<T, N, 0, VAR>;
+  constexpr int E = SH::E, G = SH::G, TX = SH::TX, NB = SH::NB;
+  constexpr int NTH = SH::NTH;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
   const Geo& g = a.g;
@@ -339,18 +363,19 @@ __device__ __forceinline__ void zinv_tile(const PassArgs& a, const TL& tl) {
   }
 }
 
-template <typename T, int N, int NG, int NSC>
-__global__ void __launch_bounds__(ColThreads<T, N>::v, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
-  zinv_tile<T, N, NG, NSC, false>(a, LaunchTile{});
+template <typename T, int N, int NG, int NSC, int VAR = 0>
+__global__ void __launch_bounds__(ColShape<T, N, 0, VAR>::NTH, MinB<T, N>::zinv) k_zinv(const PassArgs a) {
+  zinv_tile<T, N, NG, NSC, false, VAR>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
 // yinv: backward transform along y of 6 fields.  CTA = TX columns x NB z planes.
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool COH, class TL>
+template <typename T, int N, bool COH, int VAR, class TL>
 __device__ __forceinline__ void yinv_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  using SH = ColShape<T, N, 1, VAR>;
+  constexpr int E = SH::E, G = SH::G, TX = SH::TX, NB = SH::NB;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -379,9 +404,9 @@ __device__ __forceinline__ void yinv_tile(const PassArgs& a, const TL& tl) {
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yinv(const PassArgs a) {
-  yinv_tile<T, N, false>(a, LaunchTile{});
+template <typename T, int N, int VAR = 0>
+__global__ void __launch_bounds__(ColShape<T, N, 1, VAR>::NTH, MinB<T, N>::ypass) k_yinv(const PassArgs a) {
+  yinv_tile<T, N, false, VAR>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
@@ -671,10 +696,11 @@ __global__ void __launch_bounds__(RPCOf<T, N>::v * (N / EPass<T, N, 3>::v),
 // ---------------------------------------------------------------------------
 // yfwd: forward transform along y of 3 fields, keep |ky| <= Ky.
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool COH, class TL>
+template <typename T, int N, bool COH, int VAR, class TL>
 __device__ __forceinline__ void yfwd_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 1>::v, G = N / E, TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  using SH = ColShape<T, N, 1, VAR>;
+  constexpr int E = SH::E, G = SH::G, TX = SH::TX, NB = SH::NB;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -700,9 +726,9 @@ __device__ __forceinline__ void yfwd_tile(const PassArgs& a, const TL& tl) {
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_yfwd(const PassArgs a) {
-  yfwd_tile<T, N, false>(a, LaunchTile{});
+template <typename T, int N, int VAR = 0>
+__global__ void __launch_bounds__(ColShape<T, N, 1, VAR>::NTH, MinB<T, N>::ypass) k_yfwd(const PassArgs a) {
+  yfwd_tile<T, N, false, VAR>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
@@ -711,10 +737,11 @@ __global__ void __launch_bounds__(ColThreads<T, N, 1>::v, MinB<T, N>::ypass) k_y
 // nonlinear term [3 ng][cz][cy][kxp] into a6 (zero where the mode is not
 // retained).  The projection, forcing and stage update follow in k_update.
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool COH, class TL>
+template <typename T, int N, bool COH, int VAR, class TL>
 __device__ __forceinline__ void zfwd_tile(const PassArgs& a, const TL& tl) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 2>::v, G = N / E, TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
+  using SH = ColShape<T, N, 2, VAR>;
+  constexpr int E = SH::E, G = SH::G, TX = SH::TX, NB = SH::NB;
   extern __shared__ __align__(128) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const Geo& g = a.g;
@@ -746,9 +773,9 @@ __device__ __forceinline__ void zfwd_tile(const PassArgs& a, const TL& tl) {
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(ColThreads<T, N, 2>::v, MinB<T, N>::zfwd) k_zfwd(const PassArgs a) {
-  zfwd_tile<T, N, false>(a, LaunchTile{});
+template <typename T, int N, int VAR = 0>
+__global__ void __launch_bounds__(ColShape<T, N, 2, VAR>::NTH, MinB<T, N>::zfwd) k_zfwd(const PassArgs a) {
+  zfwd_tile<T, N, false, VAR>(a, LaunchTile{});
 }
 
 // ---------------------------------------------------------------------------
@@ -947,37 +974,66 @@ static cudaError_t prep(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename T, int N, int NG, int NSC>
+// Energy partials (CTAs) of the z-inverse pass in shape VAR.
+template <typename T, int N, int VAR = 0>
+int zinv_grid_blocks(const Geo& g) {
+  using SH = ColShape<T, N, 0, VAR>;
+  return (g.kxp / SH::TX) * ((g.cy + SH::NB - 1) / SH::NB);
+}
+
+template <typename T, int N, int NG, int NSC, int VAR = 0>
 cudaError_t zinv_ng(const PassArgs& a0, cudaStream_t s, int* nb) {
   PassArgs a = a0;
   prepare_args(a);
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T>::v, NB = NBOf<T, N>::v;
+  using SH = ColShape<T, N, 0, VAR>;
+  constexpr int TX = SH::TX, NB = SH::NB;
   const size_t smem = (1ull * NB * N * TX + 3ull * NB * a.g.cz * TX) * sizeof(V);
-  cudaError_t e = prep(k_zinv<T, N, NG, NSC>, smem);
+  cudaError_t e = prep(k_zinv<T, N, NG, NSC, VAR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB);
   if (nb) *nb = grid.x * grid.y;
-  k_zinv<T, N, NG, NSC><<<grid, ColThreads<T, N>::v, smem, s>>>(a);
+  k_zinv<T, N, NG, NSC, VAR><<<grid, SH::NTH, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int N>
 cudaError_t zinv_n(const PassArgs& a, cudaStream_t s, int* nb) {
   if (a.ng == 2) return zinv_ng<T, N, 2, 0>(a, s, nb);
-  return a.nsc ? zinv_ng<T, N, 1, 1>(a, s, nb) : zinv_ng<T, N, 1, 0>(a, s, nb);
+  if (a.nsc) return zinv_ng<T, N, 1, 1>(a, s, nb);
+  if constexpr (HasShapes<T, N>::v) {
+    if (a.shape[0] == 1) return zinv_ng<T, N, 1, 0, 1>(a, s, nb);
+    if constexpr (AltE<T, N>::v != EOf<T, N>::v)
+      if (a.shape[0] == 2) return zinv_ng<T, N, 1, 0, 2>(a, s, nb);
+  }
+  return zinv_ng<T, N, 1, 0>(a, s, nb);
 }
-template <typename T, int N>
-cudaError_t yinv_n(const PassArgs& a0, cudaStream_t s) {
+template <typename T, int N, int VAR = 0>
+cudaError_t yinv_nv(const PassArgs& a0, cudaStream_t s) {
   PassArgs a = a0;
   prepare_args(a);
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  using SH = ColShape<T, N, 1, VAR>;
+  constexpr int TX = SH::TX, NB = SH::NB;
   const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
-  cudaError_t e = prep(k_yinv<T, N>, smem);
+  cudaError_t e = prep(k_yinv<T, N, VAR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfi);
-  k_yinv<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
+  k_yinv<T, N, VAR><<<grid, SH::NTH, smem, s>>>(a);
   return cudaGetLastError();
+}
+// Shape variant v (0, 1, 2) of pass launcher L for a length with variants.
+#define PS_SHAPE_DISPATCH(L, var_, ...)                                                 \
+  do {                                                                                  \
+    if constexpr (HasShapes<T, N>::v) {                                                 \
+      if ((var_) == 1) return L<T, N, 1>(__VA_ARGS__);                                  \
+      if constexpr (AltE<T, N>::v != EOf<T, N>::v)                                      \
+        if ((var_) == 2) return L<T, N, 2>(__VA_ARGS__);                                \
+    }                                                                                   \
+    return L<T, N, 0>(__VA_ARGS__);                                                     \
+  } while (0)
+template <typename T, int N>
+cudaError_t yinv_n(const PassArgs& a, cudaStream_t s) {
+  PS_SHAPE_DISPATCH(yinv_nv, a.shape[1], a, s);
 }
 // Shared memory of the x pass for rpc rows: one input stage of 6 ng rows, the
 // exchange region (XLINES lines per row) and, when used, the twiddle table.
@@ -1022,31 +1078,41 @@ cudaError_t xpass_n(const PassArgs& a, cudaStream_t s) {
   return a.nsc ? xpass_ng<T, N, 1, 1>(a, s) : xpass_ng<T, N, 1, 0>(a, s);
 }
 
-template <typename T, int N>
-cudaError_t yfwd_n(const PassArgs& a0, cudaStream_t s) {
+template <typename T, int N, int VAR = 0>
+cudaError_t yfwd_nv(const PassArgs& a0, cudaStream_t s) {
   PassArgs a = a0;
   prepare_args(a);
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T, 1>::v, NB = NBOf<T, N, 1>::v;
+  using SH = ColShape<T, N, 1, VAR>;
+  constexpr int TX = SH::TX, NB = SH::NB;
   const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
-  cudaError_t e = prep(k_yfwd<T, N>, smem);
+  cudaError_t e = prep(k_yfwd<T, N, VAR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.nz + NB - 1) / NB, a.nfo);
-  k_yfwd<T, N><<<grid, ColThreads<T, N, 1>::v, smem, s>>>(a);
+  k_yfwd<T, N, VAR><<<grid, SH::NTH, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int N>
-cudaError_t zfwd_n(const PassArgs& a0, cudaStream_t s) {
+cudaError_t yfwd_n(const PassArgs& a, cudaStream_t s) {
+  PS_SHAPE_DISPATCH(yfwd_nv, a.shape[1], a, s);
+}
+template <typename T, int N, int VAR = 0>
+cudaError_t zfwd_nv(const PassArgs& a0, cudaStream_t s) {
   PassArgs a = a0;
   prepare_args(a);
   using V = typename cplx<T>::type;
-  constexpr int TX = TXOf<T, 2>::v, NB = NBOf<T, N, 2>::v;
+  using SH = ColShape<T, N, 2, VAR>;
+  constexpr int TX = SH::TX, NB = SH::NB;
   const size_t smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
-  cudaError_t e = prep(k_zfwd<T, N>, smem);
+  cudaError_t e = prep(k_zfwd<T, N, VAR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.kxp / TX, (a.g.cy + NB - 1) / NB, a.nfo);
-  k_zfwd<T, N><<<grid, ColThreads<T, N, 2>::v, smem, s>>>(a);
+  k_zfwd<T, N, VAR><<<grid, SH::NTH, smem, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T, int N>
+cudaError_t zfwd_n(const PassArgs& a, cudaStream_t s) {
+  PS_SHAPE_DISPATCH(zfwd_nv, a.shape[2], a, s);
 }
 template <typename T>
 cudaError_t update_launch(const PassArgs& a0, cudaStream_t s) {

@@ -112,11 +112,11 @@ __device__ __forceinline__ void ens_tile_n(const EnsPass& P, const PassArgs& a, 
   const int gx = P.gx, gxy = P.gx * P.gy;
   const WorkTile tl{(tile % gxy) % gx, (tile % gxy) / gx, tile / gxy, gx};
   switch (P.kind) {
-    case EK_ZINV: zinv_tile<T, N, 1, 0, true>(a, tl); break;
-    case EK_YINV: yinv_tile<T, N, true>(a, tl); break;
+    case EK_ZINV: zinv_tile<T, N, 1, 0, true, 0>(a, tl); break;
+    case EK_YINV: yinv_tile<T, N, true, 0>(a, tl); break;
     case EK_XPASS: ens_xpass_tile<T, N>(a, tile); break;
-    case EK_YFWD: yfwd_tile<T, N, true>(a, tl); break;
-    case EK_ZFWD: zfwd_tile<T, N, true>(a, tl); break;
+    case EK_YFWD: yfwd_tile<T, N, true, 0>(a, tl); break;
+    case EK_ZFWD: zfwd_tile<T, N, true, 0>(a, tl); break;
     default: break;
   }
 }

@@ -143,6 +143,8 @@ struct ps_plan {
   cudaStream_t stream = nullptr;
   int device = 0;
   int xrpc = 0;  // x-pass rows per CTA override (0 = automatic)
+  int shape[3] = {0, 0, 0};  // shape variants of the z-inverse, y and z-forward passes
+  int n_epart_run = 0;       // energy partials written by the last z-inverse launch
   unsigned wait_test_polls = 0;  // ps_plan_set_wait_test: 0 = off
   // learned LES closure (ps_plan_set_closure)
   bool les_on = false;
@@ -305,6 +307,7 @@ PassArgs base_args(ps_plan* p) {
   a.acc = p->acc;
   a.err = p->err;
   a.xrpc = p->xrpc;
+  for (int k = 0; k < 3; ++k) a.shape[k] = p->shape[k];
   a.wait_test = p->wait_test_polls ? 1 : 0;
   a.wait_polls = p->wait_test_polls;
   return a;
@@ -329,6 +332,7 @@ ps_status run_inverse_and_x(ps_plan* p, PassArgs& a) {
   ps_status s;
   int nb = 0;
   if ((s = launch(p, 0, [&] { return launch_zinv<T>(a, p->stream, &nb); }, "z-inverse pass")) != PS_OK) return s;
+  p->n_epart_run = nb;
   if ((s = launch(p, 1, [&] { return launch_yinv<T>(a, p->stream); }, "y-inverse pass")) != PS_OK) return s;
   if ((s = launch(p, 2, [&] { return launch_xpass<T>(a, p->stream); }, "x pass")) != PS_OK) return s;
   return PS_OK;
@@ -341,7 +345,7 @@ ps_status run_rhs_passes(ps_plan* p, PassArgs& a) {
   ps_status s;
   if ((s = run_inverse_and_x<T>(p, a)) != PS_OK) return s;
   if (a.e_part) {
-    if ((s = launch(p, 5, [&] { return launch_sum_partials(p->e_part, p->n_epart, p->stats, p->stream); },
+    if ((s = launch(p, 5, [&] { return launch_sum_partials(p->e_part, p->n_epart_run, p->stats, p->stream); },
                     "energy reduction")) != PS_OK)
       return s;
   }
@@ -531,6 +535,17 @@ void plan_set_xrpc(ps_plan* p, int rpc) {
   p->xrpc = rpc;
 }
 void plan_invalidate_tables(ps_plan* p) { p->if_dt = NAN; }
+bool plan_set_shape(ps_plan* p, int k, int var) {
+  if (k < 0 || k > 2) return false;
+  const int n = k == 1 ? p->g.ny : p->g.nz;
+  int c = 0, e = 0;
+  const bool ok = p->cfg.prec == PS_FP32 ? pass_shape<float>(k, n, var, &c, &e) : pass_shape<double>(k, n, var, &c, &e);
+  if (!ok) return false;
+  if (p->shape[k] != var) drop_cached_graph(p);
+  p->shape[k] = var;
+  return true;
+}
+int plan_shape(const ps_plan* p, int k) { return (k >= 0 && k < 3) ? p->shape[k] : 0; }
 void plan_set_time(ps_plan* p, double t) { p->time = t; }
 PlanView plan_view(const ps_plan* p) {
   PlanView v{};
@@ -645,8 +660,11 @@ ps_status ps_plan_create(const ps_config* cfg, void* cuda_stream, ps_plan** out)
   ALLOC(p->acc, p->sz.cmp * vb, "stage accumulator");
   ALLOC(p->tw, vb * (size_t)(p->g.nx + p->g.ny + p->g.nz), "twiddles");
   ALLOC(p->iftab, 2 * tb * (size_t)(p->g.cx + p->g.cy + p->g.cz), "integrating factors");
-  int nb = cfg->prec == PS_FP32 ? zinv_blocks<float>(p->g) : zinv_blocks<double>(p->g);
-  p->n_epart = nb;
+  const bool f32 = cfg->prec == PS_FP32;
+  p->n_epart = f32 ? zinv_blocks<float>(p->g, 0) : zinv_blocks<double>(p->g, 0);
+  p->n_epart_run = p->n_epart;
+  // room for the partials of every shape variant of the z-inverse pass
+  const int nb = f32 ? zinv_blocks<float>(p->g, -1) : zinv_blocks<double>(p->g, -1);
   ALLOC(p->e_part, sizeof(double) * (size_t)(nb > 0 ? nb : 1), "energy partials");
   ALLOC(p->stats, sizeof(double) * 4, "stats");
   ALLOC(p->umax2, sizeof(unsigned long long), "max|u|");
@@ -1008,6 +1026,24 @@ ps_status ps_plan_set_timing(ps_plan* p, int enable) {
     p->n_acc[k] = 0;
   }
   p->timing = enable != 0;
+  return PS_OK;
+}
+
+ps_status ps_plan_set_pass_shape(ps_plan* p, int pass, int variant, int* cols, int* points) {
+  if (!p) return fail(PS_ERR_INVALID_ARG, "NULL plan");
+  if (pass < 0 || pass > 2) return fail(PS_ERR_INVALID_ARG, "pass must be 0 (z-inverse), 1 (y passes) or 2 (z-forward)");
+  if (variant < 0 || variant > 2) return fail(PS_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  const bool slab = p->g.kx0 != 0 || p->g.ncx != 0 || p->g.rowlen != 0;
+  if (variant != 0 && (p->ng != 1 || p->cn.nsc || slab || !plan_set_shape(p, pass, variant)))
+    return fail(PS_ERR_UNSUPPORTED, "no such shape variant for this plan (FP32 hydrodynamic plans with lines of "
+                                    "64, 96 or 128 points; variant 2 not for 96)");
+  if (variant == 0) plan_set_shape(p, pass, 0);
+  const int n = pass == 1 ? p->g.ny : p->g.nz;
+  int c = 0, e = 0;
+  if (p->cfg.prec == PS_FP32) pass_shape<float>(pass, n, variant, &c, &e);
+  else pass_shape<double>(pass, n, variant, &c, &e);
+  if (cols) *cols = c;
+  if (points) *points = e;
   return PS_OK;
 }
 

@@ -57,6 +57,7 @@ SYMBOLS = (
     "ps_fft_r2c", "ps_fft_c2r", "ps_probe_fma_tflops", "ps_plan_set_wait_test",
     "ps_slab_create", "ps_slab_destroy", "ps_slab_info_get", "ps_slab_inverse", "ps_slab_xpass",
     "ps_slab_forward", "ps_slab_check", "ps_ensemble_check", "ps_ensemble_set_wait_test",
+    "ps_plan_set_pass_shape",
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY, HOST_CUBE_CE = 0, 1, 2, 3, 4
 MLP_NPARAM = 4934
@@ -92,7 +93,9 @@ class PsDiag(ctypes.Structure):
 
 class PsEnsTuning(ctypes.Structure):
     _fields_ = [("branches", ctypes.c_int), ("nsizes", ctypes.c_int), ("n", ctypes.c_int * 8),
-                ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double), ("persistent_step_ms", ctypes.c_double),
+                ("xrpc", ctypes.c_int * 8), ("step_ms", ctypes.c_double),
+                ("pass_cols", (ctypes.c_int * 3) * 8), ("pass_points", (ctypes.c_int * 3) * 8),
+                ("persistent_step_ms", ctypes.c_double),
                 ("persistent_ctas_per_sm", ctypes.c_int), ("persistent_order", ctypes.c_int),
                 ("persistent_tiles_per_item", ctypes.c_int * 6), ("best_mode", ctypes.c_int)]
 
@@ -136,6 +139,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.c_int]
     lib.ps_ensemble_tune.argtypes = [P, ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(PsEnsTuning)]
     lib.ps_ensemble_check.argtypes = [P]
+    lib.ps_plan_set_pass_shape.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
     lib.ps_ensemble_set_wait_test.argtypes = [P, ctypes.c_uint]
     lib.ps_mlp_forward.argtypes = [P, P, P, ctypes.c_longlong, P]
     lib.ps_mlp_grad.argtypes = [P, P, P, ctypes.c_longlong, P, P, P]
@@ -291,6 +296,14 @@ def ps_plan_set_wait_test(plan, polls: int) -> None:
     _check(load().ps_plan_set_wait_test(plan, int(polls)))
 
 
+def ps_plan_set_pass_shape(plan, pass_: int, variant: int) -> tuple[int, int]:
+    """Tile shape variant of a column pass (0 z-inverse, 1 y passes, 2 z-forward);
+    returns (kx columns per CTA, points per thread)."""
+    c, e = ctypes.c_int(), ctypes.c_int()
+    _check(load().ps_plan_set_pass_shape(plan, int(pass_), int(variant), ctypes.byref(c), ctypes.byref(e)))
+    return c.value, e.value
+
+
 def ps_probe_fma_tflops(prec: int, stream=None) -> float:
     """Measured FMA rate of the device in TFLOP/s (FP32 or FP64)."""
     out = ctypes.c_double()
@@ -389,6 +402,9 @@ def ps_ensemble_tune(ens, states, dt: float) -> dict:
     _check(load().ps_ensemble_tune(ens, _ptr_array(states), float(dt), ctypes.byref(t)))
     return {"branches": t.branches, "step_ms": t.step_ms,
             "xrpc": {int(t.n[i]): int(t.xrpc[i]) for i in range(t.nsizes)},
+            "pass_shapes": {int(t.n[i]): {p: (int(t.pass_cols[i][k]), int(t.pass_points[i][k]))
+                                          for k, p in enumerate(("z_inverse", "y_passes", "z_forward"))}
+                            for i in range(t.nsizes)},
             "persistent_step_ms": t.persistent_step_ms,
             "persistent_ctas_per_sm": t.persistent_ctas_per_sm, "persistent_order": t.persistent_order,
             "persistent_tiles_per_item": {ENS_PASSES[k]: int(t.persistent_tiles_per_item[k]) for k in range(6)},
@@ -522,6 +538,9 @@ class Plan:
 
     def step_stats(self):
         return ps_step_stats(self.handle)
+
+    def set_pass_shape(self, pass_, variant):
+        return ps_plan_set_pass_shape(self.handle, pass_, variant)
 
     def set_closure(self, params, norm=None):
         """Attach a trained LES closure (see ps_plan_set_closure); None detaches."""

@@ -89,6 +89,10 @@ def test_tuner_keeps_states_and_results(ps):
         assert torch.equal(a, b)
     assert 1 <= tuning["branches"] <= len(SIZES) and tuning["step_ms"] > 0
     assert set(tuning["xrpc"]) == {32, 48, 64, 96}
+    assert set(tuning["pass_shapes"]) == {32, 48, 64, 96}
+    for n, passes in tuning["pass_shapes"].items():
+        for cols, pts in passes.values():
+            assert cols in (4, 8) and pts in (8, 12, 16)
     ref = [s.clone() for s in states]
     ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_GRAPH)
     ps.ps_ensemble_rk_steps(ens, ref, 2e-3, 0.0, 2, ps.ENS_SEQUENTIAL)
