@@ -696,9 +696,10 @@ def run_ensemble(args, dev, stream):
     """48 independent unforced solves (16 each at 64^3, 96^3, 128^3), seeds
     1000+i, nu_i = 1e-3 + 4e-3 U(seed 2000+i), FP32, IF-RK4, dt = 1e-3:
     member-by-member launches vs one CUDA graph of the members' launch chains
-    vs one persistent kernel over a (member, pass, tile) work queue (both
-    graphs autotuned); the largest relative difference of the final states of
-    the two is reported."""
+    vs one persistent kernel over a (member, pass, tile) work queue vs batched
+    launches (one per pass for the members of a grid size; all autotuned);
+    the largest relative difference of the persistent and graph final states
+    is reported."""
     import torch
     from paper_1808_01309_gb300 import inputs, ps
     cfgs, host = [], []
@@ -716,7 +717,8 @@ def run_ensemble(args, dev, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     finals = {}
-    for mode, name in ((ps.ENS_SEQUENTIAL, "sequential"), (ps.ENS_GRAPH, "graph"), (ps.ENS_PERSISTENT, "persistent")):
+    for mode, name in ((ps.ENS_SEQUENTIAL, "sequential"), (ps.ENS_GRAPH, "graph"), (ps.ENS_PERSISTENT, "persistent"),
+                       (ps.ENS_BATCHED, "batched")):
         states = [h.clone() for h in host]
         # warm-up (for the graph: captures and instantiates the K-step graph)
         t1 = time.perf_counter()
@@ -735,6 +737,8 @@ def run_ensemble(args, dev, stream):
     out["graph_speedup"] = round(out["sequential"]["ms"] / out["graph"]["ms"], 3)
     out["persistent_speedup"] = round(out["sequential"]["ms"] / out["persistent"]["ms"], 3)
     out["persistent_vs_graph"] = round(out["graph"]["ms"] / out["persistent"]["ms"], 3)
+    out["batched_speedup"] = round(out["sequential"]["ms"] / out["batched"]["ms"], 3)
+    out["batched_vs_graph"] = round(out["graph"]["ms"] / out["batched"]["ms"], 3)
     # the graph runs the tuned tile shapes, the persistent launch the default
     # ones: equal to rounding (bitwise with equal shapes, see the GPU tests)
     out["persistent_vs_graph_max_rel"] = float(max(

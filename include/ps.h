@@ -269,11 +269,24 @@ typedef struct ps_ensemble ps_ensemble;
  * The launch is captured in a CUDA graph with the reset of its counters.  It
  * needs members of one precision, the hydrodynamic system without a closure
  * and axis lengths in {32, 48, 64, 96, 128} (PS_ERR_UNSUPPORTED otherwise);
- * its bounded waits report through ps_ensemble_check.  PS_ENS_AUTO: the mode
- * ps_ensemble_tune found faster (PS_ENS_GRAPH before tuning).  Graphs are
- * captured on the first call with given (states, dt, nsteps) and replayed by
- * later identical calls (t does not enter the right-hand side). */
-typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1, PS_ENS_PERSISTENT = 2, PS_ENS_AUTO = 3 } ps_ens_mode;
+ * its bounded waits report through ps_ensemble_check.  PS_ENS_BATCHED:
+ * members of one grid class (same grid, box, precision, dealiasing and RK
+ * order) share one launch per pass (tiles of all members in one grid; the x
+ * pass loops over (member, row group) pairs), in sub-batches of at most 32
+ * members (the tuner picks the size) that run as concurrent branches of one
+ * CUDA graph; same member restrictions as the persistent
+ * launch, results bit for bit those of PS_ENS_GRAPH at the default tile
+ * shapes.  PS_ENS_AUTO: the mode ps_ensemble_tune found fastest
+ * (PS_ENS_GRAPH before tuning).  Graphs are captured on the first call with
+ * given (states, dt, nsteps) and replayed by later identical calls (t does
+ * not enter the right-hand side). */
+typedef enum {
+  PS_ENS_SEQUENTIAL = 0,
+  PS_ENS_GRAPH = 1,
+  PS_ENS_PERSISTENT = 2,
+  PS_ENS_AUTO = 3,
+  PS_ENS_BATCHED = 4
+} ps_ens_mode;
 
 /* Result of ps_ensemble_tune: concurrent branches, and per distinct grid
  * (first nsizes entries, n = nx of the grid) the x-pass rows per CTA chosen
@@ -286,7 +299,8 @@ typedef enum { PS_ENS_SEQUENTIAL = 0, PS_ENS_GRAPH = 1, PS_ENS_PERSISTENT = 2, P
  * tiles per work item of the z-inverse,
  * y-inverse, x, y-forward, z-forward and update passes (in that order);
  * persistent_step_ms is its time of one step (-1: not supported by these
- * members).  best_mode is what PS_ENS_AUTO now runs. */
+ * members).  best_mode is what PS_ENS_AUTO now runs (graph, persistent or
+ * batched, whichever was fastest). */
 typedef struct {
   int branches;
   int nsizes;
@@ -299,6 +313,8 @@ typedef struct {
   int persistent_ctas_per_sm;
   int persistent_order;
   int persistent_tiles_per_item[6];
+  double batched_step_ms;  /* PS_ENS_BATCHED, one step (-1: not supported by these members) */
+  int batched_members_per_launch;  /* sub-batch size chosen for PS_ENS_BATCHED */
   int best_mode;
 } ps_ens_tuning;
 

@@ -16,6 +16,7 @@
 
 #include "ps.h"
 #include "ps_kernels.h"
+#include "ps_batch.cuh"
 #include "ps_persist.cuh"
 
 namespace ps {
@@ -61,6 +62,20 @@ struct ps_ensemble {
   int ctas_per_sm = 0;
   int order = 0;
   unsigned wait_test = 0;  // > 0: test hook (one dependency never completes; polls limit)
+  // batched mode: members of one grid size share each pass's launch
+  struct BatchClass {
+    std::vector<int> members;     // at most BATCH_MAX
+    std::vector<PassArgs> args;   // [stage][member]
+    double** d_sum = nullptr;     // stats word of each member
+    int nst = 0;
+  };
+  std::vector<BatchClass> bclasses;
+  int bsize = 4;  // members per batched launch (tuned): classes split into sub-batches
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bexec = nullptr;
+  std::vector<void*> bkey_states;
+  double bkey_dt = NAN;
+  int bkey_steps = -1;
   ps_ens_mode auto_mode = PS_ENS_GRAPH;
 };
 
@@ -368,6 +383,134 @@ ps_status run_persistent(ps_ensemble* e, void* const* u, double dt, double t, in
   return PS_OK;
 }
 
+void drop_bgraph(ps_ensemble* e) {
+  if (e->bexec) cudaGraphExecDestroy(e->bexec);
+  if (e->bgraph) cudaGraphDestroy(e->bgraph);
+  e->bexec = nullptr;
+  e->bgraph = nullptr;
+  e->bkey_steps = -1;
+  for (auto& c : e->bclasses)
+    if (c.d_sum) cudaFree(c.d_sum);
+  e->bclasses.clear();
+}
+
+// Why the members cannot run batched ("" if they can): the batched passes
+// cover the hydrodynamic system without a closure, lines of 32..128 points.
+std::string batch_unsupported(const ps_ensemble* e) {
+  auto ok_n = [](int n) { return n == 32 || n == 48 || n == 64 || n == 96 || n == 128; };
+  for (size_t i = 0; i < e->plans.size(); ++i) {
+    const PlanView v = plan_view(e->plans[i]);
+    if (v.eq != PS_HD) return "only the hydrodynamic system";
+    if (v.closure) return "a member has a learned closure attached";
+    if (!ok_n(v.g.nx) || !ok_n(v.g.ny) || !ok_n(v.g.nz)) return "axis lengths outside {32, 48, 64, 96, 128}";
+  }
+  return "";
+}
+
+// Members that can share launches: same grid, box, precision, dealiasing and
+// RK order (viscosity, forcing and state are per member).
+bool same_class(const ps_config& a, const ps_config& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.lx == b.lx && a.ly == b.ly && a.lz == b.lz &&
+         a.prec == b.prec && a.dealias == b.dealias && a.rk_order == b.rk_order;
+}
+
+// Captures nsteps steps of all members as batched launches: one graph branch
+// per grid class; on it, per member the integrating-factor tables, then per
+// step and RK stage one launch per pass for all members of the class.
+ps_status batch_capture(ps_ensemble* e, void* const* u, double dt, int nsteps) {
+  drop_bgraph(e);
+  const std::string why = batch_unsupported(e);
+  if (!why.empty()) return bad(PS_ERR_UNSUPPORTED, "ensemble: batched mode: " + why);
+  const size_t m = e->plans.size();
+  std::vector<bool> done(m, false);
+  for (size_t i = 0; i < m; ++i) {
+    if (done[i]) continue;
+    ps_ensemble::BatchClass c;
+    const int cap = std::max(1, std::min(e->bsize, BATCH_MAX));
+    for (size_t j = i; j < m && (int)c.members.size() < cap; ++j)
+      if (!done[j] && same_class(e->cfgs[i], e->cfgs[j])) {
+        c.members.push_back((int)j);
+        done[j] = true;
+      }
+    c.nst = plan_view(e->plans[i]).rk_stages;
+    const int M = (int)c.members.size();
+    c.args.resize((size_t)c.nst * M);
+    std::vector<double*> sums(M);
+    for (int st = 0; st < c.nst; ++st)
+      for (int k = 0; k < M; ++k)
+        c.args[(size_t)st * M + k] = plan_stage_args(e->plans[c.members[k]], u[c.members[k]], dt, st, true);
+    for (int k = 0; k < M; ++k) sums[k] = plan_view(e->plans[c.members[k]]).stats;
+    e->bclasses.push_back(c);  // owned by the ensemble from here (freed by drop_bgraph)
+    auto& cc = e->bclasses.back();
+    ENS_CU(cudaMalloc(&cc.d_sum, sums.size() * sizeof(double*)), "batched arguments");
+    ENS_CU(cudaMemcpy(cc.d_sum, sums.data(), sums.size() * sizeof(double*), cudaMemcpyHostToDevice), "batched arguments");
+  }
+  const int B = (int)e->bclasses.size();
+  if (B > (int)e->branch.size()) return bad(PS_ERR_UNSUPPORTED, "ensemble: too many grid classes");
+  std::vector<BatchArgs> bav(1);  // the launches' parameter image (about 14 KB)
+  ENS_CU(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  ps_status st = PS_OK;
+  cudaError_t ce = cudaEventRecord(e->fork, e->cap);
+  for (int b = 0; b < B && ce == cudaSuccess; ++b) ce = cudaStreamWaitEvent(e->branch[b], e->fork, 0);
+  if (ce != cudaSuccess) st = cu(ce, "fork");
+  for (int b = 0; b < B && st == PS_OK; ++b) {
+    const auto& c = e->bclasses[b];
+    cudaStream_t s = e->branch[b];
+    const int M = (int)c.members.size();
+    for (int k = 0; k < M && st == PS_OK; ++k) {
+      plan_set_stream(e->plans[c.members[k]], s);
+      st = (ps_status)plan_if_tables(e->plans[c.members[k]], dt);
+    }
+    const PlanView v = plan_view(e->plans[c.members[0]]);
+    const Geo& g = v.g;
+    const bool f32 = v.prec == PS_FP32;
+    const int lens[5] = {g.nz, g.ny, g.nx, g.ny, g.nz};
+    for (int step = 0; step < nsteps && st == PS_OK; ++step)
+      for (int k = 0; k < c.nst && st == PS_OK; ++k) {
+        BatchArgs& ba = bav[0];
+        ba = BatchArgs{};
+        for (int j = 0; j < M; ++j) ba.args[j] = c.args[(size_t)k * M + j];
+        for (int pass = 0; pass < 5 && ce == cudaSuccess; ++pass) {
+          ce = f32 ? batch_pass_f32(pass, lens[pass], ba, g, M, s) : batch_pass_f64(pass, lens[pass], ba, g, M, s);
+          if (ce == cudaSuccess && pass == 0 && k == 0) ce = batch_sum(ba, v.n_epart, c.d_sum, M, s);
+        }
+        if (ce == cudaSuccess)
+          ce = f32 ? batch_update_f32(ba, g, M, k == c.nst - 1, s) : batch_update_f64(ba, g, M, k == c.nst - 1, s);
+        if (ce != cudaSuccess) st = cu(ce, "batched pass");
+      }
+  }
+  for (int b = 0; b < B && st == PS_OK; ++b) {
+    ce = cudaEventRecord(e->join[b], e->branch[b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->cap, e->join[b], 0);
+    if (ce != cudaSuccess) st = cu(ce, "join");
+  }
+  cudaGraph_t gr = nullptr;
+  ce = cudaStreamEndCapture(e->cap, &gr);
+  if (st != PS_OK) {
+    if (gr) cudaGraphDestroy(gr);
+    return st;
+  }
+  ENS_CU(ce, "end capture");
+  e->bgraph = gr;
+  ENS_CU(cudaGraphInstantiate(&e->bexec, gr, 0), "instantiate");
+  e->bkey_states.assign(u, u + m);
+  e->bkey_dt = dt;
+  e->bkey_steps = nsteps;
+  return PS_OK;
+}
+
+ps_status run_batched(ps_ensemble* e, void* const* u, double dt, double t, int nsteps) {
+  const bool same = e->bexec && e->bkey_steps == nsteps && e->bkey_dt == dt &&
+                    std::equal(e->bkey_states.begin(), e->bkey_states.end(), u);
+  if (!same) {
+    ps_status st = batch_capture(e, u, dt, nsteps);
+    if (st != PS_OK) return st;
+  }
+  ENS_CU(cudaGraphLaunch(e->bexec, e->main), "graph launch");
+  for (ps_plan* p : e->plans) plan_set_time(p, t + nsteps * dt);
+  return PS_OK;
+}
+
 // Average milliseconds of `reps` calls of f on the main stream.
 template <class F>
 ps_status time_ms(ps_ensemble* e, int reps, F&& f, double* ms) {
@@ -431,6 +574,7 @@ ps_status ps_ensemble_destroy(ps_ensemble* e) {
   cudaStreamSynchronize(e->main);
   drop_graph(e);
   drop_pgraph(e);
+  drop_bgraph(e);
   for (void* d : {(void*)e->d_passes, (void*)e->d_args, (void*)e->d_done, (void*)e->d_head, (void*)e->d_err})
     if (d) cudaFree(d);
   for (auto p : e->plans) ps_plan_destroy(p);
@@ -456,6 +600,7 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
   if (mode == PS_ENS_SEQUENTIAL) return run_sequential(e, uhats, dt, t, nsteps);
   if (mode == PS_ENS_GRAPH) return run_graph(e, uhats, dt, t, nsteps);
   if (mode == PS_ENS_PERSISTENT) return run_persistent(e, uhats, dt, t, nsteps);
+  if (mode == PS_ENS_BATCHED) return run_batched(e, uhats, dt, t, nsteps);
   return bad(PS_ERR_INVALID_ARG, "ensemble: unknown mode");
 }
 
@@ -619,6 +764,33 @@ ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, 
       out->persistent_order = e->order;
       for (int k = 0; k < 6; ++k) out->persistent_tiles_per_item[k] = e->per[k];
       if (best < out->step_ms) e->auto_mode = PS_ENS_PERSISTENT;
+      out->best_mode = e->auto_mode;
+    }
+  }
+  // 4. batched launches (one per pass and sub-batch of a grid class; the
+  //    sub-batches are concurrent graph branches): members per launch
+  out->batched_step_ms = -1.0;
+  if (st == PS_OK && batch_unsupported(e).empty()) {
+    double ms = 1e30;
+    int best_bs = e->bsize;
+    for (int bs : {BATCH_MAX, 16, 8, 4, 2}) {
+      if (st != PS_OK) break;
+      e->bsize = bs;
+      double t_bs = 0;
+      drop_bgraph(e);
+      st = time_ms(e, 3, [&] { return run_batched(e, work.data(), dt, 0.0, 1); }, &t_bs);
+      if (st == PS_OK && t_bs < ms * 0.98) {
+        ms = t_bs;
+        best_bs = bs;
+      }
+    }
+    e->bsize = best_bs;
+    drop_bgraph(e);
+    if (st == PS_OK) {
+      out->batched_step_ms = ms;
+      out->batched_members_per_launch = best_bs;
+      const double cur = e->auto_mode == PS_ENS_PERSISTENT ? out->persistent_step_ms : out->step_ms;
+      if (ms < cur) e->auto_mode = PS_ENS_BATCHED;
       out->best_mode = e->auto_mode;
     }
   }

@@ -151,8 +151,11 @@ template <typename T>
 __global__ void __launch_bounds__(ENS_THREADS, EnsMinB<T>::v) k_ensemble(const EnsLaunch L) {
   __shared__ long long s_tick;
   __shared__ int s_stop;
+  // the current pass instance's arguments (read by every tile: kept in shared
+  // memory rather than read from global memory after every store)
+  __shared__ __align__(16) PassArgs s_args;
   const int tid = threadIdx.x;
-  int cur = 0, ready = -1;
+  int cur = 0, ready = -1, loaded = -1;
   for (;;) {
     if (tid == 0) s_tick = (long long)atomicAdd(L.head, 1ull);
     __syncthreads();
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsMinB<T>::v) k_ensemble(const E
     if (t >= L.tickets) break;
     // tickets grow within a CTA: the pass instance cursor only moves forward
     while (cur + 1 < L.npass && L.passes[cur + 1].tick0 <= t) ++cur;
-    const EnsPass& P = L.passes[cur];
+    const EnsPass P = L.passes[cur];  // a register copy (not re-read after the tiles' stores)
     if (cur != ready) {
       if (tid == 0) {
         int stop = 0;
@@ -181,7 +184,15 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsMinB<T>::v) k_ensemble(const E
       if (s_stop) break;
       ready = cur;
     }
-    const PassArgs& a = L.args[P.args];
+    if (P.args != loaded) {
+      static_assert(sizeof(PassArgs) % 4 == 0, "word copy");
+      const int* src = reinterpret_cast<const int*>(L.args + P.args);
+      int* dst = reinterpret_cast<int*>(&s_args);
+      for (int i = tid; i < (int)(sizeof(PassArgs) / 4); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      loaded = P.args;
+    }
+    const PassArgs& a = s_args;
     const int t0 = (int)(t - P.tick0) * P.per;
     const int t1 = t0 + P.per < P.ntiles ? t0 + P.per : P.ntiles;
     for (int tile = t0; tile < t1; ++tile) {

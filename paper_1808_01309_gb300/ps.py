@@ -61,7 +61,7 @@ SYMBOLS = (
 )
 HOST_AUTO, HOST_COPY, HOST_MAPPED, HOST_SMCOPY, HOST_CUBE_CE = 0, 1, 2, 3, 4
 MLP_NPARAM = 4934
-ENS_SEQUENTIAL, ENS_GRAPH, ENS_PERSISTENT, ENS_AUTO = 0, 1, 2, 3
+ENS_SEQUENTIAL, ENS_GRAPH, ENS_PERSISTENT, ENS_AUTO, ENS_BATCHED = 0, 1, 2, 3, 4
 ENS_PASSES = ("z_inverse", "y_inverse", "x_fused", "y_forward", "z_forward", "update")
 ENS_MAX_SIZES = 8
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -97,7 +97,8 @@ class PsEnsTuning(ctypes.Structure):
                 ("pass_cols", (ctypes.c_int * 3) * 8), ("pass_points", (ctypes.c_int * 3) * 8),
                 ("persistent_step_ms", ctypes.c_double),
                 ("persistent_ctas_per_sm", ctypes.c_int), ("persistent_order", ctypes.c_int),
-                ("persistent_tiles_per_item", ctypes.c_int * 6), ("best_mode", ctypes.c_int)]
+                ("persistent_tiles_per_item", ctypes.c_int * 6), ("batched_step_ms", ctypes.c_double),
+                ("batched_members_per_launch", ctypes.c_int), ("best_mode", ctypes.c_int)]
 
 
 class PsSlabInfo(ctypes.Structure):
@@ -408,7 +409,10 @@ def ps_ensemble_tune(ens, states, dt: float) -> dict:
             "persistent_step_ms": t.persistent_step_ms,
             "persistent_ctas_per_sm": t.persistent_ctas_per_sm, "persistent_order": t.persistent_order,
             "persistent_tiles_per_item": {ENS_PASSES[k]: int(t.persistent_tiles_per_item[k]) for k in range(6)},
-            "best_mode": {ENS_GRAPH: "graph", ENS_PERSISTENT: "persistent"}.get(t.best_mode, str(t.best_mode))}
+            "batched_step_ms": t.batched_step_ms,
+            "batched_members_per_launch": t.batched_members_per_launch,
+            "best_mode": {ENS_GRAPH: "graph", ENS_PERSISTENT: "persistent",
+                          ENS_BATCHED: "batched"}.get(t.best_mode, str(t.best_mode))}
 
 
 def ps_ensemble_check(ens) -> None:

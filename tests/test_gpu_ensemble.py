@@ -209,9 +209,10 @@ def test_persistent_rejects_unsupported_members(ps):
     states = [torch.zeros(3, 32, 32, 17, dtype=torch.complex64, device="cuda"),
               torch.zeros(3, 32, 32, 129, dtype=torch.complex64, device="cuda")]
     ens = ps.ps_ensemble_create(cfgs)
-    with pytest.raises(ps.PsError) as ei:
-        ps.ps_ensemble_rk_steps(ens, states, 1e-3, 0.0, 1, ps.ENS_PERSISTENT)
-    assert ei.value.status == ps.PS_ERR_UNSUPPORTED
+    for mode in (ps.ENS_PERSISTENT, ps.ENS_BATCHED):
+        with pytest.raises(ps.PsError) as ei:
+            ps.ps_ensemble_rk_steps(ens, states, 1e-3, 0.0, 1, mode)
+        assert ei.value.status == ps.PS_ERR_UNSUPPORTED
     ps.ps_ensemble_rk_steps(ens, states, 1e-3, 0.0, 1, ps.ENS_GRAPH)  # the other modes still run
     ps.ps_ensemble_destroy(ens)
 
@@ -220,8 +221,9 @@ def test_tuner_times_persistent_knobs_and_auto_mode_runs_the_faster(ps):
     cfgs, states, _ = _members(ps)
     ens = ps.ps_ensemble_create(cfgs)
     tuning = ps.ps_ensemble_tune(ens, states, 2e-3)
-    assert tuning["persistent_step_ms"] > 0
-    assert tuning["best_mode"] in ("graph", "persistent")
+    assert tuning["persistent_step_ms"] > 0 and tuning["batched_step_ms"] > 0
+    assert tuning["batched_members_per_launch"] in (2, 4, 8, 16, 32)
+    assert tuning["best_mode"] in ("graph", "persistent", "batched")
     assert tuning["persistent_ctas_per_sm"] in (0, 1) and tuning["persistent_order"] in (0, 1)
     assert all(v >= 1 for v in tuning["persistent_tiles_per_item"].values())
     ref = [s.clone() for s in states]
@@ -231,4 +233,57 @@ def test_tuner_times_persistent_knobs_and_auto_mode_runs_the_faster(ps):
     torch.cuda.synchronize()
     for a, b in zip(states, ref):
         assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+# ---- batched launches: one launch per pass for all members of a grid class
+
+def test_batched_matches_graph_bitwise_and_replays(ps):
+    cfgs, s_bat, _ = _members(ps)
+    s_graph = [s.clone() for s in s_bat]
+    ens = ps.ps_ensemble_create(cfgs)
+    for _ in range(2):  # capture, then replay of the same graph
+        ps.ps_ensemble_rk_steps(ens, s_bat, 2e-3, 0.0, 3, ps.ENS_BATCHED)
+        ps.ps_ensemble_rk_steps(ens, s_graph, 2e-3, 0.0, 3, ps.ENS_GRAPH)
+        torch.cuda.synchronize()
+        for a, b in zip(s_bat, s_graph):
+            assert torch.equal(a, b)
+    ps.ps_ensemble_destroy(ens)
+
+
+@pytest.mark.parametrize("member", [2, 6])
+def test_batched_member_matches_oracle_fp64(ps, member):
+    cfgs, states, host = _members(ps, "fp64")
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_BATCHED)
+    torch.cuda.synchronize()
+    n = SIZES[member]
+    ref = host[member]
+    cfg = oracle.Config(n, n, n, nu=cfgs[member].nu, rk_order=4)
+    for _ in range(2):
+        ref = oracle.rk_step(ref, 2e-3, cfg)
+    assert_parity(states[member].cpu().numpy(), ref, 1e-12, "batched ensemble member")
+    ps.ps_ensemble_destroy(ens)
+
+
+def test_batched_forced_rk2_classes_match_single_plans(ps):
+    shapes = [(64, 32, 48), (64, 32, 48), (32, 96, 64), (64, 32, 48)]
+    cfgs, states, keep = [], [], []
+    for i, (nx, ny, nz) in enumerate(shapes):
+        u = inputs.random_solenoidal_field(nx, ny, nz, seed=80 + i, kmax=(nx, ny, nz))
+        f = inputs.forcing_field(nx, ny, nz, seed=3 + i)
+        fd = torch.from_numpy(f).to("cuda", torch.complex64)
+        keep.append(fd)
+        cfgs.append(ps.make_config(nx, ny, nz, prec=ps.Precision.FP32, nu=1e-3 * (i + 1), rk_order=2, forcing=fd))
+        states.append(torch.from_numpy(u).to("cuda", torch.complex64))
+    single = [s.clone() for s in states]
+    ens = ps.ps_ensemble_create(cfgs)
+    ps.ps_ensemble_rk_steps(ens, states, 2e-3, 0.0, 2, ps.ENS_BATCHED)
+    for i, c in enumerate(cfgs):
+        plan = ps.Plan(c.nx, c.ny, c.nz, prec=ps.Precision.FP32, nu=c.nu, rk_order=2, forcing=keep[i])
+        for k in range(2):
+            plan.rk_step(single[i], 2e-3, t=k * 2e-3)
+        torch.cuda.synchronize()
+        assert torch.equal(states[i], single[i])
+        plan.close()
     ps.ps_ensemble_destroy(ens)
