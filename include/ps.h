@@ -337,10 +337,11 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
  * of the states.  Synchronises the ensemble stream. */
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
 
-/* Synchronises the ensemble stream and reports whether a bounded wait of a
- * persistent launch gave up since the last check (PS_ERR_TIMEOUT; the member
- * states are then invalid: the stage updates write NaN once the error word is
- * set).  Clears the report. */
+/* Synchronises the ensemble stream and reports whether a bounded device wait
+ * gave up since the last check, in any mode: a dependency wait of the
+ * persistent launch or an x-pass copy wait of a member (PS_ERR_TIMEOUT; the
+ * affected states are then invalid: the stage updates write NaN once an
+ * error word is set).  Clears the reports. */
 ps_status ps_ensemble_check(ps_ensemble* e);
 
 /* Test hook of the persistent launch's failure path: with polls > 0 one pass

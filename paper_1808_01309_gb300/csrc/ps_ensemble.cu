@@ -607,14 +607,23 @@ ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, do
 ps_status ps_ensemble_check(ps_ensemble* e) {
   if (!e) return bad(PS_ERR_INVALID_ARG, "ensemble: NULL ensemble");
   ENS_CU(cudaStreamSynchronize(e->main), "sync");
-  if (!e->d_err) return PS_OK;
-  int w = 0;
-  ENS_CU(cudaMemcpy(&w, e->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
-  if (w != 0) {
-    ENS_CU(cudaMemset(e->d_err, 0, sizeof(int)), "error word");
-    return bad(PS_ERR_TIMEOUT, "ensemble: a bounded wait of the persistent launch gave up");
+  ps_status result = PS_OK;
+  if (e->d_err) {
+    int w = 0;
+    ENS_CU(cudaMemcpy(&w, e->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (w != 0) {
+      ENS_CU(cudaMemset(e->d_err, 0, sizeof(int)), "error word");
+      result = bad(PS_ERR_TIMEOUT, "ensemble: a bounded wait of the persistent launch gave up");
+    }
   }
-  return PS_OK;
+  // the members' own words (x-pass waits of the graph, batched and
+  // sequential modes); every word is read and cleared
+  for (ps_plan* p : e->plans) {
+    plan_set_stream(p, e->main);
+    const ps_status s = (ps_status)plan_check_error(p);
+    if (result == PS_OK) result = s;
+  }
+  return result;
 }
 
 ps_status ps_ensemble_set_wait_test(ps_ensemble* e, unsigned polls) {

@@ -178,6 +178,9 @@ void plan_invalidate_tables(struct ::ps_plan* p);
 // Shape variant (ColShape) of column pass k of p; false if it has none such.
 bool plan_set_shape(struct ::ps_plan* p, int k, int var);
 int plan_shape(const struct ::ps_plan* p, int k);
+// Reads and clears the plan's device error word (synchronises its stream);
+// a ps_status value, PS_ERR_TIMEOUT if a bounded wait gave up.
+int plan_check_error(struct ::ps_plan* p);
 void plan_set_time(struct ::ps_plan* p, double t);
 // What the persistent ensemble launch (ps_persist.cu) needs of a member plan.
 struct PlanView {

@@ -546,6 +546,7 @@ bool plan_set_shape(ps_plan* p, int k, int var) {
   return true;
 }
 int plan_shape(const ps_plan* p, int k) { return (k >= 0 && k < 3) ? p->shape[k] : 0; }
+int plan_check_error(ps_plan* p) { return (int)check_device_error(p); }
 void plan_set_time(ps_plan* p, double t) { p->time = t; }
 PlanView plan_view(const ps_plan* p) {
   PlanView v{};
