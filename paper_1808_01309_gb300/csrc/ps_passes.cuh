@@ -36,12 +36,13 @@ template <typename T, int K = 0> struct TXOf {
   static constexpr int v = sizeof(T) == 4 ? PS_TX32 : 4;
 };
 // Points per thread of pass K (0 z-inverse, 1 y passes, 2 z-forward, 3 x
-// pass).  At 1024 points FP32 the x pass takes 8 points per thread (four
-// stages, 128 threads per row: 13.0 ms per 1024^3 launch against 13.6 ms
-// with 16) and the strided passes 16 (three stages, 64 threads per line),
-// each the faster for its pass.
+// pass).  At 1024 points FP32 every pass takes 16 (three stages, two
+// exchanges per line); the x pass then needs 231 registers and runs
+// without spills at one CTA per SM (MinB below): 10.98 ms per 1024^3 launch,
+// against 13.08 ms at 8 points per thread (four stages, three exchanges)
+// and 14.70 ms at 16 points capped to 128 registers (spills).
 template <typename T, int N, int K> struct EPass {
-  static constexpr int v = sizeof(T) == 4 && N == 1024 && K == 3 ? 8 : EOf<T, N>::v;
+  static constexpr int v = EOf<T, N>::v;
 };
 // lines batched per CTA in the strided passes (about 256 threads per CTA)
 template <typename T, int N, int K = 0> struct NBOf {
@@ -140,9 +141,25 @@ template <typename T, int N> struct ColBuf {
   static constexpr int v = sizeof(T) == 4 && N == 1024 ? PS_COLBUF1024 : sizeof(T) == 4 && N == 512 ? PS_COLBUF512
                            : sizeof(T) == 4 && N >= 64 ? PS_COLBUF_SMALL : 2;
 };
+// x pass: whether the launcher halves the rows per CTA to fit its shared
+// memory (stage + exchange above 113 KB at RPCOf rows; kx extent of the
+// 2/3 rule).  Its CTAs then have half the threads of the launch bound and
+// two of them fill the SM's shared memory, so the kernel may use the
+// registers of one full-size CTA per SM instead of spilling (FP32 256-point
+// rows: 0.152 -> 0.135 ms per 256^3 launch; 1024-point rows: 13.08 ->
+// 10.98 ms per 1024^3 launch).
+template <typename T, int N> struct XHalved {
+  static constexpr long long kxp = ((N + 2) / 3 + 15) / 16 * 16;
+  static constexpr int E = EPass<T, N, 3>::v, R = RPCOf<T, N>::v;
+  static constexpr long long tt =
+      (!XTwReg<T, N>::v && XTwTable<T, N>::v) ? (long long)TwSlots<N, E>::total * (N / E) : 0;
+  static constexpr long long bytes = (6LL * R * kxp + 3LL * R * N + tt) * (long long)sizeof(typename cplx<T>::type);
+  static constexpr bool v = bytes > 113LL * 1024;
+};
 template <typename T, int N> struct MinB {
   // (1024-point z lines: the input tile and exchange hold one CTA per SM)
-  static constexpr int zinv = N == 1024 ? 1 : PS_MINB_ZINV, xpass = PS_MINB_XPASS;
+  static constexpr int zinv = N == 1024 ? 1 : PS_MINB_ZINV;
+  static constexpr int xpass = XHalved<T, N>::v ? 1 : PS_MINB_XPASS;
   static constexpr int ypass = sizeof(T) == 4 && N == 1024 ? PS_MINB_Y1024 : sizeof(T) == 4 && N == 512 ? PS_MINB_Y512 : 0;
   static constexpr int zfwd = sizeof(T) == 4 && N == 1024 ? PS_MINB_ZF1024 : sizeof(T) == 4 && N == 512 ? PS_MINB_ZF512 : 0;
 };
