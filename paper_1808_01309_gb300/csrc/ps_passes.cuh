@@ -445,13 +445,14 @@ __global__ void __launch_bounds__(ColShape<T, N, 1, VAR>::NTH, MinB<T, N>::ypass
 // row.  `gathered` runs once every thread holds its points (the TMA kernel
 // refills its stage there).  COH: st is global memory written earlier in the
 // same launch (coherent loads).
-template <typename T, int N, int NG, int NSC, bool COH, class TW, class AfterGather>
+// XE: points per thread (the x pass's schedule unless a caller picks another).
+template <typename T, int N, int NG, int NSC, bool COH, class TW, class AfterGather, int XE = EPass<T, N, 3>::v>
 __device__ __forceinline__ void xpass_row(const PassArgs& a, const long long row, const bool rvalid, const int j0,
                                           const typename cplx<T>::type* st, const long long fst, const TW& tw,
                                           LinesExchange<typename cplx<T>::type, 1>& ex, T& umax2,
                                           AfterGather&& gathered) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 3>::v;
+  constexpr int E = XE;
   constexpr int NLI = 3 * NG + 2 * NSC;  // inverse packed lines
   constexpr bool HD = NG == 1 && NSC == 0;
   constexpr int NFW = NG == 2 ? 3 : 2;  // forward packed lines

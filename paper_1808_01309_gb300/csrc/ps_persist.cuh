@@ -81,10 +81,16 @@ __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
 
 // x pass on the ENS_THREADS / G consecutive rows of tile `tile`, reading its
 // input rows from global memory (written by the y-inverse pass of this launch).
+// FP32 128-point rows take 8 points per thread here (three stages): with 16
+// (two stages) this tile alone made the whole kernel spill at its 128
+// registers.
+template <typename T, int N> struct EnsXE {
+  static constexpr int v = sizeof(T) == 4 && N == 128 ? 8 : EPass<T, N, 3>::v;
+};
 template <typename T, int N>
 __device__ __forceinline__ void ens_xpass_tile(const PassArgs& a, const int tile) {
   using V = typename cplx<T>::type;
-  constexpr int E = EPass<T, N, 3>::v, G = N / E, RPC = ENS_THREADS / G;
+  constexpr int E = EnsXE<T, N>::v, G = N / E, RPC = ENS_THREADS / G;
   static_assert(G < 32, "rows of one tile share warps (warp-synchronous exchanges)");
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double red[32];
@@ -97,7 +103,9 @@ __device__ __forceinline__ void ens_xpass_tile(const PassArgs& a, const int tile
   const bool rvalid = row < rows;
   const V* B = static_cast<const V*>(a.b6) + (rvalid ? row : 0) * a.g.kxp;
   T umax2 = 0;
-  xpass_row<T, N, 1, 0, true>(a, row, rvalid, j0, B, rows * a.g.kxp, tw, ex, umax2, [] {});
+  auto none = [] {};
+  xpass_row<T, N, 1, 0, true, GlobalTw<V>, decltype(none)&, E>(a, row, rvalid, j0, B, rows * a.g.kxp, tw, ex, umax2,
+                                                                none);
   if (a.umax2) {
     const double t = block_max((double)umax2, red);
     if (tid == 0) atomicMax(a.umax2, (unsigned long long)__double_as_longlong(t));
@@ -232,7 +240,7 @@ EnsShape ens_shape_n(int kind, const Geo& g, int nfield) {
     s.ntiles = s.gx * s.gy * nfield;
     s.smem = (size_t)ColBuf<T, N>::v * NB * N * TX * sizeof(V);
   } else if (kind == EK_XPASS) {
-    constexpr int G = N / EPass<T, N, 3>::v, RPC = ENS_THREADS / G;
+    constexpr int G = N / EnsXE<T, N>::v, RPC = ENS_THREADS / G;
     const long long rows = (long long)g.nz * g.ny;
     s.ntiles = (int)((rows + RPC - 1) / RPC);
     s.gx = RPC;
