@@ -382,8 +382,19 @@ def experiment(n_dns=512, n_les=64, kc=21, nu=2e-3, dt_dns=1e-3, dt_les=5e-3, t_
             say(f"LES {name}: non-finite state")
         runs[name] = r
     les_ms = runs[next(iter(models))]["ms_per_step"]
-    out["dns"] = dict(ms_per_step=dns_ms, spectrum=np.mean(spec_dns, axis=0)[1:].tolist(), steps=per * n_eval,
-                      energy=e_dns, dissipation=eps_dns)
+    # sampling uncertainty of the DNS time mean per shell: the standard error
+    # of the mean of the n_eval samples, and the difference of the means of
+    # the two halves of the window (both relative to the mean)
+    sd = np.asarray(spec_dns)[:, 1:]
+    mean_d = sd.mean(axis=0)
+    stat = sd.std(axis=0, ddof=1) / np.sqrt(sd.shape[0]) / mean_d
+    half = np.abs(sd[: sd.shape[0] // 2].mean(axis=0) - sd[sd.shape[0] // 2:].mean(axis=0)) / mean_d
+    out["dns"] = dict(ms_per_step=dns_ms, spectrum=mean_d.tolist(), steps=per * n_eval,
+                      energy=e_dns, dissipation=eps_dns, stat_rel_err=stat.tolist(),
+                      max_stat_rel_err=float(stat.max()), half_window_rel_diff=half.tolist(),
+                      max_half_window_rel_diff=float(half.max()))
+    say(f"DNS time-mean spectrum: standard error up to {stat.max():.3f} (mean {stat.mean():.3f}), "
+        f"half-window difference up to {half.max():.3f}")
     out["les"] = runs
     out["cost_ratio"] = (dns_ms / dt_dns) / (les_ms / dt_les) if les_ms > 0 else None
     out["wall_seconds"] = time.perf_counter() - t_wall
