@@ -269,7 +269,10 @@ typedef struct ps_ensemble ps_ensemble;
  * The launch is captured in a CUDA graph with the reset of its counters.  It
  * needs members of one precision, the hydrodynamic system without a closure
  * and axis lengths in {32, 48, 64, 96, 128} (PS_ERR_UNSUPPORTED otherwise);
- * its bounded waits report through ps_ensemble_check.  PS_ENS_BATCHED:
+ * its bounded waits report through ps_ensemble_check; on 128-point x rows
+ * it takes 8 points per thread where the other modes take 16 (results agree
+ * to rounding there, bit for bit elsewhere at equal tile shapes).
+ * PS_ENS_BATCHED:
  * members of one grid class (same grid, box, precision, dealiasing and RK
  * order) share one launch per pass (tiles of all members in one grid; the x
  * pass loops over (member, row group) pairs), in sub-batches of at most 32
@@ -325,16 +328,18 @@ ps_status ps_ensemble_destroy(ps_ensemble* e);
 
 /* nsteps IF-RK steps of every member, in place on uhats[i] (device state of
  * member i, layout of its config), starting at time t.  Asynchronous on the
- * ensemble stream.  Results are identical in both modes. */
+ * ensemble stream.  The sequential, graph and batched modes give identical
+ * results at equal tile shapes (the persistent launch: see above). */
 ps_status ps_ensemble_rk_steps(ps_ensemble* e, void* const* uhats, double dt, double t, int nsteps,
                                ps_ens_mode mode);
 
 /* Autotuner: times, on device copies of uhats (left unchanged), for each
  * distinct grid the x-pass rows per CTA and the tile shape (columns per CTA,
  * radix schedule) of each column pass, then the number of concurrent graph
- * branches and the persistent launch's knobs; keeps the fastest and reports
- * them.  Allocates temporary copies
- * of the states.  Synchronises the ensemble stream. */
+ * branches, the persistent launch's knobs and the members per batched
+ * launch; keeps the fastest of each, sets the mode PS_ENS_AUTO runs and
+ * reports them.  Allocates temporary copies of the states.  Synchronises
+ * the ensemble stream. */
 ps_status ps_ensemble_tune(ps_ensemble* e, const void* const* uhats, double dt, ps_ens_tuning* out);
 
 /* Synchronises the ensemble stream and reports whether a bounded device wait
