@@ -884,7 +884,12 @@ def kernel_case(spec: str, reps: int) -> None:
     that grid (e.g. 512,512,128 for the x and y passes with 512-point lines,
     256,128,512 for the z passes); "les" runs `reps` 64^3 RK4 steps with the
     learned closure attached; "mlp" runs `reps` MLP forward evaluations of
-    64^3 samples."""
+    64^3 samples; "ensemble_persistent" / "ensemble_batched" run `reps`
+    one-step calls of a six-member FP32 ensemble (64^3, 96^3, 128^3, twice
+    each) in that mode; "aux" runs once each the kernels the other cases
+    miss (diagnostics, a host-buffer step and a small right-hand side
+    without a plan, MLP gradient and Adam step, LES training sample, filter
+    and closure gradients)."""
     import numpy as np
     import torch
 
@@ -892,6 +897,54 @@ def kernel_case(spec: str, reps: int) -> None:
     __graft_entry__.build()
     from paper_1808_01309_gb300 import inputs, les, ps
     parts = spec.split(",")
+    if parts[0] in ("ensemble_persistent", "ensemble_batched"):
+        sizes = [64, 96, 128, 64, 96, 128]
+        cfgs = [ps.make_config(n, prec=ps.Precision.FP32, nu=inputs.ensemble_viscosity(i), rk_order=4)
+                for i, n in enumerate(sizes)]
+        st = [torch.from_numpy(inputs.random_solenoidal_field(n, n, n, seed=1000 + i)).to("cuda", torch.complex64)
+              for i, n in enumerate(sizes)]
+        ens = ps.ps_ensemble_create(cfgs)
+        mode = ps.ENS_PERSISTENT if parts[0] == "ensemble_persistent" else ps.ENS_BATCHED
+        for _ in range(reps):
+            ps.ps_ensemble_rk_steps(ens, st, 1e-3, 0.0, 1, mode)
+        ps.ps_ensemble_check(ens)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": spec, "reps": reps, "u_norm": float(sum(torch.linalg.vector_norm(u) for u in st))}))
+        ps.ps_ensemble_destroy(ens)
+        return
+    if parts[0] == "aux":
+        c64 = torch.complex64
+        u = inputs.random_solenoidal_field(64, 64, 64, seed=1)
+        plan = ps.Plan(64, prec=ps.Precision.FP32, nu=2e-3, rk_order=4)
+        plan.diagnostics(torch.from_numpy(u).to("cuda", c64))
+        ps.ps_rk_step_host(plan.handle, torch.from_numpy(u.astype(np.complex64)).pin_memory(), 1e-3)
+        plan.close()
+        u32 = torch.from_numpy(inputs.random_solenoidal_field(32, 32, 32, seed=2)).to("cuda", c64)
+        ps.ps_rhs_noalloc(ps.make_config(32, prec=ps.Precision.FP32, nu=2e-3), u32, torch.empty_like(u32))
+        params = torch.from_numpy(les.init_params(1)).to("cuda")
+        B = 1 << 16
+        X, T = torch.randn((B, 5), device="cuda"), torch.randn((B, 6), device="cuda")
+        G = torch.empty(ps.MLP_NPARAM, device="cuda")
+        L = torch.empty(1, device="cuda", dtype=torch.float64)
+        ps.ps_mlp_grad(params, X, T, B, G, L)
+        ps.ps_mlp_adam(params, G, torch.zeros_like(params), torch.zeros_like(params), 1, 1e-3)
+        ud64 = torch.from_numpy(inputs.random_solenoidal_field(64, 64, 64, seed=13)).to("cuda", c64)
+        Xs, As, Ts = (torch.empty((32 ** 3, k), device="cuda") for k in (5, 9, 6))
+        ps.ps_les_training_sample(64, ud64, 32, 10, None, Xs, As, Ts)
+        ubar = torch.empty((3, 32, 32, 17), device="cuda", dtype=c64)
+        ps.ps_les_filter(64, ud64, 32, 10, ubar)
+        norm = {"mean": Xs.mean(0).double().tolist(), "std": Xs.std(0).double().tolist(), "s_tau": 0.05,
+                "s_A": float(As.square().sum(1).mean().sqrt())}
+        plan = ps.Plan(32, prec=ps.Precision.FP32, nu=1e-3)
+        plan.set_closure(params, norm)
+        force = torch.from_numpy(inputs.forcing_field(32, 32, 32, seed=3)).to("cuda", c64)
+        plan.closure_grad(params, ubar, force, G, L)
+        plan.closure_grad_transfer(params, ubar, np.zeros(16), G, L)
+        plan.rk_step(ubar, 1e-3)
+        plan.close()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": spec, "loss": float(L.item())}))
+        return
     if parts[0] == "mlp":
         P = 64 ** 3
         params = torch.from_numpy(les.init_params(1)).to("cuda")
