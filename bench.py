@@ -145,6 +145,46 @@ def ncu_traffic(kind: str, n: int):
     return None
 
 
+def ncu_smem_wavefronts(kind: str, n: int):
+    """Shared-memory wavefronts per launch of `kind` at n^3 FP32 from a
+    committed ncu summary under profiles/ (a line "smem <kind> n=<n> fp32
+    src=<hash> wavefronts_per_launch=<W>"), or None if absent or taken on
+    other kernel sources."""
+    want = source_hash(KIND_FILES[kind])
+    pat = re.compile(r"^smem\s+(\S+)\s+n=(\d+)\s+fp32\s+src=(\w+)\s+wavefronts_per_launch=([0-9.eE+]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = pat.match(line.strip())
+            if m and m.group(1) == kind and int(m.group(2)) == n and m.group(3) == want:
+                return float(m.group(4))
+    return None
+
+
+SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth of one SM: one 128-byte wavefront per clock
+
+
+def onchip_roofline(kind: str, n: int, avg_ms: float):
+    """The dominant kernel against its shared-memory bandwidth: ncu wavefronts
+    per launch x 128 B over the launch's CUDA-event time, against 128 B per
+    clock per SM at the maximum SM clock (nominal, from the unit counts)."""
+    wf = ncu_smem_wavefronts(kind, n)
+    if wf is None:
+        return None
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    peak = SMEM_BYTES_PER_CLK * nsm * mhz * 1e6 / 1e9  # GB/s
+    achieved = wf * SMEM_BYTES_PER_CLK / (avg_ms * 1e-3) / 1e9
+    return {"bound": "shared memory", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "wavefronts_per_launch": wf,
+            "peak_source": f"nominal: {SMEM_BYTES_PER_CLK} B/clk/SM x {nsm} SMs x {mhz:.0f} MHz",
+            "source": "ncu l1tex__data_pipe_lsu_wavefronts_mem_shared.sum of a committed capture (profiles/)"}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -429,7 +469,8 @@ def run_ours(args, world, rank, local):
             "dense": dense[dom], "dense_achieved": dense[dom] / (avg_ms * 1e-3) / 1e9, "step_dense": step_dense,
             "kernel_ms": kernel_ms, "kernel_share": kernel_share, "kernel_gbs": kernel_gbs,
             "kernel_frac": kernel_frac, "step_bytes": step_bytes, "split_ms_per_step": ms_split / ksplit,
-            "split_steps": ksplit, "traffic": ncu_traffic(dom, n), "hbm": hbm, "peak_src": peak_src}
+            "split_steps": ksplit, "traffic": ncu_traffic(dom, n), "hbm": hbm, "peak_src": peak_src,
+            "onchip": onchip_roofline(dom, n, avg_ms)}
 
     # ---- end to end: host buffers through the C ABI -------------------------
     e2e = None
@@ -1035,6 +1076,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": r["dom"], "achieved": round(r["achieved"], 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(r["achieved"] / hbm, 4),
                      "traffic": r["traffic"],
+                     "onchip": r["onchip"],
                      "algorithmic_bytes": r["alg"],
                      "bytes_model": "compulsory bytes of the pruned passes: each pass reads its input and writes "
                                     "its output once, retained modes and lines only (bench.algorithmic_bytes)",
