@@ -125,3 +125,13 @@ def test_reference_arm_reports_our_config():
     assert line["impl"] == "reference" and line["config"] == bench.config_of(32, 1)
     assert line["cpu_baseline"]["cores"] >= 1 and line["value"] > 0
     assert abs(line["steps"] * line["ms_per_step"] - 1e3 * 32 ** 3 / line["value"] / 1e9) < 1.0
+
+
+def test_committed_profiles_match_the_current_kernel_sources():
+    """The bench line's `traffic` and `onchip` figures come from committed ncu
+    summaries keyed by a hash of the kernel sources: a kernel change without a
+    new capture would silently drop them, so the current sources must have
+    both lines."""
+    import bench
+    assert bench.ncu_traffic("x_fused", 512) is not None
+    assert bench.ncu_smem_wavefronts("x_fused", 512) is not None
