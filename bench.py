@@ -57,7 +57,6 @@ KIND_FILES = {
 }
 CPU_N = 256       # grid of the oracle's CPU-baseline sample (one RHS: ~15-20 s)
 REF_N = 128       # grid of the reference arm's per-step sample (one RHS: ~2 s)
-ORACLE_ERR_N = 256  # grid of the per-output FP32 error table against the oracle
 
 
 def parse_args():
@@ -418,12 +417,9 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     from paper_1808_01309_gb300 import ps
 
-    # the oracle's 256^3 reference for the FP32 error table runs on the host
-    # cores while the GPU legs run (it is not timed)
-    ref_job, ref_dir = None, None
-    if rank == 0 and world == 1 and not args.no_oracle_table:
-        ref_dir = tempfile.mkdtemp(prefix="ps_oracle_")
-        ref_job = start_oracle_job({"kind": "reference_table", "n": ORACLE_ERR_N, "dir": ref_dir}, None)
+    # the FP32 error table against the oracle: the GPU side here, the oracle
+    # side in the cpu_baseline leg (the oracle runs nowhere else)
+    want_table = rank == 0 and world == 1 and not args.no_oracle_table and not args.no_cpu_baseline
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -607,8 +603,8 @@ def run_ours(args, world, rank, local):
     if args.fp32_error_steps > 0:
         err = fp32_error_per_step(args.fp32_error_steps, dev, stream)
 
-    # ---- FP32 outputs at 256^3 for the table against the oracle ---------------
-    gpu_table = fp32_outputs(ORACLE_ERR_N, dev, stream) if ref_job is not None else None
+    # ---- FP32 outputs on the cpu_baseline grid for the table against the oracle
+    gpu_table = fp32_outputs(min(n, CPU_N), dev, stream) if want_table else None
 
     ens = None
     if not args.no_ensemble:
@@ -617,15 +613,7 @@ def run_ours(args, world, rank, local):
 
     les = run_les_cost(args, dev, stream, ms_step) if args.les_steps > 0 else None
 
-    table = None
-    if ref_job is not None:
-        finish_oracle_job(ref_job)
-        table = fp32_error_table(gpu_table, ref_dir)
-        for name in os.listdir(ref_dir):
-            os.remove(os.path.join(ref_dir, name))
-        os.rmdir(ref_dir)
-
-    out.update(mhd=mhd, bq=bq, err=err, ens=ens, table=table, les=les, ms_step=ms_step, launches=launches,
+    out.update(mhd=mhd, bq=bq, err=err, ens=ens, gpu_table=gpu_table, les=les, ms_step=ms_step, launches=launches,
                clocks=clk.summary(), roof=roof, e2e=e2e, fp64=fp64, energy=e_step, max_u=umax_step)
     return out
 
@@ -711,10 +699,11 @@ def _diag_errors(g, r):
     return out
 
 
-def fp32_error_table(g, ref_dir):
+def fp32_error_table(g, ref_dir, n):
     """Per-output error of the FP32 CUDA path against the FP64 oracle on the
-    forced 256^3 workload (right-hand side, state after one RK4 step,
-    diagnostics of the initial and the stepped state)."""
+    forced n^3 workload (right-hand side, state after one RK4 step,
+    diagnostics of the initial and the stepped state); the oracle side comes
+    from the cpu_baseline leg's run."""
     import numpy as np
     ref = np.load(os.path.join(ref_dir, "table.npz"))
     with open(os.path.join(ref_dir, "diag.json")) as fh:
@@ -725,8 +714,8 @@ def fp32_error_table(g, ref_dir):
         return {"rel_l2": float(f"{np.linalg.norm(d) / np.linalg.norm(b):.3e}"),
                 "max_mode_rel": float(f"{np.max(np.abs(d)) / np.max(np.abs(b)):.3e}")}
 
-    return {"workload": f"forced {ORACLE_ERR_N}^3 (seeded field + forcing, nu = 2e-3, dt = 1e-3), FP32 CUDA path "
-                        "against the FP64 oracle",
+    return {"workload": f"forced {n}^3 (seeded field + forcing, nu = 2e-3, dt = 1e-3), FP32 CUDA path "
+                        "against the FP64 oracle (oracle side from the cpu_baseline leg's run)",
             "rhs": field(g["rhs"], ref["rhs"]), "state_after_rk4_step": field(g["u1"], ref["u1"]),
             "diagnostics_initial": _diag_errors(g["d0"], rd["d0"]),
             "diagnostics_after_step": _diag_errors(g["d1"], rd["d1"]),
@@ -830,11 +819,11 @@ def run_les_cost(args, dev, stream, ms_dns):
 # ---------------------------------------------------------------------------
 
 def oracle_job(job: dict) -> dict:
-    """Work of one oracle child process (see start_oracle_job):
-      rhs_time        : times one oracle RHS of the forced n^3 workload
-      reference_table : the oracle's RHS, one IF-RK4 step and the diagnostics
-                        of both states of the forced n^3 workload, written to
-                        job["dir"] for the FP32 error table."""
+    """Work of one oracle child process of the cpu_baseline leg (see
+    start_oracle_job): times one oracle RHS of the forced n^3 workload; with
+    job["table_dir"] it then (untimed) also takes one IF-RK4 step and the
+    diagnostics of both states and writes them with that RHS to the
+    directory, the oracle side of the FP32 error table."""
     import numpy as np
 
     import oracle
@@ -843,33 +832,37 @@ def oracle_job(job: dict) -> dict:
     w = workloads.forced(n)
     u, f = w.initial_state(), w.forcing()
     cfg = oracle.Config(n, n, n, nu=w.nu, rk_order=4)
-    if job["kind"] == "rhs_time":
-        t0 = time.perf_counter()
-        oracle.rhs(u, cfg, forcing=f)
-        return {"seconds": time.perf_counter() - t0, "n": n}
-    if job["kind"] == "reference_table":
-        rhs = oracle.rhs(u, cfg, forcing=f)
+    if job["kind"] != "rhs_time":
+        raise ValueError(f"unknown oracle job {job['kind']!r}")
+    t0 = time.perf_counter()
+    rhs = oracle.rhs(u, cfg, forcing=f)
+    secs = time.perf_counter() - t0
+    if job.get("table_dir"):
         u1 = oracle.rk_step(u, w.dt, cfg, forcing=f)
         d0, d1 = oracle.diagnostics(u, cfg), oracle.diagnostics(u1, cfg)
-        np.savez(os.path.join(job["dir"], "table.npz"), rhs=rhs, u1=u1)
+        np.savez(os.path.join(job["table_dir"], "table.npz"), rhs=rhs, u1=u1)
         js = {k: {kk: (vv.tolist() if hasattr(vv, "tolist") else vv) for kk, vv in d.items()}
               for k, d in (("d0", d0), ("d1", d1))}
-        with open(os.path.join(job["dir"], "diag.json"), "w") as fh:
+        with open(os.path.join(job["table_dir"], "diag.json"), "w") as fh:
             json.dump(js, fh)
-        return {"ok": True}
-    raise ValueError(f"unknown oracle job {job['kind']!r}")
+    return {"seconds": secs, "n": n}
 
 
 def cpu_cores() -> int:
     return os.cpu_count() or 1
 
 
-def cpu_baseline_rows(n: int):
+def cpu_baseline_rows(n: int, table_dir=None):
     """One oracle RHS of the forced n^3 workload timed in a child process with
-    one BLAS thread and with all cores; Gpoints/s per grid point."""
+    one BLAS thread and with all cores; Gpoints/s per grid point.  With
+    table_dir the all-cores run also writes the oracle side of the FP32 error
+    table there."""
     rows = {}
     for name, threads in (("single_core", 1), ("all_cores", None)):
-        r = finish_oracle_job(start_oracle_job({"kind": "rhs_time", "n": n}, threads))
+        job = {"kind": "rhs_time", "n": n}
+        if threads is None and table_dir:
+            job["table_dir"] = table_dir
+        r = finish_oracle_job(start_oracle_job(job, threads))
         rows[name] = {"value": round(n ** 3 / r["seconds"] / 1e9, 6), "unit": UNIT, "seconds": round(r["seconds"], 2),
                       "cores": 1 if threads == 1 else cpu_cores()}
     return rows
@@ -1057,9 +1050,16 @@ def main():
     if rank != 0:
         return
     cpu = None
+    table = None
     if not args.no_cpu_baseline and world == 1:
         nc = min(n, CPU_N)
-        rows = cpu_baseline_rows(nc)
+        table_dir = tempfile.mkdtemp(prefix="ps_oracle_") if res["gpu_table"] is not None else None
+        rows = cpu_baseline_rows(nc, table_dir)
+        if table_dir:
+            table = fp32_error_table(res["gpu_table"], table_dir, nc)
+            for name in os.listdir(table_dir):
+                os.remove(os.path.join(table_dir, name))
+            os.rmdir(table_dir)
         a = rows["all_cores"]
         cpu = {"value": a["value"], "unit": UNIT, "cores": a["cores"], "kind": "oracle",
                "sample": cpu_sample_desc(nc, n, a["seconds"], a["cores"]),
@@ -1099,7 +1099,7 @@ def main():
         "fp64": res["fp64"],
         "mhd": res["mhd"],
         "boussinesq": res["bq"],
-        "fp32_vs_oracle_256": res["table"],
+        "fp32_vs_oracle_256": table,
         "fp32_error_256": res["err"],
         "ensemble": res["ens"],
         "les": res["les"],

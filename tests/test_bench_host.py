@@ -113,6 +113,26 @@ def test_oracle_child_job_times_one_rhs():
     assert r["n"] == 16 and r["seconds"] > 0
 
 
+def test_cpu_baseline_job_writes_the_oracle_side_of_the_error_table(tmp_path):
+    """The FP32 error table's oracle side comes from the cpu_baseline leg's
+    all-cores run; a CUDA side equal to it up to FP32 rounding gives errors at
+    the FP32 level, one rounded to other values larger ones."""
+    import numpy as np
+    r = bench.finish_oracle_job(bench.start_oracle_job({"kind": "rhs_time", "n": 16, "table_dir": str(tmp_path)},
+                                                       None), timeout=300)
+    assert r["n"] == 16 and (tmp_path / "table.npz").exists() and (tmp_path / "diag.json").exists()
+    ref = np.load(tmp_path / "table.npz")
+    import json
+    rd = json.loads((tmp_path / "diag.json").read_text())
+    g = {"rhs": ref["rhs"].astype(np.complex64).astype(np.complex128),
+         "u1": ref["u1"].astype(np.complex64).astype(np.complex128), "d0": rd["d0"], "d1": rd["d1"]}
+    t = bench.fp32_error_table(g, str(tmp_path), 16)
+    assert 0 < t["rhs"]["rel_l2"] < 1e-6 and 0 < t["state_after_rk4_step"]["rel_l2"] < 1e-6
+    assert t["diagnostics_initial"]["energy"] == 0.0
+    g["rhs"] = g["rhs"] * (1 + 1e-3)
+    assert abs(bench.fp32_error_table(g, str(tmp_path), 16)["rhs"]["rel_l2"] - 1e-3) < 1e-5
+
+
 def test_reference_arm_reports_our_config():
     """The reference arm runs the oracle as it stands on a bounded sample and
     reports it under the same config as the GPU arm."""
