@@ -67,11 +67,11 @@ extern "C" {
 typedef enum {
   PS_OK = 0,
   PS_ERR_INVALID_ARG = 1,  /* bad pointer, size, aliasing or config value */
-  PS_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  PS_ERR_UNSUPPORTED = 2,  /* valid request this library does not implement */
   PS_ERR_OOM = 3,          /* device allocation failed */
   PS_ERR_CUDA = 4,         /* CUDA runtime or launch error */
   PS_ERR_NONFINITE = 5,    /* a diagnostic came out NaN or infinite */
-  PS_ERR_TIMEOUT = 6       /* reserved for bounded device-side waits */
+  PS_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
 } ps_status;
 
 typedef enum { PS_FP32 = 0, PS_FP64 = 1 } ps_precision;
