@@ -71,6 +71,20 @@ def test_clock_summary_parses_nvidia_smi_lines():
     assert s["sm_mhz"] == 1972.5 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
 
 
+def test_clock_records_that_force_a_second_measurement():
+    ok = {"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    # the power cap is kept (noted), even with the clock pulled down
+    assert not bench.clocks_rejected({"sm_mhz": 1500, "sm_max_mhz": 2070, "reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected({**ok, "reasons": [r]})
+    # well below the maximum with no reason: a leftover clock lock
+    assert bench.clocks_rejected({"sm_mhz": 1400, "sm_max_mhz": 2070, "reasons": []})
+    assert not bench.clocks_rejected({"sm_mhz": 1900, "sm_max_mhz": 2070, "reasons": []})
+    # no samples: nothing to reject on
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
+
+
 def test_roofline_model_bytes_add_up_to_the_step_model():
     """Per-launch model bytes of the five passes (42 S per RHS plus the RK
     updates) sum to the 198 S of one IF-RK4 step; the pruned compulsory bytes
