@@ -18,6 +18,7 @@
 #include "ps_kernels.h"
 #include "ps_batch.cuh"
 #include "ps_persist.cuh"
+#include "ps_worklist.h"
 
 namespace ps {
 void set_last_error(const std::string& msg);
@@ -214,6 +215,51 @@ ps_status persist_build(ps_ensemble* e, void* const* u, double dt, int nsteps) {
   }
   if (!e->d_err) ENS_CU(cudaMalloc(&e->d_err, sizeof(int)), "error word");
   for (auto& a : args) a.err = e->d_err;
+  // each member's pass sequence: per step and stage z-inverse, (energy sum,)
+  // y-inverse, x, y-forward, z-forward, update
+  std::vector<std::vector<EnsPass>> mp(m);  // without ticket and dependency
+  std::vector<std::vector<WlItem>> seq(m);
+  const int kinds[] = {EK_ZINV, EK_SUM, EK_YINV, EK_XPASS, EK_YFWD, EK_ZFWD, EK_UPDATE};
+  size_t smem = 0;
+  for (size_t i = 0; i < m; ++i) {
+    const PlanView v = plan_view(e->plans[i]);
+    const Geo& g = v.g;
+    for (int s = 0; s < nsteps; ++s)
+      for (int st = 0; st < nst[i]; ++st)
+        for (int kind : kinds) {
+          const bool stats = s == nsteps - 1 && st == 0;
+          if (kind == EK_SUM && !stats) continue;
+          EnsPass P{};
+          P.args = base[i] + (stats ? nst[i] : st);
+          P.kind = kind;
+          P.per = e->per[kind] > 0 ? e->per[kind] : 1;
+          EnsShape sh;
+          if (kind == EK_UPDATE) {
+            P.full = (st == nst[i] - 1) ? 1 : 0;
+            const long long n = P.full ? (long long)g.nz * g.ny * g.nh : (long long)g.cz * g.cy * g.cx;
+            sh.ntiles = (int)((n + ENS_UPDATE_MODES - 1) / ENS_UPDATE_MODES);
+          } else if (kind == EK_SUM) {
+            sh.ntiles = 1;
+            sh.gx = v.n_epart;
+            P.sum_out = v.stats;
+            P.per = 1;
+          } else {
+            const int n = kind == EK_XPASS ? g.nx : (kind == EK_YINV || kind == EK_YFWD) ? g.ny : g.nz;
+            const int nf = kind == EK_YINV ? 6 : 3;
+            sh = f32 ? ens_shape<float>(kind, n, g, nf) : ens_shape<double>(kind, n, g, nf);
+            P.n = n;
+          }
+          if (sh.ntiles <= 0) return bad(PS_ERR_UNSUPPORTED, "ensemble: persistent mode: no tiles for a pass");
+          P.ntiles = sh.ntiles;
+          P.gx = sh.gx;
+          P.gy = sh.gy;
+          smem = std::max(smem, sh.smem);
+          mp[i].push_back(P);
+          seq[i].push_back(WlItem{P.ntiles, P.per, kind != EK_SUM});
+        }
+  }
+  // member order: as created, or largest grid first (orders 1 and 2); order 2
+  // also staggers the members' sequences (ps_worklist.h)
   std::vector<int> ord(m);
   std::iota(ord.begin(), ord.end(), 0);
   if (e->order >= 1)
@@ -221,75 +267,17 @@ ps_status persist_build(ps_ensemble* e, void* const* u, double dt, int nsteps) {
       const Geo ga = plan_view(e->plans[a]).g, gb = plan_view(e->plans[b]).g;
       return (long long)ga.nx * ga.ny * ga.nz > (long long)gb.nx * gb.ny * gb.nz;
     });
-  // each member's pass sequence: per step and stage z-inverse, (energy sum,)
-  // y-inverse, x, y-forward, z-forward, update
-  struct Item {
-    int st, kind;
-    bool stats;
-  };
-  std::vector<std::vector<Item>> seq(m);
-  const int kinds[] = {EK_ZINV, EK_SUM, EK_YINV, EK_XPASS, EK_YFWD, EK_ZFWD, EK_UPDATE};
-  for (size_t i = 0; i < m; ++i)
-    for (int s = 0; s < nsteps; ++s)
-      for (int st = 0; st < nst[i]; ++st)
-        for (int kind : kinds) {
-          const bool stats = s == nsteps - 1 && st == 0;
-          if (kind == EK_SUM && !stats) continue;
-          seq[i].push_back(Item{st, kind, stats});
-        }
-  // global order: level by level, member k (in `ord`) contributing its item
-  // level - skew_k; skew 0 for every member lists all members' same pass
-  // together, order 2 staggers the members over the six passes of a stage so
-  // that memory-bound and arithmetic-bound tiles run side by side
-  std::vector<int> skew(m, 0);
-  if (e->order == 2)
-    for (size_t k = 0; k < m; ++k) skew[ord[k]] = (int)(k % 6);
-  size_t longest = 0;
-  for (size_t i = 0; i < m; ++i) longest = std::max(longest, seq[i].size() + skew[i]);
+  std::vector<WlSlot> slots;
+  const long long tick = wl_schedule(seq, ord, wl_skew(ord, e->order), &slots);
   std::vector<EnsPass> passes;
-  std::vector<int> last(m, -1);
-  size_t smem = 0;
-  long long tick = 0;
-  for (size_t lev = 0; lev < longest; ++lev)
-    for (int i : ord) {
-      const long long idx = (long long)lev - skew[i];
-      if (idx < 0 || idx >= (long long)seq[i].size()) continue;
-      const int st = seq[i][idx].st, kind = seq[i][idx].kind;
-      const bool stats = seq[i][idx].stats;
-      const PlanView v = plan_view(e->plans[i]);
-      const Geo& g = v.g;
-      EnsPass P{};
-      P.args = base[i] + (stats ? nst[i] : st);
-      P.kind = kind;
-      P.dep = last[i];
-      P.need = last[i] >= 0 ? passes[last[i]].ntiles : 0;
-      P.per = e->per[kind] > 0 ? e->per[kind] : 1;
-      EnsShape sh;
-      if (kind == EK_UPDATE) {
-        P.full = (st == nst[i] - 1) ? 1 : 0;
-        const long long n = P.full ? (long long)g.nz * g.ny * g.nh : (long long)g.cz * g.cy * g.cx;
-        sh.ntiles = (int)((n + ENS_UPDATE_MODES - 1) / ENS_UPDATE_MODES);
-      } else if (kind == EK_SUM) {
-        sh.ntiles = 1;
-        sh.gx = v.n_epart;
-        P.sum_out = v.stats;
-        P.per = 1;
-      } else {
-        const int n = kind == EK_XPASS ? g.nx : (kind == EK_YINV || kind == EK_YFWD) ? g.ny : g.nz;
-        const int nf = kind == EK_YINV ? 6 : 3;
-        sh = f32 ? ens_shape<float>(kind, n, g, nf) : ens_shape<double>(kind, n, g, nf);
-        P.n = n;
-      }
-      if (sh.ntiles <= 0) return bad(PS_ERR_UNSUPPORTED, "ensemble: persistent mode: no tiles for a pass");
-      P.ntiles = sh.ntiles;
-      P.gx = sh.gx;
-      P.gy = sh.gy;
-      P.tick0 = tick;
-      tick += (P.ntiles + P.per - 1) / P.per;
-      smem = std::max(smem, sh.smem);
-      if (kind != EK_SUM) last[i] = (int)passes.size();
-      passes.push_back(P);
-    }
+  passes.reserve(slots.size());
+  for (const WlSlot& sl : slots) {
+    EnsPass P = mp[sl.member][sl.item];
+    P.tick0 = sl.tick0;
+    P.dep = sl.dep;
+    P.need = sl.need;
+    passes.push_back(P);
+  }
   if (e->wait_test) {
     // test hook: the first pass that waits for another waits for one tile too many
     for (auto& P : passes)
@@ -422,17 +410,20 @@ ps_status batch_capture(ps_ensemble* e, void* const* u, double dt, int nsteps) {
   const std::string why = batch_unsupported(e);
   if (!why.empty()) return bad(PS_ERR_UNSUPPORTED, "ensemble: batched mode: " + why);
   const size_t m = e->plans.size();
-  std::vector<bool> done(m, false);
+  // class id of each member: the first member of the same class
+  std::vector<int> cls(m);
   for (size_t i = 0; i < m; ++i) {
-    if (done[i]) continue;
-    ps_ensemble::BatchClass c;
-    const int cap = std::max(1, std::min(e->bsize, BATCH_MAX));
-    for (size_t j = i; j < m && (int)c.members.size() < cap; ++j)
-      if (!done[j] && same_class(e->cfgs[i], e->cfgs[j])) {
-        c.members.push_back((int)j);
-        done[j] = true;
+    cls[i] = (int)i;
+    for (size_t j = 0; j < i; ++j)
+      if (same_class(e->cfgs[j], e->cfgs[i])) {
+        cls[i] = (int)j;
+        break;
       }
-    c.nst = plan_view(e->plans[i]).rk_stages;
+  }
+  for (const std::vector<int>& group : wl_batches(cls, std::min(e->bsize, BATCH_MAX))) {
+    ps_ensemble::BatchClass c;
+    c.members = group;
+    c.nst = plan_view(e->plans[group[0]]).rk_stages;
     const int M = (int)c.members.size();
     c.args.resize((size_t)c.nst * M);
     std::vector<double*> sums(M);
