@@ -118,3 +118,47 @@ def test_mhd_diagnostics_closed_forms():
     assert abs(d["magnetic_helicity"] - 3.0) < 1e-14
     # u = B Beltrami: all nonlinear terms vanish
     assert np.max(np.abs(oracle.mhd_rhs(ub, cfg))) < 1e-14
+
+
+def _beltrami(n, k):
+    """ABC field of wavenumber k (unit coefficients): curl = k times the field."""
+    return inputs.trig_field(n, n, n, [
+        (0, 1.0, ("1", 0), ("1", 0), ("s", k)), (0, 1.0, ("1", 0), ("c", k), ("1", 0)),
+        (1, 1.0, ("s", k), ("1", 0), ("1", 0)), (1, 1.0, ("1", 0), ("1", 0), ("c", k)),
+        (2, 1.0, ("1", 0), ("s", k), ("1", 0)), (2, 1.0, ("c", k), ("1", 0), ("1", 0))])
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_parallel_beltrami_fields_decay_exactly(order):
+    """u and B multiples of one Beltrami field of |k| = 2: u x omega, j x B and
+    u x B vanish, so u decays as exp(-nu |k|^2 t) and B as exp(-eta |k|^2 t)
+    with no coupling, and a Lawson step is exact at any dt.  nu != eta tells
+    the two rates apart."""
+    n, nu, eta, dt = 16, 0.05, 0.02, 0.1
+    cfg = Config(n, n, n, nu=nu, eta=eta, rk_order=order)
+    f = _beltrami(n, 2)
+    assert np.max(np.abs(oracle.curl_hat(f, cfg) - 2.0 * f)) < 1e-14
+    ub = np.concatenate([f, 0.5 * f])
+    r = oracle.mhd_rhs(ub, cfg)
+    assert np.max(np.abs(r - np.concatenate([-4.0 * nu * f, -4.0 * eta * 0.5 * f]))) < 1e-15
+    v = ub
+    for _ in range(5):
+        v = oracle.mhd_rk_step(v, dt, cfg)
+    T = 5 * dt
+    assert np.max(np.abs(v[:3] - f * math.exp(-4.0 * nu * T))) < 1e-15
+    assert np.max(np.abs(v[3:] - 0.5 * f * math.exp(-4.0 * eta * T))) < 1e-15
+
+
+def test_magnetic_helicity_of_a_wavenumber_two_field():
+    """B a Beltrami field of |k| = 2: the Coulomb-gauge potential
+    A = i k x B / |k|^2 is B/2, so the magnetic helicity sum w Re(A* . B)
+    equals the magnetic energy 1/2 sum w |B|^2 = 1.5; with u = B/3 the cross
+    helicity is 1/3 sum w |B|^2 = 1 and the kinetic energy 1.5/9."""
+    n = 16
+    cfg = Config(n, n, n)
+    f = _beltrami(n, 2)
+    d = oracle.mhd_diagnostics(np.concatenate([f / 3.0, f]), cfg)
+    assert abs(d["magnetic_energy"] - 1.5) < 1e-14
+    assert abs(d["magnetic_helicity"] - 1.5) < 1e-14
+    assert abs(d["cross_helicity"] - 1.0) < 1e-14
+    assert abs(d["energy"] - 1.5 / 9.0) < 1e-14

@@ -1,12 +1,13 @@
 """Planted mistakes: each plausible error in the oracle must fail a pin.
 
 Every case below replaces one function of the oracle (oracle/fft.py,
-oracle/spectral.py, oracle/les.py) by a copy with one mistake planted (a
+oracle/spectral.py, oracle/les.py, including the MHD system) by a copy with one mistake planted (a
 flipped sign, a transposed index, a dropped term, a wrong coefficient) and
 runs the CPU pins of tests/test_oracle_*pins.py until one of them fails.  A
 case passes when some pin fails; a mistake that no pin notices fails the case.
 CPU only; nothing here touches the CUDA path."""
 
+import dataclasses
 import math
 
 import numpy as np
@@ -19,6 +20,7 @@ from oracle import spectral as sp
 
 from . import test_oracle_fft_pins as FP
 from . import test_oracle_les_pins as LP
+from . import test_oracle_mhd_pins as MP
 from . import test_oracle_pins as P
 
 
@@ -314,8 +316,114 @@ def test_planted_les_mistake_fails_a_pin(name, monkeypatch):
     assert some_pin_fails(LES_PINS) is not None, f"no pin notices: {name}"
 
 
+# ---------------------------------------------------------------------------
+# the MHD system (Eqs. uMHD, bMHD in oracle/spectral.py)
+# ---------------------------------------------------------------------------
+
+MHD_PINS = [
+    MP.test_mhd_tendency_matches_exact_advective_form,
+    MP.test_zero_magnetic_field_reduces_to_hydrodynamics,
+    MP.test_ideal_invariants_are_not_transferred,
+    lambda: MP.test_parallel_beltrami_fields_decay_exactly(4),
+    lambda: MP.test_parallel_beltrami_fields_decay_exactly(2),
+    MP.test_mhd_diagnostics_closed_forms,
+    MP.test_magnetic_helicity_of_a_wavenumber_two_field,
+]
+
+
+def _mhd_fields(ub, cfg):
+    D = sp.dealias_mask(cfg)
+    u_hat, b_hat = ub[:3] * D, ub[3:] * D
+    return (D, sp.inverse(u_hat, cfg), sp.inverse(sp.curl_hat(u_hat, cfg), cfg), sp.inverse(b_hat, cfg),
+            sp.inverse(sp.curl_hat(b_hat, cfg), cfg))
+
+
+def _mhd_nonlinear_with_mistake(kind):
+    def f(ub, cfg):
+        D, u, om, b, j = _mhd_fields(ub, cfg)
+        lorentz = np.cross(j, b, axis=0)
+        emf = np.cross(u, b, axis=0)
+        if kind == "lorentz sign":
+            lorentz = -lorentz
+        elif kind == "lorentz dropped":
+            lorentz = 0.0 * lorentz
+        elif kind == "induction sign":
+            emf = -emf
+        elif kind == "induction field":
+            emf = np.cross(u, j, axis=0)  # current in place of the field
+        return sp.forward(np.cross(u, om, axis=0) + lorentz) * D, sp.curl_hat(sp.forward(emf), cfg) * D
+
+    return f
+
+
+_orig_mhd_nonviscous = sp._mhd_nonviscous
+_orig_mhd_rk_step = sp.mhd_rk_step
+_orig_mhd_rhs = sp.mhd_rhs
+
+
+def _mhd_nonviscous_lorentz_unprojected(ub, cfg, forcing, nonlinear_on=True):
+    if not nonlinear_on:
+        return _orig_mhd_nonviscous(ub, cfg, forcing, nonlinear_on)
+    D, u, om, b, j = _mhd_fields(ub, cfg)
+    f = sp._forcing_or_zero(forcing, cfg, ub[:3])
+    n_u = sp.project(sp.forward(np.cross(u, om, axis=0)) * D + f, cfg) * D
+    n_u = n_u + sp.forward(np.cross(j, b, axis=0)) * D  # the Lorentz force skips the projection
+    n_b = sp.curl_hat(sp.forward(np.cross(u, b, axis=0)), cfg) * D
+    return np.concatenate([n_u, n_b])
+
+
+def _mhd_rk_step_swapped_diffusivities(ub, dt, cfg, forcing=None):
+    return _orig_mhd_rk_step(ub, dt, dataclasses.replace(cfg, nu=cfg.eta, eta=cfg.nu), forcing)
+
+
+def _mhd_rhs_viscosity_on_b(ub, cfg, forcing=None):
+    return _orig_mhd_rhs(ub, dataclasses.replace(cfg, eta=cfg.nu), forcing)
+
+
+def _mhd_diagnostics_with_mistake(kind):
+    def f(ub, cfg, cfl=0.5):
+        d = sp.diagnostics(ub[:3], cfg, cfl)
+        D = sp.dealias_mask(cfg)
+        u, b = ub[:3] * D, ub[3:] * D
+        w = sp.hermitian_weight(cfg)
+        kx, ky, kz = sp.wavenumbers(cfg)
+        k2 = kx * kx + ky * ky + kz * kz
+        with np.errstate(divide="ignore", invalid="ignore"):
+            a = np.where(k2 > 0, sp.curl_hat(b, cfg) / np.where(k2 > 0, k2, 1.0), 0.0)
+        if kind == "potential without 1/|k|^2":
+            a = sp.curl_hat(b, cfg)
+        half = 1.0 if kind == "magnetic energy without 1/2" else 0.5
+        ch = 0.5 if kind == "cross helicity halved" else 1.0
+        d["magnetic_energy"] = float(np.sum(half * w * np.sum(np.abs(b) ** 2, axis=0)))
+        d["cross_helicity"] = float(np.sum(ch * w * np.real(np.sum(np.conj(u) * b, axis=0))))
+        d["magnetic_helicity"] = float(np.sum(w * np.real(np.sum(np.conj(a) * b, axis=0))))
+        return d
+
+    return f
+
+
+MHD_MISTAKES = {k: ("mhd_nonlinear", _mhd_nonlinear_with_mistake(k), [sp, oracle])
+                for k in ("lorentz sign", "lorentz dropped", "induction sign", "induction field")}
+MHD_MISTAKES.update({
+    "lorentz force not projected": ("_mhd_nonviscous", _mhd_nonviscous_lorentz_unprojected, [sp]),
+    "diffusivities swapped in the step": ("mhd_rk_step", _mhd_rk_step_swapped_diffusivities, [sp, oracle]),
+    "viscosity on B in the right-hand side": ("mhd_rhs", _mhd_rhs_viscosity_on_b, [sp, oracle]),
+})
+MHD_MISTAKES.update({k: ("mhd_diagnostics", _mhd_diagnostics_with_mistake(k), [sp, oracle])
+                     for k in ("potential without 1/|k|^2", "magnetic energy without 1/2",
+                               "cross helicity halved")})
+
+
+@pytest.mark.parametrize("name", list(MHD_MISTAKES))
+def test_planted_mhd_mistake_fails_a_pin(name, monkeypatch):
+    fn_name, fn, mods = MHD_MISTAKES[name]
+    _patch(monkeypatch, fn_name, fn, mods)
+    assert some_pin_fails(MHD_PINS) is not None, f"no pin notices: {name}"
+
+
 def test_unmodified_oracle_passes_every_listed_pin():
     """Control: with nothing planted, none of the pins used above fails."""
     assert some_pin_fails(HD_PINS) is None
     assert some_pin_fails(LES_PINS) is None
+    assert some_pin_fails(MHD_PINS) is None
     assert math.isfinite(float(np.sum(oracle.hermitian_weight(sp.Config(8, 8, 8)))))
