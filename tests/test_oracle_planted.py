@@ -1,7 +1,7 @@
 """Planted mistakes: each plausible error in the oracle must fail a pin.
 
 Every case below replaces one function of the oracle (oracle/fft.py,
-oracle/spectral.py, oracle/les.py, including the MHD system) by a copy with one mistake planted (a
+oracle/spectral.py with its MHD and Boussinesq systems, oracle/les.py) by a copy with one mistake planted (a
 flipped sign, a transposed index, a dropped term, a wrong coefficient) and
 runs the CPU pins of tests/test_oracle_*pins.py until one of them fails.  A
 case passes when some pin fails; a mistake that no pin notices fails the case.
@@ -19,6 +19,7 @@ from oracle import les
 from oracle import spectral as sp
 
 from . import test_oracle_fft_pins as FP
+from . import test_oracle_boussinesq_pins as BP
 from . import test_oracle_les_pins as LP
 from . import test_oracle_mhd_pins as MP
 from . import test_oracle_pins as P
@@ -421,9 +422,118 @@ def test_planted_mhd_mistake_fails_a_pin(name, monkeypatch):
     assert some_pin_fails(MHD_PINS) is not None, f"no pin notices: {name}"
 
 
+# ---------------------------------------------------------------------------
+# the Boussinesq system (Eqs. mom, temp, divv in oracle/spectral.py)
+# ---------------------------------------------------------------------------
+
+BQ_PINS = [
+    BP.test_tendency_matches_exact_advective_form,
+    BP.test_scalar_advection_matches_brute_force_convolution,
+    BP.test_ideal_total_energy_and_scalar_variance_are_conserved,
+    BP.test_internal_gravity_wave_tendency_and_frequency,
+    BP.test_zero_scalar_reduces_to_hydrodynamics,
+    BP.test_passive_scalar_diffusion_is_exact,
+    BP.test_velocity_tendency_is_solenoidal_and_potential_energy_diagnostic,
+    BP.test_linear_terms_carry_their_own_diffusivities,
+]
+
+_orig_bq_nonviscous = sp._bq_nonviscous
+_orig_bq_rk_step = sp.boussinesq_rk_step
+_orig_bq_rhs = sp.boussinesq_rhs
+
+
+def _bq_nonviscous_with_mistake(kind):
+    def f(ut, cfg, forcing, nonlinear_on=True):
+        D = sp.dealias_mask(cfg)
+        u_hat, th_hat = ut[:3] * D, ut[3] * D
+        v = sp._forcing_or_zero(forcing, cfg, u_hat)
+        buoy = np.zeros_like(v)
+        buoy[0 if kind == "buoyancy on x" else 2] = -cfg.n_bv * th_hat
+        if kind == "buoyancy sign":
+            buoy = -buoy
+        r_th = cfg.n_bv * (u_hat[0] if kind == "source from u_x" else u_hat[2])
+        if kind == "source N w dropped":
+            r_th = 0.0 * r_th
+        if nonlinear_on:
+            n_u, n_th = sp.boussinesq_nonlinear(ut, cfg)
+            v = v + n_u
+            r_th = r_th + n_th
+        if kind == "buoyancy not projected":
+            vel = sp.project(v, cfg) * D + buoy * D
+        else:
+            vel = sp.project(v + buoy, cfg) * D
+        return np.concatenate([vel, (r_th * D)[None]])
+
+    return f
+
+
+def _bq_nonlinear_with_mistake(kind):
+    def f(ut, cfg):
+        D = sp.dealias_mask(cfg)
+        u_hat, th_hat = ut[:3] * D, ut[3] * D
+        u = sp.inverse(u_hat, cfg)
+        om = sp.inverse(sp.curl_hat(u_hat, cfg), cfg)
+        th = sp.inverse(th_hat, cfg)
+        g = sp.forward((om if kind == "scalar advected by the vorticity" else u) * th)
+        kx, ky, kz = sp.wavenumbers(cfg)
+        sign = +1j if kind == "scalar advection sign" else -1j
+        return sp.forward(np.cross(u, om, axis=0)) * D, sign * (kx * g[0] + ky * g[1] + kz * g[2]) * D
+
+    return f
+
+
+def _bq_rk_step_swapped_diffusivities(ut, dt, cfg, forcing=None, nonlinear_on=True):
+    return _orig_bq_rk_step(ut, dt, dataclasses.replace(cfg, nu=cfg.kappa, kappa=cfg.nu), forcing, nonlinear_on)
+
+
+def _bq_rhs_viscosity_on_theta(ut, cfg, forcing=None, nonlinear_on=True):
+    return _orig_bq_rhs(ut, dataclasses.replace(cfg, kappa=cfg.nu), forcing, nonlinear_on)
+
+
+def _bq_diagnostics_potential_energy_doubled(ut, cfg, cfl=0.5):
+    d = sp.diagnostics(ut[:3], cfg, cfl)
+    th = ut[3] * sp.dealias_mask(cfg)
+    d["potential_energy"] = float(np.sum(sp.hermitian_weight(cfg) * np.abs(th) ** 2))  # 1/2 dropped
+    return d
+
+
+BQ_MISTAKES = {k: ("_bq_nonviscous", _bq_nonviscous_with_mistake(k), [sp])
+               for k in ("buoyancy sign", "buoyancy on x", "source N w dropped", "source from u_x",
+                         "buoyancy not projected")}
+BQ_MISTAKES.update({k: ("boussinesq_nonlinear", _bq_nonlinear_with_mistake(k), [sp, oracle])
+                    for k in ("scalar advection sign", "scalar advected by the vorticity")})
+BQ_MISTAKES.update({
+    "diffusivities swapped in the step": ("boussinesq_rk_step", _bq_rk_step_swapped_diffusivities, [sp, oracle]),
+    "viscosity on theta in the right-hand side": ("boussinesq_rhs", _bq_rhs_viscosity_on_theta, [sp, oracle]),
+    "potential energy without 1/2": ("boussinesq_diagnostics", _bq_diagnostics_potential_energy_doubled,
+                                     [sp, oracle]),
+})
+
+
+@pytest.mark.parametrize("name", list(BQ_MISTAKES))
+def test_planted_boussinesq_mistake_fails_a_pin(name, monkeypatch):
+    fn_name, fn, mods = BQ_MISTAKES[name]
+    _patch(monkeypatch, fn_name, fn, mods)
+    assert some_pin_fails(BQ_PINS) is not None, f"no pin notices: {name}"
+
+
 def test_unmodified_oracle_passes_every_listed_pin():
     """Control: with nothing planted, none of the pins used above fails."""
     assert some_pin_fails(HD_PINS) is None
     assert some_pin_fails(LES_PINS) is None
     assert some_pin_fails(MHD_PINS) is None
+    assert some_pin_fails(BQ_PINS) is None
+
+
+@pytest.mark.parametrize("fn_name,factory,mods,pins", [
+    ("mhd_nonlinear", _mhd_nonlinear_with_mistake, [sp, oracle], MHD_PINS),
+    ("mhd_diagnostics", _mhd_diagnostics_with_mistake, [sp, oracle], MHD_PINS),
+    ("_bq_nonviscous", _bq_nonviscous_with_mistake, [sp], BQ_PINS),
+    ("boussinesq_nonlinear", _bq_nonlinear_with_mistake, [sp, oracle], BQ_PINS),
+])
+def test_rewritten_copies_without_a_mistake_pass(fn_name, factory, mods, pins, monkeypatch):
+    """Control for the rewritten copies above: with no mistake selected each
+    one passes every pin, so a failing case comes from its planted mistake."""
+    _patch(monkeypatch, fn_name, factory("none"), mods)
+    assert some_pin_fails(pins) is None
     assert math.isfinite(float(np.sum(oracle.hermitian_weight(sp.Config(8, 8, 8)))))
