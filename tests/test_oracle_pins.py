@@ -404,6 +404,26 @@ def test_diagnostics_match_physical_space():
     assert d["max_div"] < 1e-13
 
 
+def test_shell_spectrum_of_closed_form_fields():
+    """Shells K = floor(|k| + 1/2): the Taylor-Green modes (|k| = sqrt 3) put
+    their energy 1/8 in shell 2, u = (0, 0, sin 2x cos 2y) (|k| = sqrt 8) its
+    1/8 in shell 3, the ABC flow (|k| = 1) its 3/2 in shell 1; on a box of
+    length 4 pi along x, sin(2 * 2 pi x / Lx) = sin x sits in shell 1."""
+    n = 16
+    cfg = Config(n, n, n)
+    cases = [(inputs.taylor_green(n, n, n), 2, 0.125),
+             (inputs.trig_field(n, n, n, [(2, 1.0, ("s", 2), ("c", 2), ("1", 0))]), 3, 0.125),
+             (inputs.abc_flow(n, n, n), 1, 1.5)]
+    for uh, shell, e in cases:
+        sp = oracle.diagnostics(uh, cfg)["spectrum"]
+        assert abs(sp[shell] - e) < 1e-15
+        assert np.sum(np.abs(np.delete(sp, shell))) < 1e-15
+    box = Config(n, n, n, lx=2 * TWO_PI)
+    uh = inputs.trig_field(n, n, n, [(2, 1.0, ("s", 2), ("1", 0), ("1", 0))])
+    sp = oracle.diagnostics(uh, box)["spectrum"]
+    assert abs(sp[1] - 0.25) < 1e-15 and np.sum(np.abs(np.delete(sp, 1))) < 1e-15
+
+
 def test_taylor_green_cfl_closed_form():
     cfg = Config(32, 32, 32)
     d = oracle.diagnostics(inputs.taylor_green(32, 32, 32), cfg, cfl=0.5)

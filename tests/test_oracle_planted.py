@@ -64,6 +64,7 @@ HD_PINS = [
     lambda: P.test_runge_kutta_order(4, 16.0),
     lambda: P.test_runge_kutta_order(2, 4.0),
     P.test_diagnostics_match_physical_space,
+    P.test_shell_spectrum_of_closed_form_fields,
 ]
 
 
@@ -174,6 +175,63 @@ def _rhs_viscous_sign(uh, cfg, forcing=None, nonlinear_on=True):
     return sp._nonviscous(uh, cfg, forcing, nonlinear_on) + cfg.nu * k2 * (uh * sp.dealias_mask(cfg))
 
 
+def _nonlinear_with_mistake(kind):
+    def f(uh, cfg):
+        D = sp.dealias_mask(cfg)
+        u_hat = uh if kind == "input mask dropped" else uh * D
+        u = sp.inverse(u_hat, cfg)
+        om = sp.inverse(sp.curl_hat(u_hat, cfg), cfg)
+        n = sp.forward(np.cross(u, om, axis=0))
+        return n if kind == "output mask dropped" else n * D
+
+    return f
+
+
+_orig_nonviscous = sp._nonviscous
+
+
+def _nonviscous_output_unmasked(uh, cfg, forcing, nonlinear_on):
+    # both output masks (of the nonlinear term and after the projection) dropped;
+    # either one alone is redundant with the other
+    v = sp._forcing_or_zero(forcing, cfg, uh)
+    if nonlinear_on:
+        v = v + _nonlinear_with_mistake("output mask dropped")(uh, cfg)
+    return sp.project(v, cfg)
+
+
+def _nonviscous_forcing_sign(uh, cfg, forcing, nonlinear_on):
+    neg = None if forcing is None else -np.asarray(forcing)
+    return _orig_nonviscous(uh, cfg, neg, nonlinear_on)
+
+
+def _diagnostics_with_mistake(kind):
+    def f(uh, cfg, cfl=0.5):
+        D = sp.dealias_mask(cfg)
+        u = uh * D
+        om = sp.curl_hat(u, cfg)
+        w = sp.hermitian_weight(cfg)
+        kx, ky, kz = sp.wavenumbers(cfg)
+        kmag = np.sqrt(kx * kx + ky * ky + kz * kz) + 0.0 * D
+        e_mode = 0.5 * w * np.sum(np.abs(u) ** 2, axis=0)
+        half = 1.0 if kind == "enstrophy without 1/2" else 0.5
+        enstrophy = float(np.sum(half * w * np.sum(np.abs(om) ** 2, axis=0)))
+        helicity = float(np.sum(w * np.real(np.sum(np.conj(u) * om, axis=0))))
+        max_div = float(np.max(np.abs(kx * u[0] + ky * u[1] + kz * u[2])))
+        shell = np.floor(kmag if kind == "shell by floor(|k|)" else kmag + 0.5).astype(np.int64)
+        spectrum = np.bincount(shell[D], weights=e_mode[D], minlength=int(shell[D].max()) + 1)
+        uphys = sp.inverse(u, cfg)
+        if kind == "max|u| of one component":
+            max_u = float(np.max(np.abs(uphys)))
+        else:
+            max_u = float(np.sqrt(np.max(np.sum(uphys * uphys, axis=0))))
+        pick = max if kind == "CFL on the largest spacing" else min
+        cfl_dt = cfl * pick(cfg.lx / cfg.nx, cfg.ly / cfg.ny, cfg.lz / cfg.nz) / max_u
+        return dict(energy=float(np.sum(e_mode)), enstrophy=enstrophy, helicity=helicity, max_div=max_div,
+                    max_u=max_u, cfl_dt=cfl_dt, spectrum=spectrum)
+
+    return f
+
+
 HD_MISTAKES = {
     "twiddle sign": ("_twiddles", _twiddles_conjugated, [offt]),
     "output index order": ("fft_first", _fft_first_output_transposed, [offt]),
@@ -189,7 +247,13 @@ HD_MISTAKES = {
     "hermitian weight": ("hermitian_weight", _weight_two_everywhere, [sp, oracle]),
     "box lengths swapped": ("wavenumbers", _wavenumbers_swapped_boxes, [sp, oracle]),
     "viscous term sign": ("rhs", _rhs_viscous_sign, [sp, oracle]),
+    "forcing sign": ("_nonviscous", _nonviscous_forcing_sign, [sp]),
+    "output mask dropped": ("_nonviscous", _nonviscous_output_unmasked, [sp]),
+    "input mask dropped": ("nonlinear", _nonlinear_with_mistake("input mask dropped"), [sp, oracle]),
 }
+HD_MISTAKES.update({k: ("diagnostics", _diagnostics_with_mistake(k), [sp, oracle])
+                    for k in ("enstrophy without 1/2", "shell by floor(|k|)", "max|u| of one component",
+                              "CFL on the largest spacing")})
 
 
 @pytest.mark.parametrize("name", list(HD_MISTAKES))
@@ -526,6 +590,8 @@ def test_unmodified_oracle_passes_every_listed_pin():
 
 
 @pytest.mark.parametrize("fn_name,factory,mods,pins", [
+    ("nonlinear", _nonlinear_with_mistake, [sp, oracle], HD_PINS),
+    ("diagnostics", _diagnostics_with_mistake, [sp, oracle], HD_PINS),
     ("mhd_nonlinear", _mhd_nonlinear_with_mistake, [sp, oracle], MHD_PINS),
     ("mhd_diagnostics", _mhd_diagnostics_with_mistake, [sp, oracle], MHD_PINS),
     ("_bq_nonviscous", _bq_nonviscous_with_mistake, [sp], BQ_PINS),
