@@ -5,6 +5,8 @@
   same plan configuration) against the FP64 oracle, relative L2 <= 2e-6.
 * 512^3 Taylor-Green: every mode of the RHS against the exact rational
   tendency -P[(u.grad)u] (no oracle run needed at that size).
+* 1024^3 Taylor-Green (FP32, the largest benchmark grid): the same, built
+  and compared on the device.
 * 512^3 ABC flow: the nonlinear term vanishes identically.
 * 100 IF-RK4 steps in FP32: total energy within 1e-4 of the FP64 oracle
   (64^3, oracle run in full) and of the FP64 CUDA path (256^3, whose every
@@ -71,6 +73,38 @@ def test_taylor_green_512_matches_exact_tendency(ps, prec):
             exact[:, r % n, q % n, p] = [complex(c) for c in v]
     tol = 2e-6 if prec == "fp32" else 1e-12
     assert np.max(np.abs(out - exact)) < tol * np.max(np.abs(exact))
+
+
+def _device_modes(modes, n, dtype):
+    """A state or tendency given as exact modes, built on the device (no host
+    copy of a 1024^3 field)."""
+    t = torch.zeros((3, n, n, n // 2 + 1), dtype=dtype, device="cuda")
+    for (p, q, r), v in modes.items():
+        if p >= 0:
+            t[:, r % n, q % n, p] = torch.tensor([complex(c) for c in v], dtype=dtype)
+    return t
+
+
+def test_taylor_green_1024_matches_exact_tendency(ps):
+    """The largest grid the bench times (1024^3 FP32: 16 points per thread in
+    the x pass, half the rows per CTA): every mode of the right-hand side of
+    the Taylor-Green vortex against its exact rational tendency, on the
+    device."""
+    n = 1024
+    tg = xf.trig_modes([(0, 1, ("s", 1), ("c", 1), ("c", 1)), (1, -1, ("c", 1), ("s", 1), ("c", 1))])
+    ud = _device_modes(tg, n, torch.complex64)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=0.0)
+    out = plan.rhs(ud)
+    torch.cuda.synchronize()
+    plan.close()
+    del ud
+    exact = _device_modes(xf.euler_rate(tg), n, torch.complex64)
+    scale = float(exact.abs().max())
+    err = float((out - exact).abs().max())
+    del out, exact
+    torch.cuda.empty_cache()
+    assert scale == 1.0 / 32  # the largest exact coefficient
+    assert err < 2e-6 * scale, err
 
 
 def test_abc_512_nonlinear_term_vanishes(ps):
