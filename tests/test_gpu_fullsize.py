@@ -6,7 +6,8 @@
 * 512^3 Taylor-Green: every mode of the RHS against the exact rational
   tendency -P[(u.grad)u] (no oracle run needed at that size).
 * 1024^3 Taylor-Green (FP32, the largest benchmark grid): the same, built
-  and compared on the device.
+  and compared on the device; and a band-limited seeded random field with
+  forcing and viscosity at 1024^3 against the oracle's exact 32^3 result.
 * 512^3 ABC flow: the nonlinear term vanishes identically.
 * 100 IF-RK4 steps in FP32: total energy within 1e-4 of the FP64 oracle
   (64^3, oracle run in full) and of the FP64 CUDA path (256^3, whose every
@@ -105,6 +106,46 @@ def test_taylor_green_1024_matches_exact_tendency(ps):
     torch.cuda.empty_cache()
     assert scale == 1.0 / 32  # the largest exact coefficient
     assert err < 2e-6 * scale, err
+
+
+def test_band_limited_random_field_1024_matches_oracle(ps):
+    """A seeded random solenoidal field on |p|, |q|, |r| <= 5 with the forcing
+    (2 <= |k| <= 3) and viscosity: its right-hand side lies on |p|, |q|, |r|
+    <= 10, which a 32^3 grid (2/3 half-width 10) and the 1024^3 grid both
+    hold without truncation or aliasing, so the oracle's 32^3 right-hand
+    side placed at the same signed modes is the 1024^3 one.  Every mode of
+    the 1024^3 FP32 result is compared on the device."""
+    n, m, nu, K = 1024, 32, 2e-3, 10
+    u = inputs.random_solenoidal_field(m, m, m, seed=1, kmax=(5, 5, 5))
+    f = inputs.forcing_field(m, m, m, seed=2)
+    ref = oracle.rhs(u, oracle.Config(m, m, m, nu=nu), forcing=f)
+    rows = [i for i in range(m) if abs(i if i < m // 2 else i - m) <= K]
+
+    def embed(a):
+        t = torch.zeros((3, n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+        src = torch.from_numpy(np.ascontiguousarray(a[:, :, :, : K + 1])).to("cuda", torch.complex64)
+        for zi in rows:
+            z = (zi if zi < m // 2 else zi - m) % n
+            for yi in rows:
+                y = (yi if yi < m // 2 else yi - m) % n
+                t[:, z, y, : K + 1] = src[:, zi, yi]
+        return t
+
+    ud, fd = embed(u), embed(f)
+    plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, forcing=fd)
+    out = plan.rhs(ud)
+    torch.cuda.synchronize()
+    plan.close()
+    del ud, fd
+    exact = embed(ref)
+    scale = float(exact.abs().max())
+    err = float((out - exact).abs().max())
+    rel = float(torch.linalg.vector_norm(out - exact) / torch.linalg.vector_norm(exact))
+    del out, exact
+    torch.cuda.empty_cache()
+    assert np.max(np.abs(ref[:, :, :, K + 1:])) == 0.0 and scale > 0.0
+    assert rel < 2e-6, rel
+    assert err < 2e-6 * scale, err / scale
 
 
 def test_abc_512_nonlinear_term_vanishes(ps):
