@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_1808_01309_gb300 import inputs
 
-from .parity import assert_parity
+from .parity import BAND_M, assert_device_parity, assert_parity, embed_on_device
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -143,6 +143,29 @@ def test_boussinesq_rhs_256_fp32_matches_oracle(ps):
     got = plan.rhs(torch.from_numpy(st).to("cuda", torch.complex64)).cpu().numpy().astype(np.complex128)
     assert_parity(got, ref, 2e-6, "boussinesq rhs 256")
     plan.close()
+
+
+def test_boussinesq_rhs_512_band_limited_matches_oracle(ps):
+    """The benchmark's 512^3 Boussinesq launch shapes against the oracle: u and
+    theta seeded on |p|, |q|, |r| <= 5 with the forcing, whose right-hand side
+    the oracle gives exactly on a 32^3 grid (tests/parity.py); every mode
+    compared on the device."""
+    n, m = 512, BAND_M
+    u = inputs.random_solenoidal_field(m, m, m, seed=1, kmax=(5, 5, 5))
+    th = inputs.random_scalar_field(m, m, m, seed=61, kmax=(5, 5, 5))
+    st = np.concatenate([u, th])
+    f = inputs.forcing_field(m, m, m, seed=2)
+    kw = dict(nu=2e-3, kappa=4e-3, n_bv=1.0)
+    ref = oracle.boussinesq_rhs(st, oracle.Config(m, m, m, **kw), forcing=f)
+    c64 = torch.complex64
+    plan = ps.Plan(n, prec=ps.Precision.FP32, eq=ps.Equations.BOUSSINESQ, rk_order=4,
+                   forcing=embed_on_device(f, n, torch, c64), **kw)
+    out = plan.rhs(embed_on_device(st, n, torch, c64))
+    torch.cuda.synchronize()
+    plan.close()
+    assert_device_parity(out, embed_on_device(ref, n, torch, c64), torch, 2e-6, "boussinesq rhs 512")
+    del out
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("mode", ["auto", "copy", "mapped"])

@@ -25,7 +25,7 @@ import oracle
 from paper_1808_01309_gb300 import inputs
 
 from . import exact_fourier as xf
-from .parity import assert_parity
+from .parity import BAND_K, BAND_M, assert_device_parity, assert_parity, embed_on_device
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -115,37 +115,20 @@ def test_band_limited_random_field_1024_matches_oracle(ps):
     hold without truncation or aliasing, so the oracle's 32^3 right-hand
     side placed at the same signed modes is the 1024^3 one.  Every mode of
     the 1024^3 FP32 result is compared on the device."""
-    n, m, nu, K = 1024, 32, 2e-3, 10
+    n, m, nu = 1024, BAND_M, 2e-3
     u = inputs.random_solenoidal_field(m, m, m, seed=1, kmax=(5, 5, 5))
     f = inputs.forcing_field(m, m, m, seed=2)
     ref = oracle.rhs(u, oracle.Config(m, m, m, nu=nu), forcing=f)
-    rows = [i for i in range(m) if abs(i if i < m // 2 else i - m) <= K]
-
-    def embed(a):
-        t = torch.zeros((3, n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
-        src = torch.from_numpy(np.ascontiguousarray(a[:, :, :, : K + 1])).to("cuda", torch.complex64)
-        for zi in rows:
-            z = (zi if zi < m // 2 else zi - m) % n
-            for yi in rows:
-                y = (yi if yi < m // 2 else yi - m) % n
-                t[:, z, y, : K + 1] = src[:, zi, yi]
-        return t
-
-    ud, fd = embed(u), embed(f)
+    assert np.max(np.abs(ref[:, :, :, BAND_K + 1:])) == 0.0
+    ud, fd = embed_on_device(u, n, torch, torch.complex64), embed_on_device(f, n, torch, torch.complex64)
     plan = ps.Plan(n, prec=ps.Precision.FP32, nu=nu, forcing=fd)
     out = plan.rhs(ud)
     torch.cuda.synchronize()
     plan.close()
     del ud, fd
-    exact = embed(ref)
-    scale = float(exact.abs().max())
-    err = float((out - exact).abs().max())
-    rel = float(torch.linalg.vector_norm(out - exact) / torch.linalg.vector_norm(exact))
-    del out, exact
+    assert_device_parity(out, embed_on_device(ref, n, torch, torch.complex64), torch, 2e-6, "1024^3 rhs")
+    del out
     torch.cuda.empty_cache()
-    assert np.max(np.abs(ref[:, :, :, K + 1:])) == 0.0 and scale > 0.0
-    assert rel < 2e-6, rel
-    assert err < 2e-6 * scale, err / scale
 
 
 def test_abc_512_nonlinear_term_vanishes(ps):
