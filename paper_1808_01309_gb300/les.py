@@ -155,15 +155,15 @@ def train_transfer(plan, params, norm: dict, snaps, iters: int = 500, lr: float 
 
 def shell_transfer(uhat, force, kc: int) -> np.ndarray:
     """Energy transfer spectrum T(K) = sum over shell K of w Re(conj(u) . f)
-    (w = 1 on the kx = 0 plane, 2 elsewhere) for K = 0..kc; host analysis of
-    small LES-grid fields."""
+    (w = 1 on the kx = 0 plane and, for an even grid, the kx = n/2 plane,
+    2 elsewhere) for K = 0..kc; host analysis of small LES-grid fields."""
     u = uhat.cpu().numpy().astype(np.complex128)
     f = force.cpu().numpy().astype(np.complex128)
     n = u.shape[1]
     q = np.fft.fftfreq(n, 1.0 / n)
     kz, ky, kx = np.meshgrid(q, q, np.arange(u.shape[3]), indexing="ij")
     shell = np.floor(np.sqrt(kx * kx + ky * ky + kz * kz) + 0.5).astype(int)
-    w = np.where(kx == 0, 1.0, 2.0)
+    w = np.where((kx == 0) | ((n % 2 == 0) & (kx == n // 2)), 1.0, 2.0)
     e = (w * np.real(np.conj(u) * f).sum(0)).ravel()
     return np.bincount(shell.ravel(), weights=e, minlength=kc + 1)[:kc + 1]
 
