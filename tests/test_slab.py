@@ -34,18 +34,20 @@ def test_split_covers_every_item_once_with_sizes_within_one():
         slab.split(10, 0, 0)
 
 
-def _case():
-    nx, ny, nz = 24, 12, 20
+def _case(nx=24, ny=12, nz=20):
     cfg = oracle.Config(nx, ny, nz, lx=2 * math.pi, ly=3.0, lz=5.0, nu=3e-3)
     u = inputs.random_solenoidal_field(nx, ny, nz, seed=7, ly=3.0, lz=5.0)
     f = inputs.forcing_field(nx, ny, nz, seed=2, ly=3.0, lz=5.0)
     return cfg, u, f
 
 
-@pytest.mark.parametrize("P", [1, 2, 3, 4])
-def test_loopback_slabs_match_the_oracle(P):
+@pytest.mark.parametrize("P,shape", [(1, (24, 12, 20)), (2, (24, 12, 20)), (3, (24, 12, 20)), (4, (24, 12, 20)),
+                                     (4, (8, 12, 6)), (5, (8, 8, 3))])
+def test_loopback_slabs_match_the_oracle(P, shape):
+    """Includes ranks that own no kx column (8 points along x keep 3 columns)
+    and ranks that own no z plane (3 planes over 5 ranks)."""
     from .slab_cpu_backend import CpuBackend, assemble, local_columns
-    cfg, u, f = _case()
+    cfg, u, f = _case(*shape)
     cx = slab.retained_columns(cfg.nx)
     lays = [slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, cx, P, r) for r in range(P)]
     backends = [CpuBackend(cfg, lay, local_columns(f, lay)) for lay in lays]
@@ -54,13 +56,13 @@ def test_loopback_slabs_match_the_oracle(P):
     assert_parity(got, oracle.rhs(u, cfg, forcing=f), 1e-13, f"loopback P={P}")
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, shape):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from tests.slab_cpu_backend import CpuBackend, local_columns
-        cfg, u, f = _case()
+        cfg, u, f = _case(*shape)
         lay = slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, slab.retained_columns(cfg.nx), world, rank)
         comm = slab.TorchDistributed()
         out = slab.rhs_local(CpuBackend(cfg, lay, local_columns(f, lay)), lay, local_columns(u, lay), comm)
@@ -69,22 +71,22 @@ def _rank(rank, world, port, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_gloo_ranks_match_the_oracle(world):
+@pytest.mark.parametrize("world,shape", [(2, (24, 12, 20)), (3, (24, 12, 20)), (4, (8, 12, 6))])
+def test_gloo_ranks_match_the_oracle(world, shape):
     import multiprocessing as mp
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, shape)) for r in range(world)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=180) for _ in range(world))
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    cfg, u, f = _case()
+    cfg, u, f = _case(*shape)
     lays = [slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, slab.retained_columns(cfg.nx), world, r) for r in range(world)]
     from .slab_cpu_backend import assemble
     full = assemble([got[r] for r in range(world)], lays, cfg.nx // 2 + 1)
