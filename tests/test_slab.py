@@ -92,3 +92,49 @@ def test_gloo_ranks_match_the_oracle(world, shape):
     full = assemble([got[r] for r in range(world)], lays, cfg.nx // 2 + 1)
     assert_parity(full, oracle.rhs(u, cfg, forcing=f), 1e-13, f"gloo world={world}")
     assert np.all(full[..., slab.retained_columns(cfg.nx):] == 0)
+
+
+def _rank_with_a_lost_peer(rank, world, port, q):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        q.put((rank, "left"))  # this rank fails before the exchanges and leaves
+        return
+    try:
+        from tests.slab_cpu_backend import CpuBackend, local_columns
+        cfg, u, f = _case()
+        lay = slab.SlabLayout(cfg.nx, cfg.ny, cfg.nz, slab.retained_columns(cfg.nx), world, rank)
+        slab.rhs_local(CpuBackend(cfg, lay, local_columns(f, lay)), lay, local_columns(u, lay),
+                       slab.TorchDistributed())
+        q.put((rank, "finished"))
+    except RuntimeError as e:
+        q.put((rank, "error: " + str(e).splitlines()[0][:80]))
+
+
+def test_a_lost_rank_ends_the_exchange_with_an_error():
+    """A rank that leaves before the exchanges (failure injected on the host):
+    the surviving rank's all-to-all ends with an error (gloo reports the
+    closed connection; the process group's 5 s timeout bounds the wait
+    otherwise) instead of waiting for ever."""
+    import multiprocessing as mp
+    import time
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_with_a_lost_peer, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.monotonic()
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        if p.exitcode is None:
+            p.kill()
+    assert got[1] == "left"
+    assert got[0].startswith("error"), got[0]
+    assert time.monotonic() - t0 < 100
