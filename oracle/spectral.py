@@ -41,6 +41,15 @@ Readings of the paper (each one is repeated where it is used):
      (exp(-eta |k|^2 dt/2) for the magnetic field).
   R9 (diagnostics, not in the paper): Hermitian weight w = 1 on the planes
      kx = 0 and kx = Nx/2, else 2; shells K = floor(|k| + 1/2).
+  R10 (forcing, not in the paper): a constant-in-time solenoidal forcing
+     f_hat, supplied by the caller (the seeded recipe lives with the input
+     generators); it is masked and added before the projection (R6).
+  R11 (time): the forcing is constant, so the right-hand side does not
+     depend on t.
+  R12 (MHD, Eqs. uMHD, bMHD; the forms are not stated): rotational forms
+     N_u = P F[u x omega + j x B] with j = curl B (the magnetic pressure
+     gradient is removed by P) and N_B = i k x F[u x B] = F[curl(u x B)];
+     B stays divergence-free without a projection.
   R13 (Boussinesq, Eqs. mom, temp, divv; the advection forms are not stated):
      velocity in rotational form as in R7 with the buoyancy -N theta z_hat
      added before the projection; scalar advection in divergence form
@@ -51,6 +60,8 @@ Readings of the paper (each one is repeated where it is used):
      of the same state; theta is not forced; Lawson factors
      exp(-nu |k|^2 dt/2) on u and exp(-kappa |k|^2 dt/2) on theta, the
      buoyancy coupling is part of the explicit right-hand side.
+  (R14 concerns the FP32 twiddles of the CUDA path only; this module is
+  float64 throughout.)
 """
 
 from __future__ import annotations
