@@ -86,7 +86,12 @@ typedef struct ps_plan ps_plan;
  *   prec       : arithmetic and storage precision of all fields
  *   eq         : PS_HD, or PS_MHD (Eqs. uMHD, bMHD: the state then has six
  *                components u_x, u_y, u_z, B_x, B_y, B_z; the magnetic
- *                field advances with dB/dt = curl(u x B) - eta |k|^2 B), or
+ *                field advances with dB/dt = curl(u x B) - eta |k|^2 B,
+ *                the curl taken in spectral space after the product; in
+ *                PS_FP32 that multiplies the product's rounding by |k|, so
+ *                the relative error of the induction term grows with the
+ *                grid, about 2e-6 at 128^3 to 7e-6 at 512^3 for fields
+ *                whose energy sits at low k; PS_FP64 keeps 1e-12), or
  *                PS_BOUSSINESQ (Eqs. mom, temp, divv: four components u_x,
  *                u_y, u_z, theta; du/dt = P(F[u x omega] + f - n_bv theta z)
  *                - nu |k|^2 u and dtheta/dt = -F[u . grad theta] + n_bv w
