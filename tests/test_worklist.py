@@ -25,13 +25,13 @@ ZINV, SUM, YINV, XPASS, YFWD, ZFWD, UPDATE = range(7)
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def worklist_exe(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
-    exe = str(tmp_path_factory.mktemp("wl") / "worklist_driver")
+    exe = str(tmp_path_factory.mktemp("wl") / "worklist_main")
     subprocess.run([cxx, "-std=c++17", "-O1", "-Wall", "-Werror", "-I", CSRC,
-                    os.path.join(ROOT, "tests", "worklist_driver.cpp"), "-o", exe], check=True)
+                    os.path.join(ROOT, "tests", "worklist_main.cpp"), "-o", exe], check=True)
     return exe
 
 
@@ -49,13 +49,13 @@ def member_sequence(rng, nsteps, stages):
     return seq
 
 
-def run(driver, seqs, order, ord_, cls, cap):
+def run(worklist_exe, seqs, order, ord_, cls, cap):
     lines = [f"{len(seqs)} {order} {cap}"]
     for s in seqs:
         lines.append(" ".join([str(len(s))] + [f"{nt} {per} {int(ch)}" for _, nt, per, ch in s]))
     lines.append(" ".join(map(str, ord_)))
     lines.append(" ".join(map(str, cls)))
-    out = subprocess.run([driver], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True).stdout
+    out = subprocess.run([worklist_exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True).stdout
     skew, slots, tickets, groups = None, [], None, []
     for ln in out.splitlines():
         f = ln.split()
@@ -111,7 +111,7 @@ def simulate_queue(slots, seqs, ctas, rng):
 
 @pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_persistent_work_list(driver, order, seed):
+def test_persistent_work_list(worklist_exe, order, seed):
     rng = random.Random(seed * 10 + order)
     m = rng.randint(1, 13)
     stages = rng.choice([2, 4])
@@ -120,7 +120,7 @@ def test_persistent_work_list(driver, order, seed):
     ord_ = list(range(m))
     if order >= 1:
         rng.shuffle(ord_)  # any permutation (the library sorts by grid size)
-    skew, slots, tickets, _ = run(driver, seqs, order, ord_, list(range(m)), 1)
+    skew, slots, tickets, _ = run(worklist_exe, seqs, order, ord_, list(range(m)), 1)
 
     # skew: none, or the position in the member order modulo 6
     assert skew == ([0] * m if order < 2 else [ord_.index(i) % 6 for i in range(m)])
@@ -163,11 +163,11 @@ def test_queue_simulation_detects_a_forward_dependency():
 
 
 @pytest.mark.parametrize("cap", [1, 2, 4, 32])
-def test_batched_groups(driver, cap):
+def test_batched_groups(worklist_exe, cap):
     rng = random.Random(cap)
     m = 48
     cls = [rng.choice([0, 7, 9]) for _ in range(m)]
-    _, _, _, groups = run(driver, [[] for _ in range(m)], 0, list(range(m)), cls, cap)
+    _, _, _, groups = run(worklist_exe, [[] for _ in range(m)], 0, list(range(m)), cls, cap)
     assert sorted(j for g in groups for j in g) == list(range(m))
     placed = set()
     for g in groups:
