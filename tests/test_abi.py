@@ -138,3 +138,30 @@ def test_misaligned_forcing_is_rejected_before_any_cuda_call(ps, prec, addr):
         ps.ps_plan_create(cfg)
     assert e.value.status == ps.PS_ERR_INVALID_ARG
     assert "aligned" in str(e.value)
+
+
+def test_every_entry_point_rejects_null_arguments_on_the_host(ps):
+    """Every call of the ABI, given NULL handles, NULL pointers and zero sizes,
+    returns PS_ERR_INVALID_ARG with a message before any CUDA call (this runs
+    without a GPU); the destroy calls accept NULL as a no-op."""
+    import ctypes
+    lib = ps.load()
+    strings = ("ps_kind_name", "ps_status_string", "ps_last_error")
+    for name in ps.SYMBOLS:
+        if name in strings:
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_double, ctypes.c_float):
+                args.append(0.0)
+            elif t in (ctypes.c_int, ctypes.c_uint, ctypes.c_longlong):
+                args.append(0)
+            else:
+                args.append(None)
+        st = fn(*args)
+        if name.endswith("_destroy"):
+            assert st == ps.PS_OK, name
+        else:
+            assert st == ps.PS_ERR_INVALID_ARG, (name, st)
+            assert lib.ps_last_error(), name
